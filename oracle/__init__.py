@@ -1,0 +1,20 @@
+"""CPU oracle for the embedded-ERI transformation (test infrastructure).
+
+A plain, slow, FP64 restatement of Algorithm 1 of Cui, Zhu & Chan, "Efficient
+Implementation of Ab Initio Quantum Embedding in Periodic Systems: Density Matrix
+Embedding Theory" (arXiv 1909.08596), section 2.1, together with a brute-force
+real-space supercell transformation and the checks the tests use.
+
+This package is test infrastructure. Only the tests, the smoke entry point and the
+benchmark's CPU-baseline leg may import it. It shares no code with the CUDA library
+(no kernels, headers, index tables or packing helpers) and imports nothing from it;
+the product path never calls it.
+
+Parity status: every function here is pinned by tests that do not go through the
+function itself (brute force over the supercell, a hand-derived worked example,
+closed forms, symmetries, positivity and unitary invariance); see tests/test_oracle_pins.py.
+"""
+from .mesh import k_add, k_index, k_neg, k_triplet
+from .alg1 import embedded_3idx, embedded_eri, eri_entries
+from .supercell import supercell_eri
+from .checks import orthonormality_error, realness_error, pack_s8, pair_matrix, unpack_s8

@@ -1,0 +1,200 @@
+"""Seeded synthetic lattice inputs for the embedded-ERI transformation.
+
+This module builds the inputs of the lattice-to-embedded integral transformation
+(Cui, Zhu & Chan, arXiv 1909.08596, section 2.1, Algorithm 1): the k-point
+density-fitted 3-index integrals L^{k1,k2}_{P,mu nu} and the embedding orbitals
+C^k (n_AO x n_emb per k). It holds none of the transformation's arithmetic:
+it draws real-space tensors, orthonormalises the orbitals over the Born-von Karman
+supercell and Fourier-transforms both to the k mesh. Both the CPU oracle and the
+CUDA path consume what it returns.
+
+Conventions (section 2.1, Eq. "C loemb k" and Eq. "density fitting"):
+
+* k-points and cells share the C-order index kappa(n1,n2,n3) = (n1*N2 + n2)*N3 + n3
+  on a Gamma-centred N1 x N2 x N3 mesh; k.R = 2 pi sum_d n_d m_d / N_d.
+* Real-space 3-index tensor B[P, mu, R1, nu, R2] = (P, cell 0 | mu R1, nu R2), real,
+  symmetric under the pair swap (mu,R1) <-> (nu,R2).
+* L^{k1,k2}_{P,mu nu} = sum_{R1,R2} exp(-i k1.R1 + i k2.R2) B[P, mu, R1, nu, R2],
+  so that L^{k2,k1}_{P,nu mu} = conj(L^{k1,k2}_{P,mu nu}) and, because B is real,
+  L^{-k1,-k2} = conj(L^{k1,k2}).
+* Supercell orbitals Csc[(R, mu), i], real and orthonormal over the supercell;
+  C^k_{mu i} = sum_R exp(-i k.R) Csc[(R, mu), i] (the Bloch sum of Eq. "C loemb k",
+  "paper" normalisation, Nk^-1 sum_k C^k+ C^k = 1), or that times Nk^-1/2
+  ("unitary" normalisation, sum_k C^k+ C^k = 1).
+
+Random numbers come from numpy's counter-based Philox generator keyed by
+(seed, stream, block), so any P-block of B regenerates identically on its own.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import scipy.fft
+
+# Philox stream identifiers (second key word); the P index is added for B.
+_STREAM_B = 1 << 40
+_STREAM_C = 2 << 40
+_STREAM_SCALE = 3 << 40
+_STREAM_BATH = 4 << 40
+
+
+@dataclasses.dataclass(frozen=True)
+class LatticeSpec:
+    """Shape and value recipe of one synthetic embedding problem."""
+
+    mesh: tuple            # (N1, N2, N3), Gamma-centred
+    n_ao: int              # AOs per cell
+    n_aux: int             # auxiliary functions per cell (the P index)
+    n_emb: int             # embedding orbitals per spin
+    n_spin: int = 1        # 1 restricted, 2 unrestricted
+    decay: float = 0.7     # a in exp(-a (|R1| + |R2|))
+    c_log_range: float = 0.0  # >0: orbital entries scaled by 10**U(-c_log_range, 0)
+    seed: int = 0
+    name: str = ""
+
+    @property
+    def nk(self) -> int:
+        return int(np.prod(self.mesh))
+
+
+# Shapes of the paper's three solids (section 2.2: h-BN 6x6x1, Si 4x4x4, NiO 4x4x4
+# meshes; aux basis about ten times the AO basis) plus a tiny case.
+CONFIGS = {
+    "tiny_2x2x1": LatticeSpec((2, 2, 1), 8, 40, 16, 1, 0.7, 0.0, 0, "tiny_2x2x1"),
+    "hbn_6x6x1": LatticeSpec((6, 6, 1), 26, 220, 104, 1, 0.5, 0.0, 1000, "hbn_6x6x1"),
+    "si_4x4x4": LatticeSpec((4, 4, 4), 52, 400, 200, 1, 0.6, 4.0, 2000, "si_4x4x4"),
+    "nio_4x4x4_uhf": LatticeSpec((4, 4, 4), 104, 900, 300, 2, 0.6, 0.0, 3000, "nio_4x4x4_uhf"),
+}
+
+
+def cell_vectors(mesh) -> np.ndarray:
+    """Integer cell vectors m = (m1, m2, m3) in C order, shape (Nk, 3)."""
+    n1, n2, n3 = mesh
+    g = np.stack(np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij"), -1)
+    return g.reshape(-1, 3)
+
+
+def min_image_norm(mesh) -> np.ndarray:
+    """|R| of each cell: Euclidean norm of the minimum-image integer vector."""
+    m = cell_vectors(mesh).astype(np.float64)
+    n = np.asarray(mesh, dtype=np.float64)
+    m = np.where(m > n / 2, m - n, m)
+    return np.sqrt((m * m).sum(-1))
+
+
+def phases(mesh) -> np.ndarray:
+    """E[k, R] = exp(-i k.R) with k.R = 2 pi sum_d n_d m_d / N_d."""
+    v = cell_vectors(mesh).astype(np.float64)
+    n = np.asarray(mesh, dtype=np.float64)
+    kr = 2.0 * np.pi * (v[:, None, :] * v[None, :, :] / n).sum(-1)
+    return np.exp(-1j * kr)
+
+
+def _rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=[int(seed) & (2**64 - 1), int(stream)]))
+
+
+def real_space_B(spec: LatticeSpec, p_begin: int = 0, p_end: int | None = None) -> np.ndarray:
+    """B[P, mu, R1, nu, R2] for P in [p_begin, p_end), real, pair-symmetrised.
+
+    Entries are N(0,1) * exp(-a (|R1| + |R2|)); then B <- (B + B^T_pair) / 2 with the
+    pair transpose (mu, R1) <-> (nu, R2). Each P is drawn from its own Philox stream.
+    """
+    p_end = spec.n_aux if p_end is None else p_end
+    nk, na = spec.nk, spec.n_ao
+    w = np.exp(-spec.decay * min_image_norm(spec.mesh))
+    out = np.empty((p_end - p_begin, na, nk, na, nk))
+    for p in range(p_begin, p_end):
+        b = _rng(spec.seed, _STREAM_B + p).standard_normal((na, nk, na, nk))
+        b *= w[None, :, None, None]
+        b *= w[None, None, None, :]
+        out[p - p_begin] = 0.5 * (b + b.transpose(2, 3, 0, 1))
+    return out
+
+
+def fourier_L(Bblk: np.ndarray, mesh, workers: int = -1) -> np.ndarray:
+    """L[k1, k2, P, mu, nu] = sum_{R1,R2} exp(-i k1.R1 + i k2.R2) B[P, mu, R1, nu, R2]."""
+    npb, na, nk, _, _ = Bblk.shape
+    n1, n2, n3 = mesh
+    x = Bblk.reshape(npb, na, n1, n2, n3, na, n1, n2, n3)
+    # exp(-i k.R) over R1 is the forward DFT; exp(+i k.R) over R2 is the unscaled inverse.
+    x = scipy.fft.fftn(x, axes=(2, 3, 4), workers=workers)
+    x = scipy.fft.ifftn(x, axes=(6, 7, 8), norm="forward", workers=workers)
+    x = x.reshape(npb, na, nk, na, nk)
+    return np.ascontiguousarray(x.transpose(2, 4, 0, 1, 3))
+
+
+def make_L(spec: LatticeSpec, p_block: int = 64, out: np.ndarray | None = None) -> np.ndarray:
+    """Full L[k1][k2][P][mu][nu], complex128, generated P-block by P-block."""
+    nk, na = spec.nk, spec.n_ao
+    if out is None:
+        out = np.empty((nk, nk, spec.n_aux, na, na), dtype=np.complex128)
+    for p0 in range(0, spec.n_aux, p_block):
+        p1 = min(spec.n_aux, p0 + p_block)
+        out[:, :, p0:p1] = fourier_L(real_space_B(spec, p0, p1), spec.mesh)
+    return out
+
+
+def _orthonormalise(a: np.ndarray) -> np.ndarray:
+    """Householder QR; columns flipped so that diag(R) > 0."""
+    q, r = np.linalg.qr(a)
+    s = np.sign(np.diag(r))
+    s[s == 0] = 1.0
+    return q * s[None, :]
+
+
+def supercell_orbitals(spec: LatticeSpec, spin: int = 0) -> np.ndarray:
+    """Csc[(R, mu), i], real, orthonormal over the supercell, shape (Nk*n_AO, n_emb).
+
+    Entries N(0,1) * exp(-a |R|) (times 10**U(-c, 0) when c_log_range = c > 0), then QR.
+    """
+    nk, na, n = spec.nk, spec.n_ao, spec.n_emb
+    if n > nk * na:
+        raise ValueError("n_emb exceeds the supercell dimension Nk*n_AO")
+    g = _rng(spec.seed + spin, _STREAM_C)
+    a = g.standard_normal((nk, na, n))
+    a *= np.exp(-spec.decay * min_image_norm(spec.mesh))[:, None, None]
+    if spec.c_log_range > 0:
+        a *= 10.0 ** _rng(spec.seed + spin, _STREAM_SCALE).uniform(-spec.c_log_range, 0.0, (nk, na, n))
+    return _orthonormalise(a.reshape(nk * na, n))
+
+
+def dmet_structured_orbitals(spec: LatticeSpec, n_imp: int | None = None, spin: int = 0) -> np.ndarray:
+    """Csc in the block form of Eq. "C loemb R": impurity columns are unit vectors on
+    the first n_imp AOs of cell R = 0; bath columns are orthonormal and live on R != 0."""
+    nk, na, n = spec.nk, spec.n_ao, spec.n_emb
+    n_imp = min(na, n) if n_imp is None else n_imp
+    n_bath = n - n_imp
+    if n_bath > (nk - 1) * na:
+        raise ValueError("bath larger than the environment")
+    csc = np.zeros((nk * na, n))
+    csc[np.arange(n_imp), np.arange(n_imp)] = 1.0
+    if n_bath:
+        g = _rng(spec.seed + spin, _STREAM_BATH)
+        b = g.standard_normal(((nk - 1) * na, n_bath))
+        csc[na:, n_imp:] = _orthonormalise(b)
+    return csc
+
+
+def bloch_orbitals(csc: np.ndarray, mesh, ck_norm: int = 0) -> np.ndarray:
+    """C[k, mu, i] = sum_R exp(-i k.R) Csc[(R, mu), i] (times Nk^-1/2 if ck_norm == 1)."""
+    nk = int(np.prod(mesh))
+    na = csc.shape[0] // nk
+    c = np.einsum("kR,Rmi->kmi", phases(mesh), csc.reshape(nk, na, -1))
+    if ck_norm == 1:
+        c /= math.sqrt(nk)
+    return np.ascontiguousarray(c)
+
+
+def make_problem(spec: LatticeSpec, ck_norm: int = 0, with_L: bool = True):
+    """(L, [C_alpha, C_beta?], [Csc_alpha, ...]) for one problem."""
+    cscs = [supercell_orbitals(spec, s) for s in range(spec.n_spin)]
+    cs = [bloch_orbitals(c, spec.mesh, ck_norm) for c in cscs]
+    L = make_L(spec) if with_L else None
+    return L, cs, cscs
+
+
+def spec_with(spec: LatticeSpec, **kw) -> LatticeSpec:
+    return dataclasses.replace(spec, **kw)
