@@ -1,0 +1,185 @@
+/*
+ * dmet_emb.h -- C ABI of the GB300 embedded two-electron-integral transformation.
+ *
+ * The library computes the lattice-to-embedded ERI transformation of periodic
+ * ab initio DMET (Cui, Zhu & Chan, arXiv 1909.08596, section 2.1, Algorithm 1):
+ *
+ *   L^q_{P,ij} = s_C * sum_{k1} sum_{mu nu} conj(C^{k1}_{mu i}) L^{k1,k1+q}_{P,mu nu} C^{k1+q}_{nu j}
+ *   (ij|kl)    = (1/Nk) * sum_q sum_P L^q_{P,ij} L^{-q}_{P,kl}
+ *
+ * with s_C = 1/Nk for the Bloch-sum orbitals of Eq. "C loemb k" (ck_norm = 0) and
+ * s_C = 1 for unitary-normalised orbitals (ck_norm = 1). q = k2 - k1 is the momentum
+ * transfer of a pair; Algorithm 1's k_L is -q. All k arithmetic is modulo the
+ * Gamma-centred mesh, with C-order index (n1*N2 + n2)*N3 + n3.
+ *
+ * Memory conventions (every call):
+ *  - Complex numbers are interleaved double pairs (re, im) ("complex128"), row-major.
+ *  - L  : complex128 [Nk][Nk][n_aux][n_ao][n_ao], L[k1][k2][P][mu][nu] = (P | mu k1, nu k2)
+ *         (Eq. "density fitting"; the aux index carries the implicit momentum k1 - k2).
+ *  - C  : complex128 [Nk][n_ao][n_emb] per spin, C[k][mu][i] = C^{k,AO,EO}_{mu i}.
+ *  - Lq : complex128 [q_end - q_begin][n_aux][n_emb][n_emb].
+ *  - ERI blocks: see dmet_emb_eri.
+ *  Pointers may be device pointers or host pointers (pageable or pinned); the library
+ *  classifies each with cudaPointerGetAttributes. Host inputs are staged through
+ *  plan-owned device buffers; host outputs are copied back and the call then waits for
+ *  its stream. Every pointer must be 16-byte aligned. The caller owns all input and
+ *  output buffers; the plan owns only its workspace, staging buffers and tables.
+ *
+ * Errors: every entry point returns a dmet_status_t and never aborts or traps.
+ * Argument errors are detected on the host before any work is queued. Checks that
+ * run on the device (orthonormality, symmetry of the inputs) set a per-problem device
+ * status word; dmet_emb_status() waits for the plan's stream and reports it.
+ * dmet_emb_last_error() returns a human-readable message for the calling thread.
+ */
+#ifndef DMET_EMB_H
+#define DMET_EMB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DMET_API __attribute__((visibility("default")))
+#else
+#define DMET_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmet_emb_plan_s* dmet_emb_plan_t;
+
+typedef enum {
+  DMET_OK = 0,
+  DMET_ERR_INVALID_ARG = 1,     /* bad descriptor, index or null pointer */
+  DMET_ERR_ALIGNMENT = 2,       /* a pointer is not 16-byte aligned */
+  DMET_ERR_OOM = 3,             /* workspace or staging allocation failed / over the limit */
+  DMET_ERR_NOT_ORTHONORMAL = 4, /* device check: |s_O sum_k C^k+ C^k - 1|_max > ortho_tol */
+  DMET_ERR_CUDA = 5,            /* a CUDA runtime call failed (message in dmet_emb_last_error) */
+  DMET_ERR_TIMEOUT = 6,         /* a bounded device wait expired */
+  DMET_ERR_UNSUPPORTED = 7,     /* valid request that this build does not implement */
+  DMET_ERR_SYMMETRY = 8         /* device check: inputs violate the declared symmetry */
+} dmet_status_t;
+
+typedef enum {
+  DMET_PREC_FP64 = 0,    /* every product and sum in IEEE FP64 */
+  DMET_PREC_BF16X3 = 1   /* split-BF16 products on tcgen05, FP32 accumulation per q block,
+                            FP64 cross-q accumulation */
+} dmet_prec_t;
+
+typedef enum {
+  DMET_SYM_NONE = 0,     /* no symmetry assumed: all q, all (k1, k1+q) pairs */
+  DMET_SYM_REAL = 1      /* real-space-real integrals and orbitals:
+                            L^{k2,k1}_{P,nu mu} = conj(L^{k1,k2}_{P,mu nu}),
+                            L^{-k1,-k2} = conj(L^{k1,k2}), C^{-k} = conj(C^k);
+                            the ERI is real with 8-fold symmetry */
+} dmet_sym_t;
+
+typedef enum {
+  DMET_PACK_AUTO = 0,    /* S8 for DMET_SYM_REAL, FULL otherwise */
+  DMET_PACK_S8 = 1,      /* real, 8-fold packed (requires DMET_SYM_REAL) */
+  DMET_PACK_FULL = 2     /* complex128 [n][n][n][n] */
+} dmet_pack_t;
+
+/* One embedding problem. Sizes follow section 2.1/2.2: a Gamma-centred mesh, n_ao AOs and
+ * n_aux density-fitting functions per cell, n_emb embedding orbitals per spin
+ * (n_spin = 2 for the unrestricted solver of section 2.2). */
+typedef struct {
+  int32_t mesh[3];      /* N1, N2, N3 >= 1; Nk = N1*N2*N3 <= 4096 */
+  int32_t n_ao;         /* >= 1 */
+  int32_t n_aux;        /* >= 1 */
+  int32_t n_spin;       /* 1 or 2 */
+  int32_t n_emb[2];     /* 1 <= n_emb[s] <= Nk*n_ao; n_emb[1] ignored when n_spin == 1 */
+  int32_t prec;         /* dmet_prec_t */
+  int32_t ck_norm;      /* 0: Bloch sum of Eq. "C loemb k"; 1: unitary (times Nk^-1/2) */
+  int32_t sym;          /* dmet_sym_t */
+  int32_t eri_pack;     /* dmet_pack_t */
+  int32_t check_l;      /* 1: verify the symmetries of L on the device when sym = REAL */
+  int32_t reserved;     /* must be 0 */
+  double ortho_tol;     /* <= 0 selects 1e-10 */
+  double sym_tol;       /* relative; <= 0 selects 1e-10 */
+} dmet_emb_desc_t;
+
+/* ERI output blocks per problem (dmet_emb_eri):
+ *   n_spin == 1: block 0 = (ij|kl) over spin alpha.
+ *   n_spin == 2: block 0 = alpha-alpha, block 1 = alpha-beta ((ij) alpha, (kl) beta),
+ *                block 2 = beta-beta.
+ * Layouts:
+ *   S8, same-spin block: double[npair*(npair+1)/2], npair = n(n+1)/2, pair index
+ *       IJ = i(i+1)/2 + j (i >= j), element IJ(IJ+1)/2 + KL (IJ >= KL).
+ *   S8, alpha-beta block: double[npair_a][npair_b], element [IJ][KL].
+ *   FULL: complex128 [n_a][n_a][n_b][n_b], element [i][j][k][l].
+ * Returns the number of BYTES of block `block` of `desc`, or 0 for an invalid request. */
+DMET_API size_t dmet_emb_eri_bytes(const dmet_emb_desc_t* desc, int32_t block);
+
+/* Builds a plan for n_problems problems (section 2.1, Algorithm 1's loop structure:
+ * the scheduler tables of momentum-conserving pairs per q). `stream` is a cudaStream_t
+ * (NULL = legacy default stream) on which every later call of this plan queues its work.
+ * workspace_limit bounds the plan's device workspace in bytes (0 = 8 GiB); the q-block
+ * size is chosen to fit it. Allocates device memory. Host-side validation only; no
+ * kernel runs. */
+DMET_API dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, void* stream,
+                            size_t workspace_limit, dmet_emb_plan_t* plan);
+
+/* Embedded 3-index factors L^q_{P,ij} for q in [q_begin, q_end) (Algorithm 1's inner loop:
+ * k-AO -> k-EO transform of every momentum-conserving pair, then the Fourier sum to the
+ * reference cell; the paper notes that a density-fitting solver can consume these
+ * directly and skip the contraction). C[s] and Lq_out[s] for s < n_spin.
+ * Also runs the orbital checks (orthonormality; realness when sym = REAL). */
+DMET_API dmet_status_t dmet_emb_transform_3idx(dmet_emb_plan_t plan, int32_t problem, const void* L,
+                                      const void* const* C, int32_t q_begin, int32_t q_end,
+                                      void* const* Lq_out);
+
+/* Embedded ERIs of every problem of the plan (Algorithm 1 including its final
+ * contraction over the aux index and the sum over q). L[p], C[p][s], eri_out[p][b] for
+ * problem p, spin s and output block b (see dmet_emb_eri_bytes). Output buffers are
+ * overwritten. */
+DMET_API dmet_status_t dmet_emb_eri(dmet_emb_plan_t plan, const void* const* L, const void* const* const* C,
+                           void* const* const* eri_out);
+
+/* Waits for the plan's stream and returns the device status of `problem`. If stats is not
+ * NULL it receives 4 doubles: [0] orthonormality error max|s_O sum_k C^k+C^k - 1| (worst
+ * spin), [1] relative realness error max|C^{-k} - conj C^k| / max|C|, [2] relative
+ * Hermiticity error of L, [3] relative time-reversal error of L (negative = not checked). */
+DMET_API dmet_status_t dmet_emb_status(dmet_emb_plan_t plan, int32_t problem, double* stats);
+
+/* Frees the plan's device memory, events and tables. Safe on NULL. Waits for the stream. */
+DMET_API dmet_status_t dmet_emb_destroy(dmet_emb_plan_t plan);
+
+/* The k-pair schedule of one problem (section 2.1, Algorithm 1's two loops; momentum
+ * conservation of Eq. "density fitting"). Host-only; no GPU needed. Arrays of Nk or Nk*Nk
+ * int32 entries, any may be NULL:
+ *   k2_of[q*Nk + k1] = k1 + q;  neg[k] = -k;
+ *   q_weight[q] = number of q values the contraction of q stands for (sym = REAL: 1 for
+ *                 self-conjugate q, 2 for the representative min(q, -q), 0 for the other;
+ *                 sym = NONE: 1 for every q);
+ *   n_rep[q], rep_k1[q*Nk + r], rep_half[q*Nk + r]: the k1 values whose transformed pairs are
+ *                 computed for q. sym = REAL: one k1 per orbit {k1, -k1-q} (the smaller), with
+ *                 rep_half = 1 for the fixed points k1 = -k1-q; sym = NONE: every k1, rep_half 0. */
+DMET_API dmet_status_t dmet_emb_schedule(const dmet_emb_desc_t* desc, int32_t* k2_of, int32_t* neg,
+                                int32_t* q_weight, int32_t* n_rep, int32_t* rep_k1,
+                                int32_t* rep_half);
+
+/* Per-kernel timing with CUDA events on the plan's stream. enable != 0 starts recording
+ * (and clears the counters); 0 stops. */
+DMET_API dmet_status_t dmet_emb_profile(dmet_emb_plan_t plan, int32_t enable);
+
+/* Reads the counters of kernel class `kernel` (0 .. dmet_emb_profile_count()-1): name,
+ * launches, total device milliseconds, algorithmic flops and algorithmic bytes summed over
+ * the recorded launches. Waits for the stream. */
+DMET_API int32_t dmet_emb_profile_count(void);
+DMET_API dmet_status_t dmet_emb_profile_read(dmet_emb_plan_t plan, int32_t kernel, const char** name,
+                                    int64_t* launches, double* total_ms, double* flops,
+                                    double* bytes);
+
+/* Number of kernel launches the plan has queued since it was created. */
+DMET_API int64_t dmet_emb_launch_count(dmet_emb_plan_t plan);
+
+/* Message describing the last error returned on the calling thread ("" if none). */
+DMET_API const char* dmet_emb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMET_EMB_H */

@@ -18,3 +18,4 @@ from .mesh import k_add, k_index, k_neg, k_triplet
 from .alg1 import embedded_3idx, embedded_eri, eri_entries
 from .supercell import supercell_eri
 from .checks import orthonormality_error, realness_error, pack_s8, pair_matrix, unpack_s8
+from .schedule import schedule

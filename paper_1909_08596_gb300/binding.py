@@ -1,0 +1,238 @@
+"""Thin ctypes binding of libdmetemb.so (include/dmet_emb.h), same names as the C entry points.
+
+Argument marshalling only: buffers are torch tensors (device or host) or numpy arrays
+(host), passed to the library as raw pointers. Every step of the computation runs in the
+library's CUDA kernels; if the library has not been built this module raises instead of
+falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+HEADER = os.path.join(_build.ROOT, "include", "dmet_emb.h")
+
+# dmet_status_t
+DMET_OK = 0
+DMET_ERR_INVALID_ARG = 1
+DMET_ERR_ALIGNMENT = 2
+DMET_ERR_OOM = 3
+DMET_ERR_NOT_ORTHONORMAL = 4
+DMET_ERR_CUDA = 5
+DMET_ERR_TIMEOUT = 6
+DMET_ERR_UNSUPPORTED = 7
+DMET_ERR_SYMMETRY = 8
+STATUS_NAMES = {0: "DMET_OK", 1: "DMET_ERR_INVALID_ARG", 2: "DMET_ERR_ALIGNMENT", 3: "DMET_ERR_OOM",
+                4: "DMET_ERR_NOT_ORTHONORMAL", 5: "DMET_ERR_CUDA", 6: "DMET_ERR_TIMEOUT",
+                7: "DMET_ERR_UNSUPPORTED", 8: "DMET_ERR_SYMMETRY"}
+# dmet_prec_t, dmet_sym_t, dmet_pack_t
+DMET_PREC_FP64, DMET_PREC_BF16X3 = 0, 1
+DMET_SYM_NONE, DMET_SYM_REAL = 0, 1
+DMET_PACK_AUTO, DMET_PACK_S8, DMET_PACK_FULL = 0, 1, 2
+
+
+class DmetError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class dmet_emb_desc_t(ctypes.Structure):
+    _fields_ = [
+        ("mesh", ctypes.c_int32 * 3),
+        ("n_ao", ctypes.c_int32),
+        ("n_aux", ctypes.c_int32),
+        ("n_spin", ctypes.c_int32),
+        ("n_emb", ctypes.c_int32 * 2),
+        ("prec", ctypes.c_int32),
+        ("ck_norm", ctypes.c_int32),
+        ("sym", ctypes.c_int32),
+        ("eri_pack", ctypes.c_int32),
+        ("check_l", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("ortho_tol", ctypes.c_double),
+        ("sym_tol", ctypes.c_double),
+    ]
+
+
+def make_desc(mesh, n_ao, n_aux, n_emb, n_spin=1, prec=DMET_PREC_FP64, ck_norm=0, sym=DMET_SYM_REAL,
+              eri_pack=DMET_PACK_AUTO, check_l=1, ortho_tol=0.0, sym_tol=0.0) -> dmet_emb_desc_t:
+    d = dmet_emb_desc_t()
+    d.mesh[:] = list(mesh)
+    d.n_ao, d.n_aux, d.n_spin = n_ao, n_aux, n_spin
+    ne = list(n_emb) if isinstance(n_emb, (list, tuple)) else [n_emb, n_emb if n_spin == 2 else 0]
+    d.n_emb[:] = ne + [0] * (2 - len(ne))
+    d.prec, d.ck_norm, d.sym, d.eri_pack, d.check_l = prec, ck_norm, sym, eri_pack, check_l
+    d.reserved = 0
+    d.ortho_tol, d.sym_tol = ortho_tol, sym_tol
+    return d
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1909_08596_gb300.build.build() "
+                               "(or __graft_entry__.build()); there is no fallback path")
+        L = ctypes.CDLL(LIB_PATH)
+        st = ctypes.c_int
+        L.dmet_emb_eri_bytes.argtypes = [ctypes.POINTER(dmet_emb_desc_t), ctypes.c_int32]
+        L.dmet_emb_eri_bytes.restype = ctypes.c_size_t
+        L.dmet_emb_plan.argtypes = [ctypes.POINTER(dmet_emb_desc_t), ctypes.c_int32, _P, ctypes.c_size_t,
+                                    ctypes.POINTER(_P)]
+        L.dmet_emb_plan.restype = st
+        L.dmet_emb_transform_3idx.argtypes = [_P, ctypes.c_int32, _P, ctypes.POINTER(_P), ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.POINTER(_P)]
+        L.dmet_emb_transform_3idx.restype = st
+        L.dmet_emb_eri.argtypes = [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.POINTER(_P)),
+                                   ctypes.POINTER(ctypes.POINTER(_P))]
+        L.dmet_emb_eri.restype = st
+        L.dmet_emb_status.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+        L.dmet_emb_status.restype = st
+        L.dmet_emb_destroy.argtypes = [_P]
+        L.dmet_emb_destroy.restype = st
+        ip = ctypes.POINTER(ctypes.c_int32)
+        L.dmet_emb_schedule.argtypes = [ctypes.POINTER(dmet_emb_desc_t), ip, ip, ip, ip, ip, ip]
+        L.dmet_emb_schedule.restype = st
+        L.dmet_emb_profile.argtypes = [_P, ctypes.c_int32]
+        L.dmet_emb_profile.restype = st
+        L.dmet_emb_profile_count.argtypes = []
+        L.dmet_emb_profile_count.restype = ctypes.c_int32
+        L.dmet_emb_profile_read.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_char_p),
+                                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        L.dmet_emb_profile_read.restype = st
+        L.dmet_emb_launch_count.argtypes = [_P]
+        L.dmet_emb_launch_count.restype = ctypes.c_int64
+        L.dmet_emb_last_error.argtypes = []
+        L.dmet_emb_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    """Entry points declared in include/dmet_emb.h."""
+    with open(HEADER) as f:
+        src = f.read()
+    return sorted(set(re.findall(r"DMET_API\s+[\w\s\*]+?\b(dmet_emb_\w+)\s*\(", src)))
+
+
+def _check(status):
+    if status != DMET_OK:
+        raise DmetError(status, lib().dmet_emb_last_error().decode())
+
+
+def ptr(buf) -> int:
+    """Raw address of a contiguous torch tensor or numpy array (None -> 0)."""
+    if buf is None:
+        return 0
+    if isinstance(buf, np.ndarray):
+        if not buf.flags.c_contiguous:
+            raise ValueError("numpy buffer must be C-contiguous")
+        return buf.ctypes.data
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return buf.data_ptr()
+    if isinstance(buf, int):
+        return buf
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _descs(descs):
+    if isinstance(descs, dmet_emb_desc_t):
+        descs = [descs]
+    arr = (dmet_emb_desc_t * len(descs))(*descs)
+    return arr, len(descs)
+
+
+def dmet_emb_eri_bytes(desc, block):
+    return int(lib().dmet_emb_eri_bytes(ctypes.byref(desc), block))
+
+
+def dmet_emb_plan(descs, stream=None, workspace_limit=0):
+    """Plan handle (int) for a desc or list of descs; `stream` is a cudaStream_t value."""
+    arr, n = _descs(descs)
+    out = _P()
+    _check(lib().dmet_emb_plan(arr, n, _P(stream or 0), workspace_limit, ctypes.byref(out)))
+    return out.value
+
+
+def dmet_emb_transform_3idx(plan, problem, L, C, q_begin, q_end, Lq_out):
+    cs = (_P * len(C))(*[ptr(c) for c in C])
+    outs = (_P * len(Lq_out))(*[ptr(o) for o in Lq_out])
+    _check(lib().dmet_emb_transform_3idx(_P(plan), problem, _P(ptr(L)), cs, q_begin, q_end, outs))
+
+
+def dmet_emb_eri(plan, L, C, eri_out):
+    """L: list over problems; C: list over problems of lists over spins; eri_out: list of lists."""
+    n = len(L)
+    ls = (_P * n)(*[ptr(x) for x in L])
+    crows = [(_P * len(c))(*[ptr(x) for x in c]) for c in C]
+    erows = [(_P * len(e))(*[ptr(x) for x in e]) for e in eri_out]
+    cp = (ctypes.POINTER(_P) * n)(*[ctypes.cast(r, ctypes.POINTER(_P)) for r in crows])
+    ep = (ctypes.POINTER(_P) * n)(*[ctypes.cast(r, ctypes.POINTER(_P)) for r in erows])
+    _check(lib().dmet_emb_eri(_P(plan), ls, cp, ep))
+
+
+def dmet_emb_status(plan, problem, raise_on_error=False):
+    """(status, stats[4]) after waiting for the plan's stream."""
+    stats = (ctypes.c_double * 4)()
+    s = lib().dmet_emb_status(_P(plan), problem, stats)
+    if raise_on_error:
+        _check(s)
+    return s, list(stats)
+
+
+def dmet_emb_destroy(plan):
+    _check(lib().dmet_emb_destroy(_P(plan)))
+
+
+def dmet_emb_schedule(desc):
+    nk = int(np.prod(list(desc.mesh)))
+    a = {k: np.zeros(nk * nk if k in ("k2_of", "rep_k1", "rep_half") else nk, dtype=np.int32)
+         for k in ("k2_of", "neg", "q_weight", "n_rep", "rep_k1", "rep_half")}
+    ip = ctypes.POINTER(ctypes.c_int32)
+    args = [a[k].ctypes.data_as(ip) for k in ("k2_of", "neg", "q_weight", "n_rep", "rep_k1", "rep_half")]
+    _check(lib().dmet_emb_schedule(ctypes.byref(desc), *args))
+    a["k2_of"] = a["k2_of"].reshape(nk, nk)
+    a["rep_k1"] = a["rep_k1"].reshape(nk, nk)
+    a["rep_half"] = a["rep_half"].reshape(nk, nk)
+    return a
+
+
+def dmet_emb_profile(plan, enable):
+    _check(lib().dmet_emb_profile(_P(plan), 1 if enable else 0))
+
+
+def dmet_emb_profile_count():
+    return int(lib().dmet_emb_profile_count())
+
+
+def dmet_emb_profile_read(plan, kernel):
+    name = ctypes.c_char_p()
+    launches = ctypes.c_int64()
+    ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().dmet_emb_profile_read(_P(plan), kernel, ctypes.byref(name), ctypes.byref(launches),
+                                       ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(by)))
+    return {"name": name.value.decode(), "launches": launches.value, "ms": ms.value, "flops": fl.value,
+            "bytes": by.value}
+
+
+def dmet_emb_launch_count(plan):
+    return int(lib().dmet_emb_launch_count(_P(plan)))
+
+
+def dmet_emb_last_error():
+    return lib().dmet_emb_last_error().decode()

@@ -1,0 +1,73 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dmet {
+
+// Batched complex FP64 GEMM:  D[m][n] = alpha * sum_k opA(m,k) * opB(k,n)  (+ D if beta).
+// opA(m,k) = A[k*lda + m] (A_KM) or A[m*lda + k] (A_MK), conjugated if conj_a.
+// opB(k,n) = B[k*ldb + n] (B_KN) or B[n*ldb + k] (B_NK).
+// Output address: (m/dm_div)*dm_hi + (m%dm_div)*dm_lo + (n/dn_div)*dn_hi + (n%dn_div)*dn_lo.
+// Batch z: tab == nullptr -> A += z*sA, B += z*sB, D += z*sD, K = K;
+//          else e = tab[tab0 + z] -> A += e.x*sA, B += e.y*sB, D += e.z*sD, K = e.w.
+enum { A_KM = 0, A_MK = 1 };
+enum { B_KN = 0, B_NK = 1 };
+
+struct ZgemmArgs {
+  const double2* A;
+  const double2* B;
+  double2* D;
+  const int4* tab;
+  int tab0;
+  int M, N, K;
+  long long lda, ldb;
+  long long sA, sB, sD;
+  int dm_div;
+  long long dm_hi, dm_lo;
+  int dn_div;
+  long long dn_hi, dn_lo;
+  double alpha;
+  int beta;
+  int batch;
+};
+
+cudaError_t launch_zgemm(const ZgemmArgs& a, int a_layout, bool conj_a, int b_layout, cudaStream_t s);
+
+// Real FP64 rank-K product of two [K][*] row-major operands X (ldx) and Y (ldy):
+//   mode 0 (8-fold packed, X == Y, M == N): out[m(m+1)/2 + n] += alpha * sum_k X[k][m] X[k][n], m >= n
+//   mode 1 (rectangular):                   out[m*ldo + n]    += alpha * sum_k X[k][m] Y[k][n]
+struct DsyrkArgs {
+  const double* X;
+  const double* Y;
+  double* out;
+  int M, N, K;
+  long long ldx, ldy, ldo;
+  double alpha;
+  int mode;
+};
+
+cudaError_t launch_dsyrk(const DsyrkArgs& a, cudaStream_t s);
+
+// C_rep[e][mu][i] = w_e * C[k1_e][mu][i] for the entries e of a table (x = k1, y = half flag).
+cudaError_t launch_gather_orbitals(const double2* C, double2* Crep, const int4* tab, int tab0,
+                                   int n_entries, int nao, int n, cudaStream_t s);
+
+// Real path: Z[q][P][i][j] -> X[q][P][c][IJ] = Re/Im of s * (Z_ij + Z_ji), c < nc, i >= j.
+cudaError_t launch_pack_pairs(const double2* Z, double* X, int nq, int naux, int n, int nc, double s,
+                              cudaStream_t st);
+
+// Real path 3-index output: Lq[q][P][i][j] = s * (Z_ij + Z_ji).
+cudaError_t launch_symmetrize(const double2* Z, double2* Lq, int nq, int naux, int n, double s,
+                              cudaStream_t st);
+
+// Checks. stats layout (doubles, raw maxima): [0] orthonormality, [1] |C^{-k} - conj C^k|,
+// [2] |C|, [3] Hermiticity of L, [4] time reversal of L, [5] |L|.
+cudaError_t launch_orth_reduce(const double2* S, int n, double s, double* stat, cudaStream_t st);
+cudaError_t launch_c_real_check(const double2* C, const int* neg, int nk, int nao, int n, double* stats,
+                                cudaStream_t st);
+cudaError_t launch_l_check(const double2* L, const int* neg, int nk, int naux, int nao, double* stats,
+                           cudaStream_t st);
+
+}  // namespace dmet

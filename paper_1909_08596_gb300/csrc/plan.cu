@@ -1,0 +1,979 @@
+// Host side of the C ABI: plans, the k-pair scheduler, workspace, dispatch of the
+// kernels of Algorithm 1 (section 2.1), staging of host buffers, checks and profiling.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dmet_emb.h"
+#include "internal.h"
+
+using namespace dmet;
+
+namespace {
+
+thread_local std::string g_err;
+
+dmet_status_t fail(dmet_status_t st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) return fail(DMET_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TRY(expr)                          \
+  do {                                     \
+    dmet_status_t s_ = (expr);             \
+    if (s_ != DMET_OK) return s_;          \
+  } while (0)
+
+enum KernelClass {
+  KC_CHECK_C = 0,
+  KC_CHECK_L,
+  KC_GATHER,
+  KC_TRANSFORM_1,
+  KC_TRANSFORM_2,
+  KC_PACK,
+  KC_CONTRACT,
+  KC_CONTRACT_FULL,
+  KC_COPY,
+  KC_COUNT
+};
+const char* const kKcNames[KC_COUNT] = {"check_orbitals", "check_L",          "gather_orbitals",
+                                        "half_transform_1", "half_transform_2", "pack_pairs",
+                                        "contract_s8",     "contract_full",    "host_copy"};
+
+// ------------------------------------------------------------------------------------------
+// Scheduler: momentum-conserving pairs (k1, k1 + q), negation, q weights and the
+// representative k1 of each orbit {k1, -k1 - q} (real-space-real inputs).
+
+struct Sched {
+  int nk = 0;
+  int mesh[3] = {1, 1, 1};
+  std::vector<int> k2_of, neg, qw, nrep, rep_k1, rep_half;
+};
+
+int kidx(int a, int b, int c, const int* m) {
+  a = ((a % m[0]) + m[0]) % m[0];
+  b = ((b % m[1]) + m[1]) % m[1];
+  c = ((c % m[2]) + m[2]) % m[2];
+  return (a * m[1] + b) * m[2] + c;
+}
+
+void build_schedule(const dmet_emb_desc_t& d, Sched& s) {
+  const int* m = d.mesh;
+  s.nk = m[0] * m[1] * m[2];
+  std::memcpy(s.mesh, m, sizeof(s.mesh));
+  const int nk = s.nk;
+  std::vector<int> t0(nk), t1(nk), t2(nk);
+  for (int k = 0; k < nk; ++k) {
+    t0[k] = k / (m[1] * m[2]);
+    t1[k] = (k / m[2]) % m[1];
+    t2[k] = k % m[2];
+  }
+  s.k2_of.assign((size_t)nk * nk, 0);
+  s.neg.assign(nk, 0);
+  for (int q = 0; q < nk; ++q)
+    for (int k1 = 0; k1 < nk; ++k1)
+      s.k2_of[(size_t)q * nk + k1] = kidx(t0[k1] + t0[q], t1[k1] + t1[q], t2[k1] + t2[q], m);
+  for (int k = 0; k < nk; ++k) s.neg[k] = kidx(-t0[k], -t1[k], -t2[k], m);
+  s.qw.assign(nk, 1);
+  s.nrep.assign(nk, 0);
+  s.rep_k1.assign((size_t)nk * nk, 0);
+  s.rep_half.assign((size_t)nk * nk, 0);
+  const bool real = d.sym == DMET_SYM_REAL;
+  for (int q = 0; q < nk; ++q) {
+    if (real) s.qw[q] = (q == s.neg[q]) ? 1 : (q < s.neg[q] ? 2 : 0);
+    int r = 0;
+    for (int k1 = 0; k1 < nk; ++k1) {
+      if (real) {
+        const int partner = s.neg[s.k2_of[(size_t)q * nk + k1]];  // -k1 - q
+        if (k1 > partner) continue;
+        s.rep_k1[(size_t)q * nk + r] = k1;
+        s.rep_half[(size_t)q * nk + r] = (k1 == partner) ? 1 : 0;
+      } else {
+        s.rep_k1[(size_t)q * nk + r] = k1;
+        s.rep_half[(size_t)q * nk + r] = 0;
+      }
+      ++r;
+    }
+    s.nrep[q] = r;
+  }
+}
+
+// Entry tables for one ordering of q values. Entry e = (q, r) for the r-th representative.
+struct Tables {
+  std::vector<int> order;      // q values
+  std::vector<int> start;      // prefix over order, size order+1 (entries)
+  std::vector<int4> t1;        // per entry: {k2, k1*nk + k2, e, nao}
+  std::vector<int4> t2;        // per q slot: {start, start, slot, nrep*nao}
+  std::vector<int4> gather;    // per entry: {k1, half, 0, 0}
+  int4* d_t1 = nullptr;
+  int4* d_t2 = nullptr;
+  int4* d_gather = nullptr;
+};
+
+void build_tables(const Sched& s, const std::vector<int>& order, int nao, Tables& t) {
+  t.order = order;
+  t.start.assign(order.size() + 1, 0);
+  t.t1.clear();
+  t.t2.clear();
+  t.gather.clear();
+  const int nk = s.nk;
+  for (size_t i = 0; i < order.size(); ++i) {
+    const int q = order[i];
+    t.start[i] = (int)t.t1.size();
+    for (int r = 0; r < s.nrep[q]; ++r) {
+      const int k1 = s.rep_k1[(size_t)q * nk + r];
+      const int k2 = s.k2_of[(size_t)q * nk + k1];
+      const int e = (int)t.t1.size();
+      t.t1.push_back(make_int4(k2, k1 * nk + k2, e, nao));
+      t.gather.push_back(make_int4(k1, s.rep_half[(size_t)q * nk + r], 0, 0));
+    }
+    t.t2.push_back(make_int4(t.start[i], t.start[i], (int)i, s.nrep[q] * nao));
+  }
+  t.start[order.size()] = (int)t.t1.size();
+}
+
+struct Block {
+  int b0, b1, w;  // slots [b0, b1) of an ordering, contraction weight
+};
+
+struct Prob {
+  dmet_emb_desc_t d;
+  Sched s;
+  int nk, nao, naux, nspin, n[2];
+  long long npair[2];
+  int pack;            // resolved: S8 or FULL
+  double lq_scale;     // 1/Nk (Bloch sum) or 1 (unitary)
+  double ortho_scale;  // same
+  Tables nat, con;     // natural q order; contraction order (S8 only)
+  std::vector<Block> con_blocks;
+  int bq = 1;          // q slots per block
+  int* d_neg = nullptr;
+};
+
+struct KStat {
+  long long launches = 0;
+  double flops = 0, bytes = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+};
+
+}  // namespace
+
+struct dmet_emb_plan_s {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::vector<Prob> probs;
+  size_t ws_limit = 0;
+  // workspace
+  double2* crep = nullptr;
+  double2* T = nullptr;
+  double2* Z = nullptr;
+  double2* S = nullptr;
+  double* X[2] = {nullptr, nullptr};
+  double2* lq_all[2] = {nullptr, nullptr};
+  size_t crep_b = 0, T_b = 0, Z_b = 0, S_b = 0, X_b[2] = {0, 0}, lq_all_b[2] = {0, 0};
+  double* dstats = nullptr;  // [n_problems][8]
+  // staging of host buffers
+  void* stage_in = nullptr;
+  size_t stage_in_b = 0;
+  void* stage_out = nullptr;
+  size_t stage_out_b = 0;
+  // profiling
+  bool prof = false;
+  KStat ks[KC_COUNT];
+  std::vector<cudaEvent_t> pool;
+  long long launches = 0;
+};
+
+namespace {
+
+// ------------------------------------------------------------------------------------------
+// Validation and sizes
+
+size_t eri_bytes_of(const dmet_emb_desc_t& d, int block) {
+  const int nspin = d.n_spin;
+  const int nblk = nspin == 1 ? 1 : 3;
+  if (block < 0 || block >= nblk) return 0;
+  const long long na = d.n_emb[0];
+  const long long nb = nspin == 1 ? na : d.n_emb[1];
+  const long long a = block == 2 ? nb : na;
+  const long long b = block == 0 ? na : nb;
+  int pack = d.eri_pack == DMET_PACK_AUTO ? (d.sym == DMET_SYM_REAL ? DMET_PACK_S8 : DMET_PACK_FULL) : d.eri_pack;
+  if (pack == DMET_PACK_S8) {
+    const long long pa = a * (a + 1) / 2, pb = b * (b + 1) / 2;
+    if (block == 1) return (size_t)(pa * pb) * 8;
+    return (size_t)(pa * (pa + 1) / 2) * 8;
+  }
+  return (size_t)(a * a * b * b) * 16;
+}
+
+dmet_status_t validate_desc(const dmet_emb_desc_t& d, int idx) {
+  for (int i = 0; i < 3; ++i)
+    if (d.mesh[i] < 1 || d.mesh[i] > 4096) return fail(DMET_ERR_INVALID_ARG, "problem %d: mesh[%d] = %d", idx, i, d.mesh[i]);
+  const long long nk = (long long)d.mesh[0] * d.mesh[1] * d.mesh[2];
+  if (nk > 4096) return fail(DMET_ERR_INVALID_ARG, "problem %d: Nk = %lld > 4096", idx, nk);
+  if (d.n_ao < 1 || d.n_ao > 4096) return fail(DMET_ERR_INVALID_ARG, "problem %d: n_ao = %d", idx, d.n_ao);
+  if (d.n_aux < 1 || d.n_aux > 65536) return fail(DMET_ERR_INVALID_ARG, "problem %d: n_aux = %d", idx, d.n_aux);
+  if (d.n_spin != 1 && d.n_spin != 2) return fail(DMET_ERR_INVALID_ARG, "problem %d: n_spin = %d", idx, d.n_spin);
+  for (int s = 0; s < d.n_spin; ++s) {
+    if (d.n_emb[s] < 1 || (long long)d.n_emb[s] > nk * d.n_ao)
+      return fail(DMET_ERR_INVALID_ARG, "problem %d: n_emb[%d] = %d not in [1, Nk*n_ao]", idx, s, d.n_emb[s]);
+    if (d.n_emb[s] > 2047) return fail(DMET_ERR_UNSUPPORTED, "problem %d: n_emb > 2047", idx);
+  }
+  if (d.ck_norm != 0 && d.ck_norm != 1) return fail(DMET_ERR_INVALID_ARG, "problem %d: ck_norm = %d", idx, d.ck_norm);
+  if (d.sym != DMET_SYM_NONE && d.sym != DMET_SYM_REAL) return fail(DMET_ERR_INVALID_ARG, "problem %d: sym = %d", idx, d.sym);
+  if (d.eri_pack < 0 || d.eri_pack > 2) return fail(DMET_ERR_INVALID_ARG, "problem %d: eri_pack = %d", idx, d.eri_pack);
+  if (d.eri_pack == DMET_PACK_S8 && d.sym != DMET_SYM_REAL)
+    return fail(DMET_ERR_INVALID_ARG, "problem %d: 8-fold packing needs sym = DMET_SYM_REAL", idx);
+  if (d.check_l != 0 && d.check_l != 1) return fail(DMET_ERR_INVALID_ARG, "problem %d: check_l = %d", idx, d.check_l);
+  if (d.reserved != 0) return fail(DMET_ERR_INVALID_ARG, "problem %d: reserved field must be 0", idx);
+  if (d.prec != DMET_PREC_FP64 && d.prec != DMET_PREC_BF16X3) return fail(DMET_ERR_INVALID_ARG, "problem %d: prec = %d", idx, d.prec);
+  if (d.prec != DMET_PREC_FP64) return fail(DMET_ERR_UNSUPPORTED, "problem %d: precision %d not built", idx, d.prec);
+  const long long nmax = std::max(d.n_emb[0], d.n_spin == 2 ? d.n_emb[1] : 0);
+  if ((long long)d.n_aux * nmax > INT_MAX / 2 || (long long)d.n_aux * d.n_ao > INT_MAX / 2)
+    return fail(DMET_ERR_UNSUPPORTED, "problem %d: n_aux*n too large for one launch", idx);
+  return DMET_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// ------------------------------------------------------------------------------------------
+// Launch helpers with per-class accounting and optional CUDA-event timing.
+
+cudaEvent_t get_event(dmet_emb_plan_s* P) {
+  if (!P->pool.empty()) {
+    cudaEvent_t e = P->pool.back();
+    P->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+struct Timed {
+  dmet_emb_plan_s* P;
+  int kc;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timed(dmet_emb_plan_s* p, int k, double flops, double bytes, int nlaunch = 1) : P(p), kc(k) {
+    P->ks[kc].launches += nlaunch;
+    P->ks[kc].flops += flops;
+    P->ks[kc].bytes += bytes;
+    if (kc != KC_COPY) P->launches += nlaunch;
+    if (P->prof) {
+      a = get_event(P);
+      b = get_event(P);
+      if (a) cudaEventRecord(a, P->stream);
+    }
+  }
+  ~Timed() {
+    if (P->prof && a && b) {
+      cudaEventRecord(b, P->stream);
+      P->ks[kc].ev.emplace_back(a, b);
+    }
+  }
+};
+
+ZgemmArgs zargs() {
+  ZgemmArgs z;
+  std::memset(&z, 0, sizeof(z));
+  z.dm_div = INT_MAX;
+  z.dn_div = INT_MAX;
+  z.alpha = 1.0;
+  z.batch = 1;
+  return z;
+}
+
+dmet_status_t ensure(void** p, size_t* have, size_t need) {
+  if (need <= *have) return DMET_OK;
+  if (*p) {
+    CK(cudaFree(*p));
+    *p = nullptr;
+    *have = 0;
+  }
+  if (cudaMalloc(p, need) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(DMET_ERR_OOM, "cudaMalloc of %zu bytes failed", need);
+  }
+  *have = need;
+  return DMET_OK;
+}
+
+// Orbital checks: orthonormality (Eq. "fock transform" normalisation with F = S = 1) and,
+// for real-space-real inputs, C^{-k} = conj(C^k).
+dmet_status_t run_orbital_checks(dmet_emb_plan_s* P, Prob& pr, int p, const double2* const* C) {
+  double* st = P->dstats + 8 * p;
+  for (int s = 0; s < pr.nspin; ++s) {
+    const int n = pr.n[s];
+    {
+      Timed t(P, KC_CHECK_C, 8.0 * n * n * (double)pr.nk * pr.nao, 16.0 * pr.nk * pr.nao * n, 2);
+      ZgemmArgs z = zargs();
+      z.A = C[s];
+      z.B = C[s];
+      z.D = P->S;
+      z.M = n;
+      z.N = n;
+      z.K = pr.nk * pr.nao;
+      z.lda = n;
+      z.ldb = n;
+      z.dm_lo = n;
+      z.dn_lo = 1;
+      CK(launch_zgemm(z, A_KM, true, B_KN, P->stream));
+      CK(launch_orth_reduce(P->S, n, pr.ortho_scale, st + 0, P->stream));
+    }
+    if (pr.d.sym == DMET_SYM_REAL) {
+      Timed t(P, KC_CHECK_C, 0.0, 32.0 * pr.nk * pr.nao * n);
+      CK(launch_c_real_check(C[s], pr.d_neg, pr.nk, pr.nao, n, st, P->stream));
+    }
+  }
+  return DMET_OK;
+}
+
+dmet_status_t run_l_check(dmet_emb_plan_s* P, Prob& pr, int p, const double2* L) {
+  if (pr.d.sym != DMET_SYM_REAL || !pr.d.check_l) return DMET_OK;
+  const double elems = (double)pr.nk * pr.nk * pr.naux * pr.nao * pr.nao;
+  Timed t(P, KC_CHECK_L, 0.0, 16.0 * elems);
+  CK(launch_l_check(L, pr.d_neg, pr.nk, pr.naux, pr.nao, P->dstats + 8 * p, P->stream));
+  return DMET_OK;
+}
+
+// Transformed pairs and their Fourier sum for the q slots [b0, b1) of table `tb`, spin s.
+// Writes Z (real-space-real inputs: the half sum over orbit representatives) or, for
+// sym = NONE, L^q scaled by lq_scale directly into `dest` (slot-major, z0 = b0).
+dmet_status_t run_half_transform(dmet_emb_plan_s* P, Prob& pr, const Tables& tb, int b0, int b1, int s,
+                                 const double2* L, const double2* C, double2* dest, int dest_slot0) {
+  const int n = pr.n[s], nao = pr.nao, naux = pr.naux, nk = pr.nk;
+  const int e0 = tb.start[b0], E = tb.start[b1] - e0;
+  if (E <= 0) return DMET_OK;
+  {
+    Timed t(P, KC_GATHER, 0.0, 32.0 * E * nao * n);
+    CK(launch_gather_orbitals(C, P->crep, tb.d_gather, e0, E, nao, n, P->stream));
+  }
+  {
+    // T_e[mu][P][j] = sum_nu C^{k2}_{nu j} L^{k1,k2}_{P,mu nu}   (k-AO -> k-EO, ket side)
+    ZgemmArgs z = zargs();
+    z.A = C;
+    z.B = L;
+    z.D = P->T;
+    z.tab = tb.d_t1;
+    z.tab0 = e0;
+    z.M = n;
+    z.N = naux * nao;
+    z.K = nao;
+    z.lda = n;
+    z.ldb = nao;
+    z.sA = (long long)nao * n;
+    z.sB = (long long)naux * nao * nao;
+    z.sD = (long long)nao * naux * n;
+    z.dm_lo = 1;
+    z.dn_div = nao;
+    z.dn_hi = n;
+    z.dn_lo = (long long)naux * n;
+    z.batch = E;
+    // table entries carry absolute indices; T holds this block's entries only
+    z.D = P->T - (long long)e0 * z.sD;
+    Timed t(P, KC_TRANSFORM_1, 8.0 * n * (double)naux * nao * nao * E, 0.0);
+    CK(launch_zgemm(z, A_KM, false, B_NK, P->stream));
+  }
+  {
+    // Z_q[P][i][j] = sum_{(r, mu)} w_r conj(C^{k1_r}_{mu i}) T_r[mu][P][j]   (bra side + FT to R=0)
+    const bool real = pr.d.sym == DMET_SYM_REAL;
+    ZgemmArgs z = zargs();
+    z.A = P->crep - (long long)e0 * nao * n;
+    z.B = P->T - (long long)e0 * nao * naux * n;
+    z.tab = tb.d_t2;
+    z.tab0 = b0;
+    z.M = n;
+    z.N = naux * n;
+    z.lda = n;
+    z.ldb = (long long)naux * n;
+    z.sA = (long long)nao * n;
+    z.sB = (long long)nao * naux * n;
+    z.sD = (long long)naux * n * n;
+    z.dm_lo = n;
+    z.dn_div = n;
+    z.dn_hi = (long long)n * n;
+    z.dn_lo = 1;
+    z.batch = b1 - b0;
+    z.alpha = real ? 1.0 : pr.lq_scale;
+    z.D = (real ? P->Z : dest) - (long long)(real ? b0 : dest_slot0) * z.sD;
+    double fl = 0;
+    for (int i = b0; i < b1; ++i) fl += 8.0 * n * (double)naux * n * tb.t2[i].w;
+    Timed t(P, KC_TRANSFORM_2, fl, 0.0);
+    CK(launch_zgemm(z, A_KM, true, B_KN, P->stream));
+  }
+  return DMET_OK;
+}
+
+dmet_status_t transform_range(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, int q_begin,
+                              int q_end, double2* const* out) {
+  const bool real = pr.d.sym == DMET_SYM_REAL;
+  for (int qa = q_begin; qa < q_end; qa += pr.bq) {
+    const int qb = std::min(q_end, qa + pr.bq);
+    for (int s = 0; s < pr.nspin; ++s) {
+      const long long slot = (long long)pr.naux * pr.n[s] * pr.n[s];
+      double2* dest = out[s] + (long long)(qa - q_begin) * slot;
+      TRY(run_half_transform(P, pr, pr.nat, qa, qb, s, L, C[s], dest, qa));
+      if (real) {
+        Timed t(P, KC_PACK, 0.0, 32.0 * (qb - qa) * (double)slot);
+        CK(launch_symmetrize(P->Z, dest, qb - qa, pr.naux, pr.n[s], pr.lq_scale, P->stream));
+      }
+    }
+  }
+  return DMET_OK;
+}
+
+dmet_status_t eri_s8(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, void* const* out) {
+  for (const Block& bl : pr.con_blocks) {
+    const int nq = bl.b1 - bl.b0;
+    const int nc = bl.w == 1 ? 1 : 2;
+    for (int s = 0; s < pr.nspin; ++s) {
+      TRY(run_half_transform(P, pr, pr.con, bl.b0, bl.b1, s, L, C[s], nullptr, 0));
+      const double elems = (double)nq * pr.naux * pr.n[s] * pr.n[s];
+      Timed t(P, KC_PACK, 0.0, 16.0 * elems + 8.0 * nq * pr.naux * nc * (double)pr.npair[s]);
+      CK(launch_pack_pairs(P->Z, P->X[s], nq, pr.naux, pr.n[s], nc, pr.lq_scale, P->stream));
+    }
+    const int K = nq * pr.naux * nc;
+    const double alpha = (double)bl.w / pr.nk;
+    for (int blk = 0; blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
+      const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
+      DsyrkArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.X = P->X[sa];
+      a.Y = P->X[sb];
+      a.out = (double*)out[blk];
+      a.M = (int)pr.npair[sa];
+      a.N = (int)pr.npair[sb];
+      a.K = K;
+      a.ldx = pr.npair[sa];
+      a.ldy = pr.npair[sb];
+      a.ldo = pr.npair[sb];
+      a.alpha = alpha;
+      a.mode = blk == 1 ? 1 : 0;
+      const double fl = a.mode == 0 ? (double)a.M * (a.M + 1.0) * K : 2.0 * a.M * (double)a.N * K;
+      Timed t(P, KC_CONTRACT, fl, 0.0);
+      CK(launch_dsyrk(a, P->stream));
+    }
+  }
+  return DMET_OK;
+}
+
+dmet_status_t eri_full(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, void* const* out) {
+  double2* lq[2] = {P->lq_all[0], P->lq_all[1]};
+  TRY(transform_range(P, pr, L, C, 0, pr.nk, lq));
+  for (int blk = 0; blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
+    const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
+    const long long na2 = (long long)pr.n[sa] * pr.n[sa], nb2 = (long long)pr.n[sb] * pr.n[sb];
+    for (int q = 0; q < pr.nk; ++q) {
+      // (ij|kl) += (1/Nk) sum_P L^q_{P,ij} L^{-q}_{P,kl}
+      ZgemmArgs z = zargs();
+      z.A = lq[sa] + (long long)q * pr.naux * na2;
+      z.B = lq[sb] + (long long)pr.s.neg[q] * pr.naux * nb2;
+      z.D = (double2*)out[blk];
+      z.M = (int)na2;
+      z.N = (int)nb2;
+      z.K = pr.naux;
+      z.lda = na2;
+      z.ldb = nb2;
+      z.dm_lo = nb2;
+      z.dn_lo = 1;
+      z.alpha = 1.0 / pr.nk;
+      z.beta = 1;
+      Timed t(P, KC_CONTRACT_FULL, 8.0 * (double)na2 * nb2 * pr.naux, 0.0);
+      CK(launch_zgemm(z, A_KM, false, B_KN, P->stream));
+    }
+  }
+  return DMET_OK;
+}
+
+// Workspace for a q-block size bq.
+struct WsSizes {
+  size_t crep, T, Z, S, X[2], lq_all[2];
+  size_t total() const { return crep + T + Z + S + X[0] + X[1] + lq_all[0] + lq_all[1]; }
+};
+
+void partition(const Prob& pr, const Tables& t, const std::vector<int>& wts, int bq, std::vector<Block>& out) {
+  out.clear();
+  int i = 0;
+  const int m = (int)t.order.size();
+  while (i < m) {
+    int j = i + 1;
+    while (j < m && j - i < bq && wts[j] == wts[i]) ++j;
+    out.push_back({i, j, wts[i]});
+    i = j;
+  }
+  (void)pr;
+}
+
+int max_entries(const Tables& t, int bq) {
+  int best = 0;
+  const int m = (int)t.order.size();
+  for (int i = 0; i < m; ++i) best = std::max(best, t.start[std::min(m, i + bq)] - t.start[i]);
+  return best;
+}
+
+WsSizes ws_for(const Prob& pr, int bq) {
+  WsSizes w;
+  std::memset(&w, 0, sizeof(w));
+  const int nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
+  int E = max_entries(pr.nat, bq);
+  if (pr.pack == DMET_PACK_S8) E = std::max(E, max_entries(pr.con, bq));
+  w.crep = (size_t)E * pr.nao * nmax * 16;
+  w.T = (size_t)E * pr.nao * pr.naux * nmax * 16;
+  w.Z = pr.d.sym == DMET_SYM_REAL ? (size_t)bq * pr.naux * nmax * nmax * 16 : 0;
+  w.S = (size_t)nmax * nmax * 16;
+  for (int s = 0; s < pr.nspin; ++s) {
+    if (pr.pack == DMET_PACK_S8) w.X[s] = (size_t)bq * pr.naux * 2 * pr.npair[s] * 8;
+    else w.lq_all[s] = (size_t)pr.nk * pr.naux * pr.n[s] * pr.n[s] * 16;
+  }
+  return w;
+}
+
+dmet_status_t upload_tables(Tables& t) {
+  if (t.t1.empty()) return DMET_OK;
+  CK(cudaMalloc(&t.d_t1, t.t1.size() * sizeof(int4)));
+  CK(cudaMalloc(&t.d_t2, t.t2.size() * sizeof(int4)));
+  CK(cudaMalloc(&t.d_gather, t.gather.size() * sizeof(int4)));
+  CK(cudaMemcpy(t.d_t1, t.t1.data(), t.t1.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(t.d_t2, t.t2.data(), t.t2.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(t.d_gather, t.gather.data(), t.gather.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  return DMET_OK;
+}
+
+void free_tables(Tables& t) {
+  cudaFree(t.d_t1);
+  cudaFree(t.d_t2);
+  cudaFree(t.d_gather);
+  t.d_t1 = t.d_t2 = t.d_gather = nullptr;
+}
+
+void destroy_plan(dmet_emb_plan_s* P) {
+  if (!P) return;
+  if (P->stream) cudaStreamSynchronize(P->stream);
+  else cudaDeviceSynchronize();
+  for (auto& pr : P->probs) {
+    free_tables(pr.nat);
+    free_tables(pr.con);
+    cudaFree(pr.d_neg);
+  }
+  cudaFree(P->crep);
+  cudaFree(P->T);
+  cudaFree(P->Z);
+  cudaFree(P->S);
+  for (int s = 0; s < 2; ++s) {
+    cudaFree(P->X[s]);
+    cudaFree(P->lq_all[s]);
+  }
+  cudaFree(P->dstats);
+  cudaFree(P->stage_in);
+  cudaFree(P->stage_out);
+  for (auto& k : P->ks)
+    for (auto& e : k.ev) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+  for (auto e : P->pool) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete P;
+}
+
+}  // namespace
+
+// ==========================================================================================
+// C ABI
+
+extern "C" {
+
+size_t dmet_emb_eri_bytes(const dmet_emb_desc_t* desc, int32_t block) {
+  if (!desc) return 0;
+  if (validate_desc(*desc, 0) != DMET_OK) return 0;
+  return eri_bytes_of(*desc, block);
+}
+
+const char* dmet_emb_last_error(void) { return g_err.c_str(); }
+
+int32_t dmet_emb_profile_count(void) { return KC_COUNT; }
+
+dmet_status_t dmet_emb_schedule(const dmet_emb_desc_t* desc, int32_t* k2_of, int32_t* neg, int32_t* q_weight,
+                                int32_t* n_rep, int32_t* rep_k1, int32_t* rep_half) {
+  g_err.clear();
+  if (!desc) return fail(DMET_ERR_INVALID_ARG, "desc is NULL");
+  TRY(validate_desc(*desc, 0));
+  Sched s;
+  build_schedule(*desc, s);
+  const size_t nk = s.nk;
+  if (k2_of) std::copy(s.k2_of.begin(), s.k2_of.end(), k2_of);
+  if (neg) std::copy(s.neg.begin(), s.neg.end(), neg);
+  if (q_weight) std::copy(s.qw.begin(), s.qw.end(), q_weight);
+  if (n_rep) std::copy(s.nrep.begin(), s.nrep.end(), n_rep);
+  if (rep_k1) std::copy(s.rep_k1.begin(), s.rep_k1.begin() + nk * nk, rep_k1);
+  if (rep_half) std::copy(s.rep_half.begin(), s.rep_half.begin() + nk * nk, rep_half);
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, void* stream, size_t workspace_limit,
+                            dmet_emb_plan_t* plan) {
+  g_err.clear();
+  if (!plan) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
+  *plan = nullptr;
+  if (!descs) return fail(DMET_ERR_INVALID_ARG, "descs is NULL");
+  if (n_problems < 1 || n_problems > 65536) return fail(DMET_ERR_INVALID_ARG, "n_problems = %d", n_problems);
+  for (int p = 0; p < n_problems; ++p) TRY(validate_desc(descs[p], p));
+
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
+    cudaGetLastError();
+    return fail(DMET_ERR_CUDA, "no CUDA device visible");
+  }
+  dmet_emb_plan_s* P = new dmet_emb_plan_s();
+  P->stream = (cudaStream_t)stream;
+  cudaGetDevice(&P->device);
+  P->ws_limit = workspace_limit ? workspace_limit : ((size_t)8 << 30);
+  P->probs.resize(n_problems);
+  WsSizes need;
+  std::memset(&need, 0, sizeof(need));
+  for (int p = 0; p < n_problems; ++p) {
+    Prob& pr = P->probs[p];
+    pr.d = descs[p];
+    if (pr.d.ortho_tol <= 0) pr.d.ortho_tol = 1e-10;
+    if (pr.d.sym_tol <= 0) pr.d.sym_tol = 1e-10;
+    build_schedule(pr.d, pr.s);
+    pr.nk = pr.s.nk;
+    pr.nao = pr.d.n_ao;
+    pr.naux = pr.d.n_aux;
+    pr.nspin = pr.d.n_spin;
+    pr.n[0] = pr.d.n_emb[0];
+    pr.n[1] = pr.nspin == 2 ? pr.d.n_emb[1] : 0;
+    for (int s = 0; s < 2; ++s) pr.npair[s] = (long long)pr.n[s] * (pr.n[s] + 1) / 2;
+    pr.pack = pr.d.eri_pack == DMET_PACK_AUTO ? (pr.d.sym == DMET_SYM_REAL ? DMET_PACK_S8 : DMET_PACK_FULL)
+                                              : pr.d.eri_pack;
+    pr.lq_scale = pr.d.ck_norm == 0 ? 1.0 / pr.nk : 1.0;
+    pr.ortho_scale = pr.lq_scale;
+    std::vector<int> nat(pr.nk);
+    for (int q = 0; q < pr.nk; ++q) nat[q] = q;
+    build_tables(pr.s, nat, pr.nao, pr.nat);
+    std::vector<int> con, wts;
+    if (pr.pack == DMET_PACK_S8) {
+      for (int w = 1; w <= 2; ++w)
+        for (int q = 0; q < pr.nk; ++q)
+          if (pr.s.qw[q] == w) {
+            con.push_back(q);
+            wts.push_back(w);
+          }
+      build_tables(pr.s, con, pr.nao, pr.con);
+    }
+    // q-block size: the largest (<= 8, entries per launch <= 65535) whose workspace fits.
+    int bq = 8;
+    while (bq > 1 && (ws_for(pr, bq).total() > P->ws_limit || max_entries(pr.nat, bq) > 65535)) --bq;
+    WsSizes w = ws_for(pr, bq);
+    if (w.total() > P->ws_limit) {
+      destroy_plan(P);
+      return fail(DMET_ERR_OOM, "problem %d needs %zu bytes of workspace (limit %zu)", p, w.total(), P->ws_limit);
+    }
+    pr.bq = bq;
+    if (pr.pack == DMET_PACK_S8) partition(pr, pr.con, wts, bq, pr.con_blocks);
+    need.crep = std::max(need.crep, w.crep);
+    need.T = std::max(need.T, w.T);
+    need.Z = std::max(need.Z, w.Z);
+    need.S = std::max(need.S, w.S);
+    for (int s = 0; s < 2; ++s) {
+      need.X[s] = std::max(need.X[s], w.X[s]);
+      need.lq_all[s] = std::max(need.lq_all[s], w.lq_all[s]);
+    }
+  }
+  dmet_status_t st = DMET_OK;
+  auto alloc = [&](void** ptr, size_t* have, size_t bytes) {
+    if (st == DMET_OK && bytes) st = ensure(ptr, have, bytes);
+  };
+  alloc((void**)&P->crep, &P->crep_b, need.crep);
+  alloc((void**)&P->T, &P->T_b, need.T);
+  alloc((void**)&P->Z, &P->Z_b, need.Z);
+  alloc((void**)&P->S, &P->S_b, need.S);
+  for (int s = 0; s < 2; ++s) {
+    alloc((void**)&P->X[s], &P->X_b[s], need.X[s]);
+    alloc((void**)&P->lq_all[s], &P->lq_all_b[s], need.lq_all[s]);
+  }
+  if (st == DMET_OK && cudaMalloc(&P->dstats, sizeof(double) * 8 * n_problems) != cudaSuccess) {
+    cudaGetLastError();
+    st = fail(DMET_ERR_OOM, "stats allocation failed");
+  }
+  if (st == DMET_OK && cudaMemset(P->dstats, 0, sizeof(double) * 8 * n_problems) != cudaSuccess)
+    st = fail(DMET_ERR_CUDA, "cudaMemset failed");
+  for (int p = 0; st == DMET_OK && p < n_problems; ++p) {
+    Prob& pr = P->probs[p];
+    st = upload_tables(pr.nat);
+    if (st == DMET_OK && pr.pack == DMET_PACK_S8) st = upload_tables(pr.con);
+    if (st == DMET_OK) {
+      if (cudaMalloc(&pr.d_neg, sizeof(int) * pr.nk) != cudaSuccess ||
+          cudaMemcpy(pr.d_neg, pr.s.neg.data(), sizeof(int) * pr.nk, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        st = fail(DMET_ERR_CUDA, "table upload failed");
+      }
+    }
+  }
+  if (st != DMET_OK) {
+    std::string msg = g_err;
+    destroy_plan(P);
+    g_err = msg;
+    return st;
+  }
+  *plan = P;
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_destroy(dmet_emb_plan_t plan) {
+  g_err.clear();
+  destroy_plan(plan);
+  return DMET_OK;
+}
+
+// Staging: device pointers pass through; host pointers are copied into plan buffers.
+static dmet_status_t stage_inputs(dmet_emb_plan_s* P, const Prob& pr, const void* L, const void* const* C,
+                                  const double2** Ld, const double2** Cd) {
+  const size_t lb = (size_t)pr.nk * pr.nk * pr.naux * pr.nao * pr.nao * 16;
+  size_t need = 0;
+  const bool lhost = L && !is_device_ptr(L);
+  if (lhost) need += lb;
+  bool chost[2] = {false, false};
+  size_t cb[2] = {0, 0};
+  for (int s = 0; s < pr.nspin; ++s) {
+    cb[s] = (size_t)pr.nk * pr.nao * pr.n[s] * 16;
+    chost[s] = !is_device_ptr(C[s]);
+    if (chost[s]) need += cb[s];
+  }
+  if (need) TRY(ensure(&P->stage_in, &P->stage_in_b, need));
+  char* cur = (char*)P->stage_in;
+  if (L) *Ld = (const double2*)L;
+  if (lhost) {
+    Timed t(P, KC_COPY, 0.0, (double)lb);
+    CK(cudaMemcpyAsync(cur, L, lb, cudaMemcpyHostToDevice, P->stream));
+    *Ld = (const double2*)cur;
+    cur += lb;
+  }
+  for (int s = 0; s < pr.nspin; ++s) {
+    Cd[s] = (const double2*)C[s];
+    if (chost[s]) {
+      Timed t(P, KC_COPY, 0.0, (double)cb[s]);
+      CK(cudaMemcpyAsync(cur, C[s], cb[s], cudaMemcpyHostToDevice, P->stream));
+      Cd[s] = (const double2*)cur;
+      cur += cb[s];
+    }
+  }
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_transform_3idx(dmet_emb_plan_t P, int32_t problem, const void* L, const void* const* C,
+                                      int32_t q_begin, int32_t q_end, void* const* Lq_out) {
+  g_err.clear();
+  if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
+  if (problem < 0 || problem >= (int)P->probs.size()) return fail(DMET_ERR_INVALID_ARG, "problem %d", problem);
+  Prob& pr = P->probs[problem];
+  if (!L || !C || !Lq_out) return fail(DMET_ERR_INVALID_ARG, "NULL pointer argument");
+  if (q_begin < 0 || q_end > pr.nk || q_begin > q_end) return fail(DMET_ERR_INVALID_ARG, "q range [%d, %d)", q_begin, q_end);
+  if (!aligned16(L)) return fail(DMET_ERR_ALIGNMENT, "L not 16-byte aligned");
+  for (int s = 0; s < pr.nspin; ++s) {
+    if (!C[s] || !Lq_out[s]) return fail(DMET_ERR_INVALID_ARG, "NULL pointer for spin %d", s);
+    if (!aligned16(C[s]) || !aligned16(Lq_out[s])) return fail(DMET_ERR_ALIGNMENT, "spin %d pointer not 16-byte aligned", s);
+  }
+  if (q_begin == q_end) return DMET_OK;
+  const double2* Ld = nullptr;
+  const double2* Cd[2] = {nullptr, nullptr};
+  TRY(stage_inputs(P, pr, L, C, &Ld, Cd));
+  CK(cudaMemsetAsync(P->dstats + 8 * problem, 0, 8 * sizeof(double), P->stream));
+  TRY(run_orbital_checks(P, pr, problem, Cd));
+  TRY(run_l_check(P, pr, problem, Ld));
+  double2* out[2] = {nullptr, nullptr};
+  size_t ob[2] = {0, 0}, need = 0;
+  bool ohost[2] = {false, false};
+  for (int s = 0; s < pr.nspin; ++s) {
+    ob[s] = (size_t)(q_end - q_begin) * pr.naux * pr.n[s] * pr.n[s] * 16;
+    ohost[s] = !is_device_ptr(Lq_out[s]);
+    if (ohost[s]) need += ob[s];
+    out[s] = (double2*)Lq_out[s];
+  }
+  if (need) {
+    TRY(ensure(&P->stage_out, &P->stage_out_b, need));
+    char* cur = (char*)P->stage_out;
+    for (int s = 0; s < pr.nspin; ++s)
+      if (ohost[s]) {
+        out[s] = (double2*)cur;
+        cur += ob[s];
+      }
+  }
+  TRY(transform_range(P, pr, Ld, Cd, q_begin, q_end, out));
+  if (need) {
+    for (int s = 0; s < pr.nspin; ++s)
+      if (ohost[s]) {
+        Timed t(P, KC_COPY, 0.0, (double)ob[s]);
+        CK(cudaMemcpyAsync(Lq_out[s], out[s], ob[s], cudaMemcpyDeviceToHost, P->stream));
+      }
+    CK(cudaStreamSynchronize(P->stream));
+  }
+  CK(cudaGetLastError());
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_eri(dmet_emb_plan_t P, const void* const* L, const void* const* const* C,
+                           void* const* const* eri_out) {
+  g_err.clear();
+  if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
+  if (!L || !C || !eri_out) return fail(DMET_ERR_INVALID_ARG, "NULL pointer argument");
+  const int np = (int)P->probs.size();
+  for (int p = 0; p < np; ++p) {
+    const Prob& pr = P->probs[p];
+    if (!L[p] || !C[p] || !eri_out[p]) return fail(DMET_ERR_INVALID_ARG, "problem %d: NULL pointer", p);
+    if (!aligned16(L[p])) return fail(DMET_ERR_ALIGNMENT, "problem %d: L not 16-byte aligned", p);
+    for (int s = 0; s < pr.nspin; ++s) {
+      if (!C[p][s]) return fail(DMET_ERR_INVALID_ARG, "problem %d: C[%d] is NULL", p, s);
+      if (!aligned16(C[p][s])) return fail(DMET_ERR_ALIGNMENT, "problem %d: C[%d] not 16-byte aligned", p, s);
+    }
+    for (int b = 0; b < (pr.nspin == 1 ? 1 : 3); ++b) {
+      if (!eri_out[p][b]) return fail(DMET_ERR_INVALID_ARG, "problem %d: eri_out[%d] is NULL", p, b);
+      if (!aligned16(eri_out[p][b])) return fail(DMET_ERR_ALIGNMENT, "problem %d: eri_out[%d] not 16-byte aligned", p, b);
+    }
+  }
+  for (int p = 0; p < np; ++p) {
+    Prob& pr = P->probs[p];
+    const double2* Ld = nullptr;
+    const double2* Cd[2] = {nullptr, nullptr};
+    TRY(stage_inputs(P, pr, L[p], C[p], &Ld, Cd));
+    CK(cudaMemsetAsync(P->dstats + 8 * p, 0, 8 * sizeof(double), P->stream));
+    TRY(run_orbital_checks(P, pr, p, Cd));
+    TRY(run_l_check(P, pr, p, Ld));
+    const int nblk = pr.nspin == 1 ? 1 : 3;
+    void* out[3] = {nullptr, nullptr, nullptr};
+    size_t ob[3] = {0, 0, 0}, need = 0;
+    bool ohost[3] = {false, false, false};
+    for (int b = 0; b < nblk; ++b) {
+      ob[b] = eri_bytes_of(pr.d, b);
+      ohost[b] = !is_device_ptr(eri_out[p][b]);
+      if (ohost[b]) need += ob[b];
+      out[b] = eri_out[p][b];
+    }
+    if (need) {
+      TRY(ensure(&P->stage_out, &P->stage_out_b, need));
+      char* cur = (char*)P->stage_out;
+      for (int b = 0; b < nblk; ++b)
+        if (ohost[b]) {
+          out[b] = cur;
+          cur += ob[b];
+        }
+    }
+    for (int b = 0; b < nblk; ++b) CK(cudaMemsetAsync(out[b], 0, ob[b], P->stream));
+    if (pr.pack == DMET_PACK_S8) TRY(eri_s8(P, pr, Ld, Cd, out));
+    else TRY(eri_full(P, pr, Ld, Cd, out));
+    if (need) {
+      for (int b = 0; b < nblk; ++b)
+        if (ohost[b]) {
+          Timed t(P, KC_COPY, 0.0, (double)ob[b]);
+          CK(cudaMemcpyAsync(eri_out[p][b], out[b], ob[b], cudaMemcpyDeviceToHost, P->stream));
+        }
+      CK(cudaStreamSynchronize(P->stream));
+    }
+  }
+  CK(cudaGetLastError());
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_status(dmet_emb_plan_t P, int32_t problem, double* stats) {
+  g_err.clear();
+  if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
+  if (problem < 0 || problem >= (int)P->probs.size()) return fail(DMET_ERR_INVALID_ARG, "problem %d", problem);
+  CK(cudaStreamSynchronize(P->stream));
+  double h[8];
+  CK(cudaMemcpy(h, P->dstats + 8 * problem, sizeof(h), cudaMemcpyDeviceToHost));
+  const Prob& pr = P->probs[problem];
+  const bool real = pr.d.sym == DMET_SYM_REAL;
+  const double rc = real ? h[1] / std::max(h[2], 1e-300) : -1.0;
+  const bool lchk = real && pr.d.check_l;
+  const double herm = lchk ? h[3] / std::max(h[5], 1e-300) : -1.0;
+  const double tr = lchk ? h[4] / std::max(h[5], 1e-300) : -1.0;
+  if (stats) {
+    stats[0] = h[0];
+    stats[1] = rc;
+    stats[2] = herm;
+    stats[3] = tr;
+  }
+  if (!(h[0] <= pr.d.ortho_tol))
+    return fail(DMET_ERR_NOT_ORTHONORMAL, "problem %d: orthonormality error %.3e > %.3e", problem, h[0], pr.d.ortho_tol);
+  if (real && !(rc <= pr.d.sym_tol))
+    return fail(DMET_ERR_SYMMETRY, "problem %d: C^-k != conj C^k (relative %.3e)", problem, rc);
+  if (lchk && !(herm <= pr.d.sym_tol && tr <= pr.d.sym_tol))
+    return fail(DMET_ERR_SYMMETRY, "problem %d: L symmetry violated (hermiticity %.3e, time reversal %.3e)", problem,
+                herm, tr);
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_profile(dmet_emb_plan_t P, int32_t enable) {
+  g_err.clear();
+  if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
+  CK(cudaStreamSynchronize(P->stream));
+  for (auto& k : P->ks) {
+    for (auto& e : k.ev) {
+      P->pool.push_back(e.first);
+      P->pool.push_back(e.second);
+    }
+    k.ev.clear();
+    k.launches = 0;
+    k.flops = 0;
+    k.bytes = 0;
+  }
+  P->prof = enable != 0;
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_profile_read(dmet_emb_plan_t P, int32_t kernel, const char** name, int64_t* launches,
+                                    double* total_ms, double* flops, double* bytes) {
+  g_err.clear();
+  if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
+  if (kernel < 0 || kernel >= KC_COUNT) return fail(DMET_ERR_INVALID_ARG, "kernel %d", kernel);
+  CK(cudaStreamSynchronize(P->stream));
+  KStat& k = P->ks[kernel];
+  double ms = 0;
+  for (auto& e : k.ev) {
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, e.first, e.second));
+    ms += t;
+  }
+  if (name) *name = kKcNames[kernel];
+  if (launches) *launches = k.launches;
+  if (total_ms) *total_ms = ms;
+  if (flops) *flops = k.flops;
+  if (bytes) *bytes = k.bytes;
+  return DMET_OK;
+}
+
+int64_t dmet_emb_launch_count(dmet_emb_plan_t P) { return P ? P->launches : 0; }
+
+}  // extern "C"

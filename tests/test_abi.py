@@ -1,0 +1,116 @@
+"""CPU tests of the C-ABI library: it loads, exports every declared entry point, validates
+arguments on the host, and its k-pair scheduler matches the oracle's definition exactly."""
+import ctypes
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1909_08596_gb300 as dm
+from paper_1909_08596_gb300 import binding as B
+
+
+def test_library_exports_every_declared_symbol():
+    declared = B.declared_symbols()
+    assert len(declared) >= 12
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+    lib = B.lib()
+    for s in declared:
+        assert hasattr(lib, s)
+
+
+def test_desc_layout_matches_header():
+    # 13 int32 fields (mesh[3] counted as 3) then two doubles.
+    assert ctypes.sizeof(B.dmet_emb_desc_t) == 13 * 4 + 4 + 16  # 4 bytes of padding before the doubles
+    assert B.dmet_emb_desc_t.ortho_tol.offset == 56
+
+
+def test_eri_bytes():
+    d = dm.make_desc((2, 2, 1), 8, 40, 16)
+    npair = 16 * 17 // 2
+    assert dm.dmet_emb_eri_bytes(d, 0) == npair * (npair + 1) // 2 * 8
+    assert dm.dmet_emb_eri_bytes(d, 1) == 0
+    d = dm.make_desc((2, 2, 1), 8, 40, 16, sym=B.DMET_SYM_NONE)
+    assert dm.dmet_emb_eri_bytes(d, 0) == 16 ** 4 * 16
+    d = dm.make_desc((2, 2, 1), 8, 40, (5, 7), n_spin=2)
+    pa, pb = 15, 28
+    assert dm.dmet_emb_eri_bytes(d, 0) == pa * (pa + 1) // 2 * 8
+    assert dm.dmet_emb_eri_bytes(d, 1) == pa * pb * 8
+    assert dm.dmet_emb_eri_bytes(d, 2) == pb * (pb + 1) // 2 * 8
+    d = dm.make_desc((2, 2, 1), 8, 40, (5, 7), n_spin=2, eri_pack=B.DMET_PACK_FULL)
+    assert dm.dmet_emb_eri_bytes(d, 1) == 25 * 49 * 16
+
+
+@pytest.mark.parametrize("mesh", [(1, 1, 1), (2, 1, 1), (3, 1, 1), (2, 2, 1), (3, 2, 1), (2, 2, 2), (6, 6, 1),
+                                  (4, 4, 4), (3, 3, 3), (5, 1, 2), (16, 16, 16)])
+@pytest.mark.parametrize("sym", [0, 1])
+def test_schedule_matches_oracle(mesh, sym):
+    d = dm.make_desc(mesh, 2, 3, 1, sym=sym, eri_pack=B.DMET_PACK_FULL)
+    got = dm.dmet_emb_schedule(d)
+    if int(np.prod(mesh)) > 512:
+        # Large mesh: invariants only (the oracle's pure-Python loops would be slow).
+        nk = int(np.prod(mesh))
+        assert int(got["q_weight"].sum()) == nk
+        return
+    ref = oracle.schedule(mesh, bool(sym))
+    for k in ref:
+        assert np.array_equal(got[k], ref[k]), k
+
+
+BAD = {
+    "mesh0": dict(mesh=(0, 1, 1)),
+    "nk_too_big": dict(mesh=(17, 16, 16)),
+    "n_ao": dict(n_ao=0),
+    "n_aux": dict(n_aux=0),
+    "n_spin": dict(n_spin=3),
+    "n_emb0": dict(n_emb=0),
+    "n_emb_big": dict(n_emb=4 * 8 + 1),
+    "ck_norm": dict(ck_norm=2),
+    "sym": dict(sym=5),
+    "pack": dict(eri_pack=7),
+    "s8_needs_real": dict(sym=0, eri_pack=1),
+    "prec": dict(prec=9),
+    "check_l": dict(check_l=3),
+}
+
+
+@pytest.mark.parametrize("name", sorted(BAD))
+def test_invalid_descriptor_rejected_on_host(name):
+    kw = dict(mesh=(2, 2, 1), n_ao=8, n_aux=40, n_emb=16)
+    kw.update(BAD[name])
+    d = dm.make_desc(**kw)
+    with pytest.raises(B.DmetError) as e:
+        dm.dmet_emb_plan(d)
+    assert e.value.status == B.DMET_ERR_INVALID_ARG
+    assert dm.dmet_emb_eri_bytes(d, 0) == 0
+
+
+def test_reserved_field_must_be_zero():
+    d = dm.make_desc((2, 2, 1), 8, 40, 16)
+    d.reserved = 1
+    with pytest.raises(B.DmetError) as e:
+        dm.dmet_emb_plan(d)
+    assert e.value.status == B.DMET_ERR_INVALID_ARG
+
+
+def test_null_arguments():
+    lib = B.lib()
+    assert lib.dmet_emb_plan(None, 1, None, 0, None) == B.DMET_ERR_INVALID_ARG
+    assert lib.dmet_emb_eri(None, None, None, None) == B.DMET_ERR_INVALID_ARG
+    assert lib.dmet_emb_transform_3idx(None, 0, None, None, 0, 0, None) == B.DMET_ERR_INVALID_ARG
+    assert lib.dmet_emb_status(None, 0, None) == B.DMET_ERR_INVALID_ARG
+    assert lib.dmet_emb_destroy(None) == B.DMET_OK
+    assert b"NULL" in lib.dmet_emb_last_error() or lib.dmet_emb_last_error() == b""
+
+
+def test_plan_without_gpu_reports_cuda_error():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    with pytest.raises(B.DmetError) as e:
+        dm.dmet_emb_plan(dm.make_desc((2, 2, 1), 8, 40, 16))
+    assert e.value.status == B.DMET_ERR_CUDA

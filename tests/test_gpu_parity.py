@@ -1,0 +1,215 @@
+"""GPU parity of the FP64 path against the CPU oracle, through the C ABI.
+
+Tolerance: the FP64 path must match the FP64 oracle to 1e-10 relative Frobenius norm
+(and 1e-10 relative max-abs); both sides sum the same terms in different orders, so the
+expected difference is a few ulps times the square root of the summation length.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1909_08596_gb300 import binding as B
+
+from gpu_helpers import ab_index, rel_fro, run_3idx, run_eri, s8_index, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return torch_cuda()
+
+
+def spec_of(mesh, n_ao, n_aux, n_emb, n_spin=1, seed=21, decay=0.6):
+    return synth.LatticeSpec(tuple(mesh), n_ao, n_aux, n_emb, n_spin, decay, 0.0, seed, "t")
+
+
+def desc_of(spec, **kw):
+    ne = [spec.n_emb, spec.n_emb] if spec.n_spin == 2 else [spec.n_emb, 0]
+    if "n_emb" in kw:
+        ne = kw.pop("n_emb")
+    return B.make_desc(spec.mesh, spec.n_ao, spec.n_aux, ne, n_spin=spec.n_spin, **kw)
+
+
+def oracle_s8(L, C, mesh, ck_norm=0, Cb=None):
+    eri = oracle.embedded_eri(L, C, mesh, Cb=Cb, ck_norm=ck_norm)
+    return eri
+
+
+def check_s8(got, eri):
+    ref = oracle.pack_s8(eri.real)
+    assert got.shape == ref.shape
+    assert rel_fro(got, ref) < TOL
+    assert np.abs(got - ref).max() < TOL * np.abs(ref).max()
+
+
+CASES = [
+    # mesh, n_ao, n_aux, n_emb
+    ((2, 2, 1), 8, 40, 16),      # the tiny 2x2x1 workload
+    ((1, 1, 1), 5, 7, 3),        # Nk = 1: molecular limit
+    ((3, 1, 1), 5, 7, 1),        # a single orbital
+    ((3, 1, 1), 5, 7, 13),
+    ((2, 3, 1), 6, 11, 33),      # n_emb not a multiple of 8, several pair tiles
+    ((3, 3, 1), 10, 37, 70),     # several 64-tiles with a ragged tail in every dimension
+    ((2, 2, 2), 4, 9, 20),       # 3-D mesh with self-conjugate q in all directions
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c[0])) + f"_ao{c[1]}_aux{c[2]}_n{c[3]}")
+@pytest.mark.parametrize("ck_norm", [0, 1])
+def test_eri_s8_matches_oracle(torch, case, ck_norm):
+    mesh, nao, naux, n = case
+    spec = spec_of(mesh, nao, naux, n)
+    L, Cs, _ = synth.make_problem(spec, ck_norm=ck_norm)
+    (got,), st, stats = run_eri(torch, desc_of(spec, ck_norm=ck_norm), L, Cs)
+    assert st == B.DMET_OK, stats
+    assert stats[0] < 1e-12 and 0 <= stats[1] < 1e-12 and 0 <= stats[2] < 1e-12 and 0 <= stats[3] < 1e-12
+    check_s8(got, oracle_s8(L, Cs[0], spec.mesh, ck_norm))
+
+
+def test_eri_unrestricted_blocks(torch):
+    spec = spec_of((2, 2, 1), 5, 9, 6, n_spin=2)
+    L = synth.make_L(spec)
+    ca = synth.bloch_orbitals(synth.supercell_orbitals(spec, 0), spec.mesh)
+    cb = synth.bloch_orbitals(synth.supercell_orbitals(synth.spec_with(spec, n_emb=9), 1), spec.mesh)
+    (aa, ab, bb), st, _ = run_eri(torch, desc_of(spec, n_emb=[6, 9]), L, [ca, cb])
+    assert st == B.DMET_OK
+    check_s8(aa, oracle.embedded_eri(L, ca, spec.mesh))
+    check_s8(bb, oracle.embedded_eri(L, cb, spec.mesh))
+    ref_ab = oracle.pair_matrix(oracle.embedded_eri(L, ca, spec.mesh, Cb=cb).real).ravel()
+    assert rel_fro(ab, ref_ab) < TOL
+
+
+@pytest.mark.parametrize("real", [True, False])
+def test_eri_full_matches_oracle(torch, real):
+    spec = spec_of((2, 3, 1), 3, 6, 5)
+    L, (C,), _ = synth.make_problem(spec)
+    if not real:
+        rng = np.random.default_rng(4)
+        for k in range(spec.nk):
+            q, _ = np.linalg.qr(rng.standard_normal((5, 5)) + 1j * rng.standard_normal((5, 5)))
+            C[k] = C[k] @ q
+    sym = B.DMET_SYM_REAL if real else B.DMET_SYM_NONE
+    (got,), st, _ = run_eri(torch, desc_of(spec, sym=sym, eri_pack=B.DMET_PACK_FULL), L, [C])
+    assert st == B.DMET_OK
+    ref = oracle.embedded_eri(L, C, spec.mesh).ravel()
+    assert rel_fro(got, ref) < TOL
+
+
+def test_eri_full_unrestricted_complex(torch):
+    spec = spec_of((3, 1, 1), 4, 5, 4, n_spin=2)
+    L = synth.make_L(spec)
+    rng = np.random.default_rng(9)
+    cs = []
+    for s, n in enumerate((4, 6)):
+        c = synth.bloch_orbitals(synth.supercell_orbitals(synth.spec_with(spec, n_emb=n), s), spec.mesh)
+        for k in range(spec.nk):
+            q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+            c[k] = c[k] @ q
+        cs.append(c)
+    d = desc_of(spec, n_emb=[4, 6], sym=B.DMET_SYM_NONE)
+    (aa, ab, bb), st, _ = run_eri(torch, d, L, cs)
+    assert st == B.DMET_OK
+    assert rel_fro(aa, oracle.embedded_eri(L, cs[0], spec.mesh).ravel()) < TOL
+    assert rel_fro(ab, oracle.embedded_eri(L, cs[0], spec.mesh, Cb=cs[1]).ravel()) < TOL
+    assert rel_fro(bb, oracle.embedded_eri(L, cs[1], spec.mesh).ravel()) < TOL
+
+
+@pytest.mark.parametrize("sym", [B.DMET_SYM_REAL, B.DMET_SYM_NONE])
+@pytest.mark.parametrize("ck_norm", [0, 1])
+def test_transform_3idx_matches_oracle(torch, sym, ck_norm):
+    spec = spec_of((3, 2, 1), 5, 8, 7)
+    L, (C,), _ = synth.make_problem(spec, ck_norm=ck_norm)
+    d = desc_of(spec, sym=sym, ck_norm=ck_norm, eri_pack=B.DMET_PACK_FULL)
+    (got,), st, _ = run_3idx(torch, d, L, [C], 0, spec.nk)
+    assert st == B.DMET_OK
+    ref = oracle.embedded_3idx(L, C, spec.mesh, ck_norm=ck_norm)
+    assert rel_fro(got, ref) < TOL
+
+
+def test_transform_3idx_q_ranges_partition(torch):
+    spec = spec_of((2, 3, 1), 4, 6, 6)
+    L, (C,), _ = synth.make_problem(spec)
+    d = desc_of(spec)
+    (full,), _, _ = run_3idx(torch, d, L, [C], 0, spec.nk)
+    (a,), _, _ = run_3idx(torch, d, L, [C], 0, 2)
+    (b,), _, _ = run_3idx(torch, d, L, [C], 2, spec.nk)
+    assert np.array_equal(np.concatenate([a, b]), full)
+
+
+def test_host_buffers_match_device(torch):
+    spec = spec_of((2, 2, 1), 6, 10, 9)
+    L, (C,), _ = synth.make_problem(spec)
+    d = desc_of(spec)
+    (dev,), st1, _ = run_eri(torch, d, L, [C])
+    (host,), st2, _ = run_eri(torch, d, L, [C], host=True)
+    assert st1 == st2 == B.DMET_OK
+    assert np.array_equal(dev, host)
+
+
+def test_small_workspace_gives_same_result(torch):
+    spec = spec_of((3, 3, 1), 5, 12, 11)
+    L, (C,), _ = synth.make_problem(spec)
+    d = desc_of(spec)
+    (a,), _, _ = run_eri(torch, d, L, [C])
+    (b,), _, _ = run_eri(torch, d, L, [C], workspace_limit=1 << 20)
+    assert rel_fro(b, a) < 1e-14
+
+
+def test_not_orthonormal_is_reported(torch):
+    spec = spec_of((2, 2, 1), 4, 6, 5)
+    L, (C,), _ = synth.make_problem(spec)
+    C = C * 1.001
+    _, st, stats = run_eri(torch, desc_of(spec), L, [C])
+    assert st == B.DMET_ERR_NOT_ORTHONORMAL
+    assert stats[0] > 1e-4
+
+
+def test_complex_orbitals_violate_real_symmetry(torch):
+    spec = spec_of((3, 1, 1), 4, 6, 5)
+    L, (C,), _ = synth.make_problem(spec)
+    C = C * np.exp(0.3j)  # still orthonormal; no longer C^-k = conj C^k
+    _, st, stats = run_eri(torch, desc_of(spec), L, [C])
+    assert st == B.DMET_ERR_SYMMETRY
+    assert stats[1] > 1e-3
+
+
+def test_complex_real_space_integrals_violate_time_reversal(torch):
+    spec = spec_of((3, 1, 1), 4, 6, 5)
+    L, (C,), _ = synth.make_problem(spec)
+    L = L.copy()
+    # An antisymmetric (in mu, nu) change of L^{1,2} with its Hermitian partner kept in
+    # step: Hermiticity holds, time reversal (which needs L^{1,2} symmetric here) breaks.
+    m = np.random.default_rng(2).standard_normal(L[1, 2].shape)
+    L[1, 2] += 0.01 * (m - m.transpose(0, 2, 1))
+    L[2, 1] = np.conj(L[1, 2].transpose(0, 2, 1))
+    _, st, stats = run_eri(torch, desc_of(spec), L, [C])
+    assert st == B.DMET_ERR_SYMMETRY
+    assert stats[2] < 1e-12 and stats[3] > 1e-4
+
+
+def test_hbn_full_size_sampled(torch):
+    """The h-BN-shaped 6x6x1 workload (n_AO 26, n_aux 220, n_emb 104) at full size in the
+    launch configuration the benchmark times; the oracle computes every entry on a random
+    set of 16 orbitals (column subsets are exact), and every q of L^q for three q."""
+    spec = synth.CONFIGS["hbn_6x6x1"]
+    L, (C,), _ = synth.make_problem(spec)
+    (got,), st, stats = run_eri(torch, desc_of(spec), L, [C])
+    assert st == B.DMET_OK, stats
+    rng = np.random.default_rng(0)
+    S = np.sort(rng.choice(spec.n_emb, 16, replace=False))
+    Lq = oracle.embedded_3idx(L, C[:, :, S], spec.mesh)
+    i, j, k, l = np.meshgrid(*([np.arange(16)] * 4), indexing="ij")
+    idx = np.stack([i.ravel(), j.ravel(), k.ravel(), l.ravel()], 1)
+    ref = oracle.eri_entries(Lq, Lq, spec.mesh, idx).real
+    g = got[s8_index(*(S[idx.T]))]
+    assert rel_fro(g, ref) < TOL
+    assert np.abs(g - ref).max() < TOL * np.abs(ref).max()
+    qs = [0, 7, 21]
+    for q in qs:
+        (lq,), st, _ = run_3idx(torch, desc_of(spec), L, [C], q, q + 1)
+        assert st == B.DMET_OK
+        assert rel_fro(lq[0], oracle.embedded_3idx(L, C, spec.mesh, qs=[q])[0]) < TOL
