@@ -3,7 +3,7 @@
 With the embedding orbitals written in real space, orbital i = sum_{R, mu}
 Csc[(R, mu), i] phi_{mu R}, and aux functions in every cell R0 of the supercell,
 the density-fitted ERI of Eq. "density fitting" reads
-    X[(P, R0), i, j] = sum_{R1 mu R2 nu} Csc[(R1,mu), i] (P R0 | mu R1, nu R2) Csc[(R2,nu), j],
+    X[(P, R0), i, j] = sum_{R1 mu R2 nu} conj(Csc[(R1,mu), i]) (P R0 | mu R1, nu R2) Csc[(R2,nu), j],
     (ij|kl) = sum_{P, R0} X[(P,R0), i, j] X[(P,R0), k, l],
 where translation invariance gives (P R0 | mu R1, nu R2) = B[P, mu, R1 - R0, nu, R2 - R0].
 No k-points appear, so this pins the k-space method and all of its conventions.
@@ -18,7 +18,8 @@ def _cells(mesh):
 
 
 def supercell_eri(B, mesh, Csc_a, Csc_b=None):
-    """Real (ij|kl) [na, na, nb, nb] from B[P, mu, R1, nu, R2] and supercell orbitals."""
+    """(ij|kl) [na, na, nb, nb] from B[P, mu, R1, nu, R2] and supercell orbitals (real or
+    complex; the bra orbital of each pair is conjugated)."""
     Csc_b = Csc_a if Csc_b is None else Csc_b
     cells = _cells(mesh)
     nmesh = np.asarray(mesh)
@@ -30,8 +31,8 @@ def supercell_eri(B, mesh, Csc_a, Csc_b=None):
         shifted = (cells - r0) % nmesh
         src = (shifted[:, 0] * nmesh[1] + shifted[:, 1]) * nmesh[2] + shifted[:, 2]
         Bs = Bt[:, src][:, :, :, src].reshape(n_aux, nk * n_ao, nk * n_ao)
-        xa.append(np.matmul(Csc_a.T[None], np.matmul(Bs, Csc_a)))
-        xb.append(np.matmul(Csc_b.T[None], np.matmul(Bs, Csc_b)))
+        xa.append(np.matmul(Csc_a.conj().T[None], np.matmul(Bs, Csc_a)))
+        xb.append(np.matmul(Csc_b.conj().T[None], np.matmul(Bs, Csc_b)))
     xa = np.concatenate(xa, 0)
     xb = np.concatenate(xb, 0)
     return np.tensordot(xa, xb, axes=([0], [0]))

@@ -138,11 +138,11 @@ def make_L(spec: LatticeSpec, p_block: int = 64, out: np.ndarray | None = None) 
 
 
 def _orthonormalise(a: np.ndarray) -> np.ndarray:
-    """Householder QR; columns flipped so that diag(R) > 0."""
+    """Householder QR; column phases chosen so that diag(R) is real and positive."""
     q, r = np.linalg.qr(a)
-    s = np.sign(np.diag(r))
-    s[s == 0] = 1.0
-    return q * s[None, :]
+    d = np.diag(r)
+    s = np.where(np.abs(d) > 0, d / np.where(np.abs(d) > 0, np.abs(d), 1.0), 1.0)
+    return q * s.conj()[None, :]
 
 
 def supercell_orbitals(spec: LatticeSpec, spin: int = 0) -> np.ndarray:
@@ -158,6 +158,16 @@ def supercell_orbitals(spec: LatticeSpec, spin: int = 0) -> np.ndarray:
     a *= np.exp(-spec.decay * min_image_norm(spec.mesh))[:, None, None]
     if spec.c_log_range > 0:
         a *= 10.0 ** _rng(spec.seed + spin, _STREAM_SCALE).uniform(-spec.c_log_range, 0.0, (nk, na, n))
+    return _orthonormalise(a.reshape(nk * na, n))
+
+
+def complex_supercell_orbitals(spec: LatticeSpec, spin: int = 0) -> np.ndarray:
+    """Complex Csc[(R, mu), i], orthonormal over the supercell (entries (N(0,1) + i N(0,1)) *
+    exp(-a |R|), then QR). Their Bloch sums are orthonormal but not time-reversal symmetric."""
+    nk, na, n = spec.nk, spec.n_ao, spec.n_emb
+    g = _rng(spec.seed + spin, _STREAM_C + 7)
+    a = g.standard_normal((nk, na, n)) + 1j * g.standard_normal((nk, na, n))
+    a *= np.exp(-spec.decay * min_image_norm(spec.mesh))[:, None, None]
     return _orthonormalise(a.reshape(nk * na, n))
 
 

@@ -88,10 +88,7 @@ def test_eri_full_matches_oracle(torch, real):
     spec = spec_of((2, 3, 1), 3, 6, 5)
     L, (C,), _ = synth.make_problem(spec)
     if not real:
-        rng = np.random.default_rng(4)
-        for k in range(spec.nk):
-            q, _ = np.linalg.qr(rng.standard_normal((5, 5)) + 1j * rng.standard_normal((5, 5)))
-            C[k] = C[k] @ q
+        C = synth.bloch_orbitals(synth.complex_supercell_orbitals(spec), spec.mesh)
     sym = B.DMET_SYM_REAL if real else B.DMET_SYM_NONE
     (got,), st, _ = run_eri(torch, desc_of(spec, sym=sym, eri_pack=B.DMET_PACK_FULL), L, [C])
     assert st == B.DMET_OK
@@ -102,14 +99,8 @@ def test_eri_full_matches_oracle(torch, real):
 def test_eri_full_unrestricted_complex(torch):
     spec = spec_of((3, 1, 1), 4, 5, 4, n_spin=2)
     L = synth.make_L(spec)
-    rng = np.random.default_rng(9)
-    cs = []
-    for s, n in enumerate((4, 6)):
-        c = synth.bloch_orbitals(synth.supercell_orbitals(synth.spec_with(spec, n_emb=n), s), spec.mesh)
-        for k in range(spec.nk):
-            q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
-            c[k] = c[k] @ q
-        cs.append(c)
+    cs = [synth.bloch_orbitals(synth.complex_supercell_orbitals(synth.spec_with(spec, n_emb=n), s), spec.mesh)
+          for s, n in enumerate((4, 6))]
     d = desc_of(spec, n_emb=[4, 6], sym=B.DMET_SYM_NONE)
     (aa, ab, bb), st, _ = run_eri(torch, d, L, cs)
     assert st == B.DMET_OK

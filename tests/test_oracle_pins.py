@@ -48,6 +48,17 @@ def test_brute_force_supercell(mesh, ck_norm):
     assert np.abs(eri.imag).max() < 1e-12 * np.abs(ref).max()
 
 
+def test_brute_force_complex_orbitals():
+    spec = small_spec((3, 2, 1), n_emb=5)
+    B = synth.real_space_B(spec)
+    csc = synth.complex_supercell_orbitals(spec)
+    L = synth.fourier_L(B, spec.mesh)
+    eri = oracle.embedded_eri(L, synth.bloch_orbitals(csc, spec.mesh), spec.mesh)
+    ref = oracle.supercell_eri(B, spec.mesh, csc)
+    assert rel(eri, ref) < 1e-12
+    assert np.abs(ref.imag).max() > 1e-3 * np.abs(ref).max()
+
+
 def test_brute_force_unrestricted():
     spec = small_spec((2, 2, 1), n_emb=5)
     B = synth.real_space_B(spec)
@@ -96,13 +107,8 @@ def _problem(mesh=(2, 3, 1), n_emb=6, real=True, seed=11):
     spec = small_spec(mesh, n_ao=3, n_aux=6, n_emb=n_emb, seed=seed)
     L, (C,), (csc,) = synth.make_problem(spec)
     if not real:
-        # Complex orbitals: a k-dependent unitary rotation of each C^k breaks realness
-        # in real space but keeps orthonormality.
-        rng = np.random.default_rng(seed)
-        for k in range(C.shape[0]):
-            h = rng.standard_normal((n_emb, n_emb)) + 1j * rng.standard_normal((n_emb, n_emb))
-            q, _ = np.linalg.qr(h)
-            C[k] = C[k] @ q
+        # Complex real-space orbitals: orthonormal, not time-reversal symmetric.
+        C = synth.bloch_orbitals(synth.complex_supercell_orbitals(spec), spec.mesh)
     return spec, L, C
 
 
@@ -119,6 +125,7 @@ def test_permutational_symmetry(real):
         assert np.abs(eri - eri.transpose(0, 1, 3, 2)).max() < 1e-12 * s
     else:
         assert np.abs(eri.imag).max() > 1e-6 * s
+        assert oracle.orthonormality_error(C) < 1e-13
 
 
 @pytest.mark.parametrize("real", [True, False])
