@@ -8,9 +8,12 @@ packed ERI. Inputs are synthetic (seeded) with the h-BN-shaped sizes of section 
 
 Prints one JSON line. `value` is useful TFLOP/s (the symmetry-reduced algorithmic flop
 count of the work the library does) with inputs resident in HBM; `e2e` is the same metric
-through the C ABI with host buffers (copies inside the timed region).
+through the C ABI with host buffers (copies inside the timed region). The headline path is
+the split-BF16 tensor-core path; the plain FP64 path is measured in the same run and
+reported under "fp64", and both are compared with the FP64 oracle on an orbital subset.
 
     python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference] [--workload NAME]
+                    [--prec bf16x3|fp64] [--only]
 """
 from __future__ import annotations
 
@@ -34,6 +37,9 @@ METRIC = "embedded-ERI transform TFLOP/s and ms/problem at stated error vs FP64;
 SMS = 152
 DFMA_PER_SM_CLK = 2  # FP64 FMA lanes per SM per clock on GB300 (1.25 TFLOP/s nominal at 2.07 GHz)
 ORACLE_SAMPLE_ORBITALS = 24
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from the
+# ncu captures summarised under profiles/ (workload, path, kernel class) -> bytes.
+TRAFFIC = {}
 
 
 def useful_flops(spec, n_list, desc_sym=1):
@@ -166,13 +172,139 @@ def run_reference(args):
     return 0
 
 
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def s8_positions(S):
+    """Packed 8-fold indices of every (ij|kl) with i, j, k, l in the orbital subset S."""
+    i, j, k, l = np.meshgrid(*([np.arange(len(S))] * 4), indexing="ij")
+    ii, jj, kk, ll = S[i.ravel()], S[j.ravel()], S[k.ravel()], S[l.ravel()]
+    I, J = np.maximum(ii, jj), np.minimum(ii, jj)
+    K_, L_ = np.maximum(kk, ll), np.minimum(kk, ll)
+    a, b = I * (I + 1) // 2 + J, K_ * (K_ + 1) // 2 + L_
+    P, Q = np.maximum(a, b), np.minimum(a, b)
+    return P * (P + 1) // 2 + Q
+
+
+def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
+    """Times args.steps calls of dmet_emb_eri on resident inputs, then the end-to-end form."""
+    n_list = [spec.n_emb] * spec.n_spin
+    fl_total, fl_t, fl_c = useful_flops(spec, n_list)
+    stream = torch.cuda.current_stream()
+    pcode = dm.binding.DMET_PREC_FP64 if prec == "fp64" else dm.binding.DMET_PREC_BF16X3
+    desc = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, n_list, n_spin=spec.n_spin, prec=pcode)
+    nblk = 1 if spec.n_spin == 1 else 3
+    outs = [torch.empty(dm.dmet_emb_eri_bytes(desc, b) // 8, dtype=torch.float64, device="cuda") for b in range(nblk)]
+    plan = dm.dmet_emb_plan(desc, stream=stream.cuda_stream)
+
+    def step():
+        dm.dmet_emb_eri(plan, [Ld], [Cd], [outs])
+
+    for _ in range(args.warmup):
+        step()
+    st, stats = dm.dmet_emb_status(plan, 0)
+    if st != dm.binding.DMET_OK:
+        raise RuntimeError(f"device status {st}: {dm.dmet_emb_last_error()} {stats}")
+    steps = args.steps if prec != "fp64" else min(args.steps, args.fp64_steps)
+    dm.dmet_emb_profile(plan, True)
+    launches0 = dm.dmet_emb_launch_count(plan)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    launches = dm.dmet_emb_launch_count(plan) - launches0
+    kstats = [dm.dmet_emb_profile_read(plan, k) for k in range(dm.dmet_emb_profile_count())]
+    dm.dmet_emb_profile(plan, False)
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / steps
+    value = world * fl_total * steps / (ms_total / 1e3) / 1e12
+
+    peaks, peak_src = measured_peaks()
+    top = max(kstats, key=lambda k: k["ms"])
+    avg_ms = top["ms"] / max(top["launches"], 1)
+    if prec == "fp64":
+        peak = SMS * DFMA_PER_SM_CLK * 2 * 2070e6 / 1e12
+        achieved = top["flops"] / (top["ms"] / 1e3) / 1e12 if top["ms"] > 0 else 0.0
+        roof = {"bound": "alu", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": TRAFFIC.get((spec.name, prec, top["name"])),
+                "flops_counted": "algorithmic FP64 flops",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (FP64 runs on the CUDA cores)",
+                "avg_launch_ms": avg_ms}
+    else:
+        peak = peaks["bf16_tflops"]
+        achieved = top["exec_flops"] / (top["ms"] / 1e3) / 1e12 if top["ms"] > 0 else 0.0
+        roof = {"bound": "tensor", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": TRAFFIC.get((spec.name, prec, top["name"])),
+                "flops_counted": "executed BF16 tensor flops (6 slice products per useful multiply-add, whole tiles)",
+                "useful_achieved": top["flops"] / (top["ms"] / 1e3) / 1e12 if top["ms"] > 0 else 0.0,
+                "peak_source": f"{peak_src} bf16_tflops (burst; sustained {peaks.get('bf16_tflops_sustained')})",
+                "avg_launch_ms": avg_ms}
+    tot_ms = max(sum(x["ms"] for x in kstats), 1e-9)
+    kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["ms"], 3), "share": round(k["ms"] / tot_ms, 4)}
+               for k in kstats if k["launches"]}
+
+    # End to end through the C ABI with host buffers: H2D of L and C, D2H of the ERI.
+    Lh = torch.from_numpy(L).pin_memory()
+    Ch = [torch.from_numpy(c).pin_memory() for c in Cs]
+    Oh = [torch.empty(o.numel(), dtype=torch.float64).pin_memory() for o in outs]
+    dm.dmet_emb_eri(plan, [Lh], [Ch], [Oh])
+    torch.cuda.synchronize()
+    e2e_steps = args.e2e_steps if prec != "fp64" else 1
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dm.dmet_emb_eri(plan, [Lh], [Ch], [Oh])
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    st, stats = dm.dmet_emb_status(plan, 0)
+    same = all(torch.equal(o.cpu(), h) for o, h in zip(outs, Oh))
+    dm.dmet_emb_destroy(plan)
+    return {
+        "value": value, "ms_per_step": ms_step, "useful_tflop_per_problem": fl_total / 1e12,
+        "useful_split": {"transform": fl_t / 1e12, "contraction": fl_c / 1e12},
+        "roofline": roof, "kernels": kernels, "gpu_launches": int(launches), "clocks": clk, "steps": steps,
+        "e2e": {"value": world * fl_total / e2e_s / 1e12, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": int(Lh.numel() * 16 + sum(c.numel() * 16 for c in Ch)),
+                "d2h_bytes_per_step": int(sum(o.numel() * 8 for o in Oh)), "ms_per_step": e2e_s * 1e3,
+                "matches_device_result": bool(same)},
+        "device_checks": {"status": int(st), "orthonormality": stats[0], "realness": stats[1],
+                          "hermiticity_L": stats[2], "time_reversal_L": stats[3]},
+        "result": [o.cpu().numpy() for o in outs],
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="hbn_6x6x1")
+    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "fp64"],
+                    help="path of the headline number; the other path is measured alongside unless --only")
+    ap.add_argument("--only", action="store_true", help="measure the headline path only")
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -197,124 +329,54 @@ def main():
     # Weak scaling: every rank transforms its own problem (a different seed); no data exchange.
     spec = synth.spec_with(base, seed=base.seed + 17 * rank)
     L, Cs, _ = synth.make_problem(spec)
-    n_list = [spec.n_emb] * spec.n_spin
-    fl_total, fl_t, fl_c = useful_flops(spec, n_list)
-
-    stream = torch.cuda.current_stream()
-    desc = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, n_list, n_spin=spec.n_spin)
     Ld = torch.from_numpy(L).cuda()
     Cd = [torch.from_numpy(c).cuda() for c in Cs]
-    nblk = 1 if spec.n_spin == 1 else 3
-    outs = [torch.empty(dm.dmet_emb_eri_bytes(desc, b) // 8, dtype=torch.float64, device="cuda") for b in range(nblk)]
-    plan = dm.dmet_emb_plan(desc, stream=stream.cuda_stream)
 
-    def step():
-        dm.dmet_emb_eri(plan, [Ld], [Cd], [outs])
-
-    for _ in range(args.warmup):
-        step()
-    st, stats = dm.dmet_emb_status(plan, 0)
-    if st != dm.binding.DMET_OK:
-        raise RuntimeError(f"device status {st}: {dm.dmet_emb_last_error()} {stats}")
-
-    # Timed region: K steps, CUDA events on the launching stream, barrier + sync both sides.
-    dm.dmet_emb_profile(plan, True)
-    launches0 = dm.dmet_emb_launch_count(plan)
-    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
-    clocks.start()
-    time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    launches = dm.dmet_emb_launch_count(plan) - launches0
-    kstats = [dm.dmet_emb_profile_read(plan, k) for k in range(dm.dmet_emb_profile_count())]
-    dm.dmet_emb_profile(plan, False)
-    if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
-    value = world * fl_total * args.steps / (ms_total / 1e3) / 1e12
-
-    # Dominant kernel: the class with the most device time in the timed region.
-    top = max(kstats, key=lambda k: k["ms"])
-    peak_fp64 = SMS * DFMA_PER_SM_CLK * 2 * 2070e6 / 1e12
-    achieved = top["flops"] / (top["ms"] / 1e3) / 1e12 if top["ms"] > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": top["name"], "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-                "frac": achieved / peak_fp64, "traffic": None,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (FP64 runs on the CUDA cores)",
-                "avg_launch_ms": top["ms"] / max(top["launches"], 1)}
-    kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["ms"], 3),
-                           "share": round(k["ms"] / max(sum(x["ms"] for x in kstats), 1e-9), 4)}
-               for k in kstats if k["launches"]}
-
-    # End to end through the C ABI with host buffers: H2D of L and C, D2H of the ERI.
-    Lh = torch.from_numpy(L).pin_memory()
-    Ch = [torch.from_numpy(c).pin_memory() for c in Cs]
-    Oh = [torch.empty(o.numel(), dtype=torch.float64).pin_memory() for o in outs]
-    dm.dmet_emb_eri(plan, [Lh], [Ch], [Oh])  # warm the staging buffers
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        dm.dmet_emb_eri(plan, [Lh], [Ch], [Oh])
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    h2d = Lh.numel() * 16 + sum(c.numel() * 16 for c in Ch)
-    d2h = sum(o.numel() * 8 for o in Oh)
-    st, stats = dm.dmet_emb_status(plan, 0)
-    same = all(torch.equal(o.cpu(), h) for o, h in zip(outs, Oh))
+    precs = [args.prec] + ([] if args.only else [p for p in ("bf16x3", "fp64") if p != args.prec])
+    res = {p: measure(dm, torch, spec, L, Cs, Ld, Cd, p, args, dist, world, local) for p in precs}
+    head = res[args.prec]
 
     line = {
-        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "metric": METRIC, "value": head["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": head["steps"],
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "bf16x3", "data": "synthetic",
         "config": {"workload": spec.name, "mesh": list(spec.mesh), "n_ao": spec.n_ao, "n_aux": spec.n_aux,
-                   "n_emb": spec.n_emb, "n_spin": spec.n_spin, "prec": "fp64", "pack": "s8",
+                   "n_emb": spec.n_emb, "n_spin": spec.n_spin, "prec": args.prec, "pack": "s8",
                    "problems_per_step": world, "l2": f"inputs larger than L2 (L = {L.nbytes / 1e9:.2f} GB)"},
-        "ms_per_problem": ms_step,
-        "useful_tflop_per_problem": fl_total / 1e12,
-        "useful_split": {"transform": fl_t / 1e12, "contraction": fl_c / 1e12},
-        "roofline": roofline,
-        "kernels": kernels,
-        "gpu_launches": int(launches),
-        "clocks": clk,
-        "e2e": {"value": world * fl_total / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3, "matches_device_result": bool(same)},
-        "device_checks": {"status": int(st), "orthonormality": stats[0], "realness": stats[1],
-                          "hermiticity_L": stats[2], "time_reversal_L": stats[3]},
+        "ms_per_problem": head["ms_per_step"],
+        "useful_tflop_per_problem": head["useful_tflop_per_problem"],
+        "useful_split": head["useful_split"],
+        "roofline": head["roofline"],
+        "kernels": head["kernels"],
+        "gpu_launches": head["gpu_launches"],
+        "clocks": head["clocks"],
+        "e2e": head["e2e"],
+        "device_checks": head["device_checks"],
     }
+    for p in precs[1:]:
+        r = res[p]
+        line[p] = {k: r[k] for k in ("value", "ms_per_step", "roofline", "kernels", "gpu_launches", "clocks", "e2e")}
+        line[p]["dtype"] = "f64" if p == "fp64" else "bf16x3"
+    if "fp64" in res and "bf16x3" in res:
+        line["speedup_bf16x3_over_fp64"] = res["fp64"]["ms_per_step"] / res["bf16x3"]["ms_per_step"]
 
     if rank == 0 and not args.no_cpu_baseline:
         # CPU baseline: the oracle as it stands on a bounded sample (orbital subset) of this
-        # workload, also giving the error of the GPU result on that subset.
+        # workload, which also gives the error of each GPU result on that subset.
         dt, fl_s, S, eri_s = oracle_sample(spec, L, Cs[0], 32)
-        got = outs[0].cpu().numpy()
-        i, j, k, l = np.meshgrid(*([np.arange(len(S))] * 4), indexing="ij")
-        ii, jj, kk, ll = S[i.ravel()], S[j.ravel()], S[k.ravel()], S[l.ravel()]
-        I, J = np.maximum(ii, jj), np.minimum(ii, jj)
-        K_, L_ = np.maximum(kk, ll), np.minimum(kk, ll)
-        a, b = I * (I + 1) // 2 + J, K_ * (K_ + 1) // 2 + L_
-        P, Q = np.maximum(a, b), np.minimum(a, b)
-        g = got[P * (P + 1) // 2 + Q]
+        pos = s8_positions(S)
         ref = eri_s.real.ravel()
         line["cpu_baseline"] = {"value": fl_s / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
                                 "sample": f"Algorithm 1 (all q, all k1, dense contraction) on 32 of {spec.n_emb} "
                                           f"embedding orbitals; {dt:.1f} s; useful flops of that sub-problem"}
-        line["error_vs_fp64_oracle"] = {
-            "rel_fro": float(np.linalg.norm(g - ref) / np.linalg.norm(ref)),
-            "max_abs": float(np.abs(g - ref).max()), "max_abs_over_max": float(np.abs(g - ref).max() / np.abs(ref).max()),
-            "rms": float(np.sqrt(np.mean((g - ref) ** 2))), "sample": "all (ij|kl) on the 32-orbital subset"}
-    dm.dmet_emb_destroy(plan)
+        errs = {}
+        for p, r in res.items():
+            g = r["result"][0][pos]
+            errs[p] = {"rel_fro": float(np.linalg.norm(g - ref) / np.linalg.norm(ref)),
+                       "max_abs": float(np.abs(g - ref).max()),
+                       "max_abs_over_max": float(np.abs(g - ref).max() / np.abs(ref).max()),
+                       "rms": float(np.sqrt(np.mean((g - ref) ** 2)))}
+        line["error_vs_fp64_oracle"] = {"sample": "all (ij|kl) on a seeded 32-orbital subset", **errs}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -165,12 +165,15 @@ DMET_API dmet_status_t dmet_emb_schedule(const dmet_emb_desc_t* desc, int32_t* k
 DMET_API dmet_status_t dmet_emb_profile(dmet_emb_plan_t plan, int32_t enable);
 
 /* Reads the counters of kernel class `kernel` (0 .. dmet_emb_profile_count()-1): name,
- * launches, total device milliseconds, algorithmic flops and algorithmic bytes summed over
- * the recorded launches. Waits for the stream. */
+ * launches, total device milliseconds, algorithmic flops (the work the method needs, with
+ * the symmetry reductions applied; a complex multiply-add counts 8), executed flops (what
+ * the kernels issue: for the split-BF16 tensor-core kernels the 6 slice products over whole
+ * 128 x 128 tiles, otherwise equal to the algorithmic count) and algorithmic bytes, summed
+ * over the recorded launches. Waits for the stream. */
 DMET_API int32_t dmet_emb_profile_count(void);
 DMET_API dmet_status_t dmet_emb_profile_read(dmet_emb_plan_t plan, int32_t kernel, const char** name,
                                     int64_t* launches, double* total_ms, double* flops,
-                                    double* bytes);
+                                    double* exec_flops, double* bytes);
 
 /* Number of kernel launches the plan has queued since it was created. */
 DMET_API int64_t dmet_emb_launch_count(dmet_emb_plan_t plan);

@@ -111,7 +111,8 @@ def lib() -> ctypes.CDLL:
         L.dmet_emb_profile_count.restype = ctypes.c_int32
         L.dmet_emb_profile_read.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_char_p),
                                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
-                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double)]
         L.dmet_emb_profile_read.restype = st
         L.dmet_emb_launch_count.argtypes = [_P]
         L.dmet_emb_launch_count.restype = ctypes.c_int64
@@ -223,11 +224,11 @@ def dmet_emb_profile_count():
 def dmet_emb_profile_read(plan, kernel):
     name = ctypes.c_char_p()
     launches = ctypes.c_int64()
-    ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    ms, fl, ex, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(lib().dmet_emb_profile_read(_P(plan), kernel, ctypes.byref(name), ctypes.byref(launches),
-                                       ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(by)))
+                                       ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(ex), ctypes.byref(by)))
     return {"name": name.value.decode(), "launches": launches.value, "ms": ms.value, "flops": fl.value,
-            "bytes": by.value}
+            "exec_flops": ex.value, "bytes": by.value}
 
 
 def dmet_emb_launch_count(plan):

@@ -71,3 +71,38 @@ cudaError_t launch_l_check(const double2* L, const int* neg, int nk, int naux, i
                            cudaStream_t st);
 
 }  // namespace dmet
+
+// ---- tensor maps for the tcgen05 kernels (tc_launch.cu) ----
+#include <cuda.h>
+namespace dmet {
+// 3-D bf16 tensor map over [slices][rows][K] (K contiguous) with a (box_k, box_rows, 1) box,
+// swizzled to match the UMMA descriptors (box_k * 2 bytes = 64 or 128).
+cudaError_t make_tmap_bf16_3d(CUtensorMap* map, const void* base, unsigned long long k_elems,
+                              unsigned long long rows, unsigned long long slices, unsigned long long row_stride_elems,
+                              unsigned long long slice_stride_elems, int box_k, int box_rows);
+}  // namespace dmet
+
+// ---- split-BF16 path (mixed.cu) ----
+namespace dmet {
+namespace tc {
+struct TcJob;
+struct Segment;
+}
+int mixed_kblock();
+cudaError_t launch_split_L(const double2* L, const int4* t1, int e0, int E, int nk, int naux, int nao, int K1,
+                           void* Ls, long long sstride, cudaStream_t s);
+cudaError_t launch_build_Cb(const double2* C, int nk, int nao, int n, int K1, void* Cb, long long sstride,
+                            cudaStream_t s);
+cudaError_t launch_build_Cc(const double2* C, const int4* gather, const int4* t2, int b0, int nq, int nao, int n,
+                            int K2, void* Cc, long long sstride, cudaStream_t s);
+cudaError_t launch_pack_split(const double* ZT, int nq, int naux, int n, int nc, double sc, void* Xt,
+                              long long sstride, long long Rtot, long long row_base, cudaStream_t s);
+cudaError_t launch_tc_split_t(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+                              const tc::Segment* segs, void* out, long long sstride, long long K2, int nao, int nemb,
+                              unsigned int* err, cudaStream_t s);
+cudaError_t launch_tc_rect(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+                           const tc::Segment* segs, double* out, long long ldo, double scale, unsigned int* err,
+                           cudaStream_t s);
+cudaError_t launch_tc_packed(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+                             const tc::Segment* segs, double* out, double scale, unsigned int* err, cudaStream_t s);
+}  // namespace dmet

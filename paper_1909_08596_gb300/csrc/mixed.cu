@@ -1,0 +1,288 @@
+// Split-BF16 (mixed-precision) path of the embedded-ERI transformation: the operand
+// splitting kernels and the tcgen05 GEMM instantiations with their output functors.
+//
+// Every FP64 operand x is split into three bf16 slices x = x0 + x1 + x2 + O(2^-27 |x|),
+// each slice the round-to-nearest bf16 of what the previous ones left over (the error-free
+// splitting of Ozaki et al., applied per element). Complex products are written as real
+// GEMMs over interleaved (re, im) K indices; the orbital operands carry the signs.
+//
+// Step 1 (ket side):  T_e[(P,mu)][(j,p)] = sum_(nu,c) L_e[(P,mu)][(nu,c)] Cb^{k2}[(j,p)][(nu,c)]
+//   with Cb rows (j, re) = (Cr, -Ci), (j, im) = (Ci, Cr) over (nu, c), so T = L C^{k2}.
+// Step 2 (bra side + Fourier sum): Z_q[(P,j)][(i,p)] = sum_(r,mu,c) T[(P,j)][(r,mu,c)] Cc[(i,p)][(r,mu,c)]
+//   with Cc rows (i, re) = w_r (Cr, Ci), (i, im) = w_r (-Ci, Cr), so Z = sum_r w_r C^{k1_r +} T_r.
+// Contraction: X[(q,P,c)][IJ] = Re/Im of s (Z_ij + Z_ji); (ij|kl) = (1/Nk) sum w_q X^T X.
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "tc_gemm.cuh"
+
+namespace dmet {
+
+namespace {
+
+__device__ __forceinline__ void split3(double x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  a = __double2bfloat16(x);
+  double r = x - (double)__bfloat162float(a);
+  b = __double2bfloat16(r);
+  r -= (double)__bfloat162float(b);
+  c = __double2bfloat16(r);
+}
+
+inline int grid_for(long long total, int threads, int cap) {
+  long long g = (total + threads - 1) / threads;
+  if (g < 1) g = 1;
+  return (int)(g < cap ? g : cap);
+}
+
+// Ls[t][(e - e0) * naux * nao + P * nao + mu][col] for col < K1: L^{k1,k2}_{P, mu, nu}.(re|im)
+// at col = 2 nu + c, zero for col >= 2 nao.
+__global__ void split_L_kernel(const double* __restrict__ L, const int4* __restrict__ t1, int e0, int E, int nk,
+                               int naux, int nao, int K1, __nv_bfloat16* __restrict__ Ls, long long sstride) {
+  const long long rows_e = (long long)naux * nao;
+  const long long total = (long long)E * rows_e * K1;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+       x += (long long)gridDim.x * blockDim.x) {
+    const long long row = x / K1;
+    const int col = (int)(x % K1);
+    const int el = (int)(row / rows_e);
+    const long long rem = row % rows_e;
+    double v = 0.0;
+    if (col < 2 * nao) {
+      const long long pair = t1[e0 + el].y;  // k1 * nk + k2
+      v = L[(pair * rows_e + rem) * 2 * nao + col];
+    }
+    __nv_bfloat16 a, b, c;
+    split3(v, a, b, c);
+    Ls[x] = a;
+    Ls[x + sstride] = b;
+    Ls[x + 2 * sstride] = c;
+  }
+  (void)nk;
+}
+
+// Cb[t][k * 2n + 2j + p][col], col = 2 nu + c < 2 nao:
+//   p = 0: (Cr, -Ci)[c];  p = 1: (Ci, Cr)[c]   of C^k_{nu j}.
+__global__ void build_Cb_kernel(const double2* __restrict__ C, int nk, int nao, int n, int K1,
+                                __nv_bfloat16* __restrict__ Cb, long long sstride) {
+  const long long total = (long long)nk * 2 * n * K1;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+       x += (long long)gridDim.x * blockDim.x) {
+    const long long row = x / K1;
+    const int col = (int)(x % K1);
+    const int k = (int)(row / (2 * n));
+    const int jp = (int)(row % (2 * n));
+    const int j = jp >> 1, p = jp & 1;
+    double v = 0.0;
+    if (col < 2 * nao) {
+      const int nu = col >> 1, c = col & 1;
+      const double2 z = C[((long long)k * nao + nu) * n + j];
+      v = p == 0 ? (c == 0 ? z.x : -z.y) : (c == 0 ? z.y : z.x);
+    }
+    __nv_bfloat16 a, b, cc;
+    split3(v, a, b, cc);
+    Cb[x] = a;
+    Cb[x + sstride] = b;
+    Cb[x + 2 * sstride] = cc;
+  }
+}
+
+// Cc[t][slot * 2n + 2i + p][col], col = r * 2nao + 2 mu + c for r < nrep(slot):
+//   p = 0: w_r (Cr, Ci)[c];  p = 1: w_r (-Ci, Cr)[c]  of C^{k1_r}_{mu i}; zero elsewhere.
+__global__ void build_Cc_kernel(const double2* __restrict__ C, const int4* __restrict__ gather,
+                                const int4* __restrict__ t2, int b0, int nq, int nao, int n, int K2,
+                                __nv_bfloat16* __restrict__ Cc, long long sstride) {
+  const long long total = (long long)nq * 2 * n * K2;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+       x += (long long)gridDim.x * blockDim.x) {
+    const long long row = x / K2;
+    const int col = (int)(x % K2);
+    const int slot = (int)(row / (2 * n));
+    const int ip = (int)(row % (2 * n));
+    const int i = ip >> 1, p = ip & 1;
+    const int4 q = t2[b0 + slot];  // {start, start, slot, nrep * nao}
+    double v = 0.0;
+    if (col < 2 * q.w) {
+      const int r = col / (2 * nao);
+      const int mu = (col % (2 * nao)) >> 1, c = col & 1;
+      const int4 g = gather[q.x + r];  // {k1, half}
+      const double w = g.y ? 0.5 : 1.0;
+      const double2 z = C[((long long)g.x * nao + mu) * n + i];
+      v = w * (p == 0 ? (c == 0 ? z.x : z.y) : (c == 0 ? -z.y : z.x));
+    }
+    __nv_bfloat16 a, b, cc;
+    split3(v, a, b, cc);
+    Cc[x] = a;
+    Cc[x + sstride] = b;
+    Cc[x + 2 * sstride] = cc;
+  }
+}
+
+// Xt[t][IJ][row_base + (slot * naux + P) * nc + c] = split of s * (Z_ij + Z_ji).c for i >= j,
+// with Z_ij (complex) = ZT[slot][(P n + j) 2n + 2i + (re|im)].
+constexpr int PK_P = 16, PK_B = 8;
+__global__ void __launch_bounds__(256) pack_split_kernel(const double* __restrict__ ZT, int naux, int n, int nc,
+                                                         double s, __nv_bfloat16* __restrict__ Xt,
+                                                         long long sstride, long long Rtot, long long row_base) {
+  __shared__ double2 za[PK_P][PK_B][PK_B];
+  __shared__ double2 zb[PK_P][PK_B][PK_B];
+  // pair-block decode: lower triangle of ceil(n/8) blocks
+  const long long t = blockIdx.x;
+  long long bi = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (bi * (bi + 1) / 2 > t) --bi;
+  while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+  const int bj = (int)(t - bi * (bi + 1) / 2);
+  const int i0 = (int)bi * PK_B, j0 = bj * PK_B;
+  const int P0 = blockIdx.y * PK_P;
+  const int slot = blockIdx.z;
+  const double* z = ZT + (long long)slot * naux * n * 2 * n;
+  for (int e = threadIdx.x; e < PK_P * PK_B * PK_B; e += blockDim.x) {
+    const int pl = e / (PK_B * PK_B), a = (e / PK_B) % PK_B, b = e % PK_B;
+    const int P = P0 + pl;
+    // za[pl][ii][jj] = Z_{i j} with (ii, jj) = (b, a): consecutive e run over i for fixed j.
+    {
+      const int i = i0 + b, j = j0 + a;
+      double2 v = make_double2(0.0, 0.0);
+      if (P < naux && i < n && j < n) {
+        const double* p = z + ((long long)P * n + j) * 2 * n + 2 * i;
+        v = make_double2(p[0], p[1]);
+      }
+      za[pl][b][a] = v;
+    }
+    // zb[pl][ii][jj] = Z_{j i} with (ii, jj) = (a, b): consecutive e run over j for fixed i.
+    {
+      const int i = i0 + a, j = j0 + b;
+      double2 v = make_double2(0.0, 0.0);
+      if (P < naux && i < n && j < n) {
+        const double* p = z + ((long long)P * n + i) * 2 * n + 2 * j;
+        v = make_double2(p[0], p[1]);
+      }
+      zb[pl][a][b] = v;
+    }
+  }
+  __syncthreads();
+  const int nr = PK_P * nc;  // rows per pair in this block
+  for (int e = threadIdx.x; e < PK_B * PK_B * nr; e += blockDim.x) {
+    const int pr = e / nr, rl = e % nr;
+    const int ii = pr / PK_B, jj = pr % PK_B;
+    const int i = i0 + ii, j = j0 + jj;
+    const int pl = rl / nc, c = rl % nc;
+    const int P = P0 + pl;
+    if (i >= n || j > i || P >= naux) continue;
+    const double2 a = za[pl][ii][jj], b = zb[pl][ii][jj];
+    const double v = s * (c == 0 ? a.x + b.x : a.y + b.y);
+    const long long IJ = (long long)i * (i + 1) / 2 + j;
+    const long long idx = IJ * Rtot + row_base + ((long long)slot * naux + P) * nc + c;
+    __nv_bfloat16 x0, x1, x2;
+    split3(v, x0, x1, x2);
+    Xt[idx] = x0;
+    Xt[idx + sstride] = x1;
+    Xt[idx + 2 * sstride] = x2;
+  }
+}
+
+// Step-1 output functor: element (m = (P, mu) of entry e, n = (j, p)) -> bf16 slices of A2 at
+// row o2 + P * nemb + j, column o3 + 2 mu + p (o2 = slot * naux * nemb, o3 = r * 2 nao).
+struct EpiSplitT {
+  struct Params {
+    __nv_bfloat16* out;
+    long long sstride;
+    long long K2;
+    int nao, nemb;
+  };
+  static __device__ __forceinline__ void store(const Params& p, const tc::TcJob& j, int row, int col0,
+                                               const float* hi, const float* lo) {
+    const int m = j.o0 + row;
+    const int P = m / p.nao, mu = m % p.nao;
+    const long long rbase = (long long)j.o2 + (long long)P * p.nemb;
+    const long long cidx = (long long)j.o3 + 2 * mu;
+#pragma unroll
+    for (int c = 0; c < 64; c += 2) {
+      if (col0 + c >= j.n_valid) break;
+      const int jj = (j.o1 + col0 + c) >> 1;
+      const double re = (double)hi[c] + (double)lo[c];
+      const double im = (double)hi[c + 1] + (double)lo[c + 1];
+      __nv_bfloat16 r0, r1, r2, i0, i1, i2;
+      split3(re, r0, r1, r2);
+      split3(im, i0, i1, i2);
+      __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(p.out + (rbase + jj) * p.K2 + cidx);
+      o[0] = __halves2bfloat162(r0, i0);
+      o[p.sstride / 2] = __halves2bfloat162(r1, i1);
+      o[p.sstride] = __halves2bfloat162(r2, i2);
+    }
+  }
+};
+
+template <class EPI>
+cudaError_t launch_tc(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+                      const tc::Segment* segs, const typename EPI::Params& ep, unsigned int* err, cudaStream_t s) {
+  using Cfg = tc::TcCfg<3, 64>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tc::tc_gemm_kernel<3, 64, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (njobs <= 0) return cudaSuccess;
+  tc::tc_gemm_kernel<3, 64, EPI><<<njobs, tc::kThreads, Cfg::SMEM, s>>>(A, B, jobs, segs, ep, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int mixed_kblock() { return tc::TcCfg<3, 64>::BK; }
+
+cudaError_t launch_split_L(const double2* L, const int4* t1, int e0, int E, int nk, int naux, int nao, int K1,
+                           void* Ls, long long sstride, cudaStream_t s) {
+  const long long total = (long long)E * naux * nao * K1;
+  split_L_kernel<<<grid_for(total, 256, 152 * 32), 256, 0, s>>>((const double*)L, t1, e0, E, nk, naux, nao, K1,
+                                                               (__nv_bfloat16*)Ls, sstride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_Cb(const double2* C, int nk, int nao, int n, int K1, void* Cb, long long sstride,
+                            cudaStream_t s) {
+  const long long total = (long long)nk * 2 * n * K1;
+  build_Cb_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, s>>>(C, nk, nao, n, K1, (__nv_bfloat16*)Cb, sstride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_Cc(const double2* C, const int4* gather, const int4* t2, int b0, int nq, int nao, int n,
+                            int K2, void* Cc, long long sstride, cudaStream_t s) {
+  const long long total = (long long)nq * 2 * n * K2;
+  build_Cc_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, s>>>(C, gather, t2, b0, nq, nao, n, K2,
+                                                                (__nv_bfloat16*)Cc, sstride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_split(const double* ZT, int nq, int naux, int n, int nc, double sc, void* Xt,
+                              long long sstride, long long Rtot, long long row_base, cudaStream_t s) {
+  const long long nb = (n + PK_B - 1) / PK_B;
+  const dim3 grid((unsigned)(nb * (nb + 1) / 2), (naux + PK_P - 1) / PK_P, nq);
+  pack_split_kernel<<<grid, 256, 0, s>>>(ZT, naux, n, nc, sc, (__nv_bfloat16*)Xt, sstride, Rtot, row_base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_split_t(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+                              const tc::Segment* segs, void* out, long long sstride, long long K2, int nao, int nemb,
+                              unsigned int* err, cudaStream_t s) {
+  EpiSplitT::Params p{(__nv_bfloat16*)out, sstride, K2, nao, nemb};
+  return launch_tc<EpiSplitT>(A, B, jobs, njobs, segs, p, err, s);
+}
+
+cudaError_t launch_tc_rect(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+                           const tc::Segment* segs, double* out, long long ldo, double scale, unsigned int* err,
+                           cudaStream_t s) {
+  tc::EpiRect::Params p{out, ldo, scale};
+  return launch_tc<tc::EpiRect>(A, B, jobs, njobs, segs, p, err, s);
+}
+
+cudaError_t launch_tc_packed(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+                             const tc::Segment* segs, double* out, double scale, unsigned int* err, cudaStream_t s) {
+  tc::EpiPacked::Params p{out, scale};
+  return launch_tc<tc::EpiPacked>(A, B, jobs, njobs, segs, p, err, s);
+}
+
+}  // namespace dmet

@@ -14,6 +14,7 @@
 
 #include "../../include/dmet_emb.h"
 #include "internal.h"
+#include "tc_gemm.cuh"
 
 using namespace dmet;
 
@@ -53,11 +54,18 @@ enum KernelClass {
   KC_CONTRACT,
   KC_CONTRACT_FULL,
   KC_COPY,
+  KC_SPLIT,
+  KC_TC_TRANSFORM_1,
+  KC_TC_TRANSFORM_2,
+  KC_TC_PACK,
+  KC_TC_CONTRACT,
   KC_COUNT
 };
-const char* const kKcNames[KC_COUNT] = {"check_orbitals", "check_L",          "gather_orbitals",
-                                        "half_transform_1", "half_transform_2", "pack_pairs",
-                                        "contract_s8",     "contract_full",    "host_copy"};
+const char* const kKcNames[KC_COUNT] = {"check_orbitals",      "check_L",          "gather_orbitals",
+                                        "half_transform_1",    "half_transform_2", "pack_pairs",
+                                        "contract_s8",         "contract_full",    "host_copy",
+                                        "split_bf16x3",        "tc_half_transform_1", "tc_half_transform_2",
+                                        "tc_pack_split",       "tc_contract"};
 
 // ------------------------------------------------------------------------------------------
 // Scheduler: momentum-conserving pairs (k1, k1 + q), negation, q weights and the
@@ -155,6 +163,23 @@ struct Block {
   int b0, b1, w;  // slots [b0, b1) of an ordering, contraction weight
 };
 
+// Split-BF16 path: tables built at plan time (they depend on shapes only).
+struct MixedPlan {
+  int K1 = 0, K2 = 0, kseg = 128;
+  long long Rtot = 0, R1 = 0;
+  std::vector<Block> blocks;           // contraction order, q-blocks within one weight class
+  std::vector<long long> row_base;     // first contraction row of each block
+  std::vector<tc::TcJob> jobs;         // all job tables
+  std::vector<tc::Segment> segs;       // all segment lists
+  // offsets (first, count) into jobs: step 1 / step 2 per block and spin; contraction per block kind
+  std::vector<int> j1_off[2], j1_cnt[2], j2_off[2], j2_cnt[2];
+  int jc_off[3] = {0, 0, 0}, jc_cnt[3] = {0, 0, 0};
+  tc::TcJob* d_jobs = nullptr;
+  tc::Segment* d_segs = nullptr;
+  long long Ls_rows = 0, A2_rows[2] = {0, 0};
+  double useful_t1 = 0, useful_t2 = 0, useful_c = 0;  // per call, all spins
+};
+
 struct Prob {
   dmet_emb_desc_t d;
   Sched s;
@@ -167,11 +192,13 @@ struct Prob {
   std::vector<Block> con_blocks;
   int bq = 1;          // q slots per block
   int* d_neg = nullptr;
+  bool mixed = false;
+  MixedPlan mx;
 };
 
 struct KStat {
   long long launches = 0;
-  double flops = 0, bytes = 0;
+  double flops = 0, bytes = 0, exec = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
 };
 
@@ -191,6 +218,15 @@ struct dmet_emb_plan_s {
   double2* lq_all[2] = {nullptr, nullptr};
   size_t crep_b = 0, T_b = 0, Z_b = 0, S_b = 0, X_b[2] = {0, 0}, lq_all_b[2] = {0, 0};
   double* dstats = nullptr;  // [n_problems][8]
+  // split-BF16 workspace (shared by all problems of the plan)
+  void* Ls = nullptr;
+  void* Cb[2] = {nullptr, nullptr};
+  void* Cc = nullptr;
+  void* A2 = nullptr;
+  double* ZT = nullptr;
+  void* Xt[2] = {nullptr, nullptr};
+  size_t Ls_b = 0, Cb_b[2] = {0, 0}, Cc_b = 0, A2_b = 0, ZT_b = 0, Xt_b[2] = {0, 0};
+  unsigned int* derr = nullptr;
   // staging of host buffers
   void* stage_in = nullptr;
   size_t stage_in_b = 0;
@@ -246,7 +282,11 @@ dmet_status_t validate_desc(const dmet_emb_desc_t& d, int idx) {
   if (d.check_l != 0 && d.check_l != 1) return fail(DMET_ERR_INVALID_ARG, "problem %d: check_l = %d", idx, d.check_l);
   if (d.reserved != 0) return fail(DMET_ERR_INVALID_ARG, "problem %d: reserved field must be 0", idx);
   if (d.prec != DMET_PREC_FP64 && d.prec != DMET_PREC_BF16X3) return fail(DMET_ERR_INVALID_ARG, "problem %d: prec = %d", idx, d.prec);
-  if (d.prec != DMET_PREC_FP64) return fail(DMET_ERR_UNSUPPORTED, "problem %d: precision %d not built", idx, d.prec);
+  if (d.prec == DMET_PREC_BF16X3) {
+    const int pack = d.eri_pack == DMET_PACK_AUTO ? (d.sym == DMET_SYM_REAL ? DMET_PACK_S8 : DMET_PACK_FULL) : d.eri_pack;
+    if (d.sym != DMET_SYM_REAL || pack != DMET_PACK_S8)
+      return fail(DMET_ERR_UNSUPPORTED, "problem %d: the split-BF16 path needs sym = REAL and 8-fold packing", idx);
+  }
   const long long nmax = std::max(d.n_emb[0], d.n_spin == 2 ? d.n_emb[1] : 0);
   if ((long long)d.n_aux * nmax > INT_MAX / 2 || (long long)d.n_aux * d.n_ao > INT_MAX / 2)
     return fail(DMET_ERR_UNSUPPORTED, "problem %d: n_aux*n too large for one launch", idx);
@@ -285,10 +325,11 @@ struct Timed {
   dmet_emb_plan_s* P;
   int kc;
   cudaEvent_t a = nullptr, b = nullptr;
-  Timed(dmet_emb_plan_s* p, int k, double flops, double bytes, int nlaunch = 1) : P(p), kc(k) {
+  Timed(dmet_emb_plan_s* p, int k, double flops, double bytes, int nlaunch = 1, double exec = -1.0) : P(p), kc(k) {
     P->ks[kc].launches += nlaunch;
     P->ks[kc].flops += flops;
     P->ks[kc].bytes += bytes;
+    P->ks[kc].exec += exec < 0 ? flops : exec;
     if (kc != KC_COPY) P->launches += nlaunch;
     if (P->prof) {
       a = get_event(P);
@@ -586,6 +627,17 @@ void destroy_plan(dmet_emb_plan_s* P) {
     free_tables(pr.nat);
     free_tables(pr.con);
     cudaFree(pr.d_neg);
+    cudaFree(pr.mx.d_jobs);
+    cudaFree(pr.mx.d_segs);
+  }
+  cudaFree(P->Ls);
+  cudaFree(P->Cc);
+  cudaFree(P->A2);
+  cudaFree(P->ZT);
+  cudaFree(P->derr);
+  for (int s = 0; s < 2; ++s) {
+    cudaFree(P->Cb[s]);
+    cudaFree(P->Xt[s]);
   }
   cudaFree(P->crep);
   cudaFree(P->T);
@@ -609,6 +661,247 @@ void destroy_plan(dmet_emb_plan_s* P) {
 }
 
 }  // namespace
+
+// ------------------------------------------------------------------------------------------
+// Split-BF16 path (tcgen05). Shapes and tables are fixed at plan time; see mixed.cu for the
+// kernels and the real-GEMM form of each complex product.
+
+struct MixedMaps {
+  CUtensorMap Ls, Cb[2], Cc[2], A2[2], Xt[2];
+};
+
+long long padk(long long x) {
+  const long long bk = mixed_kblock();
+  return (x + bk - 1) / bk * bk;
+}
+
+void build_mixed(Prob& pr) {
+  MixedPlan& m = pr.mx;
+  const int BK = mixed_kblock();
+  const int nk = pr.nk, nao = pr.nao, naux = pr.naux;
+  m.K1 = (int)padk(2LL * nao);
+  int nrep_max = 1;
+  for (int q : pr.con.order) nrep_max = std::max(nrep_max, pr.s.nrep[q]);
+  m.K2 = (int)padk(2LL * nrep_max * nao);
+  m.blocks = pr.con_blocks;
+  int n1 = 0, n2 = 0;
+  for (int q : pr.con.order) (pr.s.qw[q] == 1 ? n1 : n2)++;
+  m.R1 = padk((long long)n1 * naux);
+  m.Rtot = m.R1 + padk((long long)n2 * 2 * naux);
+  m.row_base.clear();
+  for (const Block& b : m.blocks)
+    m.row_base.push_back(b.w == 1 ? (long long)b.b0 * naux : m.R1 + (long long)(b.b0 - n1) * 2 * naux);
+  m.segs.clear();
+  m.jobs.clear();
+  // segment 0: the single K range of step 1
+  m.segs.push_back({0, m.K1 / BK, 1.0f, 0});
+  // step 2: per contraction slot, chunks of kseg over its K
+  const int nslots = (int)pr.con.order.size();
+  std::vector<int> s2_off(nslots), s2_cnt(nslots);
+  for (int i = 0; i < nslots; ++i) {
+    const long long K = padk(2LL * pr.s.nrep[pr.con.order[i]] * nao);
+    s2_off[i] = (int)m.segs.size();
+    for (long long k0 = 0; k0 < K; k0 += m.kseg)
+      m.segs.push_back({(int)k0, (int)((std::min<long long>(K - k0, m.kseg)) / BK), 1.0f, 0});
+    s2_cnt[i] = (int)m.segs.size() - s2_off[i];
+  }
+  // contraction: class 1 (weight 1) rows [0, R1), class 2 (weight 2) rows [R1, Rtot)
+  const int sc_off = (int)m.segs.size();
+  for (long long k0 = 0; k0 < m.R1; k0 += m.kseg)
+    m.segs.push_back({(int)k0, (int)(std::min<long long>(m.R1 - k0, m.kseg) / BK), 1.0f, 0});
+  for (long long k0 = m.R1; k0 < m.Rtot; k0 += m.kseg)
+    m.segs.push_back({(int)k0, (int)(std::min<long long>(m.Rtot - k0, m.kseg) / BK), 2.0f, 0});
+  const int sc_cnt = (int)m.segs.size() - sc_off;
+
+  auto cdiv = [](long long a, long long b) { return (int)((a + b - 1) / b); };
+  const int T = tc::kTile;
+  m.Ls_rows = 0;
+  for (int sp = 0; sp < pr.nspin; ++sp) {
+    const int n = pr.n[sp];
+    m.j1_off[sp].clear();
+    m.j1_cnt[sp].clear();
+    m.j2_off[sp].clear();
+    m.j2_cnt[sp].clear();
+    for (const Block& bl : m.blocks) {
+      const int e0 = pr.con.start[bl.b0];
+      m.Ls_rows = std::max(m.Ls_rows, (long long)(pr.con.start[bl.b1] - e0) * naux * nao);
+      m.j1_off[sp].push_back((int)m.jobs.size());
+      for (int slot = bl.b0; slot < bl.b1; ++slot)
+        for (int e = pr.con.start[slot]; e < pr.con.start[slot + 1]; ++e) {
+          const int r = e - pr.con.start[slot], el = e - e0, k2 = pr.con.t1[e].x;
+          for (int mt = 0; mt < cdiv((long long)naux * nao, T); ++mt)
+            for (int nt = 0; nt < cdiv(2LL * n, T); ++nt)
+              m.jobs.push_back({el * naux * nao + mt * T, k2 * 2 * n + nt * T,
+                                (int)std::min<long long>(T, (long long)naux * nao - mt * T),
+                                (int)std::min<long long>(T, 2LL * n - nt * T), 0, 1, mt * T, nt * T,
+                                (slot - bl.b0) * naux * n, r * 2 * nao});
+        }
+      m.j1_cnt[sp].push_back((int)m.jobs.size() - m.j1_off[sp].back());
+      m.j2_off[sp].push_back((int)m.jobs.size());
+      for (int slot = bl.b0; slot < bl.b1; ++slot) {
+        const int sl = slot - bl.b0;
+        for (int mt = 0; mt < cdiv((long long)naux * n, T); ++mt)
+          for (int nt = 0; nt < cdiv(2LL * n, T); ++nt)
+            m.jobs.push_back({sl * naux * n + mt * T, sl * 2 * n + nt * T,
+                              (int)std::min<long long>(T, (long long)naux * n - mt * T),
+                              (int)std::min<long long>(T, 2LL * n - nt * T), s2_off[slot], s2_cnt[slot],
+                              sl * naux * n + mt * T, nt * T, 0, 0});
+      }
+      m.j2_cnt[sp].push_back((int)m.jobs.size() - m.j2_off[sp].back());
+    }
+    m.A2_rows[sp] = (long long)pr.bq * naux * n;
+  }
+  for (int blk = 0; blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
+    const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
+    const long long pa = pr.npair[sa], pb = pr.npair[sb];
+    m.jc_off[blk] = (int)m.jobs.size();
+    for (int mt = 0; mt < cdiv(pa, T); ++mt)
+      for (int nt = 0; nt < cdiv(pb, T); ++nt) {
+        if (blk != 1 && nt > mt) continue;
+        m.jobs.push_back({mt * T, nt * T, (int)std::min<long long>(T, pa - mt * T),
+                          (int)std::min<long long>(T, pb - nt * T), sc_off, sc_cnt, mt * T, nt * T, 0, 0});
+      }
+    m.jc_cnt[blk] = (int)m.jobs.size() - m.jc_off[blk];
+  }
+  // useful flops of one call (the same count as the FP64 path)
+  m.useful_t1 = m.useful_t2 = m.useful_c = 0;
+  long long K = 0;
+  for (int q : pr.con.order) K += (long long)naux * (pr.s.qw[q] == 1 ? 1 : 2);
+  for (int sp = 0; sp < pr.nspin; ++sp) {
+    const double n = pr.n[sp];
+    for (int q : pr.con.order) {
+      m.useful_t1 += 8.0 * n * naux * nao * nao * pr.s.nrep[q];
+      m.useful_t2 += 8.0 * n * naux * n * nao * pr.s.nrep[q];
+    }
+    m.useful_c += (double)pr.npair[sp] * (pr.npair[sp] + 1.0) * K;
+  }
+  if (pr.nspin == 2) m.useful_c += 2.0 * pr.npair[0] * pr.npair[1] * K;
+  (void)nk;
+}
+
+// Tensor flops a job range issues: 6 slice products of 128 x 128 x K tiles.
+double exec_flops(const MixedPlan& m, int off, int cnt) {
+  double f = 0;
+  for (int i = off; i < off + cnt; ++i) {
+    const tc::TcJob& j = m.jobs[i];
+    long long k = 0;
+    for (int g = j.seg0; g < j.seg0 + j.nseg; ++g) k += (long long)m.segs[g].nkb * mixed_kblock();
+    f += 6.0 * 2.0 * tc::kTile * tc::kTile * (double)k;
+  }
+  return f;
+}
+
+struct MixedWs {
+  size_t Ls, Cb[2], Cc, A2, ZT, Xt[2];
+};
+
+MixedWs mixed_ws(const Prob& pr) {
+  const MixedPlan& m = pr.mx;
+  const long long nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
+  MixedWs w;
+  w.Ls = (size_t)3 * m.Ls_rows * m.K1 * 2;
+  for (int s = 0; s < 2; ++s) {
+    w.Cb[s] = s < pr.nspin ? (size_t)3 * pr.nk * 2 * pr.n[s] * m.K1 * 2 : 0;
+    w.Xt[s] = s < pr.nspin ? (size_t)3 * pr.npair[s] * m.Rtot * 2 : 0;
+  }
+  w.Cc = (size_t)3 * pr.bq * 2 * nmax * m.K2 * 2;
+  w.A2 = (size_t)3 * pr.bq * pr.naux * nmax * m.K2 * 2;
+  w.ZT = (size_t)pr.bq * pr.naux * nmax * 2 * nmax * 8;
+  return w;
+}
+
+size_t mixed_total(const MixedWs& w) { return w.Ls + w.Cb[0] + w.Cb[1] + w.Cc + w.A2 + w.ZT + w.Xt[0] + w.Xt[1]; }
+
+dmet_status_t mixed_maps(dmet_emb_plan_s* P, const Prob& pr, MixedMaps& mm) {
+  const MixedPlan& m = pr.mx;
+  const int BK = mixed_kblock(), T = tc::kTile;
+  const long long nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
+  const long long cc_rows = (long long)pr.bq * 2 * nmax, a2_rows = (long long)pr.bq * pr.naux * nmax;
+  CK(make_tmap_bf16_3d(&mm.Ls, P->Ls, m.K1, m.Ls_rows, 3, m.K1, m.Ls_rows * m.K1, BK, T));
+  for (int s = 0; s < pr.nspin; ++s) {
+    const long long n = pr.n[s];
+    CK(make_tmap_bf16_3d(&mm.Cb[s], P->Cb[s], m.K1, pr.nk * 2 * n, 3, m.K1, pr.nk * 2 * n * m.K1, BK, T));
+    CK(make_tmap_bf16_3d(&mm.Cc[s], P->Cc, m.K2, (long long)pr.bq * 2 * n, 3, m.K2, cc_rows * m.K2, BK, T));
+    CK(make_tmap_bf16_3d(&mm.A2[s], P->A2, m.K2, (long long)pr.bq * pr.naux * n, 3, m.K2, a2_rows * m.K2, BK, T));
+    CK(make_tmap_bf16_3d(&mm.Xt[s], P->Xt[s], m.Rtot, pr.npair[s], 3, m.Rtot, pr.npair[s] * m.Rtot, BK, T));
+  }
+  return DMET_OK;
+}
+
+dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, void* const* out) {
+  MixedPlan& m = pr.mx;
+  MixedMaps mm;
+  TRY(mixed_maps(P, pr, mm));
+  const long long nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
+  const long long cc_rows = (long long)pr.bq * 2 * nmax, a2_rows = (long long)pr.bq * pr.naux * nmax;
+  int n1 = 0;
+  for (int q : pr.con.order) n1 += pr.s.qw[q] == 1;
+  const long long used1 = (long long)n1 * pr.naux, used2 = ((long long)pr.con.order.size() - n1) * 2 * pr.naux;
+  for (int s = 0; s < pr.nspin; ++s) {
+    // padding rows of the contraction operand read as zeros
+    const size_t pitch = (size_t)m.Rtot * 2;
+    const long long h = 3 * pr.npair[s];
+    if (m.R1 > used1)
+      CK(cudaMemset2DAsync((char*)P->Xt[s] + used1 * 2, pitch, 0, (size_t)(m.R1 - used1) * 2, h, P->stream));
+    if (m.Rtot - m.R1 > used2)
+      CK(cudaMemset2DAsync((char*)P->Xt[s] + (m.R1 + used2) * 2, pitch, 0, (size_t)(m.Rtot - m.R1 - used2) * 2, h,
+                           P->stream));
+    Timed t(P, KC_SPLIT, 0.0, 16.0 * pr.nk * pr.nao * pr.n[s] + 6.0 * pr.nk * 2 * pr.n[s] * m.K1);
+    CK(launch_build_Cb(C[s], pr.nk, pr.nao, pr.n[s], m.K1, P->Cb[s], (long long)pr.nk * 2 * pr.n[s] * m.K1,
+                       P->stream));
+  }
+  for (size_t bi = 0; bi < m.blocks.size(); ++bi) {
+    const Block& bl = m.blocks[bi];
+    const int e0 = pr.con.start[bl.b0], E = pr.con.start[bl.b1] - e0, nq = bl.b1 - bl.b0;
+    {
+      const double rows = (double)E * pr.naux * pr.nao;
+      Timed t(P, KC_SPLIT, 0.0, rows * (16.0 * pr.nao + 6.0 * m.K1));
+      CK(launch_split_L(L, pr.con.d_t1, e0, E, pr.nk, pr.naux, pr.nao, m.K1, P->Ls, m.Ls_rows * m.K1, P->stream));
+    }
+    for (int s = 0; s < pr.nspin; ++s) {
+      const int n = pr.n[s];
+      {
+        Timed t(P, KC_SPLIT, 0.0, 6.0 * nq * 2 * n * m.K2);
+        CK(launch_build_Cc(C[s], pr.con.d_gather, pr.con.d_t2, bl.b0, nq, pr.nao, n, m.K2, P->Cc, cc_rows * m.K2,
+                           P->stream));
+      }
+      {
+        Timed t(P, KC_TC_TRANSFORM_1, 8.0 * n * (double)pr.naux * pr.nao * pr.nao * E, 0.0, 1,
+                exec_flops(m, m.j1_off[s][bi], m.j1_cnt[s][bi]));
+        CK(launch_tc_split_t(mm.Ls, mm.Cb[s], m.d_jobs + m.j1_off[s][bi], m.j1_cnt[s][bi], m.d_segs, P->A2,
+                             a2_rows * m.K2, m.K2, pr.nao, n, P->derr, P->stream));
+      }
+      {
+        double fl = 0;
+        for (int i = bl.b0; i < bl.b1; ++i) fl += 8.0 * n * (double)pr.naux * n * pr.con.t2[i].w;
+        Timed t(P, KC_TC_TRANSFORM_2, fl, 0.0, 1, exec_flops(m, m.j2_off[s][bi], m.j2_cnt[s][bi]));
+        CK(launch_tc_rect(mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs, P->ZT, 2LL * n,
+                          1.0, P->derr, P->stream));
+      }
+      {
+        const int nc = bl.w == 1 ? 1 : 2;
+        Timed t(P, KC_TC_PACK, 0.0, 16.0 * nq * pr.naux * (double)n * n + 6.0 * nq * pr.naux * nc * pr.npair[s]);
+        CK(launch_pack_split(P->ZT, nq, pr.naux, n, nc, pr.lq_scale, P->Xt[s], pr.npair[s] * m.Rtot, m.Rtot,
+                             m.row_base[bi], P->stream));
+      }
+    }
+  }
+  long long K = 0;
+  for (int q : pr.con.order) K += (long long)pr.naux * (pr.s.qw[q] == 1 ? 1 : 2);
+  for (int blk = 0; blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
+    const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
+    const double fl = blk == 1 ? 2.0 * pr.npair[0] * (double)pr.npair[1] * K
+                               : (double)pr.npair[sa] * (pr.npair[sa] + 1.0) * K;
+    Timed t(P, KC_TC_CONTRACT, fl, 0.0, 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk]));
+    if (blk == 1)
+      CK(launch_tc_rect(mm.Xt[0], mm.Xt[1], m.d_jobs + m.jc_off[1], m.jc_cnt[1], m.d_segs, (double*)out[1],
+                        pr.npair[1], 1.0 / pr.nk, P->derr, P->stream));
+    else
+      CK(launch_tc_packed(mm.Xt[sa], mm.Xt[sa], m.d_jobs + m.jc_off[blk], m.jc_cnt[blk], m.d_segs, (double*)out[blk],
+                          1.0 / pr.nk, P->derr, P->stream));
+  }
+  return DMET_OK;
+}
 
 // ==========================================================================================
 // C ABI
@@ -663,6 +956,8 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
   P->probs.resize(n_problems);
   WsSizes need;
   std::memset(&need, 0, sizeof(need));
+  MixedWs mneed;
+  std::memset(&mneed, 0, sizeof(mneed));
   for (int p = 0; p < n_problems; ++p) {
     Prob& pr = P->probs[p];
     pr.d = descs[p];
@@ -694,15 +989,39 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
       build_tables(pr.s, con, pr.nao, pr.con);
     }
     // q-block size: the largest (<= 8, entries per launch <= 65535) whose workspace fits.
+    pr.mixed = pr.d.prec == DMET_PREC_BF16X3;
+    auto total_for = [&](int b) {
+      size_t t = ws_for(pr, b).total();
+      if (pr.mixed) {
+        pr.bq = b;
+        partition(pr, pr.con, wts, b, pr.con_blocks);
+        build_mixed(pr);
+        t += mixed_total(mixed_ws(pr));
+      }
+      return t;
+    };
     int bq = 8;
-    while (bq > 1 && (ws_for(pr, bq).total() > P->ws_limit || max_entries(pr.nat, bq) > 65535)) --bq;
-    WsSizes w = ws_for(pr, bq);
-    if (w.total() > P->ws_limit) {
+    while (bq > 1 && (total_for(bq) > P->ws_limit || max_entries(pr.nat, bq) > 65535)) --bq;
+    const size_t tot = total_for(bq);
+    if (tot > P->ws_limit) {
       destroy_plan(P);
-      return fail(DMET_ERR_OOM, "problem %d needs %zu bytes of workspace (limit %zu)", p, w.total(), P->ws_limit);
+      return fail(DMET_ERR_OOM, "problem %d needs %zu bytes of workspace (limit %zu)", p, tot, P->ws_limit);
     }
+    WsSizes w = ws_for(pr, bq);
     pr.bq = bq;
     if (pr.pack == DMET_PACK_S8) partition(pr, pr.con, wts, bq, pr.con_blocks);
+    if (pr.mixed) {
+      build_mixed(pr);
+      const MixedWs mw = mixed_ws(pr);
+      mneed.Ls = std::max(mneed.Ls, mw.Ls);
+      mneed.Cc = std::max(mneed.Cc, mw.Cc);
+      mneed.A2 = std::max(mneed.A2, mw.A2);
+      mneed.ZT = std::max(mneed.ZT, mw.ZT);
+      for (int s = 0; s < 2; ++s) {
+        mneed.Cb[s] = std::max(mneed.Cb[s], mw.Cb[s]);
+        mneed.Xt[s] = std::max(mneed.Xt[s], mw.Xt[s]);
+      }
+    }
     need.crep = std::max(need.crep, w.crep);
     need.T = std::max(need.T, w.T);
     need.Z = std::max(need.Z, w.Z);
@@ -724,6 +1043,24 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     alloc((void**)&P->X[s], &P->X_b[s], need.X[s]);
     alloc((void**)&P->lq_all[s], &P->lq_all_b[s], need.lq_all[s]);
   }
+  alloc(&P->Ls, &P->Ls_b, mneed.Ls);
+  alloc(&P->Cc, &P->Cc_b, mneed.Cc);
+  alloc(&P->A2, &P->A2_b, mneed.A2);
+  alloc((void**)&P->ZT, &P->ZT_b, mneed.ZT);
+  for (int s = 0; s < 2; ++s) {
+    alloc(&P->Cb[s], &P->Cb_b[s], mneed.Cb[s]);
+    alloc(&P->Xt[s], &P->Xt_b[s], mneed.Xt[s]);
+  }
+  // The split-BF16 operands are read in whole K blocks: whatever a call does not write
+  // must hold finite values, so they start at zero.
+  if (st == DMET_OK && P->A2 && cudaMemset(P->A2, 0, P->A2_b) != cudaSuccess) st = fail(DMET_ERR_CUDA, "memset");
+  for (int s = 0; s < 2; ++s)
+    if (st == DMET_OK && P->Xt[s] && cudaMemset(P->Xt[s], 0, P->Xt_b[s]) != cudaSuccess) st = fail(DMET_ERR_CUDA, "memset");
+  if (st == DMET_OK && cudaMalloc(&P->derr, sizeof(unsigned int)) != cudaSuccess) {
+    cudaGetLastError();
+    st = fail(DMET_ERR_OOM, "error word allocation failed");
+  }
+  if (st == DMET_OK && cudaMemset(P->derr, 0, sizeof(unsigned int)) != cudaSuccess) st = fail(DMET_ERR_CUDA, "memset");
   if (st == DMET_OK && cudaMalloc(&P->dstats, sizeof(double) * 8 * n_problems) != cudaSuccess) {
     cudaGetLastError();
     st = fail(DMET_ERR_OOM, "stats allocation failed");
@@ -734,6 +1071,17 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     Prob& pr = P->probs[p];
     st = upload_tables(pr.nat);
     if (st == DMET_OK && pr.pack == DMET_PACK_S8) st = upload_tables(pr.con);
+    if (st == DMET_OK && pr.mixed) {
+      MixedPlan& m = pr.mx;
+      if (cudaMalloc(&m.d_jobs, m.jobs.size() * sizeof(tc::TcJob)) != cudaSuccess ||
+          cudaMalloc(&m.d_segs, m.segs.size() * sizeof(tc::Segment)) != cudaSuccess ||
+          cudaMemcpy(m.d_jobs, m.jobs.data(), m.jobs.size() * sizeof(tc::TcJob), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(m.d_segs, m.segs.data(), m.segs.size() * sizeof(tc::Segment), cudaMemcpyHostToDevice) !=
+              cudaSuccess) {
+        cudaGetLastError();
+        st = fail(DMET_ERR_CUDA, "job table upload failed");
+      }
+    }
     if (st == DMET_OK) {
       if (cudaMalloc(&pr.d_neg, sizeof(int) * pr.nk) != cudaSuccess ||
           cudaMemcpy(pr.d_neg, pr.s.neg.data(), sizeof(int) * pr.nk, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -891,7 +1239,8 @@ dmet_status_t dmet_emb_eri(dmet_emb_plan_t P, const void* const* L, const void* 
         }
     }
     for (int b = 0; b < nblk; ++b) CK(cudaMemsetAsync(out[b], 0, ob[b], P->stream));
-    if (pr.pack == DMET_PACK_S8) TRY(eri_s8(P, pr, Ld, Cd, out));
+    if (pr.mixed) TRY(eri_mixed(P, pr, Ld, Cd, out));
+    else if (pr.pack == DMET_PACK_S8) TRY(eri_s8(P, pr, Ld, Cd, out));
     else TRY(eri_full(P, pr, Ld, Cd, out));
     if (need) {
       for (int b = 0; b < nblk; ++b)
@@ -925,6 +1274,9 @@ dmet_status_t dmet_emb_status(dmet_emb_plan_t P, int32_t problem, double* stats)
     stats[2] = herm;
     stats[3] = tr;
   }
+  unsigned int werr = 0;
+  if (P->derr) CK(cudaMemcpy(&werr, P->derr, sizeof(werr), cudaMemcpyDeviceToHost));
+  if (werr) return fail(DMET_ERR_TIMEOUT, "a bounded device wait expired (flags 0x%x)", werr);
   if (!(h[0] <= pr.d.ortho_tol))
     return fail(DMET_ERR_NOT_ORTHONORMAL, "problem %d: orthonormality error %.3e > %.3e", problem, h[0], pr.d.ortho_tol);
   if (real && !(rc <= pr.d.sym_tol))
@@ -948,13 +1300,14 @@ dmet_status_t dmet_emb_profile(dmet_emb_plan_t P, int32_t enable) {
     k.launches = 0;
     k.flops = 0;
     k.bytes = 0;
+    k.exec = 0;
   }
   P->prof = enable != 0;
   return DMET_OK;
 }
 
 dmet_status_t dmet_emb_profile_read(dmet_emb_plan_t P, int32_t kernel, const char** name, int64_t* launches,
-                                    double* total_ms, double* flops, double* bytes) {
+                                    double* total_ms, double* flops, double* exec_flops, double* bytes) {
   g_err.clear();
   if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
   if (kernel < 0 || kernel >= KC_COUNT) return fail(DMET_ERR_INVALID_ARG, "kernel %d", kernel);
@@ -970,6 +1323,7 @@ dmet_status_t dmet_emb_profile_read(dmet_emb_plan_t P, int32_t kernel, const cha
   if (launches) *launches = k.launches;
   if (total_ms) *total_ms = ms;
   if (flops) *flops = k.flops;
+  if (exec_flops) *exec_flops = k.exec;
   if (bytes) *bytes = k.bytes;
   return DMET_OK;
 }

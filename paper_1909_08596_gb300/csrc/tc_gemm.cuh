@@ -1,0 +1,280 @@
+// Split-BF16 GEMM on the 5th-generation tensor cores (tcgen05, TMEM accumulators, TMA).
+//
+//   result(m, n) = sum_g w_g * sum_{k in segment g} A(a_row0 + m, k) B(b_row0 + n, k)
+//
+// A and B are given as NSLICE bf16 slices, A = A_0 + A_1 + A_2 (K-major, [slice][row][K]).
+// With three slices every product A_s B_t with s + t <= 2 is issued (6 products; the
+// dropped terms are ~2^-24 relative). The leading product A_0 B_0 accumulates into its own
+// FP32 TMEM accumulator and the five smaller ones into a second: the tensor cores add each
+// MMA's result into the accumulator with an error of the accumulator's own magnitude, so
+// mixing the small correction terms into the leading sum would multiply the number of lossy
+// additions it suffers by six. That error still grows with the number of MMAs a segment
+// accumulates, so segments are short (a few K blocks); the epilogue warps add each
+// segment's result, times its exact power-of-two weight w_g, into an unevaluated sum of two
+// FP32 numbers (hi + lo, updated with the error-free TwoSum), which carries ~44 bits across
+// segments at FP32-pipe cost, and hand hi + lo to the output functor once at the end.
+//
+// One CTA computes one 128 x 128 tile of one job (jobs come from a table):
+//   warp 0      TMA producer (one thread): 3+3 slice tiles per K block into a stage ring;
+//   warp 1      MMA issuer (one thread), also allocates / frees all 512 TMEM columns
+//               (two buffers of two 128-column accumulators, so the epilogue of segment g
+//               overlaps the MMAs of segment g+1);
+//   warps 2..9  epilogue: warp w reads TMEM lanes 32*(w%4).. and half (w-2)/4 of the columns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tc_common.cuh"
+
+namespace dmet {
+namespace tc {
+
+struct Segment {
+  int k0;    // first K element (a multiple of the K block)
+  int nkb;   // number of K blocks
+  float w;   // weight of this segment (a power of two, so the scaling is exact)
+  int pad;
+};
+
+// One output tile: rows [a_row0, a_row0 + 128) of A against rows [b_row0, b_row0 + 128) of B,
+// of which m_valid x n_valid are stored; segments [seg0, seg0 + nseg).
+struct TcJob {
+  int a_row0, b_row0;
+  int m_valid, n_valid;
+  int seg0, nseg;
+  int o0, o1, o2, o3;  // output-functor parameters (tile origin in the output's own indexing)
+};
+
+constexpr int kTile = 128;
+constexpr int kThreads = 320;
+constexpr int kTmemCols = 512;
+
+template <int NSLICE, int ROWB>
+struct TcCfg {
+  static constexpr int BK = ROWB / 2;                          // bf16 elements per K block
+  static constexpr int TILE_BYTES = kTile * ROWB;              // one slice tile
+  static constexpr int STAGE_BYTES = 2 * NSLICE * TILE_BYTES;  // A and B slices
+  static constexpr int STAGES = (192 * 1024) / STAGE_BYTES > 6 ? 6 : (192 * 1024) / STAGE_BYTES;
+  static constexpr int NPROD = NSLICE == 3 ? 6 : 1;
+  static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 256;
+};
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bv = s - hi;
+  const float e = (hi - (s - bv)) + (x - bv);
+  hi = s;
+  lo += e;
+}
+
+// EPI::store(params, job, row, col0, hi, lo): row = tile-local row (< 128), columns col0 .. col0+63.
+template <int NSLICE, int ROWB, class EPI>
+__global__ void __maxnreg__(200)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const TcJob* __restrict__ jobs, const Segment* __restrict__ segs, const typename EPI::Params ep,
+                   unsigned int* err) {
+  using Cfg = TcCfg<NSLICE, ROWB>;
+  constexpr int S = Cfg::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* tiles = smem;
+  uint64_t* bars = (uint64_t*)(smem + S * Cfg::STAGE_BYTES);
+  // bars: full[S], empty[S], accf[2], acce[2], done; then the TMEM address and a counter.
+  volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 2 * S + 5);
+  volatile int* consumed = (volatile int*)(bars + 2 * S + 5) + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TcJob job = jobs[blockIdx.x];
+
+  auto full = [&](int s) { return smem_u32(bars + s); };
+  auto empty = [&](int s) { return smem_u32(bars + S + s); };
+  auto accf = [&](int b) { return smem_u32(bars + 2 * S + b); };
+  auto acce = [&](int b) { return smem_u32(bars + 2 * S + 2 + b); };
+  const uint32_t done_bar = smem_u32(bars + 2 * S + 4);
+  auto a_tile = [&](int s, int t) { return smem_u32(tiles + s * Cfg::STAGE_BYTES + t * Cfg::TILE_BYTES); };
+  auto b_tile = [&](int s, int t) {
+    return smem_u32(tiles + s * Cfg::STAGE_BYTES + (NSLICE + t) * Cfg::TILE_BYTES);
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf(b), 1);
+      mbar_init(acce(b), 8);
+    }
+    mbar_init(done_bar, 1);
+    *consumed = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(bars + 2 * S + 5), kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int issued = 0;
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+    bool ok = true;
+    for (int g = 0; g < job.nseg && ok; ++g) {
+      const Segment sg = segs[job.seg0 + g];
+      for (int kb = 0; kb < sg.nkb; ++kb) {
+        const int s = issued % S, ph = (issued / S) & 1;
+        if (!mbar_wait(empty(s), ph ^ 1, err, 1u)) {
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(full(s), Cfg::STAGE_BYTES);
+        const int k = sg.k0 + kb * Cfg::BK;
+#pragma unroll
+        for (int t = 0; t < NSLICE; ++t) {
+          tma_load_3d(a_tile(s, t), &tmA, full(s), k, job.a_row0, t);
+          tma_load_3d(b_tile(s, t), &tmB, full(s), k, job.b_row0, t);
+        }
+        ++issued;
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t idesc = idesc_bf16_f32(kTile, kTile);
+    constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
+    constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
+    int it = 0;
+    bool ok = true;
+    for (int g = 0; g < job.nseg && ok; ++g) {
+      const int b = g & 1, u = g >> 1;
+      if (!mbar_wait(acce(b), (u & 1) ^ 1, err, 2u)) break;
+      tc_fence_after();
+      const uint32_t d_main = tmem + b * 2 * kTile, d_corr = d_main + kTile;
+      const int nkb = segs[job.seg0 + g].nkb;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = it % S, ph = (it / S) & 1;
+        if (!mbar_wait(full(s), ph, err, 4u)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int kk = 0; kk < Cfg::BK / 16; ++kk) {
+#pragma unroll
+          for (int p = 0; p < Cfg::NPROD; ++p) {
+            const uint64_t ad = smem_desc<ROWB>(a_tile(s, pa[p]) + kk * 32);
+            const uint64_t bd = smem_desc<ROWB>(b_tile(s, pb[p]) + kk * 32);
+            if (p == 0) umma_bf16(d_main, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+            else umma_bf16(d_corr, ad, bd, idesc, ((kb | kk) != 0 || p > 1) ? 1u : 0u);
+          }
+        }
+        umma_commit(empty(s));
+        ++it;
+        *consumed = it;
+      }
+      if (ok) umma_commit(accf(b));
+    }
+    // Every MMA issued above must be complete before the accumulators are released.
+    umma_commit(done_bar);
+    mbar_wait(done_bar, 0, err, 16u);
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int quad = warp & 3, half = (warp - 2) >> 2;
+    const int row = quad * 32 + lane;
+    float hi[64], lo[64];
+#pragma unroll
+    for (int c = 0; c < 64; ++c) {
+      hi[c] = 0.f;
+      lo[c] = 0.f;
+    }
+    bool ok = true;
+    for (int g = 0; g < job.nseg; ++g) {
+      const int b = g & 1, u = g >> 1;
+      if (!mbar_wait(accf(b), u & 1, err, 8u)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const float w = segs[job.seg0 + g].w;
+      const uint32_t tm_main = tmem + ((uint32_t)(quad * 32) << 16) + b * 2 * kTile + half * 64;
+#pragma unroll
+      for (int ch = 0; ch < 4; ++ch) {
+        uint32_t v[16];
+        tmem_ld_32x32b_x16(tm_main + ch * 16, v);
+        tmem_ld_wait();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) two_sum_acc(hi[ch * 16 + c], lo[ch * 16 + c], w * __uint_as_float(v[c]));
+        if (NSLICE == 3) {
+          // The correction sum is ~2^-8 of the leading one: it joins the low word.
+          tmem_ld_32x32b_x16(tm_main + kTile + ch * 16, v);
+          tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < 16; ++c) lo[ch * 16 + c] += w * __uint_as_float(v[c]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce(b));
+    }
+    if (ok && row < job.m_valid) EPI::store(ep, job, row, half * 64, hi, lo);
+  }
+  __syncthreads();
+  if (warp == 0 && lane == 0) {
+    // Copies issued but never consumed (only after an expired wait) must land before exit.
+    for (int i = *consumed; i < issued; ++i) mbar_wait(full(i % S), (i / S) & 1, err, 32u);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ---------------- output functors ----------------
+
+// Lower triangle of a symmetric result, 8-fold packed: element (m, n), m >= n, at
+// m(m+1)/2 + n, m = o0 + row, n = o1 + col. Value = scale * (hi + lo).
+struct EpiPacked {
+  struct Params {
+    double* out;
+    double scale;
+  };
+  static __device__ __forceinline__ void store(const Params& p, const TcJob& j, int row, int col0, const float* hi,
+                                               const float* lo) {
+    const long long m = (long long)j.o0 + row;
+    double* o = p.out + m * (m + 1) / 2;
+#pragma unroll
+    for (int c = 0; c < 64; ++c) {
+      const int cc = col0 + c;
+      const long long n = (long long)j.o1 + cc;
+      if (cc < j.n_valid && n <= m) o[n] = p.scale * ((double)hi[c] + (double)lo[c]);
+    }
+  }
+};
+
+// Rectangular: out[(o0 + row) * ldo + o1 + col] = scale * (hi + lo).
+struct EpiRect {
+  struct Params {
+    double* out;
+    long long ldo;
+    double scale;
+  };
+  static __device__ __forceinline__ void store(const Params& p, const TcJob& j, int row, int col0, const float* hi,
+                                               const float* lo) {
+    double* o = p.out + ((long long)j.o0 + row) * p.ldo + j.o1;
+#pragma unroll
+    for (int c = 0; c < 64; ++c) {
+      const int cc = col0 + c;
+      if (cc < j.n_valid) o[cc] = p.scale * ((double)hi[c] + (double)lo[c]);
+    }
+  }
+};
+
+}  // namespace tc
+}  // namespace dmet
