@@ -220,8 +220,13 @@ cudaError_t launch_tc(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJo
   using Cfg = tc::TcCfg<3, 64>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc::tc_gemm_kernel<3, 64, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg::SMEM);
+    // The register split inside the kernel assumes exactly kLaunchRegs registers per thread at
+    // launch; with fewer, setmaxnreg.inc could never be satisfied, so refuse to launch.
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, tc::tc_gemm_kernel<3, 64, EPI>);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs != tc::kLaunchRegs) return cudaErrorInvalidKernelImage;
+    e = cudaFuncSetAttribute(tc::tc_gemm_kernel<3, 64, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }

@@ -14,12 +14,18 @@
 // FP32 numbers (hi + lo, updated with the error-free TwoSum), which carries ~44 bits across
 // segments at FP32-pipe cost, and hand hi + lo to the output functor once at the end.
 //
-// One CTA computes one 128 x 128 tile of one job (jobs come from a table):
+// One CTA of 12 warps computes one 128 x 128 tile of one job (jobs come from a table):
 //   warp 0      TMA producer (one thread): 3+3 slice tiles per K block into a stage ring;
 //   warp 1      MMA issuer (one thread), also allocates / frees all 512 TMEM columns
 //               (two buffers of two 128-column accumulators, so the epilogue of segment g
 //               overlaps the MMAs of segment g+1);
-//   warps 2..9  epilogue: warp w reads TMEM lanes 32*(w%4).. and half (w-2)/4 of the columns.
+//   warps 2, 3  idle (they complete the first warpgroup);
+//   warps 4..11 epilogue: warp w reads TMEM lanes 32*(w%4).. and half (w-4)/4 of the columns.
+// Registers: the CTA launches with kLaunchRegs per thread; the first warpgroup gives most of
+// its registers back (setmaxnreg.dec to kCtrlRegs) and the two epilogue warpgroups take them
+// (setmaxnreg.inc to kEpiRegs), which the two-float sums of 64 columns per thread need:
+// 128 * kCtrlRegs + 256 * kEpiRegs = 384 * kLaunchRegs, and per SM sub-partition (one warp of
+// each warpgroup) kCtrlRegs + 2 * kEpiRegs <= 512.
 #pragma once
 
 #include <cuda.h>
@@ -48,8 +54,13 @@ struct TcJob {
 };
 
 constexpr int kTile = 128;
-constexpr int kThreads = 320;
+constexpr int kThreads = 384;
 constexpr int kTmemCols = 512;
+constexpr int kLaunchRegs = 168;
+constexpr int kCtrlRegs = 56;
+constexpr int kEpiRegs = 224;
+static_assert(128 * kCtrlRegs + 256 * kEpiRegs == kThreads * kLaunchRegs, "register split must match the launch");
+static_assert(kCtrlRegs + 2 * kEpiRegs <= 512, "per sub-partition register file");
 
 template <int NSLICE, int ROWB>
 struct TcCfg {
@@ -71,7 +82,7 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
 
 // EPI::store(params, job, row, col0, hi, lo): row = tile-local row (< 128), columns col0 .. col0+63.
 template <int NSLICE, int ROWB, class EPI>
-__global__ void __maxnreg__(200)
+__global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcJob* __restrict__ jobs, const Segment* __restrict__ segs, const typename EPI::Params ep,
                    unsigned int* err) {
@@ -121,71 +132,75 @@ __global__ void __maxnreg__(200)
   const uint32_t tmem = *tmem_slot;
 
   int issued = 0;
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer ----------------
-    prefetch_tmap(&tmA);
-    prefetch_tmap(&tmB);
-    bool ok = true;
-    for (int g = 0; g < job.nseg && ok; ++g) {
-      const Segment sg = segs[job.seg0 + g];
-      for (int kb = 0; kb < sg.nkb; ++kb) {
-        const int s = issued % S, ph = (issued / S) & 1;
-        if (!mbar_wait(empty(s), ph ^ 1, err, 1u)) {
-          ok = false;
-          break;
-        }
-        mbar_arrive_expect_tx(full(s), Cfg::STAGE_BYTES);
-        const int k = sg.k0 + kb * Cfg::BK;
-#pragma unroll
-        for (int t = 0; t < NSLICE; ++t) {
-          tma_load_3d(a_tile(s, t), &tmA, full(s), k, job.a_row0, t);
-          tma_load_3d(b_tile(s, t), &tmB, full(s), k, job.b_row0, t);
-        }
-        ++issued;
-      }
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer ----------------
-    constexpr uint32_t idesc = idesc_bf16_f32(kTile, kTile);
-    constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
-    constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
-    int it = 0;
-    bool ok = true;
-    for (int g = 0; g < job.nseg && ok; ++g) {
-      const int b = g & 1, u = g >> 1;
-      if (!mbar_wait(acce(b), (u & 1) ^ 1, err, 2u)) break;
-      tc_fence_after();
-      const uint32_t d_main = tmem + b * 2 * kTile, d_corr = d_main + kTile;
-      const int nkb = segs[job.seg0 + g].nkb;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = it % S, ph = (it / S) & 1;
-        if (!mbar_wait(full(s), ph, err, 4u)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-#pragma unroll
-        for (int kk = 0; kk < Cfg::BK / 16; ++kk) {
-#pragma unroll
-          for (int p = 0; p < Cfg::NPROD; ++p) {
-            const uint64_t ad = smem_desc<ROWB>(a_tile(s, pa[p]) + kk * 32);
-            const uint64_t bd = smem_desc<ROWB>(b_tile(s, pb[p]) + kk * 32);
-            if (p == 0) umma_bf16(d_main, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
-            else umma_bf16(d_corr, ad, bd, idesc, ((kb | kk) != 0 || p > 1) ? 1u : 0u);
+  if (warp < 4) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kCtrlRegs));
+    if (warp == 0 && lane == 0) {
+      // ---------------- TMA producer ----------------
+      prefetch_tmap(&tmA);
+      prefetch_tmap(&tmB);
+      bool ok = true;
+      for (int g = 0; g < job.nseg && ok; ++g) {
+        const Segment sg = segs[job.seg0 + g];
+        for (int kb = 0; kb < sg.nkb; ++kb) {
+          const int s = issued % S, ph = (issued / S) & 1;
+          if (!mbar_wait(empty(s), ph ^ 1, err, 1u)) {
+            ok = false;
+            break;
           }
+          mbar_arrive_expect_tx(full(s), Cfg::STAGE_BYTES);
+          const int k = sg.k0 + kb * Cfg::BK;
+#pragma unroll
+          for (int t = 0; t < NSLICE; ++t) {
+            tma_load_3d(a_tile(s, t), &tmA, full(s), k, job.a_row0, t);
+            tma_load_3d(b_tile(s, t), &tmB, full(s), k, job.b_row0, t);
+          }
+          ++issued;
         }
-        umma_commit(empty(s));
-        ++it;
-        *consumed = it;
       }
-      if (ok) umma_commit(accf(b));
+    } else if (warp == 1 && lane == 0) {
+      // ---------------- MMA issuer ----------------
+      constexpr uint32_t idesc = idesc_bf16_f32(kTile, kTile);
+      constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
+      constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
+      int it = 0;
+      bool ok = true;
+      for (int g = 0; g < job.nseg && ok; ++g) {
+        const int b = g & 1, u = g >> 1;
+        if (!mbar_wait(acce(b), (u & 1) ^ 1, err, 2u)) break;
+        tc_fence_after();
+        const uint32_t d_main = tmem + b * 2 * kTile, d_corr = d_main + kTile;
+        const int nkb = segs[job.seg0 + g].nkb;
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int s = it % S, ph = (it / S) & 1;
+          if (!mbar_wait(full(s), ph, err, 4u)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < Cfg::BK / 16; ++kk) {
+#pragma unroll
+            for (int p = 0; p < Cfg::NPROD; ++p) {
+              const uint64_t ad = smem_desc<ROWB>(a_tile(s, pa[p]) + kk * 32);
+              const uint64_t bd = smem_desc<ROWB>(b_tile(s, pb[p]) + kk * 32);
+              if (p == 0) umma_bf16(d_main, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+              else umma_bf16(d_corr, ad, bd, idesc, ((kb | kk) != 0 || p > 1) ? 1u : 0u);
+            }
+          }
+          umma_commit(empty(s));
+          ++it;
+          *consumed = it;
+        }
+        if (ok) umma_commit(accf(b));
+      }
+      // Every MMA issued above must be complete before the accumulators are released.
+      umma_commit(done_bar);
+      mbar_wait(done_bar, 0, err, 16u);
     }
-    // Every MMA issued above must be complete before the accumulators are released.
-    umma_commit(done_bar);
-    mbar_wait(done_bar, 0, err, 16u);
-  } else if (warp >= 2) {
+  } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kEpiRegs));
     // ---------------- epilogue ----------------
-    const int quad = warp & 3, half = (warp - 2) >> 2;
+    const int quad = warp & 3, half = (warp - 4) >> 2;
     const int row = quad * 32 + lane;
     float hi[64], lo[64];
 #pragma unroll
