@@ -140,7 +140,10 @@ DMET_API dmet_status_t dmet_emb_eri(dmet_emb_plan_t plan, const void* const* L, 
 /* Waits for the plan's stream and returns the device status of `problem`. If stats is not
  * NULL it receives 4 doubles: [0] orthonormality error max|s_O sum_k C^k+C^k - 1| (worst
  * spin), [1] relative realness error max|C^{-k} - conj C^k| / max|C|, [2] relative
- * Hermiticity error of L, [3] relative time-reversal error of L (negative = not checked). */
+ * Hermiticity error of L and [3] relative time-reversal error of L, both as the largest
+ * real or imaginary component of the difference over the largest component of L
+ * (negative = not checked). A bounded device wait that expired is reported as
+ * DMET_ERR_TIMEOUT. */
 DMET_API dmet_status_t dmet_emb_status(dmet_emb_plan_t plan, int32_t problem, double* stats);
 
 /* Frees the plan's device memory, events and tables. Safe on NULL. Waits for the stream. */

@@ -276,14 +276,21 @@ __device__ __forceinline__ void block_max_commit(double v, double* out) {
   __syncthreads();
 }
 
-__global__ void orth_reduce_kernel(const double2* __restrict__ S, int n, double s, double* stat) {
+// S = s * sum_g S_g (ng split-K partial products of C^+ C); stat = max |S_ij - delta_ij|.
+__global__ void orth_reduce_kernel(const double2* __restrict__ Sg, int ng, int n, double s, double* stat) {
   double v = 0.0;
   const long long nn = (long long)n * n;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < nn;
        x += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(x / n), j = (int)(x % n);
-    const double2 e = S[x];
-    const double re = s * e.x - (i == j ? 1.0 : 0.0), im = s * e.y;
+    double re = 0.0, im = 0.0;
+    for (int g = 0; g < ng; ++g) {
+      const double2 e = Sg[g * nn + x];
+      re += e.x;
+      im += e.y;
+    }
+    re = s * re - (i == j ? 1.0 : 0.0);
+    im = s * im;
     v = wmax(v, sqrt(re * re + im * im));
   }
   block_max_commit(v, stat);
@@ -305,29 +312,67 @@ __global__ void c_real_check_kernel(const double2* __restrict__ C, const int* __
   block_max_commit(mv, stats + 2);
 }
 
-__global__ void l_check_kernel(const double2* __restrict__ L, const int* __restrict__ neg, int nk, int naux,
-                               int nao, double* stats) {
-  double hv = 0.0, tv = 0.0, mv = 0.0;
-  const long long blk = (long long)nao * nao, pair = blk * naux, total = pair * nk * nk;
-  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
-       x += (long long)gridDim.x * blockDim.x) {
-    const long long kk = x / pair, rem = x % pair;
-    const int k1 = (int)(kk / nk), k2 = (int)(kk % nk);
-    const long long p = rem / blk;
-    const int mu = (int)((rem % blk) / nao), nu = (int)(rem % nao);
-    const double2 a = L[x];
-    const double2 h = L[((long long)k2 * nk + k1) * pair + p * blk + (long long)nu * nao + mu];
-    const double2 t = L[((long long)neg[k1] * nk + neg[k2]) * pair + rem];
-    double dr = h.x - a.x, di = h.y + a.y;
-    hv = wmax(hv, sqrt(dr * dr + di * di));
-    dr = t.x - a.x;
-    di = t.y + a.y;
-    tv = wmax(tv, sqrt(dr * dr + di * di));
-    mv = wmax(mv, sqrt(a.x * a.x + a.y * a.y));
+// |x| of a double as its bit pattern with the sign cleared: for non-negative doubles the
+// integer order is the numeric order (NaN patterns sort above +inf).
+__device__ __forceinline__ unsigned long long abits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+__device__ __forceinline__ unsigned long long warp_umax(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
   }
-  block_max_commit(hv, stats + 3);
-  block_max_commit(tv, stats + 4);
-  block_max_commit(mv, stats + 5);
+  return v;
+}
+
+// One 32 x 32 tile (mu, nu) of one block L[k1][k2][P]: its Hermitian partner
+// L[k2][k1][P][nu][mu] is read tile-transposed through shared memory so that every global
+// read is coalesced; the time-reversal partner L[-k1][-k2][P][mu][nu] is read in place.
+// Records max-norm differences (component-wise) and max |L| (component-wise).
+__global__ void __launch_bounds__(256) l_check_kernel(const double2* __restrict__ L, const int* __restrict__ neg,
+                                                      int nk, int naux, int nao, double* stats) {
+  __shared__ double2 ht[32][33];
+  const int tiles = (nao + 31) / 32;
+  const long long kk = blockIdx.x / (tiles * tiles);  // k-pair index k1 * nk + k2
+  const int tile = (int)(blockIdx.x % (tiles * tiles));
+  const int mu0 = (tile / tiles) * 32, nu0 = (tile % tiles) * 32;
+  const int P = blockIdx.y;
+  const int k1 = (int)(kk / nk), k2 = (int)(kk % nk);
+  const long long blk = (long long)nao * nao, pair = blk * naux;
+  const double2* a_blk = L + ((long long)k1 * nk + k2) * pair + P * blk;
+  const double2* h_blk = L + ((long long)k2 * nk + k1) * pair + P * blk;
+  const double2* t_blk = L + ((long long)neg[k1] * nk + neg[k2]) * pair + P * blk;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int nu = nu0 + r, mu = mu0 + tx;  // h[nu][mu], coalesced over mu
+    ht[r][tx] = (nu < nao && mu < nao) ? h_blk[(long long)nu * nao + mu] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  unsigned long long hv = 0, tv = 0, mv = 0;
+  for (int r = ty; r < 32; r += 8) {
+    const int mu = mu0 + r, nu = nu0 + tx;  // a[mu][nu], coalesced over nu
+    if (mu < nao && nu < nao) {
+      const double2 a = a_blk[(long long)mu * nao + nu];
+      const double2 h = ht[tx][r];
+      const double2 t = t_blk[(long long)mu * nao + nu];
+      const unsigned long long d0 = abits(h.x - a.x), d1 = abits(h.y + a.y);
+      const unsigned long long d2 = abits(t.x - a.x), d3 = abits(t.y + a.y);
+      const unsigned long long m0 = abits(a.x), m1 = abits(a.y);
+      hv = max(hv, max(d0, d1));
+      tv = max(tv, max(d2, d3));
+      mv = max(mv, max(m0, m1));
+    }
+  }
+  hv = warp_umax(hv);
+  tv = warp_umax(tv);
+  mv = warp_umax(mv);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(reinterpret_cast<unsigned long long*>(stats + 3), hv);
+    atomicMax(reinterpret_cast<unsigned long long*>(stats + 4), tv);
+    atomicMax(reinterpret_cast<unsigned long long*>(stats + 5), mv);
+  }
 }
 
 inline int grid_for(long long total, int threads, int cap) {
@@ -387,8 +432,8 @@ cudaError_t launch_symmetrize(const double2* Z, double2* Lq, int nq, int naux, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_orth_reduce(const double2* S, int n, double sc, double* stat, cudaStream_t s) {
-  orth_reduce_kernel<<<grid_for((long long)n * n, 256, 152), 256, 0, s>>>(S, n, sc, stat);
+cudaError_t launch_orth_reduce(const double2* Sg, int ng, int n, double sc, double* stat, cudaStream_t s) {
+  orth_reduce_kernel<<<grid_for((long long)n * n, 256, 152), 256, 0, s>>>(Sg, ng, n, sc, stat);
   return cudaGetLastError();
 }
 
@@ -401,8 +446,9 @@ cudaError_t launch_c_real_check(const double2* C, const int* neg, int nk, int na
 
 cudaError_t launch_l_check(const double2* L, const int* neg, int nk, int naux, int nao, double* stats,
                            cudaStream_t s) {
-  const long long total = (long long)nk * nk * naux * nao * nao;
-  l_check_kernel<<<grid_for(total, 256, 152 * 8), 256, 0, s>>>(L, neg, nk, naux, nao, stats);
+  const int tiles = (nao + 31) / 32;
+  const dim3 grid((unsigned)((long long)tiles * tiles * nk * nk), naux, 1);
+  l_check_kernel<<<grid, 256, 0, s>>>(L, neg, nk, naux, nao, stats);
   return cudaGetLastError();
 }
 

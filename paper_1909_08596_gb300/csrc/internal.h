@@ -63,8 +63,9 @@ cudaError_t launch_symmetrize(const double2* Z, double2* Lq, int nq, int naux, i
                               cudaStream_t st);
 
 // Checks. stats layout (doubles, raw maxima): [0] orthonormality, [1] |C^{-k} - conj C^k|,
-// [2] |C|, [3] Hermiticity of L, [4] time reversal of L, [5] |L|.
-cudaError_t launch_orth_reduce(const double2* S, int n, double s, double* stat, cudaStream_t st);
+// [2] |C|, [3] Hermiticity of L, [4] time reversal of L, [5] |L| (the last three component-wise).
+// The orthonormality reduction sums ng split-K partial products S_g = C_g^+ C_g first.
+cudaError_t launch_orth_reduce(const double2* Sg, int ng, int n, double s, double* stat, cudaStream_t st);
 cudaError_t launch_c_real_check(const double2* C, const int* neg, int nk, int nao, int n, double* stats,
                                 cudaStream_t st);
 cudaError_t launch_l_check(const double2* L, const int* neg, int nk, int naux, int nao, double* stats,
@@ -95,8 +96,10 @@ cudaError_t launch_build_Cb(const double2* C, int nk, int nao, int n, int K1, vo
                             cudaStream_t s);
 cudaError_t launch_build_Cc(const double2* C, const int4* gather, const int4* t2, int b0, int nq, int nao, int n,
                             int K2, void* Cc, long long sstride, cudaStream_t s);
-cudaError_t launch_pack_split(const double* ZT, int nq, int naux, int n, int nc, double sc, void* Xt,
-                              long long sstride, long long Rtot, long long row_base, cudaStream_t s);
+cudaError_t launch_pack_split(const void* ZT, int nq, int naux, int n, int nc, void* Xt, long long sstride,
+                              long long Rtot, long long row_base, cudaStream_t s);
+cudaError_t launch_tc_pairs(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+                            const tc::Segment* segs, void* out, long long ldo, unsigned int* err, cudaStream_t s);
 cudaError_t launch_tc_split_t(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                               const tc::Segment* segs, void* out, long long sstride, long long K2, int nao, int nemb,
                               unsigned int* err, cudaStream_t s);

@@ -1,9 +1,10 @@
 // Split-BF16 (mixed-precision) path of the embedded-ERI transformation: the operand
 // splitting kernels and the tcgen05 GEMM instantiations with their output functors.
 //
-// Every FP64 operand x is split into three bf16 slices x = x0 + x1 + x2 + O(2^-27 |x|),
+// Every FP64 operand x is split into three bf16 slices x = x0 + x1 + x2 + O(2^-26 |x|),
 // each slice the round-to-nearest bf16 of what the previous ones left over (the error-free
-// splitting of Ozaki et al., applied per element). Complex products are written as real
+// splitting of Ozaki et al., applied per element, computed from a two-float form of x so
+// that no FP64 arithmetic is needed; see split.cuh). Complex products are written as real
 // GEMMs over interleaved (re, im) K indices; the orbital operands carry the signs.
 //
 // Step 1 (ket side):  T_e[(P,mu)][(j,p)] = sum_(nu,c) L_e[(P,mu)][(nu,c)] Cb^{k2}[(j,p)][(nu,c)]
@@ -16,19 +17,12 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "split.cuh"
 #include "tc_gemm.cuh"
 
 namespace dmet {
 
 namespace {
-
-__device__ __forceinline__ void split3(double x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
-  a = __double2bfloat16(x);
-  double r = x - (double)__bfloat162float(a);
-  b = __double2bfloat16(r);
-  r -= (double)__bfloat162float(b);
-  c = __double2bfloat16(r);
-}
 
 inline int grid_for(long long total, int threads, int cap) {
   long long g = (total + threads - 1) / threads;
@@ -54,7 +48,7 @@ __global__ void split_L_kernel(const double* __restrict__ L, const int4* __restr
       v = L[(pair * rows_e + rem) * 2 * nao + col];
     }
     __nv_bfloat16 a, b, c;
-    split3(v, a, b, c);
+    split3d(v, a, b, c);
     Ls[x] = a;
     Ls[x + sstride] = b;
     Ls[x + 2 * sstride] = c;
@@ -81,7 +75,7 @@ __global__ void build_Cb_kernel(const double2* __restrict__ C, int nk, int nao, 
       v = p == 0 ? (c == 0 ? z.x : -z.y) : (c == 0 ? z.y : z.x);
     }
     __nv_bfloat16 a, b, cc;
-    split3(v, a, b, cc);
+    split3d(v, a, b, cc);
     Cb[x] = a;
     Cb[x + sstride] = b;
     Cb[x + 2 * sstride] = cc;
@@ -112,21 +106,22 @@ __global__ void build_Cc_kernel(const double2* __restrict__ C, const int4* __res
       v = w * (p == 0 ? (c == 0 ? z.x : z.y) : (c == 0 ? -z.y : z.x));
     }
     __nv_bfloat16 a, b, cc;
-    split3(v, a, b, cc);
+    split3d(v, a, b, cc);
     Cc[x] = a;
     Cc[x + sstride] = b;
     Cc[x + 2 * sstride] = cc;
   }
 }
 
-// Xt[t][IJ][row_base + (slot * naux + P) * nc + c] = split of s * (Z_ij + Z_ji).c for i >= j,
-// with Z_ij (complex) = ZT[slot][(P n + j) 2n + 2i + (re|im)].
+// Xt[t][IJ][row_base + (slot * naux + P) * nc + c] = split of (Z_ij + Z_ji).c for i >= j, where
+// each real component of Z_ij (complex) is a two-float pair ZT[slot][(P n + j) 2n + 2i + (re|im)].
+// (The factor s of L^q = s (Z + Z^T) is applied, squared, to the contraction's output.)
 constexpr int PK_P = 16, PK_B = 8;
-__global__ void __launch_bounds__(256) pack_split_kernel(const double* __restrict__ ZT, int naux, int n, int nc,
-                                                         double s, __nv_bfloat16* __restrict__ Xt,
-                                                         long long sstride, long long Rtot, long long row_base) {
-  __shared__ double2 za[PK_P][PK_B][PK_B];
-  __shared__ double2 zb[PK_P][PK_B][PK_B];
+__global__ void __launch_bounds__(256) pack_split_kernel(const float2* __restrict__ ZT, int naux, int n, int nc,
+                                                         __nv_bfloat16* __restrict__ Xt, long long sstride,
+                                                         long long Rtot, long long row_base) {
+  __shared__ float4 za[PK_P][PK_B][PK_B];  // (re.hi, re.lo, im.hi, im.lo)
+  __shared__ float4 zb[PK_P][PK_B][PK_B];
   // pair-block decode: lower triangle of ceil(n/8) blocks
   const long long t = blockIdx.x;
   long long bi = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
@@ -136,28 +131,22 @@ __global__ void __launch_bounds__(256) pack_split_kernel(const double* __restric
   const int i0 = (int)bi * PK_B, j0 = bj * PK_B;
   const int P0 = blockIdx.y * PK_P;
   const int slot = blockIdx.z;
-  const double* z = ZT + (long long)slot * naux * n * 2 * n;
+  const float4* z = reinterpret_cast<const float4*>(ZT + (long long)slot * naux * n * 2 * n);
   for (int e = threadIdx.x; e < PK_P * PK_B * PK_B; e += blockDim.x) {
     const int pl = e / (PK_B * PK_B), a = (e / PK_B) % PK_B, b = e % PK_B;
     const int P = P0 + pl;
     // za[pl][ii][jj] = Z_{i j} with (ii, jj) = (b, a): consecutive e run over i for fixed j.
     {
       const int i = i0 + b, j = j0 + a;
-      double2 v = make_double2(0.0, 0.0);
-      if (P < naux && i < n && j < n) {
-        const double* p = z + ((long long)P * n + j) * 2 * n + 2 * i;
-        v = make_double2(p[0], p[1]);
-      }
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (P < naux && i < n && j < n) v = z[((long long)P * n + j) * n + i];
       za[pl][b][a] = v;
     }
     // zb[pl][ii][jj] = Z_{j i} with (ii, jj) = (a, b): consecutive e run over j for fixed i.
     {
       const int i = i0 + a, j = j0 + b;
-      double2 v = make_double2(0.0, 0.0);
-      if (P < naux && i < n && j < n) {
-        const double* p = z + ((long long)P * n + i) * 2 * n + 2 * j;
-        v = make_double2(p[0], p[1]);
-      }
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (P < naux && i < n && j < n) v = z[((long long)P * n + i) * n + j];
       zb[pl][a][b] = v;
     }
   }
@@ -170,12 +159,16 @@ __global__ void __launch_bounds__(256) pack_split_kernel(const double* __restric
     const int pl = rl / nc, c = rl % nc;
     const int P = P0 + pl;
     if (i >= n || j > i || P >= naux) continue;
-    const double2 a = za[pl][ii][jj], b = zb[pl][ii][jj];
-    const double v = s * (c == 0 ? a.x + b.x : a.y + b.y);
+    const float4 a = za[pl][ii][jj], b = zb[pl][ii][jj];
+    const float ah = c == 0 ? a.x : a.z, al = c == 0 ? a.y : a.w;
+    const float bh = c == 0 ? b.x : b.z, bl = c == 0 ? b.y : b.w;
+    // (ah + al) + (bh + bl) as a two-float pair: TwoSum of the leading parts.
+    const float sh = ah + bh, bv = sh - ah;
+    const float sl = ((ah - (sh - bv)) + (bh - bv)) + (al + bl);
     const long long IJ = (long long)i * (i + 1) / 2 + j;
     const long long idx = IJ * Rtot + row_base + ((long long)slot * naux + P) * nc + c;
     __nv_bfloat16 x0, x1, x2;
-    split3(v, x0, x1, x2);
+    split3f(sh, sl, x0, x1, x2);
     Xt[idx] = x0;
     Xt[idx + sstride] = x1;
     Xt[idx + 2 * sstride] = x2;
@@ -201,15 +194,30 @@ struct EpiSplitT {
     for (int c = 0; c < 64; c += 2) {
       if (col0 + c >= j.n_valid) break;
       const int jj = (j.o1 + col0 + c) >> 1;
-      const double re = (double)hi[c] + (double)lo[c];
-      const double im = (double)hi[c + 1] + (double)lo[c + 1];
       __nv_bfloat16 r0, r1, r2, i0, i1, i2;
-      split3(re, r0, r1, r2);
-      split3(im, i0, i1, i2);
+      split3f(hi[c], lo[c], r0, r1, r2);
+      split3f(hi[c + 1], lo[c + 1], i0, i1, i2);
       __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(p.out + (rbase + jj) * p.K2 + cidx);
       o[0] = __halves2bfloat162(r0, i0);
       o[p.sstride / 2] = __halves2bfloat162(r1, i1);
       o[p.sstride] = __halves2bfloat162(r2, i2);
+    }
+  }
+};
+
+// Step-2 output functor: the two-float sum itself, out[(o0 + row) * ldo + o1 + col] = (hi, lo).
+struct EpiPairs {
+  struct Params {
+    float2* out;
+    long long ldo;
+  };
+  static __device__ __forceinline__ void store(const Params& p, const tc::TcJob& j, int row, int col0,
+                                               const float* hi, const float* lo) {
+    float2* o = p.out + ((long long)j.o0 + row) * p.ldo + j.o1;
+#pragma unroll
+    for (int c = 0; c < 64; ++c) {
+      const int cc = col0 + c;
+      if (cc < j.n_valid) o[cc] = make_float2(hi[c], lo[c]);
     }
   }
 };
@@ -262,11 +270,12 @@ cudaError_t launch_build_Cc(const double2* C, const int4* gather, const int4* t2
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_split(const double* ZT, int nq, int naux, int n, int nc, double sc, void* Xt,
-                              long long sstride, long long Rtot, long long row_base, cudaStream_t s) {
+cudaError_t launch_pack_split(const void* ZT, int nq, int naux, int n, int nc, void* Xt, long long sstride,
+                              long long Rtot, long long row_base, cudaStream_t s) {
   const long long nb = (n + PK_B - 1) / PK_B;
   const dim3 grid((unsigned)(nb * (nb + 1) / 2), (naux + PK_P - 1) / PK_P, nq);
-  pack_split_kernel<<<grid, 256, 0, s>>>(ZT, naux, n, nc, sc, (__nv_bfloat16*)Xt, sstride, Rtot, row_base);
+  pack_split_kernel<<<grid, 256, 0, s>>>((const float2*)ZT, naux, n, nc, (__nv_bfloat16*)Xt, sstride, Rtot,
+                                         row_base);
   return cudaGetLastError();
 }
 
@@ -282,6 +291,12 @@ cudaError_t launch_tc_rect(const CUtensorMap& A, const CUtensorMap& B, const tc:
                            cudaStream_t s) {
   tc::EpiRect::Params p{out, ldo, scale};
   return launch_tc<tc::EpiRect>(A, B, jobs, njobs, segs, p, err, s);
+}
+
+cudaError_t launch_tc_pairs(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+                            const tc::Segment* segs, void* out, long long ldo, unsigned int* err, cudaStream_t s) {
+  EpiPairs::Params p{(float2*)out, ldo};
+  return launch_tc<EpiPairs>(A, B, jobs, njobs, segs, p, err, s);
 }
 
 cudaError_t launch_tc_packed(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,

@@ -192,6 +192,7 @@ struct Prob {
   std::vector<Block> con_blocks;
   int bq = 1;          // q slots per block
   int* d_neg = nullptr;
+  int orth_groups = 1;  // split-K groups of the orthonormality product (a divisor of Nk)
   bool mixed = false;
   MixedPlan mx;
 };
@@ -378,6 +379,8 @@ dmet_status_t run_orbital_checks(dmet_emb_plan_s* P, Prob& pr, int p, const doub
   for (int s = 0; s < pr.nspin; ++s) {
     const int n = pr.n[s];
     {
+      // split-K over groups of k-points so that the small n x n product fills the GPU
+      const int ng = pr.orth_groups;
       Timed t(P, KC_CHECK_C, 8.0 * n * n * (double)pr.nk * pr.nao, 16.0 * pr.nk * pr.nao * n, 2);
       ZgemmArgs z = zargs();
       z.A = C[s];
@@ -385,13 +388,17 @@ dmet_status_t run_orbital_checks(dmet_emb_plan_s* P, Prob& pr, int p, const doub
       z.D = P->S;
       z.M = n;
       z.N = n;
-      z.K = pr.nk * pr.nao;
+      z.K = (pr.nk / ng) * pr.nao;
       z.lda = n;
       z.ldb = n;
+      z.sA = (long long)z.K * n;
+      z.sB = (long long)z.K * n;
+      z.sD = (long long)n * n;
       z.dm_lo = n;
       z.dn_lo = 1;
+      z.batch = ng;
       CK(launch_zgemm(z, A_KM, true, B_KN, P->stream));
-      CK(launch_orth_reduce(P->S, n, pr.ortho_scale, st + 0, P->stream));
+      CK(launch_orth_reduce(P->S, ng, n, pr.ortho_scale, st + 0, P->stream));
     }
     if (pr.d.sym == DMET_SYM_REAL) {
       Timed t(P, KC_CHECK_C, 0.0, 32.0 * pr.nk * pr.nao * n);
@@ -593,7 +600,7 @@ WsSizes ws_for(const Prob& pr, int bq) {
   w.crep = (size_t)E * pr.nao * nmax * 16;
   w.T = (size_t)E * pr.nao * pr.naux * nmax * 16;
   w.Z = pr.d.sym == DMET_SYM_REAL ? (size_t)bq * pr.naux * nmax * nmax * 16 : 0;
-  w.S = (size_t)nmax * nmax * 16;
+  w.S = (size_t)pr.orth_groups * nmax * nmax * 16;
   for (int s = 0; s < pr.nspin; ++s) {
     if (pr.pack == DMET_PACK_S8) w.X[s] = (size_t)bq * pr.naux * 2 * pr.npair[s] * 8;
     else w.lq_all[s] = (size_t)pr.nk * pr.naux * pr.n[s] * pr.n[s] * 16;
@@ -875,19 +882,21 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
         double fl = 0;
         for (int i = bl.b0; i < bl.b1; ++i) fl += 8.0 * n * (double)pr.naux * n * pr.con.t2[i].w;
         Timed t(P, KC_TC_TRANSFORM_2, fl, 0.0, 1, exec_flops(m, m.j2_off[s][bi], m.j2_cnt[s][bi]));
-        CK(launch_tc_rect(mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs, P->ZT, 2LL * n,
-                          1.0, P->derr, P->stream));
+        CK(launch_tc_pairs(mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs, P->ZT, 2LL * n,
+                           P->derr, P->stream));
       }
       {
         const int nc = bl.w == 1 ? 1 : 2;
         Timed t(P, KC_TC_PACK, 0.0, 16.0 * nq * pr.naux * (double)n * n + 6.0 * nq * pr.naux * nc * pr.npair[s]);
-        CK(launch_pack_split(P->ZT, nq, pr.naux, n, nc, pr.lq_scale, P->Xt[s], pr.npair[s] * m.Rtot, m.Rtot,
-                             m.row_base[bi], P->stream));
+        CK(launch_pack_split(P->ZT, nq, pr.naux, n, nc, P->Xt[s], pr.npair[s] * m.Rtot, m.Rtot, m.row_base[bi],
+                             P->stream));
       }
     }
   }
   long long K = 0;
   for (int q : pr.con.order) K += (long long)pr.naux * (pr.s.qw[q] == 1 ? 1 : 2);
+  // The operand holds Z + Z^T; L^q = s (Z + Z^T), so the product carries s^2, and 1/Nk.
+  const double oscale = pr.lq_scale * pr.lq_scale / pr.nk;
   for (int blk = 0; blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
     const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
     const double fl = blk == 1 ? 2.0 * pr.npair[0] * (double)pr.npair[1] * K
@@ -895,10 +904,10 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
     Timed t(P, KC_TC_CONTRACT, fl, 0.0, 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk]));
     if (blk == 1)
       CK(launch_tc_rect(mm.Xt[0], mm.Xt[1], m.d_jobs + m.jc_off[1], m.jc_cnt[1], m.d_segs, (double*)out[1],
-                        pr.npair[1], 1.0 / pr.nk, P->derr, P->stream));
+                        pr.npair[1], oscale, P->derr, P->stream));
     else
       CK(launch_tc_packed(mm.Xt[sa], mm.Xt[sa], m.d_jobs + m.jc_off[blk], m.jc_cnt[blk], m.d_segs, (double*)out[blk],
-                          1.0 / pr.nk, P->derr, P->stream));
+                          oscale, P->derr, P->stream));
   }
   return DMET_OK;
 }
@@ -974,6 +983,11 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     pr.pack = pr.d.eri_pack == DMET_PACK_AUTO ? (pr.d.sym == DMET_SYM_REAL ? DMET_PACK_S8 : DMET_PACK_FULL)
                                               : pr.d.eri_pack;
     pr.lq_scale = pr.d.ck_norm == 0 ? 1.0 / pr.nk : 1.0;
+    for (int g = std::min(pr.nk, 32); g >= 1; --g)
+      if (pr.nk % g == 0) {
+        pr.orth_groups = g;
+        break;
+      }
     pr.ortho_scale = pr.lq_scale;
     std::vector<int> nat(pr.nk);
     for (int q = 0; q < pr.nk; ++q) nat[q] = q;

@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "split.cuh"
 #include "tc_common.cuh"
 
 namespace dmet {
@@ -268,7 +269,7 @@ struct EpiPacked {
     for (int c = 0; c < 64; ++c) {
       const int cc = col0 + c;
       const long long n = (long long)j.o1 + cc;
-      if (cc < j.n_valid && n <= m) o[n] = p.scale * ((double)hi[c] + (double)lo[c]);
+      if (cc < j.n_valid && n <= m) o[n] = p.scale * (f2d(hi[c]) + f2d(lo[c]));
     }
   }
 };
@@ -286,7 +287,7 @@ struct EpiRect {
 #pragma unroll
     for (int c = 0; c < 64; ++c) {
       const int cc = col0 + c;
-      if (cc < j.n_valid) o[cc] = p.scale * ((double)hi[c] + (double)lo[c]);
+      if (cc < j.n_valid) o[cc] = p.scale * (f2d(hi[c]) + f2d(lo[c]));
     }
   }
 };

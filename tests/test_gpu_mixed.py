@@ -48,7 +48,7 @@ CASES = [
     ((2, 3, 1), 6, 11, 33),
     ((3, 3, 1), 10, 37, 70),
     ((2, 2, 2), 4, 9, 20),
-    ((3, 2, 1), 20, 60, 130),   # more than one 128-row tile of pairs and of (P, j) rows
+    ((3, 2, 1), 24, 60, 130),   # more than one 128-row tile of pairs and of (P, j) rows
 ]
 
 
