@@ -181,6 +181,34 @@ DMET_API dmet_status_t dmet_emb_profile_read(dmet_emb_plan_t plan, int32_t kerne
 /* Number of kernel launches the plan has queued since it was created. */
 DMET_API int64_t dmet_emb_launch_count(dmet_emb_plan_t plan);
 
+/* Size of the static device scratch array used by dmet_emb_eri_noalloc (32 MiB). */
+#define DMET_EMB_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory: a caller whose device memory is entirely owned by another
+ * allocator (for example a framework's caching pool that must account for every byte), or
+ * one that must not let an allocation synchronise the device in the middle of an embedding
+ * self-consistency loop that shares the GPU with other streams.
+ *
+ * It computes the same result as dmet_emb_eri's FP64 path for one problem, allocating
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine, no host heap. All
+ * scratch comes from one file-scope __device__ array of DMET_EMB_NOALLOC_SCRATCH_BYTES bytes,
+ * which every GPU that loads the library holds until the process exits. The caller passes
+ * device pointers (L, C[s], eri_out[b]) laid out as for dmet_emb_eri, and `stream`, a
+ * cudaStream_t (NULL = legacy default stream).
+ * Supported: prec = FP64, sym = REAL, 8-fold packing (AUTO or S8), Nk <= 64; a problem whose
+ * scratch would exceed the array is rejected with DMET_ERR_OOM and a message giving both
+ * sizes, before any work is queued. Host pointers are rejected (staging would allocate).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current) and caches it; make that first call before any stream capture.
+ * Calls share the array and leave their contents in it; the call clears what must start at
+ * zero (its check maxima and the output blocks) itself. Two calls whose work overlaps on the
+ * GPU (other streams, other host threads on the same device) race on the array: serialise
+ * them. The call is synchronous: it waits for `stream` and returns the device checks' status
+ * (DMET_ERR_NOT_ORTHONORMAL, DMET_ERR_SYMMETRY) like dmet_emb_status. */
+DMET_API dmet_status_t dmet_emb_eri_noalloc(const dmet_emb_desc_t* desc, const void* L,
+                                            const void* const* C, void* const* eri_out, void* stream);
+
 /* Message describing the last error returned on the calling thread ("" if none). */
 DMET_API const char* dmet_emb_last_error(void);
 

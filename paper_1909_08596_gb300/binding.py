@@ -116,6 +116,9 @@ def lib() -> ctypes.CDLL:
         L.dmet_emb_profile_read.restype = st
         L.dmet_emb_launch_count.argtypes = [_P]
         L.dmet_emb_launch_count.restype = ctypes.c_int64
+        L.dmet_emb_eri_noalloc.argtypes = [ctypes.POINTER(dmet_emb_desc_t), _P, ctypes.POINTER(_P),
+                                           ctypes.POINTER(_P), _P]
+        L.dmet_emb_eri_noalloc.restype = st
         L.dmet_emb_last_error.argtypes = []
         L.dmet_emb_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -185,6 +188,13 @@ def dmet_emb_eri(plan, L, C, eri_out):
     cp = (ctypes.POINTER(_P) * n)(*[ctypes.cast(r, ctypes.POINTER(_P)) for r in crows])
     ep = (ctypes.POINTER(_P) * n)(*[ctypes.cast(r, ctypes.POINTER(_P)) for r in erows])
     _check(lib().dmet_emb_eri(_P(plan), ls, cp, ep))
+
+
+def dmet_emb_eri_noalloc(desc, L, C, eri_out, stream=None):
+    """One problem's FP64 8-fold packed ERIs with no allocation (device buffers only)."""
+    cs = (_P * len(C))(*[ptr(c) for c in C])
+    outs = (_P * len(eri_out))(*[ptr(o) for o in eri_out])
+    _check(lib().dmet_emb_eri_noalloc(ctypes.byref(desc), _P(ptr(L)), cs, outs, _P(stream or 0)))
 
 
 def dmet_emb_status(plan, problem, raise_on_error=False):

@@ -6,6 +6,10 @@
 
 namespace dmet {
 
+// Message of the last error returned on the calling thread (fixed buffer, no heap).
+constexpr int kLastErrorBytes = 512;
+char* last_error_buffer();
+
 // Batched complex FP64 GEMM:  D[m][n] = alpha * sum_k opA(m,k) * opB(k,n)  (+ D if beta).
 // opA(m,k) = A[k*lda + m] (A_KM) or A[m*lda + k] (A_MK), conjugated if conj_a.
 // opB(k,n) = B[k*ldb + n] (B_KN) or B[n*ldb + k] (B_NK).

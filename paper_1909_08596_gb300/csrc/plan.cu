@@ -18,19 +18,24 @@
 
 using namespace dmet;
 
+namespace dmet {
+char* last_error_buffer() {
+  static thread_local char buf[kLastErrorBytes];
+  return buf;
+}
+}  // namespace dmet
+
 namespace {
 
-thread_local std::string g_err;
-
 dmet_status_t fail(dmet_status_t st, const char* fmt, ...) {
-  char buf[512];
   va_list ap;
   va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
+  vsnprintf(dmet::last_error_buffer(), dmet::kLastErrorBytes, fmt, ap);
   va_end(ap);
-  g_err = buf;
   return st;
 }
+
+void clear_error() { dmet::last_error_buffer()[0] = 0; }
 
 #define CK(call)                                                                           \
   do {                                                                                     \
@@ -923,13 +928,13 @@ size_t dmet_emb_eri_bytes(const dmet_emb_desc_t* desc, int32_t block) {
   return eri_bytes_of(*desc, block);
 }
 
-const char* dmet_emb_last_error(void) { return g_err.c_str(); }
+const char* dmet_emb_last_error(void) { return dmet::last_error_buffer(); }
 
 int32_t dmet_emb_profile_count(void) { return KC_COUNT; }
 
 dmet_status_t dmet_emb_schedule(const dmet_emb_desc_t* desc, int32_t* k2_of, int32_t* neg, int32_t* q_weight,
                                 int32_t* n_rep, int32_t* rep_k1, int32_t* rep_half) {
-  g_err.clear();
+  clear_error();
   if (!desc) return fail(DMET_ERR_INVALID_ARG, "desc is NULL");
   TRY(validate_desc(*desc, 0));
   Sched s;
@@ -946,7 +951,7 @@ dmet_status_t dmet_emb_schedule(const dmet_emb_desc_t* desc, int32_t* k2_of, int
 
 dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, void* stream, size_t workspace_limit,
                             dmet_emb_plan_t* plan) {
-  g_err.clear();
+  clear_error();
   if (!plan) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
   *plan = nullptr;
   if (!descs) return fail(DMET_ERR_INVALID_ARG, "descs is NULL");
@@ -1105,9 +1110,10 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     }
   }
   if (st != DMET_OK) {
-    std::string msg = g_err;
+    char msg[dmet::kLastErrorBytes];
+    std::memcpy(msg, dmet::last_error_buffer(), sizeof(msg));
     destroy_plan(P);
-    g_err = msg;
+    std::memcpy(dmet::last_error_buffer(), msg, sizeof(msg));
     return st;
   }
   *plan = P;
@@ -1115,7 +1121,7 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
 }
 
 dmet_status_t dmet_emb_destroy(dmet_emb_plan_t plan) {
-  g_err.clear();
+  clear_error();
   destroy_plan(plan);
   return DMET_OK;
 }
@@ -1157,7 +1163,7 @@ static dmet_status_t stage_inputs(dmet_emb_plan_s* P, const Prob& pr, const void
 
 dmet_status_t dmet_emb_transform_3idx(dmet_emb_plan_t P, int32_t problem, const void* L, const void* const* C,
                                       int32_t q_begin, int32_t q_end, void* const* Lq_out) {
-  g_err.clear();
+  clear_error();
   if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
   if (problem < 0 || problem >= (int)P->probs.size()) return fail(DMET_ERR_INVALID_ARG, "problem %d", problem);
   Prob& pr = P->probs[problem];
@@ -1208,7 +1214,7 @@ dmet_status_t dmet_emb_transform_3idx(dmet_emb_plan_t P, int32_t problem, const 
 
 dmet_status_t dmet_emb_eri(dmet_emb_plan_t P, const void* const* L, const void* const* const* C,
                            void* const* const* eri_out) {
-  g_err.clear();
+  clear_error();
   if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
   if (!L || !C || !eri_out) return fail(DMET_ERR_INVALID_ARG, "NULL pointer argument");
   const int np = (int)P->probs.size();
@@ -1270,7 +1276,7 @@ dmet_status_t dmet_emb_eri(dmet_emb_plan_t P, const void* const* L, const void* 
 }
 
 dmet_status_t dmet_emb_status(dmet_emb_plan_t P, int32_t problem, double* stats) {
-  g_err.clear();
+  clear_error();
   if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
   if (problem < 0 || problem >= (int)P->probs.size()) return fail(DMET_ERR_INVALID_ARG, "problem %d", problem);
   CK(cudaStreamSynchronize(P->stream));
@@ -1302,7 +1308,7 @@ dmet_status_t dmet_emb_status(dmet_emb_plan_t P, int32_t problem, double* stats)
 }
 
 dmet_status_t dmet_emb_profile(dmet_emb_plan_t P, int32_t enable) {
-  g_err.clear();
+  clear_error();
   if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
   CK(cudaStreamSynchronize(P->stream));
   for (auto& k : P->ks) {
@@ -1322,7 +1328,7 @@ dmet_status_t dmet_emb_profile(dmet_emb_plan_t P, int32_t enable) {
 
 dmet_status_t dmet_emb_profile_read(dmet_emb_plan_t P, int32_t kernel, const char** name, int64_t* launches,
                                     double* total_ms, double* flops, double* exec_flops, double* bytes) {
-  g_err.clear();
+  clear_error();
   if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
   if (kernel < 0 || kernel >= KC_COUNT) return fail(DMET_ERR_INVALID_ARG, "kernel %d", kernel);
   CK(cudaStreamSynchronize(P->stream));
