@@ -327,42 +327,43 @@ __device__ __forceinline__ unsigned long long warp_umax(unsigned long long v) {
   return v;
 }
 
-// One 32 x 32 tile (mu, nu) of one block L[k1][k2][P]: its Hermitian partner
-// L[k2][k1][P][nu][mu] is read tile-transposed through shared memory so that every global
-// read is coalesced; the time-reversal partner L[-k1][-k2][P][mu][nu] is read in place.
-// Records max-norm differences (component-wise) and max |L| (component-wise).
+// Symmetries of L over a chunk of aux indices of one k pair (k1, k2): Hermiticity against
+// L[k2][k1][P][nu][mu] (checked once per unordered pair, k1 <= k2) and time reversal against
+// L[-k1][-k2][P][mu][nu] (checked once per pair of pairs). The transposed partner is read
+// through the read-only cache, where the block's other warps have brought its lines.
+// Records max-norm differences (component-wise) and max |L| (component-wise) as bit patterns.
+constexpr int LCHK_P = 8;
 __global__ void __launch_bounds__(256) l_check_kernel(const double2* __restrict__ L, const int* __restrict__ neg,
                                                       int nk, int naux, int nao, double* stats) {
-  __shared__ double2 ht[32][33];
-  const int tiles = (nao + 31) / 32;
-  const long long kk = blockIdx.x / (tiles * tiles);  // k-pair index k1 * nk + k2
-  const int tile = (int)(blockIdx.x % (tiles * tiles));
-  const int mu0 = (tile / tiles) * 32, nu0 = (tile % tiles) * 32;
-  const int P = blockIdx.y;
-  const int k1 = (int)(kk / nk), k2 = (int)(kk % nk);
-  const long long blk = (long long)nao * nao, pair = blk * naux;
-  const double2* a_blk = L + ((long long)k1 * nk + k2) * pair + P * blk;
-  const double2* h_blk = L + ((long long)k2 * nk + k1) * pair + P * blk;
-  const double2* t_blk = L + ((long long)neg[k1] * nk + neg[k2]) * pair + P * blk;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  for (int r = ty; r < 32; r += 8) {
-    const int nu = nu0 + r, mu = mu0 + tx;  // h[nu][mu], coalesced over mu
-    ht[r][tx] = (nu < nao && mu < nao) ? h_blk[(long long)nu * nao + mu] : make_double2(0.0, 0.0);
-  }
-  __syncthreads();
+  const int pchunks = (naux + LCHK_P - 1) / LCHK_P;
+  const long long nwork = (long long)nk * nk * pchunks;
   unsigned long long hv = 0, tv = 0, mv = 0;
-  for (int r = ty; r < 32; r += 8) {
-    const int mu = mu0 + r, nu = nu0 + tx;  // a[mu][nu], coalesced over nu
-    if (mu < nao && nu < nao) {
-      const double2 a = a_blk[(long long)mu * nao + nu];
-      const double2 h = ht[tx][r];
-      const double2 t = t_blk[(long long)mu * nao + nu];
-      const unsigned long long d0 = abits(h.x - a.x), d1 = abits(h.y + a.y);
-      const unsigned long long d2 = abits(t.x - a.x), d3 = abits(t.y + a.y);
-      const unsigned long long m0 = abits(a.x), m1 = abits(a.y);
-      hv = max(hv, max(d0, d1));
-      tv = max(tv, max(d2, d3));
-      mv = max(mv, max(m0, m1));
+  for (long long w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const long long kk = w / pchunks;
+    const int P0 = (int)(w % pchunks) * LCHK_P;
+    const int k1 = (int)(kk / nk), k2 = (int)(kk % nk);
+    const long long kt = (long long)neg[k1] * nk + neg[k2];
+    const bool do_h = k1 <= k2, do_t = kk <= kt;
+    const long long blk = (long long)nao * nao, pair = blk * naux;
+    const double2* a_pair = L + kk * pair;
+    const double2* h_pair = L + ((long long)k2 * nk + k1) * pair;
+    const double2* t_pair = L + kt * pair;
+    const int pend = min(naux, P0 + LCHK_P);
+    for (int P = P0; P < pend; ++P) {
+      const long long base = (long long)P * blk;
+      for (long long e = threadIdx.x; e < blk; e += blockDim.x) {
+        const double2 a = a_pair[base + e];
+        mv = max(mv, max(abits(a.x), abits(a.y)));
+        if (do_h) {
+          const int mu = (int)(e / nao), nu = (int)(e % nao);
+          const double2 h = __ldg(h_pair + base + (long long)nu * nao + mu);
+          hv = max(hv, max(abits(h.x - a.x), abits(h.y + a.y)));
+        }
+        if (do_t) {
+          const double2 t = t_pair[base + e];
+          tv = max(tv, max(abits(t.x - a.x), abits(t.y + a.y)));
+        }
+      }
     }
   }
   hv = warp_umax(hv);
@@ -446,9 +447,9 @@ cudaError_t launch_c_real_check(const double2* C, const int* neg, int nk, int na
 
 cudaError_t launch_l_check(const double2* L, const int* neg, int nk, int naux, int nao, double* stats,
                            cudaStream_t s) {
-  const int tiles = (nao + 31) / 32;
-  const dim3 grid((unsigned)((long long)tiles * tiles * nk * nk), naux, 1);
-  l_check_kernel<<<grid, 256, 0, s>>>(L, neg, nk, naux, nao, stats);
+  const long long pchunks = (naux + LCHK_P - 1) / LCHK_P;
+  const long long nwork = (long long)nk * nk * pchunks;
+  l_check_kernel<<<(unsigned)(nwork < (1LL << 30) ? nwork : (1LL << 30)), 256, 0, s>>>(L, neg, nk, naux, nao, stats);
   return cudaGetLastError();
 }
 

@@ -239,7 +239,15 @@ cudaError_t launch_tc(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJo
     attr = true;
   }
   if (njobs <= 0) return cudaSuccess;
-  tc::tc_gemm_kernel<3, 64, EPI><<<njobs, tc::kThreads, Cfg::SMEM, s>>>(A, B, jobs, segs, ep, err);
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = njobs < nsm ? njobs : nsm;
+  tc::tc_gemm_kernel<3, 64, EPI><<<grid, tc::kThreads, Cfg::SMEM, s>>>(A, B, jobs, njobs, segs, ep, err);
   return cudaGetLastError();
 }
 

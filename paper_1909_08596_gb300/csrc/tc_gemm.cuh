@@ -14,7 +14,10 @@
 // FP32 numbers (hi + lo, updated with the error-free TwoSum), which carries ~44 bits across
 // segments at FP32-pipe cost, and hand hi + lo to the output functor once at the end.
 //
-// One CTA of 12 warps computes one 128 x 128 tile of one job (jobs come from a table):
+// A persistent CTA of 12 warps (one per SM) works through the jobs blockIdx.x, blockIdx.x +
+// gridDim.x, ...; each job is one 128 x 128 output tile (jobs come from a table). The stage
+// ring and the two accumulator buffers run on across jobs, so a job's final store overlaps
+// the next job's MMAs.
 //   warp 0      TMA producer (one thread): 3+3 slice tiles per K block into a stage ring;
 //   warp 1      MMA issuer (one thread), also allocates / frees all 512 TMEM columns
 //               (two buffers of two 128-column accumulators, so the epilogue of segment g
@@ -85,8 +88,8 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
 template <int NSLICE, int ROWB, class EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const TcJob* __restrict__ jobs, const Segment* __restrict__ segs, const typename EPI::Params ep,
-                   unsigned int* err) {
+                   const TcJob* __restrict__ jobs, int njobs, const Segment* __restrict__ segs,
+                   const typename EPI::Params ep, unsigned int* err) {
   using Cfg = TcCfg<NSLICE, ROWB>;
   constexpr int S = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
@@ -98,7 +101,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* consumed = (volatile int*)(bars + 2 * S + 5) + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const TcJob job = jobs[blockIdx.x];
 
   auto full = [&](int s) { return smem_u32(bars + s); };
   auto empty = [&](int s) { return smem_u32(bars + S + s); };
@@ -140,6 +142,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       prefetch_tmap(&tmA);
       prefetch_tmap(&tmB);
       bool ok = true;
+      for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x) {
+      const TcJob job = jobs[jb];
       for (int g = 0; g < job.nseg && ok; ++g) {
         const Segment sg = segs[job.seg0 + g];
         for (int kb = 0; kb < sg.nkb; ++kb) {
@@ -158,15 +162,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++issued;
         }
       }
+      }
     } else if (warp == 1 && lane == 0) {
       // ---------------- MMA issuer ----------------
       constexpr uint32_t idesc = idesc_bf16_f32(kTile, kTile);
       constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
       constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
-      int it = 0;
+      int it = 0, gs = 0;  // K blocks and segments issued so far (across jobs)
       bool ok = true;
-      for (int g = 0; g < job.nseg && ok; ++g) {
-        const int b = g & 1, u = g >> 1;
+      for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x) {
+      const TcJob job = jobs[jb];
+      for (int g = 0; g < job.nseg && ok; ++g, ++gs) {
+        const int b = gs & 1, u = gs >> 1;
         if (!mbar_wait(acce(b), (u & 1) ^ 1, err, 2u)) break;
         tc_fence_after();
         const uint32_t d_main = tmem + b * 2 * kTile, d_corr = d_main + kTile;
@@ -194,6 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (ok) umma_commit(accf(b));
       }
+      }
       // Every MMA issued above must be complete before the accumulators are released.
       umma_commit(done_bar);
       mbar_wait(done_bar, 0, err, 16u);
@@ -204,41 +212,45 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int quad = warp & 3, half = (warp - 4) >> 2;
     const int row = quad * 32 + lane;
     float hi[64], lo[64];
-#pragma unroll
-    for (int c = 0; c < 64; ++c) {
-      hi[c] = 0.f;
-      lo[c] = 0.f;
-    }
     bool ok = true;
-    for (int g = 0; g < job.nseg; ++g) {
-      const int b = g & 1, u = g >> 1;
-      if (!mbar_wait(accf(b), u & 1, err, 8u)) {
-        ok = false;
-        break;
+    int gs = 0;
+    for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x) {
+      const TcJob job = jobs[jb];
+#pragma unroll
+      for (int c = 0; c < 64; ++c) {
+        hi[c] = 0.f;
+        lo[c] = 0.f;
       }
-      tc_fence_after();
-      const float w = segs[job.seg0 + g].w;
-      const uint32_t tm_main = tmem + ((uint32_t)(quad * 32) << 16) + b * 2 * kTile + half * 64;
+      for (int g = 0; g < job.nseg; ++g, ++gs) {
+        const int b = gs & 1, u = gs >> 1;
+        if (!mbar_wait(accf(b), u & 1, err, 8u)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const float w = segs[job.seg0 + g].w;
+        const uint32_t tm_main = tmem + ((uint32_t)(quad * 32) << 16) + b * 2 * kTile + half * 64;
 #pragma unroll
-      for (int ch = 0; ch < 4; ++ch) {
-        uint32_t v[16];
-        tmem_ld_32x32b_x16(tm_main + ch * 16, v);
-        tmem_ld_wait();
-#pragma unroll
-        for (int c = 0; c < 16; ++c) two_sum_acc(hi[ch * 16 + c], lo[ch * 16 + c], w * __uint_as_float(v[c]));
-        if (NSLICE == 3) {
-          // The correction sum is ~2^-8 of the leading one: it joins the low word.
-          tmem_ld_32x32b_x16(tm_main + kTile + ch * 16, v);
+        for (int ch = 0; ch < 4; ++ch) {
+          uint32_t v[16];
+          tmem_ld_32x32b_x16(tm_main + ch * 16, v);
           tmem_ld_wait();
 #pragma unroll
-          for (int c = 0; c < 16; ++c) lo[ch * 16 + c] += w * __uint_as_float(v[c]);
+          for (int c = 0; c < 16; ++c) two_sum_acc(hi[ch * 16 + c], lo[ch * 16 + c], w * __uint_as_float(v[c]));
+          if (NSLICE == 3) {
+            // The correction sum is ~2^-8 of the leading one: it joins the low word.
+            tmem_ld_32x32b_x16(tm_main + kTile + ch * 16, v);
+            tmem_ld_wait();
+#pragma unroll
+            for (int c = 0; c < 16; ++c) lo[ch * 16 + c] += w * __uint_as_float(v[c]);
+          }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acce(b));
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acce(b));
+      if (ok && row < job.m_valid) EPI::store(ep, job, row, half * 64, hi, lo);
     }
-    if (ok && row < job.m_valid) EPI::store(ep, job, row, half * 64, hi, lo);
   }
   __syncthreads();
   if (warp == 0 && lane == 0) {
