@@ -62,7 +62,7 @@ class dmet_emb_desc_t(ctypes.Structure):
 
 
 def make_desc(mesh, n_ao, n_aux, n_emb, n_spin=1, prec=DMET_PREC_FP64, ck_norm=0, sym=DMET_SYM_REAL,
-              eri_pack=DMET_PACK_AUTO, check_l=1, ortho_tol=0.0, sym_tol=0.0) -> dmet_emb_desc_t:
+              eri_pack=DMET_PACK_AUTO, check_l=0, ortho_tol=0.0, sym_tol=0.0) -> dmet_emb_desc_t:
     d = dmet_emb_desc_t()
     d.mesh[:] = list(mesh)
     d.n_ao, d.n_aux, d.n_spin = n_ao, n_aux, n_spin

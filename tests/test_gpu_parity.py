@@ -64,7 +64,7 @@ def test_eri_s8_matches_oracle(torch, case, ck_norm):
     mesh, nao, naux, n = case
     spec = spec_of(mesh, nao, naux, n)
     L, Cs, _ = synth.make_problem(spec, ck_norm=ck_norm)
-    (got,), st, stats = run_eri(torch, desc_of(spec, ck_norm=ck_norm), L, Cs)
+    (got,), st, stats = run_eri(torch, desc_of(spec, ck_norm=ck_norm, check_l=1), L, Cs)
     assert st == B.DMET_OK, stats
     assert stats[0] < 1e-12 and 0 <= stats[1] < 1e-12 and 0 <= stats[2] < 1e-12 and 0 <= stats[3] < 1e-12
     check_s8(got, oracle_s8(L, Cs[0], spec.mesh, ck_norm))
@@ -177,9 +177,12 @@ def test_complex_real_space_integrals_violate_time_reversal(torch):
     m = np.random.default_rng(2).standard_normal(L[1, 2].shape)
     L[1, 2] += 0.01 * (m - m.transpose(0, 2, 1))
     L[2, 1] = np.conj(L[1, 2].transpose(0, 2, 1))
-    _, st, stats = run_eri(torch, desc_of(spec), L, [C])
+    _, st, stats = run_eri(torch, desc_of(spec, check_l=1), L, [C])
     assert st == B.DMET_ERR_SYMMETRY
     assert stats[2] < 1e-12 and stats[3] > 1e-4
+    # Without the L check the call succeeds (the check is the caller's choice).
+    _, st, stats = run_eri(torch, desc_of(spec), L, [C])
+    assert st == B.DMET_OK and stats[2] < 0 and stats[3] < 0
 
 
 def test_hbn_full_size_sampled(torch):
@@ -188,7 +191,7 @@ def test_hbn_full_size_sampled(torch):
     set of 16 orbitals (column subsets are exact), and every q of L^q for three q."""
     spec = synth.CONFIGS["hbn_6x6x1"]
     L, (C,), _ = synth.make_problem(spec)
-    (got,), st, stats = run_eri(torch, desc_of(spec), L, [C])
+    (got,), st, stats = run_eri(torch, desc_of(spec, check_l=1), L, [C])
     assert st == B.DMET_OK, stats
     rng = np.random.default_rng(0)
     S = np.sort(rng.choice(spec.n_emb, 16, replace=False))

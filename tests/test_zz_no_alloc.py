@@ -23,7 +23,7 @@ def test_noalloc_matches_eri_two_calls(n_spin):
     torch = torch_cuda()
     spec = synth.spec_with(synth.CONFIGS["tiny_2x2x1"], n_spin=n_spin)
     L, Cs, _ = synth.make_problem(spec)
-    desc = B.make_desc(spec.mesh, spec.n_ao, spec.n_aux, spec.n_emb, n_spin=n_spin)
+    desc = B.make_desc(spec.mesh, spec.n_ao, spec.n_aux, spec.n_emb, n_spin=n_spin, check_l=1)
     refs, st, _ = run_eri(torch, desc, L, Cs)
     assert st == B.DMET_OK
     Ld = torch.from_numpy(L).cuda()
