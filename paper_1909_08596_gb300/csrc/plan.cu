@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -690,6 +691,12 @@ long long padk(long long x) {
 void build_mixed(Prob& pr) {
   MixedPlan& m = pr.mx;
   const int BK = mixed_kblock();
+  // K elements per FP32 segment (a multiple of the K block); DMET_TC_KSEG overrides.
+  m.kseg = 128;
+  if (const char* e = std::getenv("DMET_TC_KSEG")) {
+    const int v = std::atoi(e);
+    if (v >= BK && v % BK == 0 && v <= 4096) m.kseg = v;
+  }
   const int nk = pr.nk, nao = pr.nao, naux = pr.naux;
   m.K1 = (int)padk(2LL * nao);
   int nrep_max = 1;
@@ -738,16 +745,18 @@ void build_mixed(Prob& pr) {
       const int e0 = pr.con.start[bl.b0];
       m.Ls_rows = std::max(m.Ls_rows, (long long)(pr.con.start[bl.b1] - e0) * naux * nao);
       m.j1_off[sp].push_back((int)m.jobs.size());
-      for (int slot = bl.b0; slot < bl.b1; ++slot)
-        for (int e = pr.con.start[slot]; e < pr.con.start[slot + 1]; ++e) {
-          const int r = e - pr.con.start[slot], el = e - e0, k2 = pr.con.t1[e].x;
-          for (int mt = 0; mt < cdiv((long long)naux * nao, T); ++mt)
-            for (int nt = 0; nt < cdiv(2LL * n, T); ++nt)
+      // Tile-major, entry-minor: consecutive jobs write the adjacent column segments (one per
+      // representative r) of the same output rows, so L2 merges them into whole lines.
+      for (int mt = 0; mt < cdiv((long long)naux * nao, T); ++mt)
+        for (int nt = 0; nt < cdiv(2LL * n, T); ++nt)
+          for (int slot = bl.b0; slot < bl.b1; ++slot)
+            for (int e = pr.con.start[slot]; e < pr.con.start[slot + 1]; ++e) {
+              const int r = e - pr.con.start[slot], el = e - e0, k2 = pr.con.t1[e].x;
               m.jobs.push_back({el * naux * nao + mt * T, k2 * 2 * n + nt * T,
                                 (int)std::min<long long>(T, (long long)naux * nao - mt * T),
                                 (int)std::min<long long>(T, 2LL * n - nt * T), 0, 1, mt * T, nt * T,
                                 (slot - bl.b0) * naux * n, r * 2 * nao});
-        }
+            }
       m.j1_cnt[sp].push_back((int)m.jobs.size() - m.j1_off[sp].back());
       m.j2_off[sp].push_back((int)m.jobs.size());
       for (int slot = bl.b0; slot < bl.b1; ++slot) {
