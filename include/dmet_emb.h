@@ -164,6 +164,19 @@ DMET_API dmet_status_t dmet_emb_schedule(const dmet_emb_desc_t* desc, int32_t* k
                                 int32_t* q_weight, int32_t* n_rep, int32_t* rep_k1,
                                 int32_t* rep_half);
 
+/* Execution of the plan's problems (the batched form of Algorithm 1's loops; the paper runs
+ * one embedding problem at a time). When every problem of a plan gets its own workspace
+ * within the plan's workspace limit, dmet_emb_eri runs the problems concurrently on the
+ * plan's side streams, forked from and joined back to the plan's stream; otherwise they run
+ * one after another. enable != 0 makes dmet_emb_eri capture its work, on its first call with
+ * device buffers, into a CUDA graph that later calls with the same buffers replay on the
+ * plan's stream (different buffers: captured again; host buffers or profiling: no graph). */
+DMET_API dmet_status_t dmet_emb_graph(dmet_emb_plan_t plan, int32_t enable);
+
+/* Device milliseconds of problem `problem` in the last call made while profiling was enabled
+ * (CUDA events around that problem's work on its stream). Waits for the stream. */
+DMET_API dmet_status_t dmet_emb_problem_ms(dmet_emb_plan_t plan, int32_t problem, double* ms);
+
 /* Per-kernel timing with CUDA events on the plan's stream. enable != 0 starts recording
  * (and clears the counters); 0 stops. */
 DMET_API dmet_status_t dmet_emb_profile(dmet_emb_plan_t plan, int32_t enable);

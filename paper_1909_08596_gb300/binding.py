@@ -114,6 +114,10 @@ def lib() -> ctypes.CDLL:
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double)]
         L.dmet_emb_profile_read.restype = st
+        L.dmet_emb_graph.argtypes = [_P, ctypes.c_int32]
+        L.dmet_emb_graph.restype = st
+        L.dmet_emb_problem_ms.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+        L.dmet_emb_problem_ms.restype = st
         L.dmet_emb_launch_count.argtypes = [_P]
         L.dmet_emb_launch_count.restype = ctypes.c_int64
         L.dmet_emb_eri_noalloc.argtypes = [ctypes.POINTER(dmet_emb_desc_t), _P, ctypes.POINTER(_P),
@@ -239,6 +243,16 @@ def dmet_emb_profile_read(plan, kernel):
                                        ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(ex), ctypes.byref(by)))
     return {"name": name.value.decode(), "launches": launches.value, "ms": ms.value, "flops": fl.value,
             "exec_flops": ex.value, "bytes": by.value}
+
+
+def dmet_emb_graph(plan, enable):
+    _check(lib().dmet_emb_graph(_P(plan), 1 if enable else 0))
+
+
+def dmet_emb_problem_ms(plan, problem):
+    ms = ctypes.c_double()
+    _check(lib().dmet_emb_problem_ms(_P(plan), problem, ctypes.byref(ms)))
+    return ms.value
 
 
 def dmet_emb_launch_count(plan):

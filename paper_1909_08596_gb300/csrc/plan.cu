@@ -211,12 +211,8 @@ struct KStat {
 
 }  // namespace
 
-struct dmet_emb_plan_s {
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  std::vector<Prob> probs;
-  size_t ws_limit = 0;
-  // workspace
+// Device scratch of one problem (or shared by every problem of a plan run one at a time).
+struct Workspace {
   double2* crep = nullptr;
   double2* T = nullptr;
   double2* Z = nullptr;
@@ -224,8 +220,7 @@ struct dmet_emb_plan_s {
   double* X[2] = {nullptr, nullptr};
   double2* lq_all[2] = {nullptr, nullptr};
   size_t crep_b = 0, T_b = 0, Z_b = 0, S_b = 0, X_b[2] = {0, 0}, lq_all_b[2] = {0, 0};
-  double* dstats = nullptr;  // [n_problems][8]
-  // split-BF16 workspace (shared by all problems of the plan)
+  // split-BF16 operands
   void* Ls = nullptr;
   void* Cb[2] = {nullptr, nullptr};
   void* Cc = nullptr;
@@ -233,12 +228,37 @@ struct dmet_emb_plan_s {
   double* ZT = nullptr;
   void* Xt[2] = {nullptr, nullptr};
   size_t Ls_b = 0, Cb_b[2] = {0, 0}, Cc_b = 0, A2_b = 0, ZT_b = 0, Xt_b[2] = {0, 0};
+};
+
+struct dmet_emb_plan_s {
+  cudaStream_t stream = nullptr;  // the caller's stream
+  int device = 0;
+  std::vector<Prob> probs;
+  size_t ws_limit = 0;
+  // One workspace per problem when they all fit the limit (problems then run concurrently on
+  // the plan's side streams), else one shared workspace (problems run one after another).
+  std::vector<Workspace> ws;
+  std::vector<int> ws_of;          // problem -> workspace
+  std::vector<cudaStream_t> side;  // side streams of the concurrent mode
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  Workspace* W = nullptr;          // workspace of the problem being enqueued
+  cudaStream_t cs = nullptr;       // stream of the problem being enqueued
+  double* dstats = nullptr;        // [n_problems][8]
   unsigned int* derr = nullptr;
   // staging of host buffers
   void* stage_in = nullptr;
   size_t stage_in_b = 0;
   void* stage_out = nullptr;
   size_t stage_out_b = 0;
+  // per-problem device time of the last profiled call
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pev;
+  // CUDA graph of the last device-pointer call (replayed while the pointers stay the same)
+  bool use_graph = false;
+  long long glaunches = 0;  // kernel launches in the captured graph
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<const void*> gkey;
+  cudaStream_t cap = nullptr;
   // profiling
   bool prof = false;
   KStat ks[KC_COUNT];
@@ -341,12 +361,12 @@ struct Timed {
     if (P->prof) {
       a = get_event(P);
       b = get_event(P);
-      if (a) cudaEventRecord(a, P->stream);
+      if (a) cudaEventRecord(a, P->cs);
     }
   }
   ~Timed() {
     if (P->prof && a && b) {
-      cudaEventRecord(b, P->stream);
+      cudaEventRecord(b, P->cs);
       P->ks[kc].ev.emplace_back(a, b);
     }
   }
@@ -391,7 +411,7 @@ dmet_status_t run_orbital_checks(dmet_emb_plan_s* P, Prob& pr, int p, const doub
       ZgemmArgs z = zargs();
       z.A = C[s];
       z.B = C[s];
-      z.D = P->S;
+      z.D = P->W->S;
       z.M = n;
       z.N = n;
       z.K = (pr.nk / ng) * pr.nao;
@@ -403,12 +423,12 @@ dmet_status_t run_orbital_checks(dmet_emb_plan_s* P, Prob& pr, int p, const doub
       z.dm_lo = n;
       z.dn_lo = 1;
       z.batch = ng;
-      CK(launch_zgemm(z, A_KM, true, B_KN, P->stream));
-      CK(launch_orth_reduce(P->S, ng, n, pr.ortho_scale, st + 0, P->stream));
+      CK(launch_zgemm(z, A_KM, true, B_KN, P->cs));
+      CK(launch_orth_reduce(P->W->S, ng, n, pr.ortho_scale, st + 0, P->cs));
     }
     if (pr.d.sym == DMET_SYM_REAL) {
       Timed t(P, KC_CHECK_C, 0.0, 32.0 * pr.nk * pr.nao * n);
-      CK(launch_c_real_check(C[s], pr.d_neg, pr.nk, pr.nao, n, st, P->stream));
+      CK(launch_c_real_check(C[s], pr.d_neg, pr.nk, pr.nao, n, st, P->cs));
     }
   }
   return DMET_OK;
@@ -418,7 +438,7 @@ dmet_status_t run_l_check(dmet_emb_plan_s* P, Prob& pr, int p, const double2* L)
   if (pr.d.sym != DMET_SYM_REAL || !pr.d.check_l) return DMET_OK;
   const double elems = (double)pr.nk * pr.nk * pr.naux * pr.nao * pr.nao;
   Timed t(P, KC_CHECK_L, 0.0, 16.0 * elems);
-  CK(launch_l_check(L, pr.d_neg, pr.nk, pr.naux, pr.nao, P->dstats + 8 * p, P->stream));
+  CK(launch_l_check(L, pr.d_neg, pr.nk, pr.naux, pr.nao, P->dstats + 8 * p, P->cs));
   return DMET_OK;
 }
 
@@ -432,14 +452,14 @@ dmet_status_t run_half_transform(dmet_emb_plan_s* P, Prob& pr, const Tables& tb,
   if (E <= 0) return DMET_OK;
   {
     Timed t(P, KC_GATHER, 0.0, 32.0 * E * nao * n);
-    CK(launch_gather_orbitals(C, P->crep, tb.d_gather, e0, E, nao, n, P->stream));
+    CK(launch_gather_orbitals(C, P->W->crep, tb.d_gather, e0, E, nao, n, P->cs));
   }
   {
     // T_e[mu][P][j] = sum_nu C^{k2}_{nu j} L^{k1,k2}_{P,mu nu}   (k-AO -> k-EO, ket side)
     ZgemmArgs z = zargs();
     z.A = C;
     z.B = L;
-    z.D = P->T;
+    z.D = P->W->T;
     z.tab = tb.d_t1;
     z.tab0 = e0;
     z.M = n;
@@ -456,16 +476,16 @@ dmet_status_t run_half_transform(dmet_emb_plan_s* P, Prob& pr, const Tables& tb,
     z.dn_lo = (long long)naux * n;
     z.batch = E;
     // table entries carry absolute indices; T holds this block's entries only
-    z.D = P->T - (long long)e0 * z.sD;
+    z.D = P->W->T - (long long)e0 * z.sD;
     Timed t(P, KC_TRANSFORM_1, 8.0 * n * (double)naux * nao * nao * E, 0.0);
-    CK(launch_zgemm(z, A_KM, false, B_NK, P->stream));
+    CK(launch_zgemm(z, A_KM, false, B_NK, P->cs));
   }
   {
     // Z_q[P][i][j] = sum_{(r, mu)} w_r conj(C^{k1_r}_{mu i}) T_r[mu][P][j]   (bra side + FT to R=0)
     const bool real = pr.d.sym == DMET_SYM_REAL;
     ZgemmArgs z = zargs();
-    z.A = P->crep - (long long)e0 * nao * n;
-    z.B = P->T - (long long)e0 * nao * naux * n;
+    z.A = P->W->crep - (long long)e0 * nao * n;
+    z.B = P->W->T - (long long)e0 * nao * naux * n;
     z.tab = tb.d_t2;
     z.tab0 = b0;
     z.M = n;
@@ -481,11 +501,11 @@ dmet_status_t run_half_transform(dmet_emb_plan_s* P, Prob& pr, const Tables& tb,
     z.dn_lo = 1;
     z.batch = b1 - b0;
     z.alpha = real ? 1.0 : pr.lq_scale;
-    z.D = (real ? P->Z : dest) - (long long)(real ? b0 : dest_slot0) * z.sD;
+    z.D = (real ? P->W->Z : dest) - (long long)(real ? b0 : dest_slot0) * z.sD;
     double fl = 0;
     for (int i = b0; i < b1; ++i) fl += 8.0 * n * (double)naux * n * tb.t2[i].w;
     Timed t(P, KC_TRANSFORM_2, fl, 0.0);
-    CK(launch_zgemm(z, A_KM, true, B_KN, P->stream));
+    CK(launch_zgemm(z, A_KM, true, B_KN, P->cs));
   }
   return DMET_OK;
 }
@@ -501,7 +521,7 @@ dmet_status_t transform_range(dmet_emb_plan_s* P, Prob& pr, const double2* L, co
       TRY(run_half_transform(P, pr, pr.nat, qa, qb, s, L, C[s], dest, qa));
       if (real) {
         Timed t(P, KC_PACK, 0.0, 32.0 * (qb - qa) * (double)slot);
-        CK(launch_symmetrize(P->Z, dest, qb - qa, pr.naux, pr.n[s], pr.lq_scale, P->stream));
+        CK(launch_symmetrize(P->W->Z, dest, qb - qa, pr.naux, pr.n[s], pr.lq_scale, P->cs));
       }
     }
   }
@@ -516,7 +536,7 @@ dmet_status_t eri_s8(dmet_emb_plan_s* P, Prob& pr, const double2* L, const doubl
       TRY(run_half_transform(P, pr, pr.con, bl.b0, bl.b1, s, L, C[s], nullptr, 0));
       const double elems = (double)nq * pr.naux * pr.n[s] * pr.n[s];
       Timed t(P, KC_PACK, 0.0, 16.0 * elems + 8.0 * nq * pr.naux * nc * (double)pr.npair[s]);
-      CK(launch_pack_pairs(P->Z, P->X[s], nq, pr.naux, pr.n[s], nc, pr.lq_scale, P->stream));
+      CK(launch_pack_pairs(P->W->Z, P->W->X[s], nq, pr.naux, pr.n[s], nc, pr.lq_scale, P->cs));
     }
     const int K = nq * pr.naux * nc;
     const double alpha = (double)bl.w / pr.nk;
@@ -524,8 +544,8 @@ dmet_status_t eri_s8(dmet_emb_plan_s* P, Prob& pr, const double2* L, const doubl
       const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
       DsyrkArgs a;
       std::memset(&a, 0, sizeof(a));
-      a.X = P->X[sa];
-      a.Y = P->X[sb];
+      a.X = P->W->X[sa];
+      a.Y = P->W->X[sb];
       a.out = (double*)out[blk];
       a.M = (int)pr.npair[sa];
       a.N = (int)pr.npair[sb];
@@ -537,14 +557,14 @@ dmet_status_t eri_s8(dmet_emb_plan_s* P, Prob& pr, const double2* L, const doubl
       a.mode = blk == 1 ? 1 : 0;
       const double fl = a.mode == 0 ? (double)a.M * (a.M + 1.0) * K : 2.0 * a.M * (double)a.N * K;
       Timed t(P, KC_CONTRACT, fl, 0.0);
-      CK(launch_dsyrk(a, P->stream));
+      CK(launch_dsyrk(a, P->cs));
     }
   }
   return DMET_OK;
 }
 
 dmet_status_t eri_full(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, void* const* out) {
-  double2* lq[2] = {P->lq_all[0], P->lq_all[1]};
+  double2* lq[2] = {P->W->lq_all[0], P->W->lq_all[1]};
   TRY(transform_range(P, pr, L, C, 0, pr.nk, lq));
   for (int blk = 0; blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
     const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
@@ -565,7 +585,7 @@ dmet_status_t eri_full(dmet_emb_plan_s* P, Prob& pr, const double2* L, const dou
       z.alpha = 1.0 / pr.nk;
       z.beta = 1;
       Timed t(P, KC_CONTRACT_FULL, 8.0 * (double)na2 * nb2 * pr.naux, 0.0);
-      CK(launch_zgemm(z, A_KM, false, B_KN, P->stream));
+      CK(launch_zgemm(z, A_KM, false, B_KN, P->cs));
     }
   }
   return DMET_OK;
@@ -632,10 +652,18 @@ void free_tables(Tables& t) {
   t.d_t1 = t.d_t2 = t.d_gather = nullptr;
 }
 
+void free_workspace(Workspace& w) {
+  void* ptrs[] = {w.crep, w.T, w.Z, w.S, w.X[0], w.X[1], w.lq_all[0], w.lq_all[1],
+                  w.Ls, w.Cb[0], w.Cb[1], w.Cc, w.A2, w.ZT, w.Xt[0], w.Xt[1]};
+  for (void* q : ptrs) cudaFree(q);
+  w = Workspace();
+}
+
 void destroy_plan(dmet_emb_plan_s* P) {
   if (!P) return;
   if (P->stream) cudaStreamSynchronize(P->stream);
   else cudaDeviceSynchronize();
+  for (cudaStream_t st : P->side) cudaStreamSynchronize(st);
   for (auto& pr : P->probs) {
     free_tables(pr.nat);
     free_tables(pr.con);
@@ -643,26 +671,20 @@ void destroy_plan(dmet_emb_plan_s* P) {
     cudaFree(pr.mx.d_jobs);
     cudaFree(pr.mx.d_segs);
   }
-  cudaFree(P->Ls);
-  cudaFree(P->Cc);
-  cudaFree(P->A2);
-  cudaFree(P->ZT);
+  for (auto& w : P->ws) free_workspace(w);
   cudaFree(P->derr);
-  for (int s = 0; s < 2; ++s) {
-    cudaFree(P->Cb[s]);
-    cudaFree(P->Xt[s]);
-  }
-  cudaFree(P->crep);
-  cudaFree(P->T);
-  cudaFree(P->Z);
-  cudaFree(P->S);
-  for (int s = 0; s < 2; ++s) {
-    cudaFree(P->X[s]);
-    cudaFree(P->lq_all[s]);
-  }
   cudaFree(P->dstats);
   cudaFree(P->stage_in);
   cudaFree(P->stage_out);
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  for (cudaStream_t st : P->side) cudaStreamDestroy(st);
+  if (P->cap) cudaStreamDestroy(P->cap);
+  if (P->fork) cudaEventDestroy(P->fork);
+  for (auto e : P->join) cudaEventDestroy(e);
+  for (auto& e : P->pev) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
   for (auto& k : P->ks)
     for (auto& e : k.ev) {
       cudaEventDestroy(e.first);
@@ -838,13 +860,13 @@ dmet_status_t mixed_maps(dmet_emb_plan_s* P, const Prob& pr, MixedMaps& mm) {
   const int BK = mixed_kblock(), T = tc::kTile;
   const long long nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
   const long long cc_rows = (long long)pr.bq * 2 * nmax, a2_rows = (long long)pr.bq * pr.naux * nmax;
-  CK(make_tmap_bf16_3d(&mm.Ls, P->Ls, m.K1, m.Ls_rows, 3, m.K1, m.Ls_rows * m.K1, BK, T));
+  CK(make_tmap_bf16_3d(&mm.Ls, P->W->Ls, m.K1, m.Ls_rows, 3, m.K1, m.Ls_rows * m.K1, BK, T));
   for (int s = 0; s < pr.nspin; ++s) {
     const long long n = pr.n[s];
-    CK(make_tmap_bf16_3d(&mm.Cb[s], P->Cb[s], m.K1, pr.nk * 2 * n, 3, m.K1, pr.nk * 2 * n * m.K1, BK, T));
-    CK(make_tmap_bf16_3d(&mm.Cc[s], P->Cc, m.K2, (long long)pr.bq * 2 * n, 3, m.K2, cc_rows * m.K2, BK, T));
-    CK(make_tmap_bf16_3d(&mm.A2[s], P->A2, m.K2, (long long)pr.bq * pr.naux * n, 3, m.K2, a2_rows * m.K2, BK, T));
-    CK(make_tmap_bf16_3d(&mm.Xt[s], P->Xt[s], m.Rtot, pr.npair[s], 3, m.Rtot, pr.npair[s] * m.Rtot, BK, T));
+    CK(make_tmap_bf16_3d(&mm.Cb[s], P->W->Cb[s], m.K1, pr.nk * 2 * n, 3, m.K1, pr.nk * 2 * n * m.K1, BK, T));
+    CK(make_tmap_bf16_3d(&mm.Cc[s], P->W->Cc, m.K2, (long long)pr.bq * 2 * n, 3, m.K2, cc_rows * m.K2, BK, T));
+    CK(make_tmap_bf16_3d(&mm.A2[s], P->W->A2, m.K2, (long long)pr.bq * pr.naux * n, 3, m.K2, a2_rows * m.K2, BK, T));
+    CK(make_tmap_bf16_3d(&mm.Xt[s], P->W->Xt[s], m.Rtot, pr.npair[s], 3, m.Rtot, pr.npair[s] * m.Rtot, BK, T));
   }
   return DMET_OK;
 }
@@ -863,13 +885,13 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
     const size_t pitch = (size_t)m.Rtot * 2;
     const long long h = 3 * pr.npair[s];
     if (m.R1 > used1)
-      CK(cudaMemset2DAsync((char*)P->Xt[s] + used1 * 2, pitch, 0, (size_t)(m.R1 - used1) * 2, h, P->stream));
+      CK(cudaMemset2DAsync((char*)P->W->Xt[s] + used1 * 2, pitch, 0, (size_t)(m.R1 - used1) * 2, h, P->cs));
     if (m.Rtot - m.R1 > used2)
-      CK(cudaMemset2DAsync((char*)P->Xt[s] + (m.R1 + used2) * 2, pitch, 0, (size_t)(m.Rtot - m.R1 - used2) * 2, h,
-                           P->stream));
+      CK(cudaMemset2DAsync((char*)P->W->Xt[s] + (m.R1 + used2) * 2, pitch, 0, (size_t)(m.Rtot - m.R1 - used2) * 2, h,
+                           P->cs));
     Timed t(P, KC_SPLIT, 0.0, 16.0 * pr.nk * pr.nao * pr.n[s] + 6.0 * pr.nk * 2 * pr.n[s] * m.K1);
-    CK(launch_build_Cb(C[s], pr.nk, pr.nao, pr.n[s], m.K1, P->Cb[s], (long long)pr.nk * 2 * pr.n[s] * m.K1,
-                       P->stream));
+    CK(launch_build_Cb(C[s], pr.nk, pr.nao, pr.n[s], m.K1, P->W->Cb[s], (long long)pr.nk * 2 * pr.n[s] * m.K1,
+                       P->cs));
   }
   for (size_t bi = 0; bi < m.blocks.size(); ++bi) {
     const Block& bl = m.blocks[bi];
@@ -877,33 +899,33 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
     {
       const double rows = (double)E * pr.naux * pr.nao;
       Timed t(P, KC_SPLIT, 0.0, rows * (16.0 * pr.nao + 6.0 * m.K1));
-      CK(launch_split_L(L, pr.con.d_t1, e0, E, pr.nk, pr.naux, pr.nao, m.K1, P->Ls, m.Ls_rows * m.K1, P->stream));
+      CK(launch_split_L(L, pr.con.d_t1, e0, E, pr.nk, pr.naux, pr.nao, m.K1, P->W->Ls, m.Ls_rows * m.K1, P->cs));
     }
     for (int s = 0; s < pr.nspin; ++s) {
       const int n = pr.n[s];
       {
         Timed t(P, KC_SPLIT, 0.0, 6.0 * nq * 2 * n * m.K2);
-        CK(launch_build_Cc(C[s], pr.con.d_gather, pr.con.d_t2, bl.b0, nq, pr.nao, n, m.K2, P->Cc, cc_rows * m.K2,
-                           P->stream));
+        CK(launch_build_Cc(C[s], pr.con.d_gather, pr.con.d_t2, bl.b0, nq, pr.nao, n, m.K2, P->W->Cc, cc_rows * m.K2,
+                           P->cs));
       }
       {
         Timed t(P, KC_TC_TRANSFORM_1, 8.0 * n * (double)pr.naux * pr.nao * pr.nao * E, 0.0, 1,
                 exec_flops(m, m.j1_off[s][bi], m.j1_cnt[s][bi]));
-        CK(launch_tc_split_t(mm.Ls, mm.Cb[s], m.d_jobs + m.j1_off[s][bi], m.j1_cnt[s][bi], m.d_segs, P->A2,
-                             a2_rows * m.K2, m.K2, pr.nao, n, P->derr, P->stream));
+        CK(launch_tc_split_t(mm.Ls, mm.Cb[s], m.d_jobs + m.j1_off[s][bi], m.j1_cnt[s][bi], m.d_segs, P->W->A2,
+                             a2_rows * m.K2, m.K2, pr.nao, n, P->derr, P->cs));
       }
       {
         double fl = 0;
         for (int i = bl.b0; i < bl.b1; ++i) fl += 8.0 * n * (double)pr.naux * n * pr.con.t2[i].w;
         Timed t(P, KC_TC_TRANSFORM_2, fl, 0.0, 1, exec_flops(m, m.j2_off[s][bi], m.j2_cnt[s][bi]));
-        CK(launch_tc_pairs(mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs, P->ZT, 2LL * n,
-                           P->derr, P->stream));
+        CK(launch_tc_pairs(mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs, P->W->ZT, 2LL * n,
+                           P->derr, P->cs));
       }
       {
         const int nc = bl.w == 1 ? 1 : 2;
         Timed t(P, KC_TC_PACK, 0.0, 16.0 * nq * pr.naux * (double)n * n + 6.0 * nq * pr.naux * nc * pr.npair[s]);
-        CK(launch_pack_split(P->ZT, nq, pr.naux, n, nc, P->Xt[s], pr.npair[s] * m.Rtot, m.Rtot, m.row_base[bi],
-                             P->stream));
+        CK(launch_pack_split(P->W->ZT, nq, pr.naux, n, nc, P->W->Xt[s], pr.npair[s] * m.Rtot, m.Rtot, m.row_base[bi],
+                             P->cs));
       }
     }
   }
@@ -918,10 +940,10 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
     Timed t(P, KC_TC_CONTRACT, fl, 0.0, 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk]));
     if (blk == 1)
       CK(launch_tc_rect(mm.Xt[0], mm.Xt[1], m.d_jobs + m.jc_off[1], m.jc_cnt[1], m.d_segs, (double*)out[1],
-                        pr.npair[1], oscale, P->derr, P->stream));
+                        pr.npair[1], oscale, P->derr, P->cs));
     else
       CK(launch_tc_packed(mm.Xt[sa], mm.Xt[sa], m.d_jobs + m.jc_off[blk], m.jc_cnt[blk], m.d_segs, (double*)out[blk],
-                          oscale, P->derr, P->stream));
+                          oscale, P->derr, P->cs));
   }
   return DMET_OK;
 }
@@ -977,10 +999,8 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
   cudaGetDevice(&P->device);
   P->ws_limit = workspace_limit ? workspace_limit : ((size_t)8 << 30);
   P->probs.resize(n_problems);
-  WsSizes need;
-  std::memset(&need, 0, sizeof(need));
-  MixedWs mneed;
-  std::memset(&mneed, 0, sizeof(mneed));
+  std::vector<WsSizes> wneed(n_problems);
+  std::vector<MixedWs> mneed(n_problems);
   for (int p = 0; p < n_problems; ++p) {
     Prob& pr = P->probs[p];
     pr.d = descs[p];
@@ -1038,52 +1058,89 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     WsSizes w = ws_for(pr, bq);
     pr.bq = bq;
     if (pr.pack == DMET_PACK_S8) partition(pr, pr.con, wts, bq, pr.con_blocks);
+    std::memset(&mneed[p], 0, sizeof(MixedWs));
     if (pr.mixed) {
       build_mixed(pr);
-      const MixedWs mw = mixed_ws(pr);
-      mneed.Ls = std::max(mneed.Ls, mw.Ls);
-      mneed.Cc = std::max(mneed.Cc, mw.Cc);
-      mneed.A2 = std::max(mneed.A2, mw.A2);
-      mneed.ZT = std::max(mneed.ZT, mw.ZT);
-      for (int s = 0; s < 2; ++s) {
-        mneed.Cb[s] = std::max(mneed.Cb[s], mw.Cb[s]);
-        mneed.Xt[s] = std::max(mneed.Xt[s], mw.Xt[s]);
-      }
+      mneed[p] = mixed_ws(pr);
     }
-    need.crep = std::max(need.crep, w.crep);
-    need.T = std::max(need.T, w.T);
-    need.Z = std::max(need.Z, w.Z);
-    need.S = std::max(need.S, w.S);
+    wneed[p] = w;
+  }
+  // Workspace: one per problem if they all fit (concurrent problems), else one shared.
+  size_t sum_all = 0;
+  for (int p = 0; p < n_problems; ++p) sum_all += wneed[p].total() + mixed_total(mneed[p]);
+  const bool concurrent = n_problems > 1 && sum_all <= P->ws_limit;
+  P->ws.resize(concurrent ? n_problems : 1);
+  P->ws_of.assign(n_problems, 0);
+  std::vector<WsSizes> wsz(P->ws.size());
+  std::vector<MixedWs> msz(P->ws.size());
+  for (size_t i = 0; i < P->ws.size(); ++i) {
+    std::memset(&wsz[i], 0, sizeof(WsSizes));
+    std::memset(&msz[i], 0, sizeof(MixedWs));
+  }
+  for (int p = 0; p < n_problems; ++p) {
+    const int i = concurrent ? p : 0;
+    P->ws_of[p] = i;
+    WsSizes& a = wsz[i];
+    const WsSizes& b = wneed[p];
+    a.crep = std::max(a.crep, b.crep);
+    a.T = std::max(a.T, b.T);
+    a.Z = std::max(a.Z, b.Z);
+    a.S = std::max(a.S, b.S);
+    MixedWs& c = msz[i];
+    const MixedWs& d = mneed[p];
+    c.Ls = std::max(c.Ls, d.Ls);
+    c.Cc = std::max(c.Cc, d.Cc);
+    c.A2 = std::max(c.A2, d.A2);
+    c.ZT = std::max(c.ZT, d.ZT);
     for (int s = 0; s < 2; ++s) {
-      need.X[s] = std::max(need.X[s], w.X[s]);
-      need.lq_all[s] = std::max(need.lq_all[s], w.lq_all[s]);
+      a.X[s] = std::max(a.X[s], b.X[s]);
+      a.lq_all[s] = std::max(a.lq_all[s], b.lq_all[s]);
+      c.Cb[s] = std::max(c.Cb[s], d.Cb[s]);
+      c.Xt[s] = std::max(c.Xt[s], d.Xt[s]);
     }
   }
   dmet_status_t st = DMET_OK;
   auto alloc = [&](void** ptr, size_t* have, size_t bytes) {
     if (st == DMET_OK && bytes) st = ensure(ptr, have, bytes);
   };
-  alloc((void**)&P->crep, &P->crep_b, need.crep);
-  alloc((void**)&P->T, &P->T_b, need.T);
-  alloc((void**)&P->Z, &P->Z_b, need.Z);
-  alloc((void**)&P->S, &P->S_b, need.S);
-  for (int s = 0; s < 2; ++s) {
-    alloc((void**)&P->X[s], &P->X_b[s], need.X[s]);
-    alloc((void**)&P->lq_all[s], &P->lq_all_b[s], need.lq_all[s]);
+  for (size_t i = 0; i < P->ws.size(); ++i) {
+    Workspace& W = P->ws[i];
+    const WsSizes& need = wsz[i];
+    const MixedWs& mn = msz[i];
+    alloc((void**)&W.crep, &W.crep_b, need.crep);
+    alloc((void**)&W.T, &W.T_b, need.T);
+    alloc((void**)&W.Z, &W.Z_b, need.Z);
+    alloc((void**)&W.S, &W.S_b, need.S);
+    for (int s = 0; s < 2; ++s) {
+      alloc((void**)&W.X[s], &W.X_b[s], need.X[s]);
+      alloc((void**)&W.lq_all[s], &W.lq_all_b[s], need.lq_all[s]);
+    }
+    alloc(&W.Ls, &W.Ls_b, mn.Ls);
+    alloc(&W.Cc, &W.Cc_b, mn.Cc);
+    alloc(&W.A2, &W.A2_b, mn.A2);
+    alloc((void**)&W.ZT, &W.ZT_b, mn.ZT);
+    for (int s = 0; s < 2; ++s) {
+      alloc(&W.Cb[s], &W.Cb_b[s], mn.Cb[s]);
+      alloc(&W.Xt[s], &W.Xt_b[s], mn.Xt[s]);
+    }
+    // The split-BF16 operands are read in whole K blocks: whatever a call does not write
+    // must hold finite values, so they start at zero.
+    if (st == DMET_OK && W.A2 && cudaMemset(W.A2, 0, W.A2_b) != cudaSuccess) st = fail(DMET_ERR_CUDA, "memset");
+    for (int s = 0; s < 2; ++s)
+      if (st == DMET_OK && W.Xt[s] && cudaMemset(W.Xt[s], 0, W.Xt_b[s]) != cudaSuccess)
+        st = fail(DMET_ERR_CUDA, "memset");
   }
-  alloc(&P->Ls, &P->Ls_b, mneed.Ls);
-  alloc(&P->Cc, &P->Cc_b, mneed.Cc);
-  alloc(&P->A2, &P->A2_b, mneed.A2);
-  alloc((void**)&P->ZT, &P->ZT_b, mneed.ZT);
-  for (int s = 0; s < 2; ++s) {
-    alloc(&P->Cb[s], &P->Cb_b[s], mneed.Cb[s]);
-    alloc(&P->Xt[s], &P->Xt_b[s], mneed.Xt[s]);
+  if (st == DMET_OK && concurrent) {
+    const int nside = std::min(n_problems, 8);
+    P->side.assign(nside, nullptr);
+    P->join.assign(nside, nullptr);
+    for (int i = 0; st == DMET_OK && i < nside; ++i)
+      if (cudaStreamCreateWithFlags(&P->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&P->join[i], cudaEventDisableTiming) != cudaSuccess)
+        st = fail(DMET_ERR_CUDA, "side stream creation failed");
+    if (st == DMET_OK && cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming) != cudaSuccess)
+      st = fail(DMET_ERR_CUDA, "event creation failed");
   }
-  // The split-BF16 operands are read in whole K blocks: whatever a call does not write
-  // must hold finite values, so they start at zero.
-  if (st == DMET_OK && P->A2 && cudaMemset(P->A2, 0, P->A2_b) != cudaSuccess) st = fail(DMET_ERR_CUDA, "memset");
-  for (int s = 0; s < 2; ++s)
-    if (st == DMET_OK && P->Xt[s] && cudaMemset(P->Xt[s], 0, P->Xt_b[s]) != cudaSuccess) st = fail(DMET_ERR_CUDA, "memset");
   if (st == DMET_OK && cudaMalloc(&P->derr, sizeof(unsigned int)) != cudaSuccess) {
     cudaGetLastError();
     st = fail(DMET_ERR_OOM, "error word allocation failed");
@@ -1154,7 +1211,7 @@ static dmet_status_t stage_inputs(dmet_emb_plan_s* P, const Prob& pr, const void
   if (L) *Ld = (const double2*)L;
   if (lhost) {
     Timed t(P, KC_COPY, 0.0, (double)lb);
-    CK(cudaMemcpyAsync(cur, L, lb, cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(cur, L, lb, cudaMemcpyHostToDevice, P->cs));
     *Ld = (const double2*)cur;
     cur += lb;
   }
@@ -1162,7 +1219,7 @@ static dmet_status_t stage_inputs(dmet_emb_plan_s* P, const Prob& pr, const void
     Cd[s] = (const double2*)C[s];
     if (chost[s]) {
       Timed t(P, KC_COPY, 0.0, (double)cb[s]);
-      CK(cudaMemcpyAsync(cur, C[s], cb[s], cudaMemcpyHostToDevice, P->stream));
+      CK(cudaMemcpyAsync(cur, C[s], cb[s], cudaMemcpyHostToDevice, P->cs));
       Cd[s] = (const double2*)cur;
       cur += cb[s];
     }
@@ -1184,10 +1241,12 @@ dmet_status_t dmet_emb_transform_3idx(dmet_emb_plan_t P, int32_t problem, const 
     if (!aligned16(C[s]) || !aligned16(Lq_out[s])) return fail(DMET_ERR_ALIGNMENT, "spin %d pointer not 16-byte aligned", s);
   }
   if (q_begin == q_end) return DMET_OK;
+  P->cs = P->stream;
+  P->W = &P->ws[P->ws_of[problem]];
   const double2* Ld = nullptr;
   const double2* Cd[2] = {nullptr, nullptr};
   TRY(stage_inputs(P, pr, L, C, &Ld, Cd));
-  CK(cudaMemsetAsync(P->dstats + 8 * problem, 0, 8 * sizeof(double), P->stream));
+  CK(cudaMemsetAsync(P->dstats + 8 * problem, 0, 8 * sizeof(double), P->cs));
   TRY(run_orbital_checks(P, pr, problem, Cd));
   TRY(run_l_check(P, pr, problem, Ld));
   double2* out[2] = {nullptr, nullptr};
@@ -1213,11 +1272,89 @@ dmet_status_t dmet_emb_transform_3idx(dmet_emb_plan_t P, int32_t problem, const 
     for (int s = 0; s < pr.nspin; ++s)
       if (ohost[s]) {
         Timed t(P, KC_COPY, 0.0, (double)ob[s]);
-        CK(cudaMemcpyAsync(Lq_out[s], out[s], ob[s], cudaMemcpyDeviceToHost, P->stream));
+        CK(cudaMemcpyAsync(Lq_out[s], out[s], ob[s], cudaMemcpyDeviceToHost, P->cs));
       }
-    CK(cudaStreamSynchronize(P->stream));
+    CK(cudaStreamSynchronize(P->cs));
   }
   CK(cudaGetLastError());
+  return DMET_OK;
+}
+
+// Queues problem p on P->cs with workspace P->W (Algorithm 1 for that problem).
+static dmet_status_t enqueue_problem(dmet_emb_plan_s* P, int p, const void* L, const void* const* C,
+                                     void* const* eri_out) {
+  Prob& pr = P->probs[p];
+  if (P->prof) {
+    if ((int)P->pev.size() < (int)P->probs.size()) P->pev.resize(P->probs.size(), {nullptr, nullptr});
+    for (cudaEvent_t* e : {&P->pev[p].first, &P->pev[p].second})
+      if (!*e) CK(cudaEventCreate(e));
+    CK(cudaEventRecord(P->pev[p].first, P->cs));
+  }
+  const double2* Ld = nullptr;
+  const double2* Cd[2] = {nullptr, nullptr};
+  TRY(stage_inputs(P, pr, L, C, &Ld, Cd));
+  CK(cudaMemsetAsync(P->dstats + 8 * p, 0, 8 * sizeof(double), P->cs));
+  TRY(run_orbital_checks(P, pr, p, Cd));
+  TRY(run_l_check(P, pr, p, Ld));
+  const int nblk = pr.nspin == 1 ? 1 : 3;
+  void* out[3] = {nullptr, nullptr, nullptr};
+  size_t ob[3] = {0, 0, 0}, need = 0;
+  bool ohost[3] = {false, false, false};
+  for (int b = 0; b < nblk; ++b) {
+    ob[b] = eri_bytes_of(pr.d, b);
+    ohost[b] = !is_device_ptr(eri_out[b]);
+    if (ohost[b]) need += ob[b];
+    out[b] = eri_out[b];
+  }
+  if (need) {
+    TRY(ensure(&P->stage_out, &P->stage_out_b, need));
+    char* cur = (char*)P->stage_out;
+    for (int b = 0; b < nblk; ++b)
+      if (ohost[b]) {
+        out[b] = cur;
+        cur += ob[b];
+      }
+  }
+  for (int b = 0; b < nblk; ++b) CK(cudaMemsetAsync(out[b], 0, ob[b], P->cs));
+  if (pr.mixed) TRY(eri_mixed(P, pr, Ld, Cd, out));
+  else if (pr.pack == DMET_PACK_S8) TRY(eri_s8(P, pr, Ld, Cd, out));
+  else TRY(eri_full(P, pr, Ld, Cd, out));
+  if (need) {
+    for (int b = 0; b < nblk; ++b)
+      if (ohost[b]) {
+        Timed t(P, KC_COPY, 0.0, (double)ob[b]);
+        CK(cudaMemcpyAsync(eri_out[b], out[b], ob[b], cudaMemcpyDeviceToHost, P->cs));
+      }
+  }
+  if (P->prof) CK(cudaEventRecord(P->pev[p].second, P->cs));
+  return DMET_OK;
+}
+
+// Queues every problem behind `origin`: concurrently on the side streams (fork/join) when each
+// problem has its own workspace and no host staging is needed, else one after another.
+static dmet_status_t enqueue_all(dmet_emb_plan_s* P, cudaStream_t origin, bool staged, const void* const* L,
+                                 const void* const* const* C, void* const* const* eri_out) {
+  const int np = (int)P->probs.size();
+  if (!staged && !P->side.empty()) {
+    const int ns = (int)P->side.size();
+    CK(cudaEventRecord(P->fork, origin));
+    for (int i = 0; i < ns; ++i) CK(cudaStreamWaitEvent(P->side[i], P->fork, 0));
+    for (int p = 0; p < np; ++p) {
+      P->cs = P->side[p % ns];
+      P->W = &P->ws[P->ws_of[p]];
+      TRY(enqueue_problem(P, p, L[p], C[p], eri_out[p]));
+    }
+    for (int i = 0; i < ns; ++i) {
+      CK(cudaEventRecord(P->join[i], P->side[i]));
+      CK(cudaStreamWaitEvent(origin, P->join[i], 0));
+    }
+    return DMET_OK;
+  }
+  for (int p = 0; p < np; ++p) {
+    P->cs = origin;
+    P->W = &P->ws[P->ws_of[p]];
+    TRY(enqueue_problem(P, p, L[p], C[p], eri_out[p]));
+  }
   return DMET_OK;
 }
 
@@ -1227,60 +1364,88 @@ dmet_status_t dmet_emb_eri(dmet_emb_plan_t P, const void* const* L, const void* 
   if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
   if (!L || !C || !eri_out) return fail(DMET_ERR_INVALID_ARG, "NULL pointer argument");
   const int np = (int)P->probs.size();
+  bool staged = false;
+  std::vector<const void*> key;
   for (int p = 0; p < np; ++p) {
     const Prob& pr = P->probs[p];
     if (!L[p] || !C[p] || !eri_out[p]) return fail(DMET_ERR_INVALID_ARG, "problem %d: NULL pointer", p);
     if (!aligned16(L[p])) return fail(DMET_ERR_ALIGNMENT, "problem %d: L not 16-byte aligned", p);
+    staged |= !is_device_ptr(L[p]);
+    key.push_back(L[p]);
     for (int s = 0; s < pr.nspin; ++s) {
       if (!C[p][s]) return fail(DMET_ERR_INVALID_ARG, "problem %d: C[%d] is NULL", p, s);
       if (!aligned16(C[p][s])) return fail(DMET_ERR_ALIGNMENT, "problem %d: C[%d] not 16-byte aligned", p, s);
+      staged |= !is_device_ptr(C[p][s]);
+      key.push_back(C[p][s]);
     }
     for (int b = 0; b < (pr.nspin == 1 ? 1 : 3); ++b) {
       if (!eri_out[p][b]) return fail(DMET_ERR_INVALID_ARG, "problem %d: eri_out[%d] is NULL", p, b);
       if (!aligned16(eri_out[p][b])) return fail(DMET_ERR_ALIGNMENT, "problem %d: eri_out[%d] not 16-byte aligned", p, b);
+      staged |= !is_device_ptr(eri_out[p][b]);
+      key.push_back(eri_out[p][b]);
     }
   }
-  for (int p = 0; p < np; ++p) {
-    Prob& pr = P->probs[p];
-    const double2* Ld = nullptr;
-    const double2* Cd[2] = {nullptr, nullptr};
-    TRY(stage_inputs(P, pr, L[p], C[p], &Ld, Cd));
-    CK(cudaMemsetAsync(P->dstats + 8 * p, 0, 8 * sizeof(double), P->stream));
-    TRY(run_orbital_checks(P, pr, p, Cd));
-    TRY(run_l_check(P, pr, p, Ld));
-    const int nblk = pr.nspin == 1 ? 1 : 3;
-    void* out[3] = {nullptr, nullptr, nullptr};
-    size_t ob[3] = {0, 0, 0}, need = 0;
-    bool ohost[3] = {false, false, false};
-    for (int b = 0; b < nblk; ++b) {
-      ob[b] = eri_bytes_of(pr.d, b);
-      ohost[b] = !is_device_ptr(eri_out[p][b]);
-      if (ohost[b]) need += ob[b];
-      out[b] = eri_out[p][b];
+  if (!staged && P->use_graph && !P->prof) {
+    // Replay the captured graph while the buffers are the same; otherwise capture anew.
+    if (!(P->gexec && key == P->gkey)) {
+      if (P->gexec) {
+        CK(cudaGraphExecDestroy(P->gexec));
+        P->gexec = nullptr;
+      }
+      if (!P->cap) CK(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
+      const long long l0 = P->launches;
+      CK(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
+      const dmet_status_t st = enqueue_all(P, P->cap, false, L, C, eri_out);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(P->cap, &g);
+      if (st != DMET_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return fail(DMET_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+      const cudaError_t ei = cudaGraphInstantiate(&P->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess) {
+        P->gexec = nullptr;
+        return fail(DMET_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(ei));
+      }
+      P->gkey = key;
+      P->glaunches = P->launches - l0;
+      P->launches = l0;
     }
-    if (need) {
-      TRY(ensure(&P->stage_out, &P->stage_out_b, need));
-      char* cur = (char*)P->stage_out;
-      for (int b = 0; b < nblk; ++b)
-        if (ohost[b]) {
-          out[b] = cur;
-          cur += ob[b];
-        }
-    }
-    for (int b = 0; b < nblk; ++b) CK(cudaMemsetAsync(out[b], 0, ob[b], P->stream));
-    if (pr.mixed) TRY(eri_mixed(P, pr, Ld, Cd, out));
-    else if (pr.pack == DMET_PACK_S8) TRY(eri_s8(P, pr, Ld, Cd, out));
-    else TRY(eri_full(P, pr, Ld, Cd, out));
-    if (need) {
-      for (int b = 0; b < nblk; ++b)
-        if (ohost[b]) {
-          Timed t(P, KC_COPY, 0.0, (double)ob[b]);
-          CK(cudaMemcpyAsync(eri_out[p][b], out[b], ob[b], cudaMemcpyDeviceToHost, P->stream));
-        }
-      CK(cudaStreamSynchronize(P->stream));
-    }
+    CK(cudaGraphLaunch(P->gexec, P->stream));
+    P->launches += P->glaunches;
+    return DMET_OK;
   }
+  TRY(enqueue_all(P, P->stream, staged, L, C, eri_out));
+  if (staged) CK(cudaStreamSynchronize(P->stream));
   CK(cudaGetLastError());
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_graph(dmet_emb_plan_t P, int32_t enable) {
+  clear_error();
+  if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
+  P->use_graph = enable != 0;
+  if (!P->use_graph && P->gexec) {
+    CK(cudaStreamSynchronize(P->stream));
+    CK(cudaGraphExecDestroy(P->gexec));
+    P->gexec = nullptr;
+    P->gkey.clear();
+  }
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_problem_ms(dmet_emb_plan_t P, int32_t problem, double* ms) {
+  clear_error();
+  if (!P || !ms) return fail(DMET_ERR_INVALID_ARG, "NULL argument");
+  if (problem < 0 || problem >= (int)P->probs.size()) return fail(DMET_ERR_INVALID_ARG, "problem %d", problem);
+  if (problem >= (int)P->pev.size() || !P->pev[problem].first)
+    return fail(DMET_ERR_INVALID_ARG, "problem %d has no profiled call", problem);
+  CK(cudaStreamSynchronize(P->stream));
+  float t = 0;
+  CK(cudaEventElapsedTime(&t, P->pev[problem].first, P->pev[problem].second));
+  *ms = t;
   return DMET_OK;
 }
 

@@ -69,6 +69,27 @@ CONFIGS = {
 }
 
 
+# Meshes of the batched workload (Nk = 8, 27, 36, 64).
+BATCH_MESHES = {8: (2, 2, 2), 27: (3, 3, 3), 36: (6, 6, 1), 64: (4, 4, 4)}
+
+
+def batch_specs(n_problems: int = 48, seed: int = 4000, n_ao_range=(6, 12), n_emb_range=(16, 48),
+                decay: float = 0.7):
+    """Seeded list of uneven embedding problems: Nk drawn from {8, 27, 36, 64}, n_AO uniform in
+    n_ao_range, n_aux = floor(8.5 n_AO + 1/2), n_emb uniform in n_emb_range (capped at Nk n_AO),
+    every other problem unrestricted."""
+    rng = np.random.Generator(np.random.Philox(key=[seed, 5 << 40]))
+    out = []
+    for p in range(n_problems):
+        nk = int(rng.choice([8, 27, 36, 64]))
+        nao = int(rng.integers(n_ao_range[0], n_ao_range[1] + 1))
+        naux = int(math.floor(8.5 * nao + 0.5))
+        n = int(rng.integers(n_emb_range[0], min(n_emb_range[1], nk * nao) + 1))
+        out.append(LatticeSpec(BATCH_MESHES[nk], nao, naux, n, 1 + (p % 2), decay, 0.0, seed * 100 + p,
+                               f"batch{n_problems}_{p}"))
+    return out
+
+
 def cell_vectors(mesh) -> np.ndarray:
     """Integer cell vectors m = (m1, m2, m3) in C order, shape (Nk, 3)."""
     n1, n2, n3 = mesh
