@@ -203,6 +203,11 @@ def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
     nblk = 1 if spec.n_spin == 1 else 3
     outs = [torch.empty(dm.dmet_emb_eri_bytes(desc, b) // 8, dtype=torch.float64, device="cuda") for b in range(nblk)]
     plan = dm.dmet_emb_plan(desc, stream=stream.cuda_stream)
+    tile_widths = None
+    if prec != "fp64" and not args.no_autotune:
+        # Tile widths of the transform GEMMs chosen by timing (outside the timed region).
+        dm.dmet_emb_autotune(plan, [Ld], [Cd], [outs])
+        tile_widths = dm.dmet_emb_tile_widths(plan, 0)
 
     def step():
         dm.dmet_emb_eri(plan, [Ld], [Cd], [outs])
@@ -284,6 +289,7 @@ def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
         "value": value, "ms_per_step": ms_step, "useful_tflop_per_problem": fl_total / 1e12,
         "useful_split": {"transform": fl_t / 1e12, "contraction": fl_c / 1e12},
         "roofline": roof, "kernels": kernels, "gpu_launches": int(launches), "clocks": clk, "steps": steps,
+        "tile_widths": tile_widths,
         "e2e": {"value": world * fl_total / e2e_s / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": int(Lh.numel() * 16 + sum(c.numel() * 16 for c in Ch)),
                 "d2h_bytes_per_step": int(sum(o.numel() * 8 for o in Oh)), "ms_per_step": e2e_s * 1e3,
@@ -377,6 +383,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -424,6 +431,7 @@ def main():
         "clocks": head["clocks"],
         "e2e": head["e2e"],
         "device_checks": head["device_checks"],
+        "tile_widths": head.get("tile_widths"),
     }
     for p in precs[1:]:
         r = res[p]

@@ -177,6 +177,19 @@ DMET_API dmet_status_t dmet_emb_graph(dmet_emb_plan_t plan, int32_t enable);
  * (CUDA events around that problem's work on its stream). Waits for the stream. */
 DMET_API dmet_status_t dmet_emb_problem_ms(dmet_emb_plan_t plan, int32_t problem, double* ms);
 
+/* Autotuner of the split-BF16 path: for every problem it times the two transform GEMMs'
+ * output tile widths (128, 112 and 96 columns; the width that wastes least on the problem's
+ * 2 n_emb output columns is not always the fastest) by running dmet_emb_eri on the given
+ * buffers (device pointers; the outputs are overwritten with valid results), keeps the
+ * fastest for each problem and, if the environment variable DMET_TUNE_CACHE names a file,
+ * appends the choice there; dmet_emb_plan reads that file for later plans of the same shape.
+ * A captured graph is discarded. No counterpart in the paper (it is a GPU tiling choice). */
+DMET_API dmet_status_t dmet_emb_autotune(dmet_emb_plan_t plan, const void* const* L, const void* const* const* C,
+                                         void* const* const* eri_out);
+
+/* The tile widths in use for `problem`: bn[0] (half transform 1), bn[1] (half transform 2). */
+DMET_API dmet_status_t dmet_emb_tile_widths(dmet_emb_plan_t plan, int32_t problem, int32_t* bn);
+
 /* Per-kernel timing with CUDA events on the plan's stream. enable != 0 starts recording
  * (and clears the counters); 0 stops. */
 DMET_API dmet_status_t dmet_emb_profile(dmet_emb_plan_t plan, int32_t enable);

@@ -118,6 +118,11 @@ def lib() -> ctypes.CDLL:
         L.dmet_emb_graph.restype = st
         L.dmet_emb_problem_ms.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
         L.dmet_emb_problem_ms.restype = st
+        L.dmet_emb_autotune.argtypes = [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.POINTER(_P)),
+                                        ctypes.POINTER(ctypes.POINTER(_P))]
+        L.dmet_emb_autotune.restype = st
+        L.dmet_emb_tile_widths.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.dmet_emb_tile_widths.restype = st
         L.dmet_emb_launch_count.argtypes = [_P]
         L.dmet_emb_launch_count.restype = ctypes.c_int64
         L.dmet_emb_eri_noalloc.argtypes = [ctypes.POINTER(dmet_emb_desc_t), _P, ctypes.POINTER(_P),
@@ -183,15 +188,31 @@ def dmet_emb_transform_3idx(plan, problem, L, C, q_begin, q_end, Lq_out):
     _check(lib().dmet_emb_transform_3idx(_P(plan), problem, _P(ptr(L)), cs, q_begin, q_end, outs))
 
 
-def dmet_emb_eri(plan, L, C, eri_out):
-    """L: list over problems; C: list over problems of lists over spins; eri_out: list of lists."""
+def _problem_arrays(L, C, eri_out):
     n = len(L)
     ls = (_P * n)(*[ptr(x) for x in L])
     crows = [(_P * len(c))(*[ptr(x) for x in c]) for c in C]
     erows = [(_P * len(e))(*[ptr(x) for x in e]) for e in eri_out]
     cp = (ctypes.POINTER(_P) * n)(*[ctypes.cast(r, ctypes.POINTER(_P)) for r in crows])
     ep = (ctypes.POINTER(_P) * n)(*[ctypes.cast(r, ctypes.POINTER(_P)) for r in erows])
+    return ls, cp, ep, (crows, erows)
+
+
+def dmet_emb_eri(plan, L, C, eri_out):
+    """L: list over problems; C: list over problems of lists over spins; eri_out: list of lists."""
+    ls, cp, ep, _keep = _problem_arrays(L, C, eri_out)
     _check(lib().dmet_emb_eri(_P(plan), ls, cp, ep))
+
+
+def dmet_emb_autotune(plan, L, C, eri_out):
+    ls, cp, ep, _keep = _problem_arrays(L, C, eri_out)
+    _check(lib().dmet_emb_autotune(_P(plan), ls, cp, ep))
+
+
+def dmet_emb_tile_widths(plan, problem):
+    bn = (ctypes.c_int32 * 2)()
+    _check(lib().dmet_emb_tile_widths(_P(plan), problem, bn))
+    return list(bn)
 
 
 def dmet_emb_eri_noalloc(desc, L, C, eri_out, stream=None):

@@ -102,9 +102,9 @@ cudaError_t launch_build_Cc(const double2* C, const int4* gather, const int4* t2
                             int K2, void* Cc, long long sstride, cudaStream_t s);
 cudaError_t launch_pack_split(const void* ZT, int nq, int naux, int n, int nc, void* Xt, long long sstride,
                               long long Rtot, long long row_base, cudaStream_t s);
-cudaError_t launch_tc_pairs(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+cudaError_t launch_tc_pairs(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                             const tc::Segment* segs, void* out, long long ldo, unsigned int* err, cudaStream_t s);
-cudaError_t launch_tc_split_t(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+cudaError_t launch_tc_split_t(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                               const tc::Segment* segs, void* out, long long sstride, long long K2, int nao, int nemb,
                               unsigned int* err, cudaStream_t s);
 cudaError_t launch_tc_rect(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,

@@ -184,6 +184,7 @@ struct EpiSplitT {
     long long K2;
     int nao, nemb;
   };
+  template <int H>
   static __device__ __forceinline__ void store(const Params& p, const tc::TcJob& j, int row, int col0,
                                                const float* hi, const float* lo) {
     const int m = j.o0 + row;
@@ -191,7 +192,7 @@ struct EpiSplitT {
     const long long rbase = (long long)j.o2 + (long long)P * p.nemb;
     const long long cidx = (long long)j.o3 + 2 * mu;
 #pragma unroll
-    for (int c = 0; c < 64; c += 2) {
+    for (int c = 0; c < H; c += 2) {
       if (col0 + c >= j.n_valid) break;
       const int jj = (j.o1 + col0 + c) >> 1;
       __nv_bfloat16 r0, r1, r2, i0, i1, i2;
@@ -211,30 +212,32 @@ struct EpiPairs {
     float2* out;
     long long ldo;
   };
+  template <int H>
   static __device__ __forceinline__ void store(const Params& p, const tc::TcJob& j, int row, int col0,
                                                const float* hi, const float* lo) {
     float2* o = p.out + ((long long)j.o0 + row) * p.ldo + j.o1;
 #pragma unroll
-    for (int c = 0; c < 64; ++c) {
+    for (int c = 0; c < H; ++c) {
       const int cc = col0 + c;
       if (cc < j.n_valid) o[cc] = make_float2(hi[c], lo[c]);
     }
   }
 };
 
-template <class EPI>
-cudaError_t launch_tc(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                      const tc::Segment* segs, const typename EPI::Params& ep, unsigned int* err, cudaStream_t s) {
-  using Cfg = tc::TcCfg<3, 64>;
+template <int BN, class EPI>
+cudaError_t launch_tc_bn(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+                         const tc::Segment* segs, const typename EPI::Params& ep, unsigned int* err, cudaStream_t s) {
+  using Cfg = tc::TcCfg<3, 64, BN>;
   static bool attr = false;
   if (!attr) {
     // The register split inside the kernel assumes exactly kLaunchRegs registers per thread at
     // launch; with fewer, setmaxnreg.inc could never be satisfied, so refuse to launch.
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, tc::tc_gemm_kernel<3, 64, EPI>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, tc::tc_gemm_kernel<3, 64, BN, EPI>);
     if (e != cudaSuccess) return e;
     if (fa.numRegs != tc::kLaunchRegs) return cudaErrorInvalidKernelImage;
-    e = cudaFuncSetAttribute(tc::tc_gemm_kernel<3, 64, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    e = cudaFuncSetAttribute(tc::tc_gemm_kernel<3, 64, BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Cfg::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -247,13 +250,24 @@ cudaError_t launch_tc(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJo
     if (e != cudaSuccess) return e;
   }
   const int grid = njobs < nsm ? njobs : nsm;
-  tc::tc_gemm_kernel<3, 64, EPI><<<grid, tc::kThreads, Cfg::SMEM, s>>>(A, B, jobs, njobs, segs, ep, err);
+  tc::tc_gemm_kernel<3, 64, BN, EPI><<<grid, tc::kThreads, Cfg::SMEM, s>>>(A, B, jobs, njobs, segs, ep, err);
   return cudaGetLastError();
+}
+
+template <class EPI>
+cudaError_t launch_tc(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+                      const tc::Segment* segs, const typename EPI::Params& ep, unsigned int* err, cudaStream_t s) {
+  switch (bn) {
+    case 128: return launch_tc_bn<128, EPI>(A, B, jobs, njobs, segs, ep, err, s);
+    case 112: return launch_tc_bn<112, EPI>(A, B, jobs, njobs, segs, ep, err, s);
+    case 96: return launch_tc_bn<96, EPI>(A, B, jobs, njobs, segs, ep, err, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
-int mixed_kblock() { return tc::TcCfg<3, 64>::BK; }
+int mixed_kblock() { return tc::TcCfg<3, 64, 128>::BK; }
 
 cudaError_t launch_split_L(const double2* L, const int4* t1, int e0, int E, int nk, int naux, int nao, int K1,
                            void* Ls, long long sstride, cudaStream_t s) {
@@ -287,30 +301,30 @@ cudaError_t launch_pack_split(const void* ZT, int nq, int naux, int n, int nc, v
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_split_t(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+cudaError_t launch_tc_split_t(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                               const tc::Segment* segs, void* out, long long sstride, long long K2, int nao, int nemb,
                               unsigned int* err, cudaStream_t s) {
   EpiSplitT::Params p{(__nv_bfloat16*)out, sstride, K2, nao, nemb};
-  return launch_tc<EpiSplitT>(A, B, jobs, njobs, segs, p, err, s);
+  return launch_tc<EpiSplitT>(bn, A, B, jobs, njobs, segs, p, err, s);
 }
 
 cudaError_t launch_tc_rect(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                            const tc::Segment* segs, double* out, long long ldo, double scale, unsigned int* err,
                            cudaStream_t s) {
   tc::EpiRect::Params p{out, ldo, scale};
-  return launch_tc<tc::EpiRect>(A, B, jobs, njobs, segs, p, err, s);
+  return launch_tc<tc::EpiRect>(128, A, B, jobs, njobs, segs, p, err, s);
 }
 
-cudaError_t launch_tc_pairs(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+cudaError_t launch_tc_pairs(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                             const tc::Segment* segs, void* out, long long ldo, unsigned int* err, cudaStream_t s) {
   EpiPairs::Params p{(float2*)out, ldo};
-  return launch_tc<EpiPairs>(A, B, jobs, njobs, segs, p, err, s);
+  return launch_tc<EpiPairs>(bn, A, B, jobs, njobs, segs, p, err, s);
 }
 
 cudaError_t launch_tc_packed(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                              const tc::Segment* segs, double* out, double scale, unsigned int* err, cudaStream_t s) {
   tc::EpiPacked::Params p{out, scale};
-  return launch_tc<tc::EpiPacked>(A, B, jobs, njobs, segs, p, err, s);
+  return launch_tc<tc::EpiPacked>(128, A, B, jobs, njobs, segs, p, err, s);
 }
 
 }  // namespace dmet

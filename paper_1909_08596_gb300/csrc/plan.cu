@@ -172,6 +172,7 @@ struct Block {
 // Split-BF16 path: tables built at plan time (they depend on shapes only).
 struct MixedPlan {
   int K1 = 0, K2 = 0, kseg = 128;
+  int bn1 = 128, bn2 = 128;            // output tile widths of the two transform GEMMs
   long long Rtot = 0, R1 = 0;
   std::vector<Block> blocks;           // contraction order, q-blocks within one weight class
   std::vector<long long> row_base;     // first contraction row of each block
@@ -769,14 +770,15 @@ void build_mixed(Prob& pr) {
       m.j1_off[sp].push_back((int)m.jobs.size());
       // Tile-major, entry-minor: consecutive jobs write the adjacent column segments (one per
       // representative r) of the same output rows, so L2 merges them into whole lines.
+      const int B1 = m.bn1, B2 = m.bn2;
       for (int mt = 0; mt < cdiv((long long)naux * nao, T); ++mt)
-        for (int nt = 0; nt < cdiv(2LL * n, T); ++nt)
+        for (int nt = 0; nt < cdiv(2LL * n, B1); ++nt)
           for (int slot = bl.b0; slot < bl.b1; ++slot)
             for (int e = pr.con.start[slot]; e < pr.con.start[slot + 1]; ++e) {
               const int r = e - pr.con.start[slot], el = e - e0, k2 = pr.con.t1[e].x;
-              m.jobs.push_back({el * naux * nao + mt * T, k2 * 2 * n + nt * T,
+              m.jobs.push_back({el * naux * nao + mt * T, k2 * 2 * n + nt * B1,
                                 (int)std::min<long long>(T, (long long)naux * nao - mt * T),
-                                (int)std::min<long long>(T, 2LL * n - nt * T), 0, 1, mt * T, nt * T,
+                                (int)std::min<long long>(B1, 2LL * n - nt * B1), 0, 1, mt * T, nt * B1,
                                 (slot - bl.b0) * naux * n, r * 2 * nao});
             }
       m.j1_cnt[sp].push_back((int)m.jobs.size() - m.j1_off[sp].back());
@@ -784,11 +786,11 @@ void build_mixed(Prob& pr) {
       for (int slot = bl.b0; slot < bl.b1; ++slot) {
         const int sl = slot - bl.b0;
         for (int mt = 0; mt < cdiv((long long)naux * n, T); ++mt)
-          for (int nt = 0; nt < cdiv(2LL * n, T); ++nt)
-            m.jobs.push_back({sl * naux * n + mt * T, sl * 2 * n + nt * T,
+          for (int nt = 0; nt < cdiv(2LL * n, B2); ++nt)
+            m.jobs.push_back({sl * naux * n + mt * T, sl * 2 * n + nt * B2,
                               (int)std::min<long long>(T, (long long)naux * n - mt * T),
-                              (int)std::min<long long>(T, 2LL * n - nt * T), s2_off[slot], s2_cnt[slot],
-                              sl * naux * n + mt * T, nt * T, 0, 0});
+                              (int)std::min<long long>(B2, 2LL * n - nt * B2), s2_off[slot], s2_cnt[slot],
+                              sl * naux * n + mt * T, nt * B2, 0, 0});
       }
       m.j2_cnt[sp].push_back((int)m.jobs.size() - m.j2_off[sp].back());
     }
@@ -822,14 +824,14 @@ void build_mixed(Prob& pr) {
   (void)nk;
 }
 
-// Tensor flops a job range issues: 6 slice products of 128 x 128 x K tiles.
-double exec_flops(const MixedPlan& m, int off, int cnt) {
+// Tensor flops a job range issues: 6 slice products of 128 x bn x K tiles.
+double exec_flops(const MixedPlan& m, int off, int cnt, int bn) {
   double f = 0;
   for (int i = off; i < off + cnt; ++i) {
     const tc::TcJob& j = m.jobs[i];
     long long k = 0;
     for (int g = j.seg0; g < j.seg0 + j.nseg; ++g) k += (long long)m.segs[g].nkb * mixed_kblock();
-    f += 6.0 * 2.0 * tc::kTile * tc::kTile * (double)k;
+    f += 6.0 * 2.0 * tc::kTile * bn * (double)k;
   }
   return f;
 }
@@ -863,8 +865,8 @@ dmet_status_t mixed_maps(dmet_emb_plan_s* P, const Prob& pr, MixedMaps& mm) {
   CK(make_tmap_bf16_3d(&mm.Ls, P->W->Ls, m.K1, m.Ls_rows, 3, m.K1, m.Ls_rows * m.K1, BK, T));
   for (int s = 0; s < pr.nspin; ++s) {
     const long long n = pr.n[s];
-    CK(make_tmap_bf16_3d(&mm.Cb[s], P->W->Cb[s], m.K1, pr.nk * 2 * n, 3, m.K1, pr.nk * 2 * n * m.K1, BK, T));
-    CK(make_tmap_bf16_3d(&mm.Cc[s], P->W->Cc, m.K2, (long long)pr.bq * 2 * n, 3, m.K2, cc_rows * m.K2, BK, T));
+    CK(make_tmap_bf16_3d(&mm.Cb[s], P->W->Cb[s], m.K1, pr.nk * 2 * n, 3, m.K1, pr.nk * 2 * n * m.K1, BK, m.bn1));
+    CK(make_tmap_bf16_3d(&mm.Cc[s], P->W->Cc, m.K2, (long long)pr.bq * 2 * n, 3, m.K2, cc_rows * m.K2, BK, m.bn2));
     CK(make_tmap_bf16_3d(&mm.A2[s], P->W->A2, m.K2, (long long)pr.bq * pr.naux * n, 3, m.K2, a2_rows * m.K2, BK, T));
     CK(make_tmap_bf16_3d(&mm.Xt[s], P->W->Xt[s], m.Rtot, pr.npair[s], 3, m.Rtot, pr.npair[s] * m.Rtot, BK, T));
   }
@@ -910,15 +912,15 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
       }
       {
         Timed t(P, KC_TC_TRANSFORM_1, 8.0 * n * (double)pr.naux * pr.nao * pr.nao * E, 0.0, 1,
-                exec_flops(m, m.j1_off[s][bi], m.j1_cnt[s][bi]));
-        CK(launch_tc_split_t(mm.Ls, mm.Cb[s], m.d_jobs + m.j1_off[s][bi], m.j1_cnt[s][bi], m.d_segs, P->W->A2,
+                exec_flops(m, m.j1_off[s][bi], m.j1_cnt[s][bi], m.bn1));
+        CK(launch_tc_split_t(m.bn1, mm.Ls, mm.Cb[s], m.d_jobs + m.j1_off[s][bi], m.j1_cnt[s][bi], m.d_segs, P->W->A2,
                              a2_rows * m.K2, m.K2, pr.nao, n, P->derr, P->cs));
       }
       {
         double fl = 0;
         for (int i = bl.b0; i < bl.b1; ++i) fl += 8.0 * n * (double)pr.naux * n * pr.con.t2[i].w;
-        Timed t(P, KC_TC_TRANSFORM_2, fl, 0.0, 1, exec_flops(m, m.j2_off[s][bi], m.j2_cnt[s][bi]));
-        CK(launch_tc_pairs(mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs, P->W->ZT, 2LL * n,
+        Timed t(P, KC_TC_TRANSFORM_2, fl, 0.0, 1, exec_flops(m, m.j2_off[s][bi], m.j2_cnt[s][bi], m.bn2));
+        CK(launch_tc_pairs(m.bn2, mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs, P->W->ZT, 2LL * n,
                            P->derr, P->cs));
       }
       {
@@ -937,7 +939,7 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
     const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
     const double fl = blk == 1 ? 2.0 * pr.npair[0] * (double)pr.npair[1] * K
                                : (double)pr.npair[sa] * (pr.npair[sa] + 1.0) * K;
-    Timed t(P, KC_TC_CONTRACT, fl, 0.0, 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk]));
+    Timed t(P, KC_TC_CONTRACT, fl, 0.0, 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk], tc::kTile));
     if (blk == 1)
       CK(launch_tc_rect(mm.Xt[0], mm.Xt[1], m.d_jobs + m.jc_off[1], m.jc_cnt[1], m.d_segs, (double*)out[1],
                         pr.npair[1], oscale, P->derr, P->cs));
@@ -946,6 +948,66 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
                           oscale, P->derr, P->cs));
   }
   return DMET_OK;
+}
+
+// Rebuilds the split-BF16 job tables of a problem (after its tile widths changed) and uploads them.
+dmet_status_t upload_mixed(Prob& pr) {
+  build_mixed(pr);
+  MixedPlan& m = pr.mx;
+  cudaFree(m.d_jobs);
+  cudaFree(m.d_segs);
+  m.d_jobs = nullptr;
+  m.d_segs = nullptr;
+  if (cudaMalloc(&m.d_jobs, m.jobs.size() * sizeof(tc::TcJob)) != cudaSuccess ||
+      cudaMalloc(&m.d_segs, m.segs.size() * sizeof(tc::Segment)) != cudaSuccess ||
+      cudaMemcpy(m.d_jobs, m.jobs.data(), m.jobs.size() * sizeof(tc::TcJob), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m.d_segs, m.segs.data(), m.segs.size() * sizeof(tc::Segment), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DMET_ERR_CUDA, "job table upload failed");
+  }
+  return DMET_OK;
+}
+
+// Tuning cache: one line per problem shape, "mesh0 mesh1 mesh2 n_ao n_aux n0 n1 n_spin bn1 bn2".
+std::string tune_key(const Prob& pr) {
+  char b[160];
+  snprintf(b, sizeof(b), "%d %d %d %d %d %d %d %d", pr.d.mesh[0], pr.d.mesh[1], pr.d.mesh[2], pr.nao, pr.naux, pr.n[0],
+           pr.n[1], pr.nspin);
+  return b;
+}
+
+bool tune_cache_lookup(const Prob& pr, int& bn1, int& bn2) {
+  const char* path = std::getenv("DMET_TUNE_CACHE");
+  if (!path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  const std::string key = tune_key(pr);
+  char line[256];
+  bool found = false;
+  while (fgets(line, sizeof(line), f)) {
+    int v[10];
+    if (sscanf(line, "%d %d %d %d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7], &v[8],
+               &v[9]) != 10)
+      continue;
+    char k[160];
+    snprintf(k, sizeof(k), "%d %d %d %d %d %d %d %d", v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]);
+    if (key == k && (v[8] == 128 || v[8] == 112 || v[8] == 96) && (v[9] == 128 || v[9] == 112 || v[9] == 96)) {
+      bn1 = v[8];
+      bn2 = v[9];
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void tune_cache_store(const Prob& pr) {
+  const char* path = std::getenv("DMET_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d\n", tune_key(pr).c_str(), pr.mx.bn1, pr.mx.bn2);
+  fclose(f);
 }
 
 // ==========================================================================================
@@ -1038,6 +1100,7 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     }
     // q-block size: the largest (<= 8, entries per launch <= 65535) whose workspace fits.
     pr.mixed = pr.d.prec == DMET_PREC_BF16X3;
+    if (pr.mixed) tune_cache_lookup(pr, pr.mx.bn1, pr.mx.bn2);
     auto total_for = [&](int b) {
       size_t t = ws_for(pr, b).total();
       if (pr.mixed) {
@@ -1446,6 +1509,65 @@ dmet_status_t dmet_emb_problem_ms(dmet_emb_plan_t P, int32_t problem, double* ms
   float t = 0;
   CK(cudaEventElapsedTime(&t, P->pev[problem].first, P->pev[problem].second));
   *ms = t;
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_autotune(dmet_emb_plan_t P, const void* const* L, const void* const* const* C,
+                                void* const* const* eri_out) {
+  clear_error();
+  if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
+  bool any = false;
+  for (const Prob& pr : P->probs) any |= pr.mixed;
+  if (!any) return DMET_OK;
+  const bool prof = P->prof;
+  if (P->gexec) {
+    CK(cudaStreamSynchronize(P->stream));
+    CK(cudaGraphExecDestroy(P->gexec));
+    P->gexec = nullptr;
+    P->gkey.clear();
+  }
+  const int cand[3] = {128, 112, 96};
+  const int np = (int)P->probs.size();
+  std::vector<double> best(np, 1e300);
+  std::vector<int> best_bn(np, 128);
+  for (int c : cand) {
+    for (Prob& pr : P->probs)
+      if (pr.mixed) {
+        pr.mx.bn1 = pr.mx.bn2 = c;
+        TRY(upload_mixed(pr));
+      }
+    P->prof = false;
+    TRY(dmet_emb_eri(P, L, C, eri_out));  // warm-up with this tile width
+    P->prof = true;
+    TRY(dmet_emb_eri(P, L, C, eri_out));
+    CK(cudaStreamSynchronize(P->stream));
+    for (int p = 0; p < np; ++p) {
+      if (!P->probs[p].mixed) continue;
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, P->pev[p].first, P->pev[p].second));
+      if (ms < best[p]) {
+        best[p] = ms;
+        best_bn[p] = c;
+      }
+    }
+  }
+  for (int p = 0; p < np; ++p) {
+    Prob& pr = P->probs[p];
+    if (!pr.mixed) continue;
+    pr.mx.bn1 = pr.mx.bn2 = best_bn[p];
+    TRY(upload_mixed(pr));
+    tune_cache_store(pr);
+  }
+  P->prof = prof;
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_tile_widths(dmet_emb_plan_t P, int32_t problem, int32_t* bn) {
+  clear_error();
+  if (!P || !bn) return fail(DMET_ERR_INVALID_ARG, "NULL argument");
+  if (problem < 0 || problem >= (int)P->probs.size()) return fail(DMET_ERR_INVALID_ARG, "problem %d", problem);
+  bn[0] = P->probs[problem].mx.bn1;
+  bn[1] = P->probs[problem].mx.bn2;
   return DMET_OK;
 }
 

@@ -15,7 +15,7 @@
 // segments at FP32-pipe cost, and hand hi + lo to the output functor once at the end.
 //
 // A persistent CTA of 12 warps (one per SM) works through the jobs blockIdx.x, blockIdx.x +
-// gridDim.x, ...; each job is one 128 x 128 output tile (jobs come from a table). The stage
+// gridDim.x, ...; each job is one 128 x BN output tile (jobs come from a table). The stage
 // ring and the two accumulator buffers run on across jobs, so a job's final store overlaps
 // the next job's MMAs.
 //   warp 0      TMA producer (one thread): 3+3 slice tiles per K block into a stage ring;
@@ -23,7 +23,7 @@
 //               (two buffers of two 128-column accumulators, so the epilogue of segment g
 //               overlaps the MMAs of segment g+1);
 //   warps 2, 3  idle (they complete the first warpgroup);
-//   warps 4..11 epilogue: warp w reads TMEM lanes 32*(w%4).. and half (w-4)/4 of the columns.
+//   warps 4..11 epilogue: warp w reads TMEM lanes 32*(w%4).. and half (w-4)/4 of the BN columns.
 // Registers: the CTA launches with kLaunchRegs per thread; the first warpgroup gives most of
 // its registers back (setmaxnreg.dec to kCtrlRegs) and the two epilogue warpgroups take them
 // (setmaxnreg.inc to kEpiRegs), which the two-float sums of 64 columns per thread need:
@@ -66,14 +66,20 @@ constexpr int kEpiRegs = 224;
 static_assert(128 * kCtrlRegs + 256 * kEpiRegs == kThreads * kLaunchRegs, "register split must match the launch");
 static_assert(kCtrlRegs + 2 * kEpiRegs <= 512, "per sub-partition register file");
 
-template <int NSLICE, int ROWB>
+// BN: output columns per tile (the UMMA N), 128, 112 or 96. Each of the four accumulators
+// (two buffers of leading + correction sums) starts on a 128-column boundary of TMEM.
+template <int NSLICE, int ROWB, int BN>
 struct TcCfg {
-  static constexpr int BK = ROWB / 2;                          // bf16 elements per K block
-  static constexpr int TILE_BYTES = kTile * ROWB;              // one slice tile
-  static constexpr int STAGE_BYTES = 2 * NSLICE * TILE_BYTES;  // A and B slices
+  static_assert(BN % 32 == 16 || BN % 32 == 0, "BN must be a multiple of 16");
+  static_assert(BN <= 128 && BN >= 64, "4 BN TMEM columns must fit");
+  static constexpr int BK = ROWB / 2;                           // bf16 elements per K block
+  static constexpr int A_BYTES = kTile * ROWB;                  // one A slice tile
+  static constexpr int B_BYTES = BN * ROWB;                     // one B slice tile
+  static constexpr int STAGE_BYTES = NSLICE * (A_BYTES + B_BYTES);
   static constexpr int STAGES = (192 * 1024) / STAGE_BYTES > 6 ? 6 : (192 * 1024) / STAGE_BYTES;
   static constexpr int NPROD = NSLICE == 3 ? 6 : 1;
   static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 256;
+  static constexpr int HALF = BN / 2;                           // columns per epilogue warp
 };
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
@@ -84,14 +90,15 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
   lo += e;
 }
 
-// EPI::store(params, job, row, col0, hi, lo): row = tile-local row (< 128), columns col0 .. col0+63.
-template <int NSLICE, int ROWB, class EPI>
+// EPI::store<H>(params, job, row, col0, hi, lo): row = tile-local row (< 128), columns col0 .. col0+H-1.
+template <int NSLICE, int ROWB, int BN, class EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcJob* __restrict__ jobs, int njobs, const Segment* __restrict__ segs,
                    const typename EPI::Params ep, unsigned int* err) {
-  using Cfg = TcCfg<NSLICE, ROWB>;
+  using Cfg = TcCfg<NSLICE, ROWB, BN>;
   constexpr int S = Cfg::STAGES;
+  constexpr int H = Cfg::HALF;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* tiles = smem;
@@ -107,9 +114,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto accf = [&](int b) { return smem_u32(bars + 2 * S + b); };
   auto acce = [&](int b) { return smem_u32(bars + 2 * S + 2 + b); };
   const uint32_t done_bar = smem_u32(bars + 2 * S + 4);
-  auto a_tile = [&](int s, int t) { return smem_u32(tiles + s * Cfg::STAGE_BYTES + t * Cfg::TILE_BYTES); };
+  auto a_tile = [&](int s, int t) { return smem_u32(tiles + s * Cfg::STAGE_BYTES + t * Cfg::A_BYTES); };
   auto b_tile = [&](int s, int t) {
-    return smem_u32(tiles + s * Cfg::STAGE_BYTES + (NSLICE + t) * Cfg::TILE_BYTES);
+    return smem_u32(tiles + s * Cfg::STAGE_BYTES + NSLICE * Cfg::A_BYTES + t * Cfg::B_BYTES);
   };
 
   if (threadIdx.x == 0) {
@@ -165,7 +172,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     } else if (warp == 1 && lane == 0) {
       // ---------------- MMA issuer ----------------
-      constexpr uint32_t idesc = idesc_bf16_f32(kTile, kTile);
+      constexpr uint32_t idesc = idesc_bf16_f32(kTile, BN);
       constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
       constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
       int it = 0, gs = 0;  // K blocks and segments issued so far (across jobs)
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int b = gs & 1, u = gs >> 1;
         if (!mbar_wait(acce(b), (u & 1) ^ 1, err, 2u)) break;
         tc_fence_after();
-        const uint32_t d_main = tmem + b * 2 * kTile, d_corr = d_main + kTile;
+        const uint32_t d_main = tmem + b * 2 * kTile, d_corr = d_main + kTile;  // 128-column aligned
         const int nkb = segs[job.seg0 + g].nkb;
         for (int kb = 0; kb < nkb; ++kb) {
           const int s = it % S, ph = (it / S) & 1;
@@ -211,13 +218,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue ----------------
     const int quad = warp & 3, half = (warp - 4) >> 2;
     const int row = quad * 32 + lane;
-    float hi[64], lo[64];
+    float hi[H], lo[H];
     bool ok = true;
     int gs = 0;
     for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x) {
       const TcJob job = jobs[jb];
 #pragma unroll
-      for (int c = 0; c < 64; ++c) {
+      for (int c = 0; c < H; ++c) {
         hi[c] = 0.f;
         lo[c] = 0.f;
       }
@@ -229,27 +236,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         const float w = segs[job.seg0 + g].w;
-        const uint32_t tm_main = tmem + ((uint32_t)(quad * 32) << 16) + b * 2 * kTile + half * 64;
+        const uint32_t tm_main = tmem + ((uint32_t)(quad * 32) << 16) + b * 2 * kTile + half * H;
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-          uint32_t v[16];
-          tmem_ld_32x32b_x16(tm_main + ch * 16, v);
+        for (int ch = 0; ch < H / 8; ++ch) {
+          uint32_t v[8];
+          tmem_ld_32x32b_x8(tm_main + ch * 8, v);
           tmem_ld_wait();
 #pragma unroll
-          for (int c = 0; c < 16; ++c) two_sum_acc(hi[ch * 16 + c], lo[ch * 16 + c], w * __uint_as_float(v[c]));
+          for (int c = 0; c < 8; ++c) two_sum_acc(hi[ch * 8 + c], lo[ch * 8 + c], w * __uint_as_float(v[c]));
           if (NSLICE == 3) {
             // The correction sum is ~2^-8 of the leading one: it joins the low word.
-            tmem_ld_32x32b_x16(tm_main + kTile + ch * 16, v);
+            tmem_ld_32x32b_x8(tm_main + kTile + ch * 8, v);
             tmem_ld_wait();
 #pragma unroll
-            for (int c = 0; c < 16; ++c) lo[ch * 16 + c] += w * __uint_as_float(v[c]);
+            for (int c = 0; c < 8; ++c) lo[ch * 8 + c] += w * __uint_as_float(v[c]);
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acce(b));
       }
-      if (ok && row < job.m_valid) EPI::store(ep, job, row, half * 64, hi, lo);
+      if (ok && row < job.m_valid) EPI::template store<H>(ep, job, row, half * H, hi, lo);
     }
   }
   __syncthreads();
@@ -273,12 +280,13 @@ struct EpiPacked {
     double* out;
     double scale;
   };
+  template <int H>
   static __device__ __forceinline__ void store(const Params& p, const TcJob& j, int row, int col0, const float* hi,
                                                const float* lo) {
     const long long m = (long long)j.o0 + row;
     double* o = p.out + m * (m + 1) / 2;
 #pragma unroll
-    for (int c = 0; c < 64; ++c) {
+    for (int c = 0; c < H; ++c) {
       const int cc = col0 + c;
       const long long n = (long long)j.o1 + cc;
       if (cc < j.n_valid && n <= m) o[n] = p.scale * (f2d(hi[c]) + f2d(lo[c]));
@@ -293,11 +301,12 @@ struct EpiRect {
     long long ldo;
     double scale;
   };
+  template <int H>
   static __device__ __forceinline__ void store(const Params& p, const TcJob& j, int row, int col0, const float* hi,
                                                const float* lo) {
     double* o = p.out + ((long long)j.o0 + row) * p.ldo + j.o1;
 #pragma unroll
-    for (int c = 0; c < 64; ++c) {
+    for (int c = 0; c < H; ++c) {
       const int cc = col0 + c;
       if (cc < j.n_valid) o[cc] = p.scale * (f2d(hi[c]) + f2d(lo[c]));
     }

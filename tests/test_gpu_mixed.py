@@ -105,3 +105,53 @@ def test_mixed_hbn_full_size_sampled(torch):
     idx = np.stack([i.ravel(), j.ravel(), k.ravel(), l.ravel()], 1)
     ref = oracle.eri_entries(Lq, Lq, spec.mesh, idx).real
     check(got[s8_index(*(S[idx.T]))], ref)
+
+
+@pytest.mark.parametrize("bn", [128, 112, 96])
+def test_mixed_tile_widths(torch, bn, tmp_path, monkeypatch):
+    """Every output tile width of the transform GEMMs gives the same parity (forced through the
+    tuning cache that dmet_emb_plan reads)."""
+    import paper_1909_08596_gb300 as dm
+    spec = spec_of((3, 2, 1), 10, 30, 55)
+    L, Cs, _ = synth.make_problem(spec)
+    cache = tmp_path / "tune.txt"
+    cache.write_text(f"3 2 1 10 30 55 0 1 {bn} {bn}\n")
+    monkeypatch.setenv("DMET_TUNE_CACHE", str(cache))
+    d = desc_of(spec)
+    Ld = torch.from_numpy(L).cuda()
+    Cd = [torch.from_numpy(c).cuda() for c in Cs]
+    out = torch.empty(B.dmet_emb_eri_bytes(d, 0) // 8, dtype=torch.float64, device="cuda")
+    plan = dm.dmet_emb_plan(d, stream=torch.cuda.current_stream().cuda_stream)
+    try:
+        assert dm.dmet_emb_tile_widths(plan, 0) == [bn, bn]
+        dm.dmet_emb_eri(plan, [Ld], [Cd], [[out]])
+        st, _ = dm.dmet_emb_status(plan, 0)
+    finally:
+        dm.dmet_emb_destroy(plan)
+    assert st == B.DMET_OK
+    check(out.cpu().numpy(), oracle.pack_s8(oracle.embedded_eri(L, Cs[0], spec.mesh).real))
+
+
+def test_mixed_autotune(torch, tmp_path, monkeypatch):
+    import paper_1909_08596_gb300 as dm
+    spec = spec_of((3, 3, 1), 10, 37, 70)
+    L, Cs, _ = synth.make_problem(spec)
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("DMET_TUNE_CACHE", str(cache))
+    d = desc_of(spec)
+    Ld = torch.from_numpy(L).cuda()
+    Cd = [torch.from_numpy(c).cuda() for c in Cs]
+    out = torch.empty(B.dmet_emb_eri_bytes(d, 0) // 8, dtype=torch.float64, device="cuda")
+    plan = dm.dmet_emb_plan(d, stream=torch.cuda.current_stream().cuda_stream)
+    try:
+        dm.dmet_emb_autotune(plan, [Ld], [Cd], [[out]])
+        widths = dm.dmet_emb_tile_widths(plan, 0)
+        out.fill_(float("nan"))
+        dm.dmet_emb_eri(plan, [Ld], [Cd], [[out]])
+        st, _ = dm.dmet_emb_status(plan, 0)
+    finally:
+        dm.dmet_emb_destroy(plan)
+    assert st == B.DMET_OK
+    assert widths[0] in (128, 112, 96) and widths[1] in (128, 112, 96)
+    assert cache.read_text().split()[-2:] == [str(widths[0]), str(widths[1])]
+    check(out.cpu().numpy(), oracle.pack_s8(oracle.embedded_eri(L, Cs[0], spec.mesh).real))
