@@ -950,6 +950,21 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
   return DMET_OK;
 }
 
+// Clears the per-kernel counters (their events go back to the pool).
+void reset_profile(dmet_emb_plan_s* P) {
+  for (auto& k : P->ks) {
+    for (auto& e : k.ev) {
+      P->pool.push_back(e.first);
+      P->pool.push_back(e.second);
+    }
+    k.ev.clear();
+    k.launches = 0;
+    k.flops = 0;
+    k.bytes = 0;
+    k.exec = 0;
+  }
+}
+
 // Rebuilds the split-BF16 job tables of a problem (after its tile widths changed) and uploads them.
 dmet_status_t upload_mixed(Prob& pr) {
   build_mixed(pr);
@@ -1528,8 +1543,12 @@ dmet_status_t dmet_emb_autotune(dmet_emb_plan_t P, const void* const* L, const v
   }
   const int cand[3] = {128, 112, 96};
   const int np = (int)P->probs.size();
-  std::vector<double> best(np, 1e300);
-  std::vector<int> best_bn(np, 128);
+  int nmixed = 0;
+  for (const Prob& pr : P->probs) nmixed += pr.mixed;
+  // One mixed problem: the two transform GEMMs are timed (and chosen) separately from the
+  // per-kernel CUDA events; several: each problem's whole time decides one width for both.
+  std::vector<double> best(np, 1e300), best1(np, 1e300), best2(np, 1e300);
+  std::vector<int> bn1(np, 128), bn2(np, 128);
   for (int c : cand) {
     for (Prob& pr : P->probs)
       if (pr.mixed) {
@@ -1538,26 +1557,39 @@ dmet_status_t dmet_emb_autotune(dmet_emb_plan_t P, const void* const* L, const v
       }
     P->prof = false;
     TRY(dmet_emb_eri(P, L, C, eri_out));  // warm-up with this tile width
+    reset_profile(P);
     P->prof = true;
     TRY(dmet_emb_eri(P, L, C, eri_out));
     CK(cudaStreamSynchronize(P->stream));
+    double t1 = 0, t2 = 0;
+    for (int k : {(int)KC_TC_TRANSFORM_1, (int)KC_TC_TRANSFORM_2})
+      for (auto& e : P->ks[k].ev) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e.first, e.second));
+        (k == KC_TC_TRANSFORM_1 ? t1 : t2) += ms;
+      }
     for (int p = 0; p < np; ++p) {
       if (!P->probs[p].mixed) continue;
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, P->pev[p].first, P->pev[p].second));
-      if (ms < best[p]) {
+      if (nmixed == 1) {
+        if (t1 < best1[p]) best1[p] = t1, bn1[p] = c;
+        if (t2 < best2[p]) best2[p] = t2, bn2[p] = c;
+      } else if (ms < best[p]) {
         best[p] = ms;
-        best_bn[p] = c;
+        bn1[p] = bn2[p] = c;
       }
     }
   }
   for (int p = 0; p < np; ++p) {
     Prob& pr = P->probs[p];
     if (!pr.mixed) continue;
-    pr.mx.bn1 = pr.mx.bn2 = best_bn[p];
+    pr.mx.bn1 = bn1[p];
+    pr.mx.bn2 = bn2[p];
     TRY(upload_mixed(pr));
     tune_cache_store(pr);
   }
+  reset_profile(P);
   P->prof = prof;
   return DMET_OK;
 }
@@ -1607,17 +1639,7 @@ dmet_status_t dmet_emb_profile(dmet_emb_plan_t P, int32_t enable) {
   clear_error();
   if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
   CK(cudaStreamSynchronize(P->stream));
-  for (auto& k : P->ks) {
-    for (auto& e : k.ev) {
-      P->pool.push_back(e.first);
-      P->pool.push_back(e.second);
-    }
-    k.ev.clear();
-    k.launches = 0;
-    k.flops = 0;
-    k.bytes = 0;
-    k.exec = 0;
-  }
+  reset_profile(P);
   P->prof = enable != 0;
   return DMET_OK;
 }

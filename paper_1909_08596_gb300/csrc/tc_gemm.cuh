@@ -237,20 +237,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const float w = segs[job.seg0 + g].w;
         const uint32_t tm_main = tmem + ((uint32_t)(quad * 32) << 16) + b * 2 * kTile + half * H;
+        // Up to 32 columns of both accumulators per round trip: all loads, then one wait.
 #pragma unroll
-        for (int ch = 0; ch < H / 8; ++ch) {
-          uint32_t v[8];
-          tmem_ld_32x32b_x8(tm_main + ch * 8, v);
+        for (int g0 = 0; g0 < H; g0 += 32) {
+          uint32_t vm[32], vc[32];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (g0 + q * 8 < H) {
+              tmem_ld_32x32b_x8(tm_main + g0 + q * 8, vm + q * 8);
+              if (NSLICE == 3) tmem_ld_32x32b_x8(tm_main + kTile + g0 + q * 8, vc + q * 8);
+            }
           tmem_ld_wait();
 #pragma unroll
-          for (int c = 0; c < 8; ++c) two_sum_acc(hi[ch * 8 + c], lo[ch * 8 + c], w * __uint_as_float(v[c]));
-          if (NSLICE == 3) {
-            // The correction sum is ~2^-8 of the leading one: it joins the low word.
-            tmem_ld_32x32b_x8(tm_main + kTile + ch * 8, v);
-            tmem_ld_wait();
-#pragma unroll
-            for (int c = 0; c < 8; ++c) lo[ch * 8 + c] += w * __uint_as_float(v[c]);
-          }
+          for (int c = 0; c < 32; ++c)
+            if (g0 + c < H) {
+              two_sum_acc(hi[g0 + c], lo[g0 + c], w * __uint_as_float(vm[c]));
+              // The correction sum is ~2^-8 of the leading one: it joins the low word.
+              if (NSLICE == 3) lo[g0 + c] += w * __uint_as_float(vc[c]);
+            }
         }
         tc_fence_before();
         __syncwarp();
