@@ -800,12 +800,16 @@ void build_mixed(Prob& pr) {
     const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
     const long long pa = pr.npair[sa], pb = pr.npair[sb];
     m.jc_off[blk] = (int)m.jobs.size();
-    for (int mt = 0; mt < cdiv(pa, T); ++mt)
-      for (int nt = 0; nt < cdiv(pb, T); ++nt) {
-        if (blk != 1 && nt > mt) continue;
-        m.jobs.push_back({mt * T, nt * T, (int)std::min<long long>(T, pa - mt * T),
-                          (int)std::min<long long>(T, pb - nt * T), sc_off, sc_cnt, mt * T, nt * T, 0, 0});
-      }
+    // Bands of 8 tile rows, column-major inside a band: the CTAs running at the same time
+    // share few row blocks of the operands, which raises their L2 hit rate.
+    const int mts = cdiv(pa, T), nts = cdiv(pb, T), band = 8;
+    for (int m0b = 0; m0b < mts; m0b += band)
+      for (int nt = 0; nt < nts; ++nt)
+        for (int mt = m0b; mt < std::min(mts, m0b + band); ++mt) {
+          if (blk != 1 && nt > mt) continue;
+          m.jobs.push_back({mt * T, nt * T, (int)std::min<long long>(T, pa - mt * T),
+                            (int)std::min<long long>(T, pb - nt * T), sc_off, sc_cnt, mt * T, nt * T, 0, 0});
+        }
     m.jc_cnt[blk] = (int)m.jobs.size() - m.jc_off[blk];
   }
   // useful flops of one call (the same count as the FP64 path)
