@@ -184,6 +184,7 @@ struct EpiSplitT {
     long long K2;
     int nao, nemb;
   };
+  static constexpr bool kStaged = false;  // lanes already write adjacent columns of one row
   template <int H>
   static __device__ __forceinline__ void store(const Params& p, const tc::TcJob& j, int row, int col0,
                                                const float* hi, const float* lo) {
@@ -195,13 +196,12 @@ struct EpiSplitT {
     for (int c = 0; c < H; c += 2) {
       if (col0 + c >= j.n_valid) break;
       const int jj = (j.o1 + col0 + c) >> 1;
-      __nv_bfloat16 r0, r1, r2, i0, i1, i2;
-      split3f(hi[c], lo[c], r0, r1, r2);
-      split3f(hi[c + 1], lo[c + 1], i0, i1, i2);
+      __nv_bfloat162 x0, x1, x2;  // (re, im) of slices 0, 1, 2
+      split3f2(hi[c], lo[c], hi[c + 1], lo[c + 1], x0, x1, x2);
       __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(p.out + (rbase + jj) * p.K2 + cidx);
-      o[0] = __halves2bfloat162(r0, i0);
-      o[p.sstride / 2] = __halves2bfloat162(r1, i1);
-      o[p.sstride] = __halves2bfloat162(r2, i2);
+      o[0] = x0;
+      o[p.sstride / 2] = x1;
+      o[p.sstride] = x2;
     }
   }
 };
@@ -212,15 +212,15 @@ struct EpiPairs {
     float2* out;
     long long ldo;
   };
-  template <int H>
-  static __device__ __forceinline__ void store(const Params& p, const tc::TcJob& j, int row, int col0,
-                                               const float* hi, const float* lo) {
-    float2* o = p.out + ((long long)j.o0 + row) * p.ldo + j.o1;
-#pragma unroll
-    for (int c = 0; c < H; ++c) {
-      const int cc = col0 + c;
-      if (cc < j.n_valid) o[cc] = make_float2(hi[c], lo[c]);
-    }
+  static constexpr bool kStaged = true;
+  static __device__ __forceinline__ unsigned long long value(const Params&, float hi, float lo) {
+    return (unsigned long long)__float_as_uint(hi) | ((unsigned long long)__float_as_uint(lo) << 32);
+  }
+  static __device__ __forceinline__ void put(const Params& p, const tc::TcJob& j, int row, int col,
+                                             unsigned long long v) {
+    if (row < j.m_valid && col < j.n_valid)
+      p.out[((long long)j.o0 + row) * p.ldo + j.o1 + col] =
+          make_float2(__uint_as_float((unsigned int)v), __uint_as_float((unsigned int)(v >> 32)));
   }
 };
 
@@ -311,7 +311,8 @@ cudaError_t launch_tc_split_t(int bn, const CUtensorMap& A, const CUtensorMap& B
 cudaError_t launch_tc_rect(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                            const tc::Segment* segs, double* out, long long ldo, double scale, unsigned int* err,
                            cudaStream_t s) {
-  tc::EpiRect::Params p{out, ldo, scale};
+  const float sh = (float)scale;
+  tc::EpiRect::Params p{out, ldo, sh, (float)(scale - (double)sh)};
   return launch_tc<tc::EpiRect>(128, A, B, jobs, njobs, segs, p, err, s);
 }
 
@@ -323,7 +324,8 @@ cudaError_t launch_tc_pairs(int bn, const CUtensorMap& A, const CUtensorMap& B, 
 
 cudaError_t launch_tc_packed(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                              const tc::Segment* segs, double* out, double scale, unsigned int* err, cudaStream_t s) {
-  tc::EpiPacked::Params p{out, scale};
+  const float sh = (float)scale;
+  tc::EpiPacked::Params p{out, sh, (float)(scale - (double)sh)};
   return launch_tc<tc::EpiPacked>(128, A, B, jobs, njobs, segs, p, err, s);
 }
 

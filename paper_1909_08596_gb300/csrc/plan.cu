@@ -754,6 +754,12 @@ void build_mixed(Prob& pr) {
   for (long long k0 = m.R1; k0 < m.Rtot; k0 += m.kseg)
     m.segs.push_back({(int)k0, (int)(std::min<long long>(m.Rtot - k0, m.kseg) / BK), 2.0f, 0});
   const int sc_cnt = (int)m.segs.size() - sc_off;
+  // A correction-sum run never spans a change of weight.
+  for (size_t i = 1; i < m.segs.size(); ++i)
+    if (m.segs[i].w != m.segs[i - 1].w) {
+      m.segs[i - 1].flags |= tc::kRunLast;
+      m.segs[i].flags |= tc::kRunFirst;
+    }
 
   auto cdiv = [](long long a, long long b) { return (int)((a + b - 1) / b); };
   const int T = tc::kTile;

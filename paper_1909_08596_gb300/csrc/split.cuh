@@ -53,6 +53,18 @@ __device__ __forceinline__ void split3f(float hi, float lo, __nv_bfloat16& a, __
   c = __float2bfloat16_rn(r - __bfloat162float(b));
 }
 
+// split3f on two values at once, with paired conversions (bit-identical to two split3f calls):
+// .x of each result slice comes from (h0, l0), .y from (h1, l1).
+__device__ __forceinline__ void split3f2(float h0, float l0, float h1, float l1, __nv_bfloat162& a,
+                                         __nv_bfloat162& b, __nv_bfloat162& c) {
+  a = __floats2bfloat162_rn(h0, h1);
+  const float2 af = __bfloat1622float2(a);
+  const float r0 = (h0 - af.x) + l0, r1 = (h1 - af.y) + l1;
+  b = __floats2bfloat162_rn(r0, r1);
+  const float2 bf = __bfloat1622float2(b);
+  c = __floats2bfloat162_rn(r0 - bf.x, r1 - bf.y);
+}
+
 __device__ __forceinline__ void split3d(double x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
   const float2 p = d2ff(x);
   split3f(p.x, p.y, a, b, c);

@@ -9,21 +9,27 @@
 // MMA's result into the accumulator with an error of the accumulator's own magnitude, so
 // mixing the small correction terms into the leading sum would multiply the number of lossy
 // additions it suffers by six. That error still grows with the number of MMAs a segment
-// accumulates, so segments are short (a few K blocks); the epilogue warps add each
-// segment's result, times its exact power-of-two weight w_g, into an unevaluated sum of two
-// FP32 numbers (hi + lo, updated with the error-free TwoSum), which carries ~44 bits across
-// segments at FP32-pipe cost, and hand hi + lo to the output functor once at the end.
+// accumulates, so the leading sum runs over short segments (a few K blocks); the epilogue
+// warps add each segment's result, times its exact power-of-two weight w_g, into an
+// unevaluated sum of two FP32 numbers (hi + lo, updated with the error-free TwoSum), which
+// carries ~44 bits across segments at FP32-pipe cost, and hand hi + lo to the output
+// functor once at the end. The correction sum is ~2^-8 of the leading one, so its own
+// rounding error stays ~2^-8 below the leading sum's even over a whole job: it accumulates
+// over a run of segments of equal weight (a job's segments, split where the weight
+// changes) and is read once per run, which halves the accumulator traffic per segment.
 //
 // A persistent CTA of 12 warps (one per SM) works through the jobs blockIdx.x, blockIdx.x +
 // gridDim.x, ...; each job is one 128 x BN output tile (jobs come from a table). The stage
 // ring and the two accumulator buffers run on across jobs, so a job's final store overlaps
 // the next job's MMAs.
 //   warp 0      TMA producer (one thread): 3+3 slice tiles per K block into a stage ring;
-//   warp 1      MMA issuer (one thread), also allocates / frees all 512 TMEM columns
-//               (two buffers of two 128-column accumulators, so the epilogue of segment g
-//               overlaps the MMAs of segment g+1);
+//   warp 1      MMA issuer (one thread), also allocates / frees all 512 TMEM columns:
+//               two leading-sum buffers (segment parity), so the epilogue of segment g
+//               overlaps the MMAs of segment g+1, and two correction buffers (run parity);
 //   warps 2, 3  idle (they complete the first warpgroup);
-//   warps 4..11 epilogue: warp w reads TMEM lanes 32*(w%4).. and half (w-4)/4 of the BN columns.
+//   warps 4..11 epilogue: warp w reads TMEM lanes 32*(w%4).. and half (w-4)/4 of the BN columns;
+//               most output functors store through a per-warp shared-memory transpose, so
+//               that each store instruction writes whole row segments instead of 32 rows.
 // Registers: the CTA launches with kLaunchRegs per thread; the first warpgroup gives most of
 // its registers back (setmaxnreg.dec to kCtrlRegs) and the two epilogue warpgroups take them
 // (setmaxnreg.inc to kEpiRegs), which the two-float sums of 64 columns per thread need:
@@ -42,11 +48,15 @@ namespace dmet {
 namespace tc {
 
 struct Segment {
-  int k0;    // first K element (a multiple of the K block)
-  int nkb;   // number of K blocks
-  float w;   // weight of this segment (a power of two, so the scaling is exact)
-  int pad;
+  int k0;     // first K element (a multiple of the K block)
+  int nkb;    // number of K blocks
+  float w;    // weight of this segment (a power of two, so the scaling is exact)
+  int flags;  // kRunFirst / kRunLast: bounds of a correction-sum run inside a job
 };
+// A job's first and last segments always bound a run; these flags add bounds inside a job.
+// Every segment of a run must carry the same weight.
+constexpr int kRunFirst = 1;
+constexpr int kRunLast = 2;
 
 // One output tile: rows [a_row0, a_row0 + 128) of A against rows [b_row0, b_row0 + 128) of B,
 // of which m_valid x n_valid are stored; segments [seg0, seg0 + nseg).
@@ -78,7 +88,8 @@ struct TcCfg {
   static constexpr int STAGE_BYTES = NSLICE * (A_BYTES + B_BYTES);
   static constexpr int STAGES = (192 * 1024) / STAGE_BYTES > 6 ? 6 : (192 * 1024) / STAGE_BYTES;
   static constexpr int NPROD = NSLICE == 3 ? 6 : 1;
-  static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 256;
+  static constexpr int STAGING = 8 * 32 * 8 * 8;                // epilogue transpose: 8 warps x 32 x 8 words
+  static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 256 + STAGING;
   static constexpr int HALF = BN / 2;                           // columns per epilogue warp
 };
 
@@ -90,7 +101,40 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
   lo += e;
 }
 
-// EPI::store<H>(params, job, row, col0, hi, lo): row = tile-local row (< 128), columns col0 .. col0+H-1.
+// Stores a warp's 32 rows x H columns through a 32 x 8 transpose in shared memory (element
+// (r, c) at r * 8 + (c ^ (r & 7)), a swizzle that keeps both phases at two to four
+// wavefronts): each store instruction then covers 4 rows x 8 consecutive columns.
+template <int H, class EPI>
+__device__ __forceinline__ void staged_store(const typename EPI::Params& ep, const TcJob& job, int row0, int col0,
+                                             const float* hi, const float* lo, unsigned long long* stg, int lane) {
+#pragma unroll
+  for (int c0 = 0; c0 < H; c0 += 8) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      // two 32-bit halves: no aligned register pair is needed for the 64-bit value
+      const unsigned long long v = EPI::value(ep, hi[c0 + c], lo[c0 + c]);
+      uint32_t* w = reinterpret_cast<uint32_t*>(stg + lane * 8 + (c ^ (lane & 7)));
+      w[0] = (uint32_t)v;
+      w[1] = (uint32_t)(v >> 32);
+    }
+    __syncwarp();
+    // (An opaque copy of the lane index keeps the compiler from hoisting the eight row
+    // addresses of every 8-column block out of the loop, which would spill.)
+    int ln;
+    asm volatile("mov.b32 %0, %1;" : "=r"(ln) : "r"(lane));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = i * 4 + (ln >> 3), c = ln & 7;
+      EPI::put(ep, job, row0 + r, col0 + c0 + c, stg[r * 8 + (c ^ (r & 7))]);
+    }
+    __syncwarp();
+  }
+}
+
+// Output functors either store per thread, EPI::store<H>(params, job, row, col0, hi, lo) with
+// row = tile-local row (< 128) and columns col0 .. col0+H-1, or (kStaged) give the 8-byte
+// value of an element, EPI::value(params, hi, lo), and write it, EPI::put(params, job, row,
+// col, v), skipping elements outside the job's valid region.
 template <int NSLICE, int ROWB, int BN, class EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -106,6 +150,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // bars: full[S], empty[S], accf[2], acce[2], done; then the TMEM address and a counter.
   volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 2 * S + 5);
   volatile int* consumed = (volatile int*)(bars + 2 * S + 5) + 1;
+  unsigned long long* staging = (unsigned long long*)(smem + S * Cfg::STAGE_BYTES + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -175,23 +220,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       constexpr uint32_t idesc = idesc_bf16_f32(kTile, BN);
       constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
       constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
-      int it = 0, gs = 0;  // K blocks and segments issued so far (across jobs)
+      int it = 0, gs = 0, run = -1;  // K blocks, segments and correction runs so far (across jobs)
       bool ok = true;
       for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x) {
       const TcJob job = jobs[jb];
       for (int g = 0; g < job.nseg && ok; ++g, ++gs) {
         const int b = gs & 1, u = gs >> 1;
+        // The buffer of segment gs - 2 is free once the epilogue has read it; the epilogue
+        // reads a run's correction sum before it releases the run's last segment, so this
+        // also frees the correction buffer of run `run - 1` (every run has >= 1 segment).
         if (!mbar_wait(acce(b), (u & 1) ^ 1, err, 2u)) break;
         tc_fence_after();
-        const uint32_t d_main = tmem + b * 2 * kTile, d_corr = d_main + kTile;  // 128-column aligned
-        const int nkb = segs[job.seg0 + g].nkb;
+        const Segment sg = segs[job.seg0 + g];
+        const bool first = g == 0 || (sg.flags & kRunFirst);
+        run += first;
+        // 128-column aligned: leading sums at 0 / 128, correction sums at 256 / 384
+        const uint32_t d_main = tmem + b * kTile, d_corr = tmem + (2 + (run & 1)) * kTile;
+        const int nkb = sg.nkb;
         for (int kb = 0; kb < nkb; ++kb) {
           const int s = it % S, ph = (it / S) & 1;
           if (!mbar_wait(full(s), ph, err, 4u)) {
             ok = false;
             break;
           }
-          tc_fence_after();
+          // (TMA wrote the stage and the MMAs read it, both through the async proxy; the
+          // mbarrier's phase completion orders them, so no tcgen05 fence belongs here.)
 #pragma unroll
           for (int kk = 0; kk < Cfg::BK / 16; ++kk) {
 #pragma unroll
@@ -199,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint64_t ad = smem_desc<ROWB>(a_tile(s, pa[p]) + kk * 32);
               const uint64_t bd = smem_desc<ROWB>(b_tile(s, pb[p]) + kk * 32);
               if (p == 0) umma_bf16(d_main, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
-              else umma_bf16(d_corr, ad, bd, idesc, ((kb | kk) != 0 || p > 1) ? 1u : 0u);
+              else umma_bf16(d_corr, ad, bd, idesc, (!first || (kb | kk) != 0 || p > 1) ? 1u : 0u);
             }
           }
           umma_commit(empty(s));
@@ -220,14 +273,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row = quad * 32 + lane;
     float hi[H], lo[H];
     bool ok = true;
-    int gs = 0;
+    int gs = 0, run = -1;
     for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x) {
       const TcJob job = jobs[jb];
-#pragma unroll
-      for (int c = 0; c < H; ++c) {
-        hi[c] = 0.f;
-        lo[c] = 0.f;
-      }
       for (int g = 0; g < job.nseg; ++g, ++gs) {
         const int b = gs & 1, u = gs >> 1;
         if (!mbar_wait(accf(b), u & 1, err, 8u)) {
@@ -235,32 +283,57 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const float w = segs[job.seg0 + g].w;
-        const uint32_t tm_main = tmem + ((uint32_t)(quad * 32) << 16) + b * 2 * kTile + half * H;
-        // Up to 32 columns of both accumulators per round trip: all loads, then one wait.
+        const Segment sg = segs[job.seg0 + g];
+        const float w = sg.w;
+        run += g == 0 || (sg.flags & kRunFirst);
+        const bool last = NSLICE == 3 && (g == job.nseg - 1 || (sg.flags & kRunLast));
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + half * H;
+        const uint32_t tm_main = lane_base + b * kTile, tm_corr = lane_base + (2 + (run & 1)) * kTile;
+        // Up to 32 columns per round trip: all loads, then one wait.
 #pragma unroll
         for (int g0 = 0; g0 < H; g0 += 32) {
-          uint32_t vm[32], vc[32];
+          uint32_t v[32];
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            if (g0 + q * 8 < H) {
-              tmem_ld_32x32b_x8(tm_main + g0 + q * 8, vm + q * 8);
-              if (NSLICE == 3) tmem_ld_32x32b_x8(tm_main + kTile + g0 + q * 8, vc + q * 8);
-            }
+            if (g0 + q * 8 < H) tmem_ld_32x32b_x8(tm_main + g0 + q * 8, v + q * 8);
           tmem_ld_wait();
+          // A job's first segment starts the two-float sums (no TwoSum needed).
+          if (g == 0) {
 #pragma unroll
-          for (int c = 0; c < 32; ++c)
-            if (g0 + c < H) {
-              two_sum_acc(hi[g0 + c], lo[g0 + c], w * __uint_as_float(vm[c]));
-              // The correction sum is ~2^-8 of the leading one: it joins the low word.
-              if (NSLICE == 3) lo[g0 + c] += w * __uint_as_float(vc[c]);
-            }
+            for (int c = 0; c < 32; ++c)
+              if (g0 + c < H) {
+                hi[g0 + c] = w * __uint_as_float(v[c]);
+                lo[g0 + c] = 0.f;
+              }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+              if (g0 + c < H) two_sum_acc(hi[g0 + c], lo[g0 + c], w * __uint_as_float(v[c]));
+          }
+        }
+        if (last) {
+          // The correction sum is ~2^-8 of the leading one: it joins the low word.
+#pragma unroll
+          for (int g0 = 0; g0 < H; g0 += 32) {
+            uint32_t v[32];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (g0 + q * 8 < H) tmem_ld_32x32b_x8(tm_corr + g0 + q * 8, v + q * 8);
+            tmem_ld_wait();
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+              if (g0 + c < H) lo[g0 + c] += w * __uint_as_float(v[c]);
+          }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acce(b));
       }
-      if (ok && row < job.m_valid) EPI::template store<H>(ep, job, row, half * H, hi, lo);
+      if constexpr (EPI::kStaged) {
+        if (ok) staged_store<H, EPI>(ep, job, quad * 32, half * H, hi, lo, staging + (warp - 4) * 256, lane);
+      } else {
+        if (ok && row < job.m_valid) EPI::template store<H>(ep, job, row, half * H, hi, lo);
+      }
     }
   }
   __syncthreads();
@@ -277,43 +350,51 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ---------------- output functors ----------------
 
+// scale * (hi + lo) rounded once to FP32 and widened exactly, with scale = sh + sl given as
+// two floats: the product of the two pairs is formed with an exact FMA residual (the dropped
+// lo * sl is ~2^-48 relative), so the only rounding is the final one, 2^-24 relative, which
+// is below the split-BF16 path's own error and keeps the FP64 pipe (1/64 of the FP32 rate on
+// this part) out of the epilogue.
+__device__ __forceinline__ double scaled_pair(float hi, float lo, float sh, float sl) {
+  const float p = hi * sh;
+  const float e = fmaf(hi, sh, -p) + fmaf(hi, sl, lo * sh);
+  return f2d(p + e);
+}
+
 // Lower triangle of a symmetric result, 8-fold packed: element (m, n), m >= n, at
-// m(m+1)/2 + n, m = o0 + row, n = o1 + col. Value = scale * (hi + lo).
+// m(m+1)/2 + n, m = o0 + row, n = o1 + col. Value = scale * (hi + lo), scale = sh + sl.
 struct EpiPacked {
   struct Params {
     double* out;
-    double scale;
+    float sh, sl;
   };
-  template <int H>
-  static __device__ __forceinline__ void store(const Params& p, const TcJob& j, int row, int col0, const float* hi,
-                                               const float* lo) {
-    const long long m = (long long)j.o0 + row;
-    double* o = p.out + m * (m + 1) / 2;
-#pragma unroll
-    for (int c = 0; c < H; ++c) {
-      const int cc = col0 + c;
-      const long long n = (long long)j.o1 + cc;
-      if (cc < j.n_valid && n <= m) o[n] = p.scale * (f2d(hi[c]) + f2d(lo[c]));
-    }
+  static constexpr bool kStaged = true;
+  static __device__ __forceinline__ unsigned long long value(const Params& p, float hi, float lo) {
+    return (unsigned long long)__double_as_longlong(scaled_pair(hi, lo, p.sh, p.sl));
+  }
+  static __device__ __forceinline__ void put(const Params& p, const TcJob& j, int row, int col,
+                                             unsigned long long v) {
+    const long long m = (long long)j.o0 + row, n = (long long)j.o1 + col;
+    if (row < j.m_valid && col < j.n_valid && n <= m)
+      p.out[m * (m + 1) / 2 + n] = __longlong_as_double((long long)v);
   }
 };
 
-// Rectangular: out[(o0 + row) * ldo + o1 + col] = scale * (hi + lo).
+// Rectangular: out[(o0 + row) * ldo + o1 + col] = scale * (hi + lo), scale = sh + sl.
 struct EpiRect {
   struct Params {
     double* out;
     long long ldo;
-    double scale;
+    float sh, sl;
   };
-  template <int H>
-  static __device__ __forceinline__ void store(const Params& p, const TcJob& j, int row, int col0, const float* hi,
-                                               const float* lo) {
-    double* o = p.out + ((long long)j.o0 + row) * p.ldo + j.o1;
-#pragma unroll
-    for (int c = 0; c < H; ++c) {
-      const int cc = col0 + c;
-      if (cc < j.n_valid) o[cc] = p.scale * (f2d(hi[c]) + f2d(lo[c]));
-    }
+  static constexpr bool kStaged = true;
+  static __device__ __forceinline__ unsigned long long value(const Params& p, float hi, float lo) {
+    return (unsigned long long)__double_as_longlong(scaled_pair(hi, lo, p.sh, p.sl));
+  }
+  static __device__ __forceinline__ void put(const Params& p, const TcJob& j, int row, int col,
+                                             unsigned long long v) {
+    if (row < j.m_valid && col < j.n_valid)
+      p.out[((long long)j.o0 + row) * p.ldo + j.o1 + col] = __longlong_as_double((long long)v);
   }
 };
 
