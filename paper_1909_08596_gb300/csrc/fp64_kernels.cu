@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(256, 2) zgemm_fp64_kernel(const ZgemmArgs d) {
   __shared__ __align__(16) double2 Bs[ZBK][TN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  if (d.lower && n0 >= m0 + TM) return;  // the whole CTA leaves together
   const double2* A = d.A;
   const double2* B = d.B;
   double2* D = d.D;
@@ -276,13 +277,15 @@ __device__ __forceinline__ void block_max_commit(double v, double* out) {
   __syncthreads();
 }
 
-// S = s * sum_g S_g (ng split-K partial products of C^+ C); stat = max |S_ij - delta_ij|.
+// S = s * sum_g S_g (ng split-K partial products of C^+ C); stat = max |S_ij - delta_ij| over
+// the lower triangle j <= i (S is Hermitian, and only those tiles of S_g are computed).
 __global__ void orth_reduce_kernel(const double2* __restrict__ Sg, int ng, int n, double s, double* stat) {
   double v = 0.0;
   const long long nn = (long long)n * n;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < nn;
        x += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(x / n), j = (int)(x % n);
+    if (j > i) continue;
     double re = 0.0, im = 0.0;
     for (int g = 0; g < ng; ++g) {
       const double2 e = Sg[g * nn + x];

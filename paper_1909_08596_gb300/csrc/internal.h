@@ -35,6 +35,7 @@ struct ZgemmArgs {
   double alpha;
   int beta;
   int batch;
+  int lower;  // nonzero: skip tiles strictly above the diagonal (Hermitian results)
 };
 
 cudaError_t launch_zgemm(const ZgemmArgs& a, int a_layout, bool conj_a, int b_layout, cudaStream_t s);

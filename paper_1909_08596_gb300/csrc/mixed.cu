@@ -31,29 +31,29 @@ inline int grid_for(long long total, int threads, int cap) {
 }
 
 // Ls[t][(e - e0) * naux * nao + P * nao + mu][col] for col < K1: L^{k1,k2}_{P, mu, nu}.(re|im)
-// at col = 2 nu + c, zero for col >= 2 nao.
-__global__ void split_L_kernel(const double* __restrict__ L, const int4* __restrict__ t1, int e0, int E, int nk,
-                               int naux, int nao, int K1, __nv_bfloat16* __restrict__ Ls, long long sstride) {
-  const long long rows_e = (long long)naux * nao;
-  const long long total = (long long)E * rows_e * K1;
-  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
-       x += (long long)gridDim.x * blockDim.x) {
-    const long long row = x / K1;
-    const int col = (int)(x % K1);
-    const int el = (int)(row / rows_e);
-    const long long rem = row % rows_e;
-    double v = 0.0;
-    if (col < 2 * nao) {
-      const long long pair = t1[e0 + el].y;  // k1 * nk + k2
-      v = L[(pair * rows_e + rem) * 2 * nao + col];
-    }
-    __nv_bfloat16 a, b, c;
-    split3d(v, a, b, c);
-    Ls[x] = a;
-    Ls[x + sstride] = b;
-    Ls[x + 2 * sstride] = c;
+// at col = 2 nu + c, zero for col >= 2 nao. One thread per (row, nu): it reads the complex
+// element (16 bytes; a warp reads a row's run of nu) and writes one bf16 (re, im) pair per
+// slice. blockIdx.y is the entry; all index arithmetic within an entry is 32-bit.
+__global__ void __launch_bounds__(256) split_L_kernel(const double2* __restrict__ L, const int4* __restrict__ t1,
+                                                      int e0, int naux, int nao, int K1,
+                                                      __nv_bfloat162* __restrict__ Ls, long long sstride2) {
+  const int el = blockIdx.y;
+  const int rows_e = naux * nao, half = K1 >> 1;
+  const int total = rows_e * half;
+  const long long pair = t1[e0 + el].y;  // k1 * nk + k2
+  const double2* src = L + pair * rows_e * nao;
+  __nv_bfloat162* dst = Ls + (long long)el * total;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < total; x += gridDim.x * blockDim.x) {
+    const int row = x / half, nu = x - row * half;
+    double2 v = make_double2(0.0, 0.0);
+    if (nu < nao) v = src[(long long)row * nao + nu];
+    const float2 re = d2ff(v.x), im = d2ff(v.y);
+    __nv_bfloat162 a, b, c;
+    split3f2(re.x, re.y, im.x, im.y, a, b, c);
+    dst[x] = a;
+    dst[x + sstride2] = b;
+    dst[x + 2 * sstride2] = c;
   }
-  (void)nk;
 }
 
 // Cb[t][k * 2n + 2j + p][col], col = 2 nu + c < 2 nao:
@@ -271,9 +271,17 @@ int mixed_kblock() { return tc::TcCfg<3, 64, 128>::BK; }
 
 cudaError_t launch_split_L(const double2* L, const int4* t1, int e0, int E, int nk, int naux, int nao, int K1,
                            void* Ls, long long sstride, cudaStream_t s) {
-  const long long total = (long long)E * naux * nao * K1;
-  split_L_kernel<<<grid_for(total, 256, 152 * 32), 256, 0, s>>>((const double*)L, t1, e0, E, nk, naux, nao, K1,
-                                                               (__nv_bfloat16*)Ls, sstride);
+  if (E <= 0) return cudaSuccess;
+  if ((long long)naux * nao * (K1 / 2) >= (1LL << 31) || E > 65535) return cudaErrorInvalidValue;
+  // about 16 blocks of 256 threads per SM over all entries, at least one per entry
+  const long long per_entry = (long long)naux * nao * (K1 / 2);
+  long long gx = (152LL * 16 + E - 1) / E;
+  const long long need = (per_entry + 255) / 256;
+  if (gx > need) gx = need;
+  if (gx < 1) gx = 1;
+  split_L_kernel<<<dim3((unsigned)gx, (unsigned)E), 256, 0, s>>>(L, t1, e0, naux, nao, K1, (__nv_bfloat162*)Ls,
+                                                                sstride / 2);
+  (void)nk;
   return cudaGetLastError();
 }
 

@@ -373,6 +373,22 @@ struct Timed {
   }
 };
 
+// Split-K groups of the orthonormality product C^+ C (K = Nk n_AO rows of C): a divisor of K
+// whose chunks hold >= 8 rows (one k-step of the FP64 kernel), as many as make about four
+// CTAs per SM over the lower-triangle tiles, with the partial products kept under 256 MB.
+int orth_groups_for(int nk, int nao, int n) {
+  const long long K = (long long)nk * nao;
+  const long long tiles = (n + 63) / 64, lower = tiles * (tiles + 1) / 2;
+  const long long want = std::max(1LL, 4 * 152 / lower);
+  const long long cap = std::max(1LL, (256LL << 20) / std::max(1LL, (long long)n * n * 16));
+  int best = 1;
+  for (long long g = 1; g <= K; ++g) {
+    if (K % g || K / g < 8 || g > want || g > cap) continue;
+    best = (int)g;
+  }
+  return best;
+}
+
 ZgemmArgs zargs() {
   ZgemmArgs z;
   std::memset(&z, 0, sizeof(z));
@@ -408,14 +424,16 @@ dmet_status_t run_orbital_checks(dmet_emb_plan_s* P, Prob& pr, int p, const doub
     {
       // split-K over groups of k-points so that the small n x n product fills the GPU
       const int ng = pr.orth_groups;
-      Timed t(P, KC_CHECK_C, 8.0 * n * n * (double)pr.nk * pr.nao, 16.0 * pr.nk * pr.nao * n, 2);
+      const int tiles = (n + 63) / 64;
+      Timed t(P, KC_CHECK_C, 8.0 * 64 * 64 * (tiles * (tiles + 1) / 2) * (double)pr.nk * pr.nao,
+              16.0 * pr.nk * pr.nao * n, 2);
       ZgemmArgs z = zargs();
       z.A = C[s];
       z.B = C[s];
       z.D = P->W->S;
       z.M = n;
       z.N = n;
-      z.K = (pr.nk / ng) * pr.nao;
+      z.K = (pr.nk * pr.nao) / ng;  // the (k, mu) rows split into ng equal chunks
       z.lda = n;
       z.ldb = n;
       z.sA = (long long)z.K * n;
@@ -424,6 +442,7 @@ dmet_status_t run_orbital_checks(dmet_emb_plan_s* P, Prob& pr, int p, const doub
       z.dm_lo = n;
       z.dn_lo = 1;
       z.batch = ng;
+      z.lower = 1;
       CK(launch_zgemm(z, A_KM, true, B_KN, P->cs));
       CK(launch_orth_reduce(P->W->S, ng, n, pr.ortho_scale, st + 0, P->cs));
     }
@@ -1104,11 +1123,7 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     pr.pack = pr.d.eri_pack == DMET_PACK_AUTO ? (pr.d.sym == DMET_SYM_REAL ? DMET_PACK_S8 : DMET_PACK_FULL)
                                               : pr.d.eri_pack;
     pr.lq_scale = pr.d.ck_norm == 0 ? 1.0 / pr.nk : 1.0;
-    for (int g = std::min(pr.nk, 32); g >= 1; --g)
-      if (pr.nk % g == 0) {
-        pr.orth_groups = g;
-        break;
-      }
+    pr.orth_groups = orth_groups_for(pr.nk, pr.nao, std::max(pr.n[0], pr.n[1]));
     pr.ortho_scale = pr.lq_scale;
     std::vector<int> nat(pr.nk);
     for (int q = 0; q < pr.nk; ++q) nat[q] = q;
