@@ -227,7 +227,7 @@ struct EpiPairs {
 template <int BN, class EPI>
 cudaError_t launch_tc_bn(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                          const tc::Segment* segs, const typename EPI::Params& ep, unsigned int* err, cudaStream_t s) {
-  using Cfg = tc::TcCfg<3, 64, BN>;
+  using Cfg = tc::TcCfg<3, 64, BN, EPI::kStaged>;
   static bool attr = false;
   if (!attr) {
     // The register split inside the kernel assumes exactly kLaunchRegs registers per thread at
@@ -267,7 +267,7 @@ cudaError_t launch_tc(int bn, const CUtensorMap& A, const CUtensorMap& B, const 
 
 }  // namespace
 
-int mixed_kblock() { return tc::TcCfg<3, 64, 128>::BK; }
+int mixed_kblock() { return tc::TcCfg<3, 64, 128, true>::BK; }
 
 cudaError_t launch_split_L(const double2* L, const int4* t1, int e0, int E, int nk, int naux, int nao, int K1,
                            void* Ls, long long sstride, cudaStream_t s) {

@@ -940,15 +940,22 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
                            P->cs));
       }
       {
-        Timed t(P, KC_TC_TRANSFORM_1, 8.0 * n * (double)pr.naux * pr.nao * pr.nao * E, 0.0, 1,
+        // algorithmic bytes: the L slices read once, T written once as three bf16 slices
+        const double by = 6.0 * E * pr.naux * pr.nao * (m.K1 + 2.0 * n);
+        Timed t(P, KC_TC_TRANSFORM_1, 8.0 * n * (double)pr.naux * pr.nao * pr.nao * E, by, 1,
                 exec_flops(m, m.j1_off[s][bi], m.j1_cnt[s][bi], m.bn1));
         CK(launch_tc_split_t(m.bn1, mm.Ls, mm.Cb[s], m.d_jobs + m.j1_off[s][bi], m.j1_cnt[s][bi], m.d_segs, P->W->A2,
                              a2_rows * m.K2, m.K2, pr.nao, n, P->derr, P->cs));
       }
       {
-        double fl = 0;
-        for (int i = bl.b0; i < bl.b1; ++i) fl += 8.0 * n * (double)pr.naux * n * pr.con.t2[i].w;
-        Timed t(P, KC_TC_TRANSFORM_2, fl, 0.0, 1, exec_flops(m, m.j2_off[s][bi], m.j2_cnt[s][bi], m.bn2));
+        double fl = 0, by = 0;
+        for (int i = bl.b0; i < bl.b1; ++i) {
+          fl += 8.0 * n * (double)pr.naux * n * pr.con.t2[i].w;
+          // the slot's T slices (K = its padded 2 n_rep n_AO) read once, Z written as two-float pairs
+          const double K = (double)padk(2LL * pr.s.nrep[pr.con.order[i]] * pr.nao);
+          by += 6.0 * pr.naux * n * K + 6.0 * 2 * n * K + 8.0 * pr.naux * n * 2.0 * n;
+        }
+        Timed t(P, KC_TC_TRANSFORM_2, fl, by, 1, exec_flops(m, m.j2_off[s][bi], m.j2_cnt[s][bi], m.bn2));
         CK(launch_tc_pairs(m.bn2, mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs, P->W->ZT, 2LL * n,
                            P->derr, P->cs));
       }
@@ -968,7 +975,10 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
     const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
     const double fl = blk == 1 ? 2.0 * pr.npair[0] * (double)pr.npair[1] * K
                                : (double)pr.npair[sa] * (pr.npair[sa] + 1.0) * K;
-    Timed t(P, KC_TC_CONTRACT, fl, 0.0, 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk], tc::kTile));
+    // algorithmic bytes: both operands' slices read once, the packed FP64 result written once
+    const double by = 6.0 * m.Rtot * (double)(pr.npair[sa] + (blk == 1 ? pr.npair[sb] : 0)) +
+                      8.0 * (blk == 1 ? (double)pr.npair[sa] * pr.npair[sb] : pr.npair[sa] * (pr.npair[sa] + 1.0) / 2);
+    Timed t(P, KC_TC_CONTRACT, fl, by, 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk], tc::kTile));
     if (blk == 1)
       CK(launch_tc_rect(mm.Xt[0], mm.Xt[1], m.d_jobs + m.jc_off[1], m.jc_cnt[1], m.d_segs, (double*)out[1],
                         pr.npair[1], oscale, P->derr, P->cs));

@@ -31,10 +31,10 @@
 //               most output functors store through a per-warp shared-memory transpose, so
 //               that each store instruction writes whole row segments instead of 32 rows.
 // Registers: the CTA launches with kLaunchRegs per thread; the first warpgroup gives most of
-// its registers back (setmaxnreg.dec to kCtrlRegs) and the two epilogue warpgroups take them
-// (setmaxnreg.inc to kEpiRegs), which the two-float sums of 64 columns per thread need:
-// 128 * kCtrlRegs + 256 * kEpiRegs = 384 * kLaunchRegs, and per SM sub-partition (one warp of
-// each warpgroup) kCtrlRegs + 2 * kEpiRegs <= 512.
+// its registers back (setmaxnreg.dec to kCtrlRegs) and the epilogue warpgroups take them
+// (setmaxnreg.inc to kEpiRegs), which the two-float sums of up to 64 columns per thread need:
+// 128 * kCtrlRegs + 128 * kEpiGroups * kEpiRegs <= kThreads * kLaunchRegs, and per SM
+// sub-partition (one warp of each warpgroup) kCtrlRegs + kEpiGroups * kEpiRegs <= 512.
 #pragma once
 
 #include <cuda.h>
@@ -68,17 +68,23 @@ struct TcJob {
 };
 
 constexpr int kTile = 128;
-constexpr int kThreads = 384;
+constexpr int kEpiGroups = 2;                    // epilogue warpgroups
+constexpr int kEpiWarps = 4 * kEpiGroups;
+constexpr int kThreads = 128 * (1 + kEpiGroups);
 constexpr int kTmemCols = 512;
-constexpr int kLaunchRegs = 168;
+constexpr int kLaunchRegs = 168;  // 65536 / 384, in the 8-register allocation unit
 constexpr int kCtrlRegs = 56;
 constexpr int kEpiRegs = 224;
-static_assert(128 * kCtrlRegs + 256 * kEpiRegs == kThreads * kLaunchRegs, "register split must match the launch");
-static_assert(kCtrlRegs + 2 * kEpiRegs <= 512, "per sub-partition register file");
+static_assert(kLaunchRegs * kThreads <= 65536, "register file");
+static_assert(128 * kCtrlRegs + 128 * kEpiGroups * kEpiRegs <= kThreads * kLaunchRegs,
+              "the register split must fit in what the CTA launches with");
+static_assert(kCtrlRegs + kEpiGroups * kEpiRegs <= 512, "per sub-partition register file");
 
 // BN: output columns per tile (the UMMA N), 128, 112 or 96. Each of the four accumulators
 // (two buffers of leading + correction sums) starts on a 128-column boundary of TMEM.
-template <int NSLICE, int ROWB, int BN>
+// STAGED: the output functor stores through the shared-memory transpose. The stage ring
+// takes what the 227 KB of shared memory leave (4 to 6 stages).
+template <int NSLICE, int ROWB, int BN, bool STAGED>
 struct TcCfg {
   static_assert(BN % 32 == 16 || BN % 32 == 0, "BN must be a multiple of 16");
   static_assert(BN <= 128 && BN >= 64, "4 BN TMEM columns must fit");
@@ -86,11 +92,14 @@ struct TcCfg {
   static constexpr int A_BYTES = kTile * ROWB;                  // one A slice tile
   static constexpr int B_BYTES = BN * ROWB;                     // one B slice tile
   static constexpr int STAGE_BYTES = NSLICE * (A_BYTES + B_BYTES);
-  static constexpr int STAGES = (192 * 1024) / STAGE_BYTES > 6 ? 6 : (192 * 1024) / STAGE_BYTES;
   static constexpr int NPROD = NSLICE == 3 ? 6 : 1;
-  static constexpr int STAGING = 8 * 32 * 8 * 8;                // epilogue transpose: 8 warps x 32 x 8 words
+  static constexpr int STAGING = STAGED ? kEpiWarps * 32 * 8 * 8 : 0;  // epilogue transpose: 32 x 8 words per warp
+  static constexpr int RING = 232448 - 1024 - 256 - STAGING;    // 227 KB less alignment, barriers, staging
+  static constexpr int STAGES = RING / STAGE_BYTES > 6 ? 6 : RING / STAGE_BYTES;
   static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 256 + STAGING;
-  static constexpr int HALF = BN / 2;                           // columns per epilogue warp
+  static_assert(STAGES >= 2 && SMEM <= 232448, "shared memory");
+  static constexpr int PART = BN / kEpiGroups;                  // columns per epilogue warp
+  static_assert(PART % 4 == 0, "epilogue column share");
 };
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
@@ -107,8 +116,29 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
 template <int H, class EPI>
 __device__ __forceinline__ void staged_store(const typename EPI::Params& ep, const TcJob& job, int row0, int col0,
                                              const float* hi, const float* lo, unsigned long long* stg, int lane) {
+  static_assert(H % 4 == 0, "column share");
 #pragma unroll
   for (int c0 = 0; c0 < H; c0 += 8) {
+    if (c0 + 8 > H) {
+      // 4-column tail: the block is 32 x 4, each store instruction covers 8 rows x 4 columns.
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const unsigned long long v = EPI::value(ep, hi[c0 + c], lo[c0 + c]);
+        uint32_t* w = reinterpret_cast<uint32_t*>(stg + lane * 8 + (c ^ (lane & 7)));
+        w[0] = (uint32_t)v;
+        w[1] = (uint32_t)(v >> 32);
+      }
+      __syncwarp();
+      int ln;
+      asm volatile("mov.b32 %0, %1;" : "=r"(ln) : "r"(lane));
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = i * 8 + (ln >> 2), c = ln & 3;
+        EPI::put(ep, job, row0 + r, col0 + c0 + c, stg[r * 8 + (c ^ (r & 7))]);
+      }
+      __syncwarp();
+      break;
+    }
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       // two 32-bit halves: no aligned register pair is needed for the 64-bit value
@@ -140,9 +170,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcJob* __restrict__ jobs, int njobs, const Segment* __restrict__ segs,
                    const typename EPI::Params ep, unsigned int* err) {
-  using Cfg = TcCfg<NSLICE, ROWB, BN>;
+  using Cfg = TcCfg<NSLICE, ROWB, BN, EPI::kStaged>;
   constexpr int S = Cfg::STAGES;
-  constexpr int H = Cfg::HALF;
+  constexpr int H = Cfg::PART;
+  constexpr int kChunk = 32;  // TMEM columns per load round trip
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* tiles = smem;
@@ -171,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf(b), 1);
-      mbar_init(acce(b), 8);
+      mbar_init(acce(b), kEpiWarps);
     }
     mbar_init(done_bar, 1);
     *consumed = 0;
@@ -269,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kEpiRegs));
     // ---------------- epilogue ----------------
-    const int quad = warp & 3, half = (warp - 4) >> 2;
+    const int quad = warp & 3, half = (warp - 4) >> 2;  // (half: this warp's column share)
     const int row = quad * 32 + lane;
     float hi[H], lo[H];
     bool ok = true;
@@ -289,39 +320,39 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool last = NSLICE == 3 && (g == job.nseg - 1 || (sg.flags & kRunLast));
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + half * H;
         const uint32_t tm_main = lane_base + b * kTile, tm_corr = lane_base + (2 + (run & 1)) * kTile;
-        // Up to 32 columns per round trip: all loads, then one wait.
+        // Up to kChunk columns per round trip: all loads, then one wait.
 #pragma unroll
-        for (int g0 = 0; g0 < H; g0 += 32) {
-          uint32_t v[32];
+        for (int g0 = 0; g0 < H; g0 += kChunk) {
+          uint32_t v[kChunk];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
+          for (int q = 0; q < kChunk / 8; ++q)
             if (g0 + q * 8 < H) tmem_ld_32x32b_x8(tm_main + g0 + q * 8, v + q * 8);
           tmem_ld_wait();
           // A job's first segment starts the two-float sums (no TwoSum needed).
           if (g == 0) {
 #pragma unroll
-            for (int c = 0; c < 32; ++c)
+            for (int c = 0; c < kChunk; ++c)
               if (g0 + c < H) {
                 hi[g0 + c] = w * __uint_as_float(v[c]);
                 lo[g0 + c] = 0.f;
               }
           } else {
 #pragma unroll
-            for (int c = 0; c < 32; ++c)
+            for (int c = 0; c < kChunk; ++c)
               if (g0 + c < H) two_sum_acc(hi[g0 + c], lo[g0 + c], w * __uint_as_float(v[c]));
           }
         }
         if (last) {
           // The correction sum is ~2^-8 of the leading one: it joins the low word.
 #pragma unroll
-          for (int g0 = 0; g0 < H; g0 += 32) {
-            uint32_t v[32];
+          for (int g0 = 0; g0 < H; g0 += kChunk) {
+            uint32_t v[kChunk];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < kChunk / 8; ++q)
               if (g0 + q * 8 < H) tmem_ld_32x32b_x8(tm_corr + g0 + q * 8, v + q * 8);
             tmem_ld_wait();
 #pragma unroll
-            for (int c = 0; c < 32; ++c)
+            for (int c = 0; c < kChunk; ++c)
               if (g0 + c < H) lo[g0 + c] += w * __uint_as_float(v[c]);
           }
         }

@@ -64,6 +64,8 @@ class LatticeSpec:
 CONFIGS = {
     "tiny_2x2x1": LatticeSpec((2, 2, 1), 8, 40, 16, 1, 0.7, 0.0, 0, "tiny_2x2x1"),
     "hbn_6x6x1": LatticeSpec((6, 6, 1), 26, 220, 104, 1, 0.5, 0.0, 1000, "hbn_6x6x1"),
+    # the same cell on a 4x4x1 mesh (L = 0.61 GB): the case the profiler captures kernel by kernel
+    "hbn_4x4x1": LatticeSpec((4, 4, 1), 26, 220, 104, 1, 0.5, 0.0, 1100, "hbn_4x4x1"),
     "si_4x4x4": LatticeSpec((4, 4, 4), 52, 400, 200, 1, 0.6, 4.0, 2000, "si_4x4x4"),
     "nio_4x4x4_uhf": LatticeSpec((4, 4, 4), 104, 900, 300, 2, 0.6, 0.0, 3000, "nio_4x4x4_uhf"),
 }
