@@ -112,5 +112,9 @@ cudaError_t launch_tc_rect(const CUtensorMap& A, const CUtensorMap& B, const tc:
                            const tc::Segment* segs, double* out, long long ldo, double scale, unsigned int* err,
                            cudaStream_t s);
 cudaError_t launch_tc_packed(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                             const tc::Segment* segs, double* out, double scale, unsigned int* err, cudaStream_t s);
+                             const tc::Segment* segs, double* out, double scale, void* part, unsigned int* err,
+                             cudaStream_t s);
+// Sums the K parts of the split tiles of a packed contraction (the parts' jobs: jobs[0 .. ntiles * f)).
+cudaError_t launch_combine_parts(const tc::TcJob* jobs, int ntiles, int f, const void* part, double* out, double scale,
+                                 cudaStream_t s);
 }  // namespace dmet

@@ -213,7 +213,7 @@ struct EpiPairs {
     long long ldo;
   };
   static constexpr bool kStaged = true;
-  static __device__ __forceinline__ unsigned long long value(const Params&, float hi, float lo) {
+  static __device__ __forceinline__ unsigned long long value(const Params&, const tc::TcJob&, float hi, float lo) {
     return (unsigned long long)__float_as_uint(hi) | ((unsigned long long)__float_as_uint(lo) << 32);
   }
   static __device__ __forceinline__ void put(const Params& p, const tc::TcJob& j, int row, int col,
@@ -265,7 +265,39 @@ cudaError_t launch_tc(int bn, const CUtensorMap& A, const CUtensorMap& B, const 
   }
 }
 
+// The split tiles of a packed contraction: tile t (its first part is jobs[t * f]) is the sum of
+// its f K parts, part[t * f + p][row][col] = (hi, lo); the sum is formed with TwoSum, scaled as
+// the contraction's own epilogue does, and stored where that epilogue would have stored it.
+__global__ void __launch_bounds__(256) combine_parts_kernel(const tc::TcJob* __restrict__ jobs, int f,
+                                                            const uint2* __restrict__ part, double* __restrict__ out,
+                                                            float sh, float sl) {
+  const tc::TcJob j = jobs[(long long)blockIdx.x * f];
+  const int T = tc::kTile;
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < T * T; e += gridDim.y * blockDim.x) {
+    const int row = e / T, col = e % T;
+    if (row >= j.m_valid || col >= j.n_valid) continue;
+    const long long m = (long long)j.o0 + row, n = (long long)j.o1 + col;
+    if (n > m) continue;
+    float hi = 0.f, lo = 0.f;
+    for (int q = 0; q < f; ++q) {
+      const uint2 v = part[((long long)blockIdx.x * f + q) * T * T + e];
+      tc::two_sum_acc(hi, lo, __uint_as_float(v.x));
+      lo += __uint_as_float(v.y);
+    }
+    out[m * (m + 1) / 2 + n] = tc::scaled_pair(hi, lo, sh, sl);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_combine_parts(const tc::TcJob* jobs, int ntiles, int f, const void* part, double* out, double scale,
+                                 cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  const float sh = (float)scale;
+  combine_parts_kernel<<<dim3((unsigned)ntiles, 8), 256, 0, s>>>(jobs, f, (const uint2*)part, out, sh,
+                                                                 (float)(scale - (double)sh));
+  return cudaGetLastError();
+}
 
 int mixed_kblock() { return tc::TcCfg<3, 64, 128, true>::BK; }
 
@@ -331,9 +363,10 @@ cudaError_t launch_tc_pairs(int bn, const CUtensorMap& A, const CUtensorMap& B, 
 }
 
 cudaError_t launch_tc_packed(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                             const tc::Segment* segs, double* out, double scale, unsigned int* err, cudaStream_t s) {
+                             const tc::Segment* segs, double* out, double scale, void* part, unsigned int* err,
+                             cudaStream_t s) {
   const float sh = (float)scale;
-  tc::EpiPacked::Params p{out, sh, (float)(scale - (double)sh)};
+  tc::EpiPacked::Params p{out, sh, (float)(scale - (double)sh), (unsigned long long*)part};
   return launch_tc<tc::EpiPacked>(128, A, B, jobs, njobs, segs, p, err, s);
 }
 

@@ -181,6 +181,8 @@ struct MixedPlan {
   // offsets (first, count) into jobs: step 1 / step 2 per block and spin; contraction per block kind
   std::vector<int> j1_off[2], j1_cnt[2], j2_off[2], j2_cnt[2];
   int jc_off[3] = {0, 0, 0}, jc_cnt[3] = {0, 0, 0};
+  // per contraction block: split tiles (their K parts are the last jc_split_n * jc_split_f jobs)
+  int jc_split_n[3] = {0, 0, 0}, jc_split_f[3] = {1, 1, 1};
   tc::TcJob* d_jobs = nullptr;
   tc::Segment* d_segs = nullptr;
   long long Ls_rows = 0, A2_rows[2] = {0, 0};
@@ -730,6 +732,20 @@ long long padk(long long x) {
   return (x + bk - 1) / bk * bk;
 }
 
+int device_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      n <= 0)
+    return 152;
+  return n;
+}
+
+// Bytes of the step-2 output workspace (two-float pairs of one q-block's Z).
+long long zt_bytes(const Prob& pr) {
+  const long long nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
+  return (long long)pr.bq * pr.naux * nmax * 2 * nmax * 8;
+}
+
 void build_mixed(Prob& pr) {
   MixedPlan& m = pr.mx;
   const int BK = mixed_kblock();
@@ -836,6 +852,37 @@ void build_mixed(Prob& pr) {
                             (int)std::min<long long>(T, pb - nt * T), sc_off, sc_cnt, mt * T, nt * T, 0, 0});
         }
     m.jc_cnt[blk] = (int)m.jobs.size() - m.jc_off[blk];
+    // The persistent CTAs take jobs round-robin, so the tiles past the last multiple of the SM
+    // count form a short last wave. Those tiles are split in K into f parts (summed afterwards
+    // by combine_parts, in the two-float form) so that the last wave fills the GPU. The parts'
+    // partial sums go to the step-2 workspace, which the contraction does not otherwise use.
+    m.jc_split_n[blk] = 0;
+    m.jc_split_f[blk] = 1;
+    if (blk != 1) {
+      const int G = device_sms();
+      const int tail = m.jc_cnt[blk] % G;
+      int f = tail ? std::min(G / tail, 8) : 1;
+      f = std::min(f, sc_cnt);
+      const long long cap = zt_bytes(pr) / ((long long)T * T * 8);
+      while (f >= 2 && (long long)tail * f > cap) --f;
+      if (tail && f >= 2) {
+        std::vector<tc::TcJob> tl(m.jobs.end() - tail, m.jobs.end());
+        m.jobs.resize(m.jobs.size() - tail);
+        for (int t = 0; t < tail; ++t)
+          for (int q = 0; q < f; ++q) {
+            tc::TcJob j = tl[t];
+            const int a = q * sc_cnt / f, b = (q + 1) * sc_cnt / f;
+            j.seg0 = sc_off + a;
+            j.nseg = b - a;
+            j.o2 = 1;
+            j.o3 = t * f + q;
+            m.jobs.push_back(j);
+          }
+        m.jc_cnt[blk] = (int)m.jobs.size() - m.jc_off[blk];
+        m.jc_split_n[blk] = tail;
+        m.jc_split_f[blk] = f;
+      }
+    }
   }
   // useful flops of one call (the same count as the FP64 path)
   m.useful_t1 = m.useful_t2 = m.useful_c = 0;
@@ -880,7 +927,7 @@ MixedWs mixed_ws(const Prob& pr) {
   }
   w.Cc = (size_t)3 * pr.bq * 2 * nmax * m.K2 * 2;
   w.A2 = (size_t)3 * pr.bq * pr.naux * nmax * m.K2 * 2;
-  w.ZT = (size_t)pr.bq * pr.naux * nmax * 2 * nmax * 8;
+  w.ZT = (size_t)zt_bytes(pr);
   return w;
 }
 
@@ -978,13 +1025,18 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
     // algorithmic bytes: both operands' slices read once, the packed FP64 result written once
     const double by = 6.0 * m.Rtot * (double)(pr.npair[sa] + (blk == 1 ? pr.npair[sb] : 0)) +
                       8.0 * (blk == 1 ? (double)pr.npair[sa] * pr.npair[sb] : pr.npair[sa] * (pr.npair[sa] + 1.0) / 2);
-    Timed t(P, KC_TC_CONTRACT, fl, by, 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk], tc::kTile));
-    if (blk == 1)
+    const int nsplit = m.jc_split_n[blk], f = m.jc_split_f[blk];
+    Timed t(P, KC_TC_CONTRACT, fl, by, nsplit ? 2 : 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk], tc::kTile));
+    if (blk == 1) {
       CK(launch_tc_rect(mm.Xt[0], mm.Xt[1], m.d_jobs + m.jc_off[1], m.jc_cnt[1], m.d_segs, (double*)out[1],
                         pr.npair[1], oscale, P->derr, P->cs));
-    else
+    } else {
       CK(launch_tc_packed(mm.Xt[sa], mm.Xt[sa], m.d_jobs + m.jc_off[blk], m.jc_cnt[blk], m.d_segs, (double*)out[blk],
-                          oscale, P->derr, P->cs));
+                          oscale, P->W->ZT, P->derr, P->cs));
+      if (nsplit)
+        CK(launch_combine_parts(m.d_jobs + m.jc_off[blk] + m.jc_cnt[blk] - nsplit * f, nsplit, f, P->W->ZT,
+                                (double*)out[blk], oscale, P->cs));
+    }
   }
   return DMET_OK;
 }

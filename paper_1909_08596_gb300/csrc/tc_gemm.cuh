@@ -59,7 +59,8 @@ constexpr int kRunFirst = 1;
 constexpr int kRunLast = 2;
 
 // One output tile: rows [a_row0, a_row0 + 128) of A against rows [b_row0, b_row0 + 128) of B,
-// of which m_valid x n_valid are stored; segments [seg0, seg0 + nseg).
+// of which m_valid x n_valid are stored; segments [seg0, seg0 + nseg). A job may also be one
+// K part of a tile (the output functor then stores the unscaled two-float partial sum).
 struct TcJob {
   int a_row0, b_row0;
   int m_valid, n_valid;
@@ -123,7 +124,7 @@ __device__ __forceinline__ void staged_store(const typename EPI::Params& ep, con
       // 4-column tail: the block is 32 x 4, each store instruction covers 8 rows x 4 columns.
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const unsigned long long v = EPI::value(ep, hi[c0 + c], lo[c0 + c]);
+        const unsigned long long v = EPI::value(ep, job, hi[c0 + c], lo[c0 + c]);
         uint32_t* w = reinterpret_cast<uint32_t*>(stg + lane * 8 + (c ^ (lane & 7)));
         w[0] = (uint32_t)v;
         w[1] = (uint32_t)(v >> 32);
@@ -142,7 +143,7 @@ __device__ __forceinline__ void staged_store(const typename EPI::Params& ep, con
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       // two 32-bit halves: no aligned register pair is needed for the 64-bit value
-      const unsigned long long v = EPI::value(ep, hi[c0 + c], lo[c0 + c]);
+      const unsigned long long v = EPI::value(ep, job, hi[c0 + c], lo[c0 + c]);
       uint32_t* w = reinterpret_cast<uint32_t*>(stg + lane * 8 + (c ^ (lane & 7)));
       w[0] = (uint32_t)v;
       w[1] = (uint32_t)(v >> 32);
@@ -163,7 +164,7 @@ __device__ __forceinline__ void staged_store(const typename EPI::Params& ep, con
 
 // Output functors either store per thread, EPI::store<H>(params, job, row, col0, hi, lo) with
 // row = tile-local row (< 128) and columns col0 .. col0+H-1, or (kStaged) give the 8-byte
-// value of an element, EPI::value(params, hi, lo), and write it, EPI::put(params, job, row,
+// value of an element, EPI::value(params, job, hi, lo), and write it, EPI::put(params, job, row,
 // col, v), skipping elements outside the job's valid region.
 template <int NSLICE, int ROWB, int BN, class EPI>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -394,20 +395,28 @@ __device__ __forceinline__ double scaled_pair(float hi, float lo, float sh, floa
 
 // Lower triangle of a symmetric result, 8-fold packed: element (m, n), m >= n, at
 // m(m+1)/2 + n, m = o0 + row, n = o1 + col. Value = scale * (hi + lo), scale = sh + sl.
+// A job with o2 != 0 is K part o3 of a split tile: it stores the unscaled pair (hi, lo) of
+// every element of the tile to part[o3][row][col] (128 x 128), for combine_parts to sum.
 struct EpiPacked {
   struct Params {
     double* out;
     float sh, sl;
+    unsigned long long* part;
   };
   static constexpr bool kStaged = true;
-  static __device__ __forceinline__ unsigned long long value(const Params& p, float hi, float lo) {
+  static __device__ __forceinline__ unsigned long long value(const Params& p, const TcJob& j, float hi, float lo) {
+    if (j.o2) return (unsigned long long)__float_as_uint(hi) | ((unsigned long long)__float_as_uint(lo) << 32);
     return (unsigned long long)__double_as_longlong(scaled_pair(hi, lo, p.sh, p.sl));
   }
   static __device__ __forceinline__ void put(const Params& p, const TcJob& j, int row, int col,
                                              unsigned long long v) {
+    if (row >= j.m_valid || col >= j.n_valid) return;
+    if (j.o2) {
+      p.part[((long long)j.o3 * kTile + row) * kTile + col] = v;
+      return;
+    }
     const long long m = (long long)j.o0 + row, n = (long long)j.o1 + col;
-    if (row < j.m_valid && col < j.n_valid && n <= m)
-      p.out[m * (m + 1) / 2 + n] = __longlong_as_double((long long)v);
+    if (n <= m) p.out[m * (m + 1) / 2 + n] = __longlong_as_double((long long)v);
   }
 };
 
@@ -419,7 +428,7 @@ struct EpiRect {
     float sh, sl;
   };
   static constexpr bool kStaged = true;
-  static __device__ __forceinline__ unsigned long long value(const Params& p, float hi, float lo) {
+  static __device__ __forceinline__ unsigned long long value(const Params& p, const TcJob&, float hi, float lo) {
     return (unsigned long long)__double_as_longlong(scaled_pair(hi, lo, p.sh, p.sl));
   }
   static __device__ __forceinline__ void put(const Params& p, const TcJob& j, int row, int col,
