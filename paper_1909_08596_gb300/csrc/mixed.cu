@@ -43,16 +43,28 @@ __global__ void __launch_bounds__(256) split_L_kernel(const double2* __restrict_
   const long long pair = t1[e0 + el].y;  // k1 * nk + k2
   const double2* src = L + pair * rows_e * nao;
   __nv_bfloat162* dst = Ls + (long long)el * total;
-  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < total; x += gridDim.x * blockDim.x) {
-    const int row = x / half, nu = x - row * half;
-    double2 v = make_double2(0.0, 0.0);
-    if (nu < nao) v = src[(long long)row * nao + nu];
-    const float2 re = d2ff(v.x), im = d2ff(v.y);
-    __nv_bfloat162 a, b, c;
-    split3f2(re.x, re.y, im.x, im.y, a, b, c);
-    dst[x] = a;
-    dst[x + sstride2] = b;
-    dst[x + 2 * sstride2] = c;
+  // Four elements per trip, all loads issued before the first conversion (memory-level parallelism).
+  const int stride = gridDim.x * blockDim.x;
+  for (int x0 = blockIdx.x * blockDim.x + threadIdx.x; x0 < total; x0 += 4 * stride) {
+    double2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int x = x0 + u * stride;
+      const int row = x / half, nu = x - row * half;
+      v[u] = make_double2(0.0, 0.0);
+      if (x < total && nu < nao) v[u] = src[(long long)row * nao + nu];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int x = x0 + u * stride;
+      if (x >= total) break;
+      const float2 re = d2ff(v[u].x), im = d2ff(v[u].y);
+      __nv_bfloat162 a, b, c;
+      split3f2(re.x, re.y, im.x, im.y, a, b, c);
+      dst[x] = a;
+      dst[x + sstride2] = b;
+      dst[x + 2 * sstride2] = c;
+    }
   }
 }
 
@@ -132,23 +144,27 @@ __global__ void __launch_bounds__(256) pack_split_kernel(const float2* __restric
   const int P0 = blockIdx.y * PK_P;
   const int slot = blockIdx.z;
   const float4* z = reinterpret_cast<const float4*>(ZT + (long long)slot * naux * n * 2 * n);
-  for (int e = threadIdx.x; e < PK_P * PK_B * PK_B; e += blockDim.x) {
+  // All eight loads of a thread are issued before any is stored (256 threads, 1024 elements).
+  constexpr int kPer = PK_P * PK_B * PK_B / 256;
+  float4 va[kPer], vb[kPer];
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int e = threadIdx.x + r * 256;
     const int pl = e / (PK_B * PK_B), a = (e / PK_B) % PK_B, b = e % PK_B;
     const int P = P0 + pl;
     // za[pl][ii][jj] = Z_{i j} with (ii, jj) = (b, a): consecutive e run over i for fixed j.
-    {
-      const int i = i0 + b, j = j0 + a;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (P < naux && i < n && j < n) v = z[((long long)P * n + j) * n + i];
-      za[pl][b][a] = v;
-    }
+    va[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (P < naux && i0 + b < n && j0 + a < n) va[r] = z[((long long)P * n + j0 + a) * n + i0 + b];
     // zb[pl][ii][jj] = Z_{j i} with (ii, jj) = (a, b): consecutive e run over j for fixed i.
-    {
-      const int i = i0 + a, j = j0 + b;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (P < naux && i < n && j < n) v = z[((long long)P * n + i) * n + j];
-      zb[pl][a][b] = v;
-    }
+    vb[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (P < naux && i0 + a < n && j0 + b < n) vb[r] = z[((long long)P * n + i0 + a) * n + j0 + b];
+  }
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int e = threadIdx.x + r * 256;
+    const int pl = e / (PK_B * PK_B), a = (e / PK_B) % PK_B, b = e % PK_B;
+    za[pl][b][a] = va[r];
+    zb[pl][a][b] = vb[r];
   }
   __syncthreads();
   const int nr = PK_P * nc;  // rows per pair in this block
@@ -304,11 +320,11 @@ int mixed_kblock() { return tc::TcCfg<3, 64, 128, true>::BK; }
 cudaError_t launch_split_L(const double2* L, const int4* t1, int e0, int E, int nk, int naux, int nao, int K1,
                            void* Ls, long long sstride, cudaStream_t s) {
   if (E <= 0) return cudaSuccess;
-  if ((long long)naux * nao * (K1 / 2) >= (1LL << 31) || E > 65535) return cudaErrorInvalidValue;
+  if ((long long)naux * nao * (K1 / 2) >= (1LL << 30) || E > 65535) return cudaErrorInvalidValue;
   // about 16 blocks of 256 threads per SM over all entries, at least one per entry
   const long long per_entry = (long long)naux * nao * (K1 / 2);
   long long gx = (152LL * 16 + E - 1) / E;
-  const long long need = (per_entry + 255) / 256;
+  const long long need = (per_entry + 1023) / 1024;  // four elements per thread at least
   if (gx > need) gx = need;
   if (gx < 1) gx = 1;
   split_L_kernel<<<dim3((unsigned)gx, (unsigned)E), 256, 0, s>>>(L, t1, e0, naux, nao, K1, (__nv_bfloat162*)Ls,
