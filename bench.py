@@ -39,7 +39,14 @@ DFMA_PER_SM_CLK = 2  # FP64 FMA lanes per SM per clock on GB300 (1.25 TFLOP/s no
 ORACLE_SAMPLE_ORBITALS = 24
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from the
 # ncu captures summarised under profiles/ (workload, path, kernel class) -> bytes.
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the dominant kernels, averaged over the launches of one call, from an
+# ncu capture of the same revision (profiles/*_bf16x3_hbn_4x4x1.txt give the command); valid only for the
+# kernels as they are at that revision.
+TRAFFIC = {
+    ("hbn_6x6x1", "bf16x3", "tc_half_transform_1"): 1.489e9,
+    ("hbn_6x6x1", "bf16x3", "tc_half_transform_2"): 1.186e9,
+    ("hbn_6x6x1", "bf16x3", "tc_contract"): 1.273e9,
+}
 
 
 def useful_flops(spec, n_list, desc_sym=1):
