@@ -22,7 +22,10 @@
  *  Pointers may be device pointers or host pointers (pageable or pinned); the library
  *  classifies each with cudaPointerGetAttributes. Host inputs are staged through
  *  plan-owned device buffers; host outputs are copied back and the call then waits for
- *  its stream. Every pointer must be 16-byte aligned. The caller owns all input and
+ *  its stream. For a real-orbital (sym = REAL, 8-fold packed) problem without check_l,
+ *  dmet_emb_eri transfers from a host L only the (k1, k2) blocks its schedule reads: one
+ *  k1 per orbit {k1, -k1-q} and one q per pair {q, -q} (the others follow from the
+ *  symmetries the caller declared), about a quarter of L. Every pointer must be 16-byte aligned. The caller owns all input and
  *  output buffers; the plan owns only its workspace, staging buffers and tables.
  *
  * Errors: every entry point returns a dmet_status_t and never aborts or traps.

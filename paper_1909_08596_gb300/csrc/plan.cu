@@ -1357,9 +1357,13 @@ dmet_status_t dmet_emb_destroy(dmet_emb_plan_t plan) {
   return DMET_OK;
 }
 
-// Staging: device pointers pass through; host pointers are copied into plan buffers.
+// Staging: device pointers pass through; host pointers are copied into plan buffers. With
+// `subset`, a host L that the 8-fold-packed schedule reads only in part (one (k1, k2) block per
+// transformed pair, see Tables::t1) is copied block run by block run into the same offsets of
+// the staging buffer; the blocks the schedule never reads are not transferred (unless the L
+// symmetry check, which reads every block, is on).
 static dmet_status_t stage_inputs(dmet_emb_plan_s* P, const Prob& pr, const void* L, const void* const* C,
-                                  const double2** Ld, const double2** Cd) {
+                                  const double2** Ld, const double2** Cd, bool subset = false) {
   const size_t lb = (size_t)pr.nk * pr.nk * pr.naux * pr.nao * pr.nao * 16;
   size_t need = 0;
   const bool lhost = L && !is_device_ptr(L);
@@ -1375,8 +1379,29 @@ static dmet_status_t stage_inputs(dmet_emb_plan_s* P, const Prob& pr, const void
   char* cur = (char*)P->stage_in;
   if (L) *Ld = (const double2*)L;
   if (lhost) {
-    Timed t(P, KC_COPY, 0.0, (double)lb);
-    CK(cudaMemcpyAsync(cur, L, lb, cudaMemcpyHostToDevice, P->cs));
+    if (subset && pr.pack == DMET_PACK_S8 && !pr.d.check_l && !pr.con.t1.empty()) {
+      // runs of consecutive pair indices among the transformed pairs
+      std::vector<int> pairs;
+      pairs.reserve(pr.con.t1.size());
+      for (const int4& e : pr.con.t1) pairs.push_back(e.y);
+      std::sort(pairs.begin(), pairs.end());
+      pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+      const size_t bb = lb / ((size_t)pr.nk * pr.nk);  // bytes of one (k1, k2) block
+      std::vector<std::pair<size_t, size_t>> runs;     // (first pair, number of pairs)
+      for (size_t i = 0; i < pairs.size();) {
+        size_t j = i + 1;
+        while (j < pairs.size() && pairs[j] == pairs[j - 1] + 1) ++j;
+        runs.emplace_back((size_t)pairs[i], j - i);
+        i = j;
+      }
+      Timed t(P, KC_COPY, 0.0, (double)pairs.size() * bb);
+      for (const auto& r : runs)
+        CK(cudaMemcpyAsync(cur + r.first * bb, (const char*)L + r.first * bb, r.second * bb, cudaMemcpyHostToDevice,
+                           P->cs));
+    } else {
+      Timed t(P, KC_COPY, 0.0, (double)lb);
+      CK(cudaMemcpyAsync(cur, L, lb, cudaMemcpyHostToDevice, P->cs));
+    }
     *Ld = (const double2*)cur;
     cur += lb;
   }
@@ -1457,7 +1482,7 @@ static dmet_status_t enqueue_problem(dmet_emb_plan_s* P, int p, const void* L, c
   }
   const double2* Ld = nullptr;
   const double2* Cd[2] = {nullptr, nullptr};
-  TRY(stage_inputs(P, pr, L, C, &Ld, Cd));
+  TRY(stage_inputs(P, pr, L, C, &Ld, Cd, /*subset=*/true));
   CK(cudaMemsetAsync(P->dstats + 8 * p, 0, 8 * sizeof(double), P->cs));
   TRY(run_orbital_checks(P, pr, p, Cd));
   TRY(run_l_check(P, pr, p, Ld));

@@ -155,3 +155,17 @@ def test_mixed_autotune(torch, tmp_path, monkeypatch):
     assert widths[0] in (128, 112, 96) and widths[1] in (128, 112, 96)
     assert cache.read_text().split()[-2:] == [str(widths[0]), str(widths[1])]
     check(out.cpu().numpy(), oracle.pack_s8(oracle.embedded_eri(L, Cs[0], spec.mesh).real))
+
+
+@pytest.mark.parametrize("check_l", [0, 1])
+def test_mixed_host_inputs_match_device(torch, check_l):
+    """Host-resident L and C give the device result: only the (k1, k2) blocks the schedule reads
+    are transferred (all of them with check_l), and nothing else of L is needed."""
+    spec = spec_of((3, 3, 1), 6, 11, 20)
+    L, Cs, _ = synth.make_problem(spec)
+    d = desc_of(spec, check_l=check_l)
+    dev, st1, _ = run_eri(torch, d, L, Cs)
+    host, st2, _ = run_eri(torch, d, L, Cs, host=True)
+    assert st1 == st2 == B.DMET_OK
+    assert np.array_equal(dev[0], host[0])
+    check(host[0], oracle.pack_s8(oracle.embedded_eri(L, Cs[0], spec.mesh).real))
