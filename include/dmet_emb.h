@@ -25,7 +25,9 @@
  *  its stream. For a real-orbital (sym = REAL, 8-fold packed) problem without check_l,
  *  dmet_emb_eri transfers from a host L only the (k1, k2) blocks its schedule reads: one
  *  k1 per orbit {k1, -k1-q} and one q per pair {q, -q} (the others follow from the
- *  symmetries the caller declared), about a quarter of L. Every pointer must be 16-byte aligned. The caller owns all input and
+ *  symmetries the caller declared), about a quarter of L; the blocks of each q-block are
+ *  copied on an internal stream (ordered after the work already queued on the plan's
+ *  stream) while the previous q-block is being transformed. Every pointer must be 16-byte aligned. The caller owns all input and
  *  output buffers; the plan owns only its workspace, staging buffers and tables.
  *
  * Errors: every entry point returns a dmet_status_t and never aborts or traps.

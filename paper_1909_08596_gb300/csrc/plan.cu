@@ -254,6 +254,16 @@ struct dmet_emb_plan_s {
   size_t stage_in_b = 0;
   void* stage_out = nullptr;
   size_t stage_out_b = 0;
+  // Host L transferred block by block on its own stream: the problem being enqueued waits on
+  // xev[b] (its contraction block b's pairs have landed) before its first read of L in block b.
+  cudaStream_t xs = nullptr;
+  cudaEvent_t xstart = nullptr;
+  std::vector<cudaEvent_t> xev;
+  bool xpending = false;
+  int xnext = 0;              // next block whose copies are still to be queued
+  const char* xsrc = nullptr;  // host L of the problem being enqueued
+  char* xdst = nullptr;        // its staging buffer
+  size_t xbb = 0;              // bytes of one (k1, k2) block
   // per-problem device time of the last profiled call
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pev;
   // CUDA graph of the last device-pointer call (replayed while the pointers stay the same)
@@ -268,6 +278,7 @@ struct dmet_emb_plan_s {
   std::vector<cudaEvent_t> pool;
   long long launches = 0;
 };
+
 
 namespace {
 
@@ -334,6 +345,7 @@ bool is_device_ptr(const void* p) {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+
 // ------------------------------------------------------------------------------------------
 // Launch helpers with per-class accounting and optional CUDA-event timing.
 
@@ -349,6 +361,41 @@ cudaEvent_t get_event(dmet_emb_plan_s* P) {
     return nullptr;
   }
   return e;
+}
+
+// Queues on the copy stream the host-to-device copies of the L blocks that contraction block b of
+// the problem being enqueued reads (runs of consecutive pair indices; each pair belongs to one q,
+// so to one block), and records xev[b]. Block b + 1's copies are queued right after block b's
+// kernels, so that they run on the copy engines while those kernels run.
+static dmet_status_t queue_block_copies(dmet_emb_plan_s* P, const Prob& pr, int b) {
+  if (!P->xpending || b != P->xnext || b >= (int)pr.con_blocks.size()) return DMET_OK;
+  const Block& bl = pr.con_blocks[b];
+  std::vector<int> pairs;
+  for (int e = pr.con.start[bl.b0]; e < pr.con.start[bl.b1]; ++e) pairs.push_back(pr.con.t1[e].y);
+  std::sort(pairs.begin(), pairs.end());
+  pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+  cudaEvent_t ta = nullptr, tb = nullptr;
+  if (P->prof) {
+    ta = get_event(P);
+    tb = get_event(P);
+    if (ta) CK(cudaEventRecord(ta, P->xs));
+  }
+  for (size_t i = 0; i < pairs.size();) {
+    size_t j = i + 1;
+    while (j < pairs.size() && pairs[j] == pairs[j - 1] + 1) ++j;
+    const size_t off = (size_t)pairs[i] * P->xbb, len = (j - i) * P->xbb;
+    CK(cudaMemcpyAsync(P->xdst + off, P->xsrc + off, len, cudaMemcpyHostToDevice, P->xs));
+    i = j;
+  }
+  CK(cudaEventRecord(P->xev[b], P->xs));
+  if (ta && tb) {
+    CK(cudaEventRecord(tb, P->xs));
+    P->ks[KC_COPY].ev.emplace_back(ta, tb);
+  }
+  P->ks[KC_COPY].bytes += (double)pairs.size() * P->xbb;
+  P->ks[KC_COPY].launches += 1;
+  P->xnext = b + 1;
+  return DMET_OK;
 }
 
 struct Timed {
@@ -551,7 +598,12 @@ dmet_status_t transform_range(dmet_emb_plan_s* P, Prob& pr, const double2* L, co
 }
 
 dmet_status_t eri_s8(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, void* const* out) {
-  for (const Block& bl : pr.con_blocks) {
+  for (size_t bi = 0; bi < pr.con_blocks.size(); ++bi) {
+    const Block& bl = pr.con_blocks[bi];
+    if (P->xpending) {
+      TRY(queue_block_copies(P, pr, (int)bi));
+      CK(cudaStreamWaitEvent(P->cs, P->xev[bi], 0));
+    }
     const int nq = bl.b1 - bl.b0;
     const int nc = bl.w == 1 ? 1 : 2;
     for (int s = 0; s < pr.nspin; ++s) {
@@ -713,6 +765,12 @@ void destroy_plan(dmet_emb_plan_s* P) {
       cudaEventDestroy(e.second);
     }
   for (auto e : P->pool) cudaEventDestroy(e);
+  if (P->xs) {
+    cudaStreamSynchronize(P->xs);
+    cudaStreamDestroy(P->xs);
+  }
+  if (P->xstart) cudaEventDestroy(P->xstart);
+  for (auto e : P->xev) cudaEventDestroy(e);
   cudaGetLastError();
   delete P;
 }
@@ -974,6 +1032,10 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
   for (size_t bi = 0; bi < m.blocks.size(); ++bi) {
     const Block& bl = m.blocks[bi];
     const int e0 = pr.con.start[bl.b0], E = pr.con.start[bl.b1] - e0, nq = bl.b1 - bl.b0;
+    if (P->xpending) {
+      TRY(queue_block_copies(P, pr, (int)bi));
+      CK(cudaStreamWaitEvent(P->cs, P->xev[bi], 0));
+    }
     {
       const double rows = (double)E * pr.naux * pr.nao;
       Timed t(P, KC_SPLIT, 0.0, rows * (16.0 * pr.nao + 6.0 * m.K1));
@@ -1365,6 +1427,7 @@ dmet_status_t dmet_emb_destroy(dmet_emb_plan_t plan) {
 static dmet_status_t stage_inputs(dmet_emb_plan_s* P, const Prob& pr, const void* L, const void* const* C,
                                   const double2** Ld, const double2** Cd, bool subset = false) {
   const size_t lb = (size_t)pr.nk * pr.nk * pr.naux * pr.nao * pr.nao * 16;
+  P->xpending = false;
   size_t need = 0;
   const bool lhost = L && !is_device_ptr(L);
   if (lhost) need += lb;
@@ -1377,42 +1440,46 @@ static dmet_status_t stage_inputs(dmet_emb_plan_s* P, const Prob& pr, const void
   }
   if (need) TRY(ensure(&P->stage_in, &P->stage_in_b, need));
   char* cur = (char*)P->stage_in;
+  // C first (small; the orbital checks need it before any L block)
+  {
+    char* cc = cur + (lhost ? lb : 0);
+    for (int s = 0; s < pr.nspin; ++s) {
+      Cd[s] = (const double2*)C[s];
+      if (chost[s]) {
+        Timed t(P, KC_COPY, 0.0, (double)cb[s]);
+        CK(cudaMemcpyAsync(cc, C[s], cb[s], cudaMemcpyHostToDevice, P->cs));
+        Cd[s] = (const double2*)cc;
+        cc += cb[s];
+      }
+    }
+  }
   if (L) *Ld = (const double2*)L;
   if (lhost) {
     if (subset && pr.pack == DMET_PACK_S8 && !pr.d.check_l && !pr.con.t1.empty()) {
-      // runs of consecutive pair indices among the transformed pairs
-      std::vector<int> pairs;
-      pairs.reserve(pr.con.t1.size());
-      for (const int4& e : pr.con.t1) pairs.push_back(e.y);
-      std::sort(pairs.begin(), pairs.end());
-      pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
-      const size_t bb = lb / ((size_t)pr.nk * pr.nk);  // bytes of one (k1, k2) block
-      std::vector<std::pair<size_t, size_t>> runs;     // (first pair, number of pairs)
-      for (size_t i = 0; i < pairs.size();) {
-        size_t j = i + 1;
-        while (j < pairs.size() && pairs[j] == pairs[j - 1] + 1) ++j;
-        runs.emplace_back((size_t)pairs[i], j - i);
-        i = j;
+      if (!P->xs) {
+        CK(cudaStreamCreateWithFlags(&P->xs, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&P->xstart, cudaEventDisableTiming));
       }
-      Timed t(P, KC_COPY, 0.0, (double)pairs.size() * bb);
-      for (const auto& r : runs)
-        CK(cudaMemcpyAsync(cur + r.first * bb, (const char*)L + r.first * bb, r.second * bb, cudaMemcpyHostToDevice,
-                           P->cs));
+      while (P->xev.size() < pr.con_blocks.size()) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        P->xev.push_back(e);
+      }
+      // the staging buffer is free once the work queued before this call has read it
+      CK(cudaEventRecord(P->xstart, P->cs));
+      CK(cudaStreamWaitEvent(P->xs, P->xstart, 0));
+      P->xsrc = (const char*)L;
+      P->xdst = cur;
+      P->xbb = lb / ((size_t)pr.nk * pr.nk);
+      P->xnext = 0;
+      P->xpending = true;
+      TRY(queue_block_copies(P, pr, 0));
     } else {
       Timed t(P, KC_COPY, 0.0, (double)lb);
       CK(cudaMemcpyAsync(cur, L, lb, cudaMemcpyHostToDevice, P->cs));
     }
     *Ld = (const double2*)cur;
     cur += lb;
-  }
-  for (int s = 0; s < pr.nspin; ++s) {
-    Cd[s] = (const double2*)C[s];
-    if (chost[s]) {
-      Timed t(P, KC_COPY, 0.0, (double)cb[s]);
-      CK(cudaMemcpyAsync(cur, C[s], cb[s], cudaMemcpyHostToDevice, P->cs));
-      Cd[s] = (const double2*)cur;
-      cur += cb[s];
-    }
   }
   return DMET_OK;
 }
@@ -1506,9 +1573,12 @@ static dmet_status_t enqueue_problem(dmet_emb_plan_s* P, int p, const void* L, c
       }
   }
   for (int b = 0; b < nblk; ++b) CK(cudaMemsetAsync(out[b], 0, ob[b], P->cs));
-  if (pr.mixed) TRY(eri_mixed(P, pr, Ld, Cd, out));
-  else if (pr.pack == DMET_PACK_S8) TRY(eri_s8(P, pr, Ld, Cd, out));
-  else TRY(eri_full(P, pr, Ld, Cd, out));
+  dmet_status_t st = DMET_OK;
+  if (pr.mixed) st = eri_mixed(P, pr, Ld, Cd, out);
+  else if (pr.pack == DMET_PACK_S8) st = eri_s8(P, pr, Ld, Cd, out);
+  else st = eri_full(P, pr, Ld, Cd, out);
+  P->xpending = false;
+  TRY(st);
   if (need) {
     for (int b = 0; b < nblk; ++b)
       if (ohost[b]) {

@@ -169,3 +169,25 @@ def test_mixed_host_inputs_match_device(torch, check_l):
     assert st1 == st2 == B.DMET_OK
     assert np.array_equal(dev[0], host[0])
     check(host[0], oracle.pack_s8(oracle.embedded_eri(L, Cs[0], spec.mesh).real))
+
+
+def test_mixed_pinned_host_inputs_match_device(torch):
+    """Pinned host L (which the GPU can address directly) gives the device result."""
+    import paper_1909_08596_gb300 as dm
+    spec = spec_of((3, 3, 1), 6, 11, 20)
+    L, Cs, _ = synth.make_problem(spec)
+    d = desc_of(spec)
+    dev, st1, _ = run_eri(torch, d, L, Cs)
+    Lh = torch.from_numpy(L).pin_memory()
+    Ch = [torch.from_numpy(c).pin_memory() for c in Cs]
+    Oh = [torch.empty(dm.dmet_emb_eri_bytes(d, 0) // 8, dtype=torch.float64).pin_memory()]
+    plan = dm.dmet_emb_plan(d, stream=torch.cuda.current_stream().cuda_stream)
+    try:
+        for _ in range(2):  # the second call reuses the staging buffer
+            dm.dmet_emb_eri(plan, [Lh], [Ch], [Oh])
+            torch.cuda.synchronize()
+            st2, _ = dm.dmet_emb_status(plan, 0)
+            assert st1 == st2 == B.DMET_OK
+            assert np.array_equal(dev[0], Oh[0].numpy())
+    finally:
+        dm.dmet_emb_destroy(plan)
