@@ -681,6 +681,12 @@ void partition(const Prob& pr, const Tables& t, const std::vector<int>& wts, int
     out.push_back({i, j, wts[i]});
     i = j;
   }
+  // Largest blocks first: with host inputs each block's L is copied while the previous block is
+  // transformed, so the work left after the last copy is the smallest block's. (Each block
+  // keeps its slots, rows and output terms; only the order of processing changes.)
+  std::stable_sort(out.begin(), out.end(), [&](const Block& a, const Block& b) {
+    return t.start[a.b1] - t.start[a.b0] > t.start[b.b1] - t.start[b.b0];
+  });
   (void)pr;
 }
 
