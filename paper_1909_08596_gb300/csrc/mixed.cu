@@ -128,13 +128,16 @@ __global__ void build_Cc_kernel(const double2* __restrict__ C, const int4* __res
 // Xt[t][IJ][row_base + (slot * naux + P) * nc + c] = split of (Z_ij + Z_ji).c for i >= j, where
 // each real component of Z_ij (complex) is a two-float pair ZT[slot][(P n + j) 2n + 2i + (re|im)].
 // (The factor s of L^q = s (Z + Z^T) is applied, squared, to the contraction's output.)
-constexpr int PK_P = 16, PK_B = 8;
+constexpr int PK_P = 64, PK_B = 4;
 __global__ void __launch_bounds__(256) pack_split_kernel(const float2* __restrict__ ZT, int naux, int n, int nc,
                                                          __nv_bfloat16* __restrict__ Xt, long long sstride,
                                                          long long Rtot, long long row_base) {
-  __shared__ float4 za[PK_P][PK_B][PK_B];  // (re.hi, re.lo, im.hi, im.lo)
-  __shared__ float4 zb[PK_P][PK_B][PK_B];
-  // pair-block decode: lower triangle of ceil(n/8) blocks
+  // (re.hi, re.lo, im.hi, im.lo) of (pl, ii, jj) at [pl][ii * PK_B + jj]; the odd row pitch puts
+  // consecutive pl (the lanes of the write phase) in different banks.
+  constexpr int kPitch = PK_B * PK_B + 1;
+  __shared__ float4 za[PK_P][kPitch];
+  __shared__ float4 zb[PK_P][kPitch];
+  // pair-block decode: lower triangle of ceil(n / PK_B) blocks
   const long long t = blockIdx.x;
   long long bi = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
   while (bi * (bi + 1) / 2 > t) --bi;
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(256) pack_split_kernel(const float2* __restric
   const int P0 = blockIdx.y * PK_P;
   const int slot = blockIdx.z;
   const float4* z = reinterpret_cast<const float4*>(ZT + (long long)slot * naux * n * 2 * n);
-  // All eight loads of a thread are issued before any is stored (256 threads, 1024 elements).
+  // All loads of a thread are issued before any is stored (256 threads).
   constexpr int kPer = PK_P * PK_B * PK_B / 256;
   float4 va[kPer], vb[kPer];
 #pragma unroll
@@ -163,8 +166,8 @@ __global__ void __launch_bounds__(256) pack_split_kernel(const float2* __restric
   for (int r = 0; r < kPer; ++r) {
     const int e = threadIdx.x + r * 256;
     const int pl = e / (PK_B * PK_B), a = (e / PK_B) % PK_B, b = e % PK_B;
-    za[pl][b][a] = va[r];
-    zb[pl][a][b] = vb[r];
+    za[pl][b * PK_B + a] = va[r];
+    zb[pl][a * PK_B + b] = vb[r];
   }
   __syncthreads();
   const int nr = PK_P * nc;  // rows per pair in this block
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(256) pack_split_kernel(const float2* __restric
     const int pl = rl / nc, c = rl % nc;
     const int P = P0 + pl;
     if (i >= n || j > i || P >= naux) continue;
-    const float4 a = za[pl][ii][jj], b = zb[pl][ii][jj];
+    const float4 a = za[pl][ii * PK_B + jj], b = zb[pl][ii * PK_B + jj];
     const float ah = c == 0 ? a.x : a.z, al = c == 0 ? a.y : a.w;
     const float bh = c == 0 ? b.x : b.z, bl = c == 0 ? b.y : b.w;
     // (ah + al) + (bh + bl) as a two-float pair: TwoSum of the leading parts.
