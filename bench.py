@@ -131,6 +131,26 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def rank_spec(base, rank):
+    """Weak scaling: every rank transforms its own problem of the same shape (its own seed)."""
+    return synth.spec_with(base, seed=base.seed + 17 * rank)
+
+
+def max_over_ranks(dist, ms, device):
+    """The job's time is the slowest rank's (a MAX all-reduce; the only collective, outside the data path)."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_tflops(world, flops_per_problem, steps, ms_total):
+    """Whole-job throughput: every rank's problems over the slowest rank's time."""
+    return world * flops_per_problem * steps / (ms_total / 1e3) / 1e12
+
+
 def oracle_sample(spec, L, C, n_sub, seed=0):
     """Runs the CPU oracle (Algorithm 1 as written: every q, every k1, dense contraction) on a
     seeded subset of n_sub embedding orbitals; returns (seconds, useful flops, orbital subset,
@@ -246,12 +266,9 @@ def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
     launches = dm.dmet_emb_launch_count(plan) - launches0
     kstats = [dm.dmet_emb_profile_read(plan, k) for k in range(dm.dmet_emb_profile_count())]
     dm.dmet_emb_profile(plan, False)
-    if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(dist, ms_total, "cuda")
     ms_step = ms_total / steps
-    value = world * fl_total * steps / (ms_total / 1e3) / 1e12
+    value = job_tflops(world, fl_total, steps, ms_total)
 
     peaks, peak_src = measured_peaks()
     top = max(kstats, key=lambda k: k["ms"])
@@ -439,7 +456,7 @@ def main():
 
     base = synth.CONFIGS[args.workload]
     # Weak scaling: every rank transforms its own problem (a different seed); no data exchange.
-    spec = synth.spec_with(base, seed=base.seed + 17 * rank)
+    spec = rank_spec(base, rank)
     L, Cs, _ = synth.make_problem(spec)
     Ld = torch.from_numpy(L).cuda()
     Cd = [torch.from_numpy(c).cuda() for c in Cs]
