@@ -36,3 +36,18 @@ def supercell_eri(B, mesh, Csc_a, Csc_b=None):
     xa = np.concatenate(xa, 0)
     xb = np.concatenate(xb, 0)
     return np.tensordot(xa, xb, axes=([0], [0]))
+
+
+def supercell_fock(f, mesh, Csc):
+    """Csc^+ Fsc Csc with Fsc[(R1, mu), (R2, nu)] = f[mu, nu, R2 - R1]: the Fock matrix of the
+    supercell orbitals, with no k-points (pins Eq. "fock transform" and its conventions)."""
+    cells = _cells(mesh)
+    nmesh = np.asarray(mesh)
+    n_ao, nk = f.shape[0], f.shape[2]
+    Fsc = np.zeros((nk * n_ao, nk * n_ao))
+    for a, r1 in enumerate(cells):
+        d = (cells - r1) % nmesh
+        idx = (d[:, 0] * nmesh[1] + d[:, 1]) * nmesh[2] + d[:, 2]
+        for b in range(nk):
+            Fsc[a * n_ao:(a + 1) * n_ao, b * n_ao:(b + 1) * n_ao] = f[:, :, idx[b]]
+    return Csc.conj().T @ Fsc @ Csc

@@ -38,6 +38,8 @@ _STREAM_B = 1 << 40
 _STREAM_C = 2 << 40
 _STREAM_SCALE = 3 << 40
 _STREAM_BATH = 4 << 40
+_STREAM_FOCK = 5 << 40
+_STREAM_DM = 6 << 40
 
 
 @dataclasses.dataclass(frozen=True)
@@ -227,6 +229,38 @@ def make_problem(spec: LatticeSpec, ck_norm: int = 0, with_L: bool = True):
     cs = [bloch_orbitals(c, spec.mesh, ck_norm) for c in cscs]
     L = make_L(spec) if with_L else None
     return L, cs, cscs
+
+
+def real_space_fock(spec: LatticeSpec, spin: int = 0) -> np.ndarray:
+    """f[mu, nu, R], real: the mean-field Fock matrix between AO mu of cell 0 and AO nu of cell R.
+
+    Entries N(0,1) * exp(-a |R|), then symmetrised so that f[nu, mu, -R] = f[mu, nu, R] (a
+    real, Hermitian one-particle operator that is invariant under lattice translations).
+    """
+    nk, na = spec.nk, spec.n_ao
+    g = _rng(spec.seed + spin, _STREAM_FOCK).standard_normal((na, na, nk))
+    g *= np.exp(-spec.decay * min_image_norm(spec.mesh))[None, None, :]
+    cells = cell_vectors(spec.mesh)
+    n = np.asarray(spec.mesh)
+    neg = (-cells) % n
+    neg_idx = (neg[:, 0] * n[1] + neg[:, 1]) * n[2] + neg[:, 2]
+    return 0.5 * (g + g.transpose(1, 0, 2)[:, :, neg_idx])
+
+
+def fock_k(f: np.ndarray, mesh) -> np.ndarray:
+    """F[k, mu, nu] = sum_R exp(+i k.R) f[mu, nu, R]: the Fock matrix at k, Hermitian."""
+    return np.ascontiguousarray(np.einsum("kR,mnR->kmn", phases(mesh).conj(), f))
+
+
+def embedding_density(n: int, seed: int, n_occ: int | None = None) -> np.ndarray:
+    """gamma [n, n], real symmetric with eigenvalues in [0, 2] (a spin-summed one-particle
+    density matrix of the embedding space): 2 on n_occ random orthonormal directions, U(0, 2)
+    on the others."""
+    g = _rng(seed, _STREAM_DM)
+    q, _ = np.linalg.qr(g.standard_normal((n, n)))
+    n_occ = n // 2 if n_occ is None else n_occ
+    occ = np.concatenate([np.full(n_occ, 2.0), g.uniform(0.0, 2.0, n - n_occ)])
+    return np.ascontiguousarray((q * occ[None, :]) @ q.T)
 
 
 def spec_with(spec: LatticeSpec, **kw) -> LatticeSpec:
