@@ -315,6 +315,35 @@ def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
             e["exec_tflops"] = round(k["exec_flops"] / (k["ms"] / 1e3) / 1e12, 1)
         kernels[k["name"]] = e
 
+    # The embedding one-particle Hamiltonian from this ERI (dmet_emb_fock, FP64 kernels): timed on
+    # its own, after the ERI, with a synthetic mean-field Fock matrix and embedding density.
+    fock = None
+    if spec.n_spin == 1:
+        Fk = torch.from_numpy(synth.fock_k(synth.real_space_fock(spec), spec.mesh)).cuda()
+        gam = torch.from_numpy(synth.embedding_density(spec.n_emb, spec.seed)).cuda()
+        fo = torch.empty((spec.n_emb, spec.n_emb), dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            dm.dmet_emb_fock(plan, Fk, Cd[0], outs[0], gam, fo)
+        dm.dmet_emb_profile(plan, True)
+        reps = 10
+        ef0, ef1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ef0.record(stream)
+        for _ in range(reps):
+            dm.dmet_emb_fock(plan, Fk, Cd[0], outs[0], gam, fo)
+        ef1.record(stream)
+        torch.cuda.synchronize()
+        fk = [k for k in (dm.dmet_emb_profile_read(plan, i) for i in range(dm.dmet_emb_profile_count()))
+              if k["name"] == "embedding_fock"][0]
+        dm.dmet_emb_profile(plan, False)
+        f_ms = ef0.elapsed_time(ef1) / reps
+        f_peak = SMS * DFMA_PER_SM_CLK * 2 * 2070e6 / 1e12
+        f_tf = fk["flops"] / reps / (f_ms / 1e3) / 1e12
+        fock = {"ms": f_ms, "launches_per_call": fk["launches"] // reps,
+                "roofline": {"bound": "alu", "achieved": f_tf, "peak": f_peak, "unit": "TFLOP/s", "frac": f_tf / f_peak,
+                             "flops_counted": "FP64 flops the kernels execute (transform GEMMs; 10 per visit of an ordered "
+                                              "pair of pairs for Coulomb and exchange)",
+                             "peak_source": "derived FP64 peak (152 SMs x 2 FMA/clk x 2 x 2070 MHz)"}}
+
     # End to end through the C ABI with host buffers: H2D of L and C, D2H of the ERI.
     Lh = torch.from_numpy(L).pin_memory()
     Ch = [torch.from_numpy(c).pin_memory() for c in Cs]
@@ -346,6 +375,7 @@ def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
                 "matches_device_result": bool(same)},
         "device_checks": {"status": int(st), "orthonormality": stats[0], "realness": stats[1],
                           "hermiticity_L": stats[2], "time_reversal_L": stats[3]},
+        "embedding_fock": fock,
         "result": [o.cpu().numpy() for o in outs],
     }
 
@@ -482,6 +512,7 @@ def main():
         "e2e": head["e2e"],
         "device_checks": head["device_checks"],
         "tile_widths": head.get("tile_widths"),
+        "embedding_fock": head.get("embedding_fock"),
     }
     for p in precs[1:]:
         r = res[p]

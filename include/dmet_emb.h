@@ -152,6 +152,25 @@ DMET_API dmet_status_t dmet_emb_eri(dmet_emb_plan_t plan, const void* const* L, 
  * DMET_ERR_TIMEOUT. */
 DMET_API dmet_status_t dmet_emb_status(dmet_emb_plan_t plan, int32_t problem, double* stats);
 
+/* The embedding one-particle Hamiltonian of section 2.1: the Fock matrix of Eq. "fock
+ * transform", F0 = s sum_k C^{k+} F^k C^k (s = 1/Nk for ck_norm = 0, 1 for ck_norm = 1: the
+ * normalisation under which the orbitals are orthonormal), minus the double counting of
+ * Eq. "fock double counting", the Coulomb and exchange of the embedding density gamma in the
+ * embedding ERIs:
+ *     fock_out_ij = F0_ij - [ sum_kl (ij|kl) gamma_lk - 1/2 sum_kl (ik|lj) gamma_kl ].
+ * For restricted problems with real orbitals and the 8-fold packed ERI (n_spin = 1, sym =
+ * REAL, pack S8 or AUTO); others return DMET_ERR_UNSUPPORTED. Device pointers only:
+ *   F        complex128 [Nk][n_ao][n_ao], F[k][mu][nu] = F^{k,AO}_{mu nu} (Hermitian; the
+ *            Hartree-Fock operator of the mean-field calculation, as the paper specifies);
+ *   C        the problem's orbitals, as for dmet_emb_eri;
+ *   eri      the problem's packed ERI as dmet_emb_eri wrote it (FP64, n(n+1)/2 (n(n+1)/2 + 1)/2);
+ *   gamma    FP64 [n][n], symmetric, spin-summed, in the embedding basis;
+ *   fock_out FP64 [n][n] (the real part of F0, whose imaginary part vanishes for real orbitals).
+ * FP64 throughout; queued on the plan's stream; grows a plan-owned scratch buffer on first use
+ * (about 16 Nk n_AO n + 16 Nk n^2 bytes). */
+DMET_API dmet_status_t dmet_emb_fock(dmet_emb_plan_t plan, int32_t problem, const void* F, const void* C,
+                                     const double* eri, const double* gamma, double* fock_out);
+
 /* Frees the plan's device memory, events and tables. Safe on NULL. Waits for the stream. */
 DMET_API dmet_status_t dmet_emb_destroy(dmet_emb_plan_t plan);
 

@@ -107,6 +107,8 @@ def lib() -> ctypes.CDLL:
         L.dmet_emb_schedule.restype = st
         L.dmet_emb_profile.argtypes = [_P, ctypes.c_int32]
         L.dmet_emb_profile.restype = st
+        L.dmet_emb_fock.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P]
+        L.dmet_emb_fock.restype = st
         L.dmet_emb_profile_count.argtypes = []
         L.dmet_emb_profile_count.restype = ctypes.c_int32
         L.dmet_emb_profile_read.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_char_p),
@@ -250,6 +252,11 @@ def dmet_emb_schedule(desc):
 
 def dmet_emb_profile(plan, enable):
     _check(lib().dmet_emb_profile(_P(plan), 1 if enable else 0))
+
+
+def dmet_emb_fock(plan, F, C, eri, gamma, fock_out, problem=0):
+    """Embedding Fock matrix with the double counting removed (device tensors; see dmet_emb_fock)."""
+    _check(lib().dmet_emb_fock(_P(plan), problem, ptr(F), ptr(C), ptr(eri), ptr(gamma), ptr(fock_out)))
 
 
 def dmet_emb_profile_count():

@@ -65,13 +65,14 @@ enum KernelClass {
   KC_TC_TRANSFORM_2,
   KC_TC_PACK,
   KC_TC_CONTRACT,
+  KC_FOCK,
   KC_COUNT
 };
 const char* const kKcNames[KC_COUNT] = {"check_orbitals",      "check_L",          "gather_orbitals",
                                         "half_transform_1",    "half_transform_2", "pack_pairs",
                                         "contract_s8",         "contract_full",    "host_copy",
                                         "split_bf16x3",        "tc_half_transform_1", "tc_half_transform_2",
-                                        "tc_pack_split",       "tc_contract"};
+                                        "tc_pack_split",       "tc_contract",      "embedding_fock"};
 
 // ------------------------------------------------------------------------------------------
 // Scheduler: momentum-conserving pairs (k1, k1 + q), negation, q weights and the
@@ -254,6 +255,9 @@ struct dmet_emb_plan_s {
   size_t stage_in_b = 0;
   void* stage_out = nullptr;
   size_t stage_out_b = 0;
+  // scratch of dmet_emb_fock (grown on demand)
+  void* fock_ws = nullptr;
+  size_t fock_ws_b = 0;
   // Host L transferred block by block on its own stream: the problem being enqueued waits on
   // xev[b] (its contraction block b's pairs have landed) before its first read of L in block b.
   cudaStream_t xs = nullptr;
@@ -756,6 +760,7 @@ void destroy_plan(dmet_emb_plan_s* P) {
   cudaFree(P->dstats);
   cudaFree(P->stage_in);
   cudaFree(P->stage_out);
+  cudaFree(P->fock_ws);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   for (cudaStream_t st : P->side) cudaStreamDestroy(st);
   if (P->cap) cudaStreamDestroy(P->cap);
@@ -1788,6 +1793,85 @@ dmet_status_t dmet_emb_tile_widths(dmet_emb_plan_t P, int32_t problem, int32_t* 
   if (problem < 0 || problem >= (int)P->probs.size()) return fail(DMET_ERR_INVALID_ARG, "problem %d", problem);
   bn[0] = P->probs[problem].mx.bn1;
   bn[1] = P->probs[problem].mx.bn2;
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_fock(dmet_emb_plan_t P, int32_t problem, const void* F, const void* C, const double* eri,
+                            const double* gamma, double* fock_out) {
+  clear_error();
+  if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
+  if (problem < 0 || problem >= (int)P->probs.size()) return fail(DMET_ERR_INVALID_ARG, "problem %d", problem);
+  Prob& pr = P->probs[problem];
+  if (pr.nspin != 1 || pr.d.sym != DMET_SYM_REAL || pr.pack != DMET_PACK_S8)
+    return fail(DMET_ERR_UNSUPPORTED, "problem %d: the embedding Fock matrix needs n_spin = 1, real orbitals and "
+                "the 8-fold packed ERI", problem);
+  if (!F || !C || !eri || !gamma || !fock_out) return fail(DMET_ERR_INVALID_ARG, "NULL pointer argument");
+  const void* ptrs[5] = {F, C, eri, gamma, fock_out};
+  for (const void* q : ptrs)
+    if (!is_device_ptr(q)) return fail(DMET_ERR_INVALID_ARG, "dmet_emb_fock takes device pointers only");
+  if (!aligned16(F) || !aligned16(C)) return fail(DMET_ERR_ALIGNMENT, "F or C not 16-byte aligned");
+  if (((uintptr_t)eri | (uintptr_t)gamma | (uintptr_t)fock_out) & 7u)
+    return fail(DMET_ERR_ALIGNMENT, "eri, gamma or fock_out not 8-byte aligned");
+  const long long nk = pr.nk, nao = pr.nao, n = pr.n[0], npair = n * (n + 1) / 2;
+  // scratch: W = F^k C^k [k][mu][j], G = C^k+ W [k][i][j], F0, J, K [n][n], pair table, weighted gamma
+  const size_t bW = (size_t)(nk * nao * n) * 16, bG = (size_t)(nk * n * n) * 16, bM = (size_t)(n * n) * 8;
+  const size_t bP = (size_t)npair * 8, need = bW + bG + 3 * bM + 2 * bP + 256;
+  P->cs = P->stream;
+  TRY(ensure(&P->fock_ws, &P->fock_ws_b, need));
+  char* w = (char*)P->fock_ws;
+  double2* W = (double2*)w;
+  double2* G = (double2*)(w + bW);
+  double* F0 = (double*)(w + bW + bG);
+  double* J = F0 + n * n;
+  double* K = J + n * n;
+  void* pairs = (void*)(K + n * n);
+  double* g = (double*)((char*)pairs + bP);
+  // flops executed: the two complex GEMMs, and per (row pair, column pair) visit one Coulomb and up
+  // to four exchange multiply-adds
+  Timed t(P, KC_FOCK, 8.0 * nk * (nao * nao * n + nao * n * n) + 10.0 * npair * npair,
+          16.0 * nk * (nao * nao + nao * n) + 8.0 * npair * (npair + 1) / 2 + 8.0 * n * n * 2, 6);
+  {
+    // W[k] = F^k C^k: opA(mu, nu) = conj(F[k][nu][mu]) = F[k][mu][nu] (F^k is Hermitian)
+    ZgemmArgs z = zargs();
+    z.A = (const double2*)F;
+    z.B = (const double2*)C;
+    z.D = W;
+    z.M = (int)nao;
+    z.N = (int)n;
+    z.K = (int)nao;
+    z.lda = nao;
+    z.ldb = n;
+    z.sA = nao * nao;
+    z.sB = nao * n;
+    z.sD = nao * n;
+    z.dm_lo = n;
+    z.dn_lo = 1;
+    z.batch = (int)nk;
+    CK(launch_zgemm(z, A_KM, true, B_KN, P->cs));
+  }
+  {
+    // G[k] = C^k+ W[k]
+    ZgemmArgs z = zargs();
+    z.A = (const double2*)C;
+    z.B = W;
+    z.D = G;
+    z.M = (int)n;
+    z.N = (int)n;
+    z.K = (int)nao;
+    z.lda = n;
+    z.ldb = n;
+    z.sA = nao * n;
+    z.sB = nao * n;
+    z.sD = n * n;
+    z.dm_lo = n;
+    z.dn_lo = 1;
+    z.batch = (int)nk;
+    CK(launch_zgemm(z, A_KM, true, B_KN, P->cs));
+  }
+  CK(launch_fock_reduce(G, (int)nk, (int)n, pr.ortho_scale, F0, P->cs));
+  CK(cudaMemsetAsync(K, 0, bM, P->cs));
+  CK(launch_coulomb_exchange(eri, gamma, (int)n, pairs, g, J, K, P->cs));
+  CK(launch_fock_combine(F0, J, K, (int)n, fock_out, P->cs));
   return DMET_OK;
 }
 
