@@ -21,77 +21,68 @@ __global__ void fock_reduce_kernel(const double2* __restrict__ G, int nk, int n,
   }
 }
 
-// pairs[P] = (l, j) with l >= j, P = l(l+1)/2 + j; g[P] = gamma_lj (2 - delta_lj).
-__global__ void pair_table_kernel(const double* __restrict__ gamma, int n, int2* __restrict__ pairs,
-                                  double* __restrict__ g) {
-  for (int l = blockIdx.x; l < n; l += gridDim.x)
-    for (int j = threadIdx.x; j <= l; j += blockDim.x) {
-      const long long P = (long long)l * (l + 1) / 2 + j;
-      pairs[P] = make_int2(l, j);
-      g[P] = (l == j ? 1.0 : 2.0) * gamma[(long long)l * n + j];
-    }
-}
-
-// One pair row A = (i, k), i >= k, per block, over every pair column B = (l, j), l >= j, with
-// v = (ik|lj) read from the packed lower triangle (the element at max(A,B)(max+1)/2 + min):
-//   J[i][k] = J[k][i] = sum_B v g[B];
-//   K[a][d] += v gamma_bc for each image (a b | c d) of (ik|lj) with its bra from {(i,k), (k,i)}
-//   and its ket from {(l,j), (j,l)} (distinct images only); the images with bra and ket
-//   exchanged are added when the row B is processed, so every ordered image counts once.
-// The exchange rows i and k accumulate in shared memory and are added to K once per block.
+// One block per (orbital i, chunk of k). For each k of the chunk the block stages the pair row
+// A = {i, k} of the packed ERI in shared memory, V[B] = (ik|B) for every pair B (the element at
+// max(A,B)(max+1)/2 + min), and then
+//   thread j:  K_ij += sum_l (ik|lj) gamma_kl = sum_l V[{l, j}] gamma_kl,
+//   all:       J_ik  = sum_{l,j} (ik|lj) gamma_jl = sum_B V[B] gamma_B (2 - delta_B).
+// K row i is complete once every chunk has added its part; J_ik is written by the block of i.
 __global__ void __launch_bounds__(256) coulomb_exchange_kernel(const double* __restrict__ eri,
-                                                               const int2* __restrict__ pairs,
-                                                               const double* __restrict__ g,
-                                                               const double* __restrict__ gamma, int n,
+                                                               const double* __restrict__ gamma, int n, int kchunk,
                                                                double* __restrict__ J, double* __restrict__ K) {
   extern __shared__ double sm[];
-  double* gi = sm;          // gamma row i
-  double* gk = sm + n;      // gamma row k
-  double* ki = sm + 2 * n;  // exchange row i
-  double* kk = sm + 3 * n;  // exchange row k
-  __shared__ double red[32];
   const long long npair = (long long)n * (n + 1) / 2;
-  for (long long A = blockIdx.x; A < npair; A += gridDim.x) {
-    const int2 ik = pairs[A];
-    const int i = ik.x, k = ik.y;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-      gi[t] = gamma[(long long)i * n + t];
-      gk[t] = gamma[(long long)k * n + t];
-      ki[t] = 0.0;
-      kk[t] = 0.0;
-    }
-    __syncthreads();
-    double jsum = 0.0;
+  double* row = sm;              // [npair]
+  double* gk = sm + npair;       // gamma row k [n]
+  __shared__ double red[8];
+  const int i = blockIdx.x;
+  const int k0 = blockIdx.y * kchunk, k1 = min(n, k0 + kchunk);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // K_ij for j = threadIdx.x + 256 u
+  for (int k = k0; k < k1; ++k) {
+    const long long A = i >= k ? (long long)i * (i + 1) / 2 + k : (long long)k * (k + 1) / 2 + i;
     const long long rowA = A * (A + 1) / 2;
-    for (long long B = threadIdx.x; B < npair; B += blockDim.x) {
-      const double v = B <= A ? eri[rowA + B] : eri[B * (B + 1) / 2 + A];
-      const int2 lj = pairs[B];
-      const int l = lj.x, j = lj.y;
-      jsum += v * g[B];
-      atomicAdd(&ki[j], v * gk[l]);
-      if (l != j) atomicAdd(&ki[l], v * gk[j]);
-      if (i != k) {
-        atomicAdd(&kk[j], v * gi[l]);
-        if (l != j) atomicAdd(&kk[l], v * gi[j]);
+    __syncthreads();  // the previous k's readers are done
+    for (long long B = threadIdx.x; B < npair; B += blockDim.x)
+      row[B] = B <= A ? eri[rowA + B] : eri[B * (B + 1) / 2 + A];
+    for (int t = threadIdx.x; t < n; t += blockDim.x) gk[t] = gamma[(long long)k * n + t];
+    __syncthreads();
+    // exchange
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = threadIdx.x + 256 * u;
+      if (j < n) {
+        double s = 0.0;
+        const long long jj = (long long)j * (j + 1) / 2;
+        for (int l = 0; l < n; ++l) {
+          const long long B = l >= j ? (long long)l * (l + 1) / 2 + j : jj + l;
+          s = fma(row[B], gk[l], s);
+        }
+        acc[u] += s;
       }
     }
-    // block sum of jsum
-    for (int o = 16; o; o >>= 1) jsum += __shfl_xor_sync(0xffffffffu, jsum, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = jsum;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (threadIdx.x == 0) {
-        J[(long long)i * n + k] = s;
-        J[(long long)k * n + i] = s;
-      }
+    // Coulomb: gamma_B (2 - delta_B) over the pairs B = {l, j}, l >= j
+    double js = 0.0;
+    for (int l = threadIdx.x >> 5; l < n; l += blockDim.x >> 5) {
+      const long long base = (long long)l * (l + 1) / 2;
+      for (int j = threadIdx.x & 31; j <= l; j += 32)
+        js = fma(row[base + j], (l == j ? 1.0 : 2.0) * gamma[(long long)l * n + j], js);
     }
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-      atomicAdd(&K[(long long)i * n + t], ki[t]);
-      if (i != k) atomicAdd(&K[(long long)k * n + t], kk[t]);
-    }
+    for (int o = 16; o; o >>= 1) js += __shfl_xor_sync(0xffffffffu, js, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = js;
     __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      J[(long long)i * n + k] = t;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int j = threadIdx.x + 256 * u;
+    if (j < n) {
+      if (gridDim.y == 1) K[(long long)i * n + j] = acc[u];
+      else atomicAdd(&K[(long long)i * n + j], acc[u]);
+    }
   }
 }
 
@@ -114,20 +105,24 @@ cudaError_t launch_fock_reduce(const double2* G, int nk, int n, double s, double
   return cudaGetLastError();
 }
 
-cudaError_t launch_coulomb_exchange(const double* eri, const double* gamma, int n, void* pairs, double* g, double* J,
-                                    double* K, cudaStream_t st) {
+cudaError_t launch_coulomb_exchange(const double* eri, const double* gamma, int n, double* J, double* K,
+                                    cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  pair_table_kernel<<<n < 1024 ? n : 1024, 128, 0, st>>>(gamma, n, (int2*)pairs, g);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (n > 1024) return cudaErrorInvalidValue;
   const long long npair = (long long)n * (n + 1) / 2;
-  const size_t smem = (size_t)4 * n * sizeof(double);
+  const size_t smem = (size_t)(npair + n) * sizeof(double);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;  // the caller checks the size first
   if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(coulomb_exchange_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(coulomb_exchange_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const int grid = (int)(npair < 152 * 8 ? npair : 152 * 8);
-  coulomb_exchange_kernel<<<grid, 256, smem, st>>>(eri, (const int2*)pairs, g, gamma, n, J, K);
+  // about four blocks per SM in all
+  int chunks = (4 * 152 + n - 1) / n;
+  if (chunks > n) chunks = n;
+  if (chunks < 1) chunks = 1;
+  const int kchunk = (n + chunks - 1) / chunks;
+  chunks = (n + kchunk - 1) / kchunk;
+  coulomb_exchange_kernel<<<dim3((unsigned)n, (unsigned)chunks), 256, smem, st>>>(eri, gamma, n, kchunk, J, K);
   return cudaGetLastError();
 }
 

@@ -71,10 +71,10 @@ cudaError_t launch_symmetrize(const double2* Z, double2* Lq, int nq, int naux, i
 // [2] |C|, [3] Hermiticity of L, [4] time reversal of L, [5] |L| (the last three component-wise).
 // The orthonormality reduction sums ng split-K partial products S_g = C_g^+ C_g first.
 // Embedding Fock matrix (fock.cu): F0 = s sum_k Re G[k]; J and K of gamma from the 8-fold packed
-// ERI (pairs: n(n+1)/2 int2, g: n(n+1)/2 doubles of scratch; K must start at zero); out = F0 - J + K/2.
+// ERI (K must start at zero; n(n+1)/2 + n doubles of shared memory, so n <= 232); out = F0 - J + K/2.
 cudaError_t launch_fock_reduce(const double2* G, int nk, int n, double s, double* F0, cudaStream_t st);
-cudaError_t launch_coulomb_exchange(const double* eri, const double* gamma, int n, void* pairs, double* g, double* J,
-                                    double* K, cudaStream_t st);
+cudaError_t launch_coulomb_exchange(const double* eri, const double* gamma, int n, double* J, double* K,
+                                    cudaStream_t st);
 cudaError_t launch_fock_combine(const double* F0, const double* J, const double* K, int n, double* out,
                                 cudaStream_t st);
 cudaError_t launch_orth_reduce(const double2* Sg, int ng, int n, double s, double* stat, cudaStream_t st);

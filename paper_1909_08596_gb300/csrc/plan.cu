@@ -1806,6 +1806,9 @@ dmet_status_t dmet_emb_fock(dmet_emb_plan_t P, int32_t problem, const void* F, c
     return fail(DMET_ERR_UNSUPPORTED, "problem %d: the embedding Fock matrix needs n_spin = 1, real orbitals and "
                 "the 8-fold packed ERI", problem);
   if (!F || !C || !eri || !gamma || !fock_out) return fail(DMET_ERR_INVALID_ARG, "NULL pointer argument");
+  if ((long long)pr.n[0] * (pr.n[0] + 1) / 2 + pr.n[0] > 227LL * 1024 / 8)
+    return fail(DMET_ERR_UNSUPPORTED, "problem %d: n_emb %d is above the 232 orbitals that dmet_emb_fock handles "
+                "(one ERI pair row must fit in shared memory)", problem, pr.n[0]);
   const void* ptrs[5] = {F, C, eri, gamma, fock_out};
   for (const void* q : ptrs)
     if (!is_device_ptr(q)) return fail(DMET_ERR_INVALID_ARG, "dmet_emb_fock takes device pointers only");
@@ -1813,9 +1816,9 @@ dmet_status_t dmet_emb_fock(dmet_emb_plan_t P, int32_t problem, const void* F, c
   if (((uintptr_t)eri | (uintptr_t)gamma | (uintptr_t)fock_out) & 7u)
     return fail(DMET_ERR_ALIGNMENT, "eri, gamma or fock_out not 8-byte aligned");
   const long long nk = pr.nk, nao = pr.nao, n = pr.n[0], npair = n * (n + 1) / 2;
-  // scratch: W = F^k C^k [k][mu][j], G = C^k+ W [k][i][j], F0, J, K [n][n], pair table, weighted gamma
+  // scratch: W = F^k C^k [k][mu][j], G = C^k+ W [k][i][j], F0, J, K [n][n]
   const size_t bW = (size_t)(nk * nao * n) * 16, bG = (size_t)(nk * n * n) * 16, bM = (size_t)(n * n) * 8;
-  const size_t bP = (size_t)npair * 8, need = bW + bG + 3 * bM + 2 * bP + 256;
+  const size_t need = bW + bG + 3 * bM + 256;
   P->cs = P->stream;
   TRY(ensure(&P->fock_ws, &P->fock_ws_b, need));
   char* w = (char*)P->fock_ws;
@@ -1824,12 +1827,9 @@ dmet_status_t dmet_emb_fock(dmet_emb_plan_t P, int32_t problem, const void* F, c
   double* F0 = (double*)(w + bW + bG);
   double* J = F0 + n * n;
   double* K = J + n * n;
-  void* pairs = (void*)(K + n * n);
-  double* g = (double*)((char*)pairs + bP);
-  // flops executed: the two complex GEMMs, and per (row pair, column pair) visit one Coulomb and up
-  // to four exchange multiply-adds
-  Timed t(P, KC_FOCK, 8.0 * nk * (nao * nao * n + nao * n * n) + 10.0 * npair * npair,
-          16.0 * nk * (nao * nao + nao * n) + 8.0 * npair * (npair + 1) / 2 + 8.0 * n * n * 2, 6);
+  // flops executed: the two complex GEMMs; per (i, k): n^2 exchange and n(n+1)/2 Coulomb multiply-adds
+  Timed t(P, KC_FOCK, 8.0 * nk * (nao * nao * n + nao * n * n) + 2.0 * n * n * (n * n + npair),
+          16.0 * nk * (nao * nao + nao * n) + 8.0 * npair * (npair + 1) / 2 + 8.0 * n * n * 2, 5);
   {
     // W[k] = F^k C^k: opA(mu, nu) = conj(F[k][nu][mu]) = F[k][mu][nu] (F^k is Hermitian)
     ZgemmArgs z = zargs();
@@ -1870,7 +1870,7 @@ dmet_status_t dmet_emb_fock(dmet_emb_plan_t P, int32_t problem, const void* F, c
   }
   CK(launch_fock_reduce(G, (int)nk, (int)n, pr.ortho_scale, F0, P->cs));
   CK(cudaMemsetAsync(K, 0, bM, P->cs));
-  CK(launch_coulomb_exchange(eri, gamma, (int)n, pairs, g, J, K, P->cs));
+  CK(launch_coulomb_exchange(eri, gamma, (int)n, J, K, P->cs));
   CK(launch_fock_combine(F0, J, K, (int)n, fock_out, P->cs));
   return DMET_OK;
 }
