@@ -340,8 +340,8 @@ def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
         f_tf = fk["flops"] / reps / (f_ms / 1e3) / 1e12
         fock = {"ms": f_ms, "launches_per_call": fk["launches"] // reps,
                 "roofline": {"bound": "alu", "achieved": f_tf, "peak": f_peak, "unit": "TFLOP/s", "frac": f_tf / f_peak,
-                             "flops_counted": "FP64 flops the kernels execute (transform GEMMs; 10 per visit of an ordered "
-                                              "pair of pairs for Coulomb and exchange)",
+                             "flops_counted": "FP64 flops the kernels execute (transform GEMMs; 2 n^2 exchange and "
+                                              "n(n+1)/2 Coulomb multiply-adds per ERI pair row)",
                              "peak_source": "derived FP64 peak (152 SMs x 2 FMA/clk x 2 x 2070 MHz)"}}
 
     # End to end through the C ABI with host buffers: H2D of L and C, D2H of the ERI.

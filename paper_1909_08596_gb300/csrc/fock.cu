@@ -21,46 +21,47 @@ __global__ void fock_reduce_kernel(const double2* __restrict__ G, int nk, int n,
   }
 }
 
-// One block per (orbital i, chunk of k). For each k of the chunk the block stages the pair row
-// A = {i, k} of the packed ERI in shared memory, V[B] = (ik|B) for every pair B (the element at
-// max(A,B)(max+1)/2 + min), and then
-//   thread j:  K_ij += sum_l (ik|lj) gamma_kl = sum_l V[{l, j}] gamma_kl,
-//   all:       J_ik  = sum_{l,j} (ik|lj) gamma_jl = sum_B V[B] gamma_B (2 - delta_B).
-// K row i is complete once every chunk has added its part; J_ik is written by the block of i.
+// One block per pair row A = {i, k}, i >= k: the block stages the row of the packed ERI in shared
+// memory, V[B] = (ik|B) for every pair B (the element at max(A,B)(max+1)/2 + min), and then
+//   thread j:  K_ij += sum_l (ik|lj) gamma_kl   and, for i != k,   K_kj += sum_l (ki|lj) gamma_il,
+//   all:       J_ik  = J_ki = sum_{l,j} (ik|lj) gamma_jl = sum_B V[B] gamma_B (2 - delta_B),
+// with V[{l, j}] = (ik|lj) = (ki|lj) (real orbitals). Each row is read once; the exchange rows are
+// added to K (which starts at zero) with one atomic add per element and block.
 __global__ void __launch_bounds__(256) coulomb_exchange_kernel(const double* __restrict__ eri,
-                                                               const double* __restrict__ gamma, int n, int kchunk,
+                                                               const double* __restrict__ gamma, int n,
                                                                double* __restrict__ J, double* __restrict__ K) {
   extern __shared__ double sm[];
   const long long npair = (long long)n * (n + 1) / 2;
-  double* row = sm;              // [npair]
-  double* gk = sm + npair;       // gamma row k [n]
+  double* row = sm;             // [npair]
+  double* gi = sm + npair;      // gamma row i [n]
+  double* gk = gi + n;          // gamma row k [n]
   __shared__ double red[8];
-  const int i = blockIdx.x;
-  const int k0 = blockIdx.y * kchunk, k1 = min(n, k0 + kchunk);
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // K_ij for j = threadIdx.x + 256 u
-  for (int k = k0; k < k1; ++k) {
-    const long long A = i >= k ? (long long)i * (i + 1) / 2 + k : (long long)k * (k + 1) / 2 + i;
+  for (long long A = blockIdx.x; A < npair; A += gridDim.x) {
+    // (i, k) of A: i = floor((sqrt(8A + 1) - 1) / 2), made exact
+    long long il = (long long)((sqrt(8.0 * (double)A + 1.0) - 1.0) * 0.5);
+    while (il * (il + 1) / 2 > A) --il;
+    while ((il + 1) * (il + 2) / 2 <= A) ++il;
+    const int i = (int)il, k = (int)(A - il * (il + 1) / 2);
     const long long rowA = A * (A + 1) / 2;
-    __syncthreads();  // the previous k's readers are done
+    __syncthreads();  // the previous row's readers are done
     for (long long B = threadIdx.x; B < npair; B += blockDim.x)
       row[B] = B <= A ? eri[rowA + B] : eri[B * (B + 1) / 2 + A];
-    for (int t = threadIdx.x; t < n; t += blockDim.x) gk[t] = gamma[(long long)k * n + t];
-    __syncthreads();
-    // exchange
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = threadIdx.x + 256 * u;
-      if (j < n) {
-        double s = 0.0;
-        const long long jj = (long long)j * (j + 1) / 2;
-        for (int l = 0; l < n; ++l) {
-          const long long B = l >= j ? (long long)l * (l + 1) / 2 + j : jj + l;
-          s = fma(row[B], gk[l], s);
-        }
-        acc[u] += s;
-      }
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      gi[t] = gamma[(long long)i * n + t];
+      gk[t] = gamma[(long long)k * n + t];
     }
-    // Coulomb: gamma_B (2 - delta_B) over the pairs B = {l, j}, l >= j
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      double si = 0.0, sk = 0.0;
+      const long long jj = (long long)j * (j + 1) / 2;
+      for (int l = 0; l < n; ++l) {
+        const double v = row[l >= j ? (long long)l * (l + 1) / 2 + j : jj + l];
+        si = fma(v, gk[l], si);
+        sk = fma(v, gi[l], sk);
+      }
+      atomicAdd(&K[(long long)i * n + j], si);
+      if (i != k) atomicAdd(&K[(long long)k * n + j], sk);
+    }
     double js = 0.0;
     for (int l = threadIdx.x >> 5; l < n; l += blockDim.x >> 5) {
       const long long base = (long long)l * (l + 1) / 2;
@@ -74,14 +75,7 @@ __global__ void __launch_bounds__(256) coulomb_exchange_kernel(const double* __r
       double t = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
       J[(long long)i * n + k] = t;
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int j = threadIdx.x + 256 * u;
-    if (j < n) {
-      if (gridDim.y == 1) K[(long long)i * n + j] = acc[u];
-      else atomicAdd(&K[(long long)i * n + j], acc[u]);
+      J[(long long)k * n + i] = t;
     }
   }
 }
@@ -110,19 +104,14 @@ cudaError_t launch_coulomb_exchange(const double* eri, const double* gamma, int 
   if (n <= 0) return cudaSuccess;
   if (n > 1024) return cudaErrorInvalidValue;
   const long long npair = (long long)n * (n + 1) / 2;
-  const size_t smem = (size_t)(npair + n) * sizeof(double);
+  const size_t smem = (size_t)(npair + 2 * n) * sizeof(double);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;  // the caller checks the size first
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(coulomb_exchange_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  // about four blocks per SM in all
-  int chunks = (4 * 152 + n - 1) / n;
-  if (chunks > n) chunks = n;
-  if (chunks < 1) chunks = 1;
-  const int kchunk = (n + chunks - 1) / chunks;
-  chunks = (n + kchunk - 1) / kchunk;
-  coulomb_exchange_kernel<<<dim3((unsigned)n, (unsigned)chunks), 256, smem, st>>>(eri, gamma, n, kchunk, J, K);
+  const int grid = (int)(npair < 152 * 16 ? npair : 152 * 16);
+  coulomb_exchange_kernel<<<grid, 256, smem, st>>>(eri, gamma, n, J, K);
   return cudaGetLastError();
 }
 

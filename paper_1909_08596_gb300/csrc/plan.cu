@@ -1806,7 +1806,7 @@ dmet_status_t dmet_emb_fock(dmet_emb_plan_t P, int32_t problem, const void* F, c
     return fail(DMET_ERR_UNSUPPORTED, "problem %d: the embedding Fock matrix needs n_spin = 1, real orbitals and "
                 "the 8-fold packed ERI", problem);
   if (!F || !C || !eri || !gamma || !fock_out) return fail(DMET_ERR_INVALID_ARG, "NULL pointer argument");
-  if ((long long)pr.n[0] * (pr.n[0] + 1) / 2 + pr.n[0] > 227LL * 1024 / 8)
+  if ((long long)pr.n[0] * (pr.n[0] + 1) / 2 + 2LL * pr.n[0] > 227LL * 1024 / 8)
     return fail(DMET_ERR_UNSUPPORTED, "problem %d: n_emb %d is above the 232 orbitals that dmet_emb_fock handles "
                 "(one ERI pair row must fit in shared memory)", problem, pr.n[0]);
   const void* ptrs[5] = {F, C, eri, gamma, fock_out};
@@ -1827,8 +1827,9 @@ dmet_status_t dmet_emb_fock(dmet_emb_plan_t P, int32_t problem, const void* F, c
   double* F0 = (double*)(w + bW + bG);
   double* J = F0 + n * n;
   double* K = J + n * n;
-  // flops executed: the two complex GEMMs; per (i, k): n^2 exchange and n(n+1)/2 Coulomb multiply-adds
-  Timed t(P, KC_FOCK, 8.0 * nk * (nao * nao * n + nao * n * n) + 2.0 * n * n * (n * n + npair),
+  // flops executed: the two complex GEMMs; per pair row {i, k}: 2 n^2 exchange and n(n+1)/2 Coulomb
+  // multiply-adds
+  Timed t(P, KC_FOCK, 8.0 * nk * (nao * nao * n + nao * n * n) + 2.0 * npair * (2.0 * n * n + npair),
           16.0 * nk * (nao * nao + nao * n) + 8.0 * npair * (npair + 1) / 2 + 8.0 * n * n * 2, 5);
   {
     // W[k] = F^k C^k: opA(mu, nu) = conj(F[k][nu][mu]) = F[k][mu][nu] (F^k is Hermitian)
