@@ -345,34 +345,37 @@ def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
                              "peak_source": "derived FP64 peak (152 SMs x 2 FMA/clk x 2 x 2070 MHz)"}}
 
     # End to end through the C ABI with host buffers: H2D of L and C, D2H of the ERI.
-    Lh = torch.from_numpy(L).pin_memory()
-    Ch = [torch.from_numpy(c).pin_memory() for c in Cs]
-    Oh = [torch.empty(o.numel(), dtype=torch.float64).pin_memory() for o in outs]
-    dm.dmet_emb_eri(plan, [Lh], [Ch], [Oh])
-    torch.cuda.synchronize()
-    e2e_steps = args.e2e_steps if prec != "fp64" else 1
-    dm.dmet_emb_profile(plan, False)  # clears the counters (no events are recorded)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    e2e = None
+    if not args.no_e2e:
+        Lh = torch.from_numpy(L).pin_memory()
+        Ch = [torch.from_numpy(c).pin_memory() for c in Cs]
+        Oh = [torch.empty(o.numel(), dtype=torch.float64).pin_memory() for o in outs]
         dm.dmet_emb_eri(plan, [Lh], [Ch], [Oh])
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    # bytes the library moved between host and device (it transfers only the L blocks its schedule reads)
-    copy_b = sum(k["bytes"] for k in (dm.dmet_emb_profile_read(plan, i) for i in range(dm.dmet_emb_profile_count()))
-                 if k["name"] == "host_copy") / e2e_steps
-    d2h_b = int(sum(o.numel() * 8 for o in Oh))
+        torch.cuda.synchronize()
+        e2e_steps = args.e2e_steps if prec != "fp64" else 1
+        dm.dmet_emb_profile(plan, False)  # clears the counters (no events are recorded)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            dm.dmet_emb_eri(plan, [Lh], [Ch], [Oh])
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        # bytes the library moved between host and device (it transfers only the L blocks its schedule reads)
+        copy_b = sum(k["bytes"] for k in (dm.dmet_emb_profile_read(plan, i) for i in range(dm.dmet_emb_profile_count()))
+                     if k["name"] == "host_copy") / e2e_steps
+        d2h_b = int(sum(o.numel() * 8 for o in Oh))
+        same = all(torch.equal(o.cpu(), h) for o, h in zip(outs, Oh))
+        e2e = {"value": world * fl_total / e2e_s / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(copy_b) - d2h_b, "d2h_bytes_per_step": d2h_b,
+               "host_L_bytes": int(Lh.numel() * 16), "ms_per_step": e2e_s * 1e3,
+               "matches_device_result": bool(same)}
     st, stats = dm.dmet_emb_status(plan, 0)
-    same = all(torch.equal(o.cpu(), h) for o, h in zip(outs, Oh))
     dm.dmet_emb_destroy(plan)
     return {
         "value": value, "ms_per_step": ms_step, "useful_tflop_per_problem": fl_total / 1e12,
         "useful_split": {"transform": fl_t / 1e12, "contraction": fl_c / 1e12},
         "roofline": roof, "kernels": kernels, "gpu_launches": int(launches), "clocks": clk, "steps": steps,
         "tile_widths": tile_widths,
-        "e2e": {"value": world * fl_total / e2e_s / 1e12, "unit": "TFLOP/s",
-                "h2d_bytes_per_step": int(copy_b) - d2h_b, "d2h_bytes_per_step": d2h_b,
-                "host_L_bytes": int(Lh.numel() * 16), "ms_per_step": e2e_s * 1e3,
-                "matches_device_result": bool(same)},
+        "e2e": e2e,
         "device_checks": {"status": int(st), "orthonormality": stats[0], "realness": stats[1],
                           "hermiticity_L": stats[2], "time_reversal_L": stats[3]},
         "embedding_fock": fock,
@@ -463,6 +466,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the end-to-end measurement (it pins a host copy of L: for the largest workloads)")
     ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
