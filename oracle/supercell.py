@@ -38,16 +38,38 @@ def supercell_eri(B, mesh, Csc_a, Csc_b=None):
     return np.tensordot(xa, xb, axes=([0], [0]))
 
 
-def supercell_fock(f, mesh, Csc):
-    """Csc^+ Fsc Csc with Fsc[(R1, mu), (R2, nu)] = f[mu, nu, R2 - R1]: the Fock matrix of the
-    supercell orbitals, with no k-points (pins Eq. "fock transform" and its conventions)."""
+def supercell_matrix(f, mesh):
+    """Fsc[(R1, mu), (R2, nu)] = f[mu, nu, R2 - R1]: a translation-invariant one-particle operator
+    written out over the supercell from its blocks f[:, :, R] between cell 0 and cell R."""
     cells = _cells(mesh)
     nmesh = np.asarray(mesh)
     n_ao, nk = f.shape[0], f.shape[2]
-    Fsc = np.zeros((nk * n_ao, nk * n_ao))
+    Fsc = np.zeros((nk * n_ao, nk * n_ao), dtype=f.dtype)
     for a, r1 in enumerate(cells):
         d = (cells - r1) % nmesh
         idx = (d[:, 0] * nmesh[1] + d[:, 1]) * nmesh[2] + d[:, 2]
         for b in range(nk):
             Fsc[a * n_ao:(a + 1) * n_ao, b * n_ao:(b + 1) * n_ao] = f[:, :, idx[b]]
-    return Csc.conj().T @ Fsc @ Csc
+    return Fsc
+
+
+def supercell_fock(f, mesh, Csc):
+    """Csc^+ Fsc Csc with Fsc[(R1, mu), (R2, nu)] = f[mu, nu, R2 - R1]: the Fock matrix of the
+    supercell orbitals, with no k-points (pins Eq. "fock transform" and its conventions)."""
+    return Csc.conj().T @ supercell_matrix(f, mesh) @ Csc
+
+
+def supercell_density(h, mesh, n_elec):
+    """Gamma = sum over the n_elec lowest eigenvectors v of the supercell Hamiltonian built from
+    h[i, j, R] of v v^T: the mean-field density matrix of the whole supercell, with no k-points."""
+    w, v = np.linalg.eigh(supercell_matrix(h, mesh))
+    occ = v[:, np.argsort(w, kind="stable")[:n_elec]]
+    return occ @ occ.conj().T
+
+
+def supercell_bath(Gamma, n_lo, val):
+    """Left singular vectors and singular values of the block Gamma[(R != 0, i), (0, j in val)],
+    taken straight from the supercell density matrix (Eq. "bath R SVD" without k-points)."""
+    block = Gamma[n_lo:, :][:, list(val)]
+    u, s, _ = np.linalg.svd(block, full_matrices=False)
+    return u, s

@@ -265,3 +265,69 @@ def embedding_density(n: int, seed: int, n_occ: int | None = None) -> np.ndarray
 
 def spec_with(spec: LatticeSpec, **kw) -> LatticeSpec:
     return dataclasses.replace(spec, **kw)
+
+
+_STREAM_MF = 7 << 40
+_STREAM_LO = 8 << 40
+
+
+def mean_field_hamiltonian(spec: LatticeSpec, n_occ: int, spin: int = 0, hop: float = 0.9) -> np.ndarray:
+    """h[i, j, R], real: a gapped, translation-invariant one-particle Hamiltonian on the n_AO
+    localized orbitals of every cell (the LO basis of section 2.1).
+
+    On-site energies are -1 on n_occ LOs drawn at random and +1 on the others. Every other
+    element is N(0,1) exp(-a |R|), symmetrised so that h[j, i, -R] = h[i, j, R], and the whole
+    perturbation is scaled so that the sum over R of its spectral norms is hop < 1. Each k then
+    has exactly n_occ levels below zero, so the lowest n_occ bands are separated by a gap of at
+    least 2 (1 - hop) and filling them gives the same determinant as filling the Nk n_occ lowest
+    levels of the supercell.
+    """
+    nk, na = spec.nk, spec.n_ao
+    g = _rng(spec.seed + spin, _STREAM_MF)
+    v = g.standard_normal((na, na, nk)) * np.exp(-spec.decay * min_image_norm(spec.mesh))[None, None, :]
+    cells = cell_vectors(spec.mesh)
+    n = np.asarray(spec.mesh)
+    neg = (-cells) % n
+    neg_idx = (neg[:, 0] * n[1] + neg[:, 1]) * n[2] + neg[:, 2]
+    v = 0.5 * (v + v.transpose(1, 0, 2)[:, :, neg_idx])
+    v[:, :, 0][np.diag_indices(na)] = 0.0
+    norm = sum(np.linalg.norm(v[:, :, r], 2) for r in range(nk))
+    v *= hop / max(norm, 1e-300)
+    occ = g.permutation(na)[:n_occ]
+    eps = np.ones(na)
+    eps[occ] = -1.0
+    v[:, :, 0] += np.diag(eps)
+    return v
+
+
+def mean_field_density(h: np.ndarray, mesh, n_occ: int) -> np.ndarray:
+    """gamma[k, i, j] = sum over the n_occ lowest eigenvectors c of h^k of c c^+ (one spin; an
+    idempotent density matrix), with h^k = sum_R exp(+i k.R) h[:, :, R] as for the Fock matrix."""
+    hk = fock_k(h, mesh)
+    out = np.empty_like(hk)
+    for k in range(hk.shape[0]):
+        w, c = np.linalg.eigh(hk[k])
+        c = c[:, np.argsort(w, kind="stable")[:n_occ]]
+        out[k] = c @ c.conj().T
+    return out
+
+
+def lo_rotation(spec: LatticeSpec, spin: int = 0, scale: float = 0.5) -> np.ndarray:
+    """C^{k,AO,LO} [k, mu, i]: a unitary matrix at every k with C^{-k} = conj C^k (a real,
+    orthogonal, translation-invariant AO-to-LO rotation of the supercell), the Cayley transform
+    (1 - X^k)(1 + X^k)^-1 of X^k = sum_R exp(-i k.R) x(R), where x(R) is real, N(0,1) scale
+    exp(-a |R|), made antisymmetric under x(-R) = -x(R)^T."""
+    nk, na = spec.nk, spec.n_ao
+    x = _rng(spec.seed + spin, _STREAM_LO).standard_normal((na, na, nk))
+    x *= scale * np.exp(-spec.decay * min_image_norm(spec.mesh))[None, None, :]
+    cells = cell_vectors(spec.mesh)
+    n = np.asarray(spec.mesh)
+    neg = (-cells) % n
+    neg_idx = (neg[:, 0] * n[1] + neg[:, 1]) * n[2] + neg[:, 2]
+    x = 0.5 * (x - x.transpose(1, 0, 2)[:, :, neg_idx])
+    xk = np.einsum("kR,mnR->kmn", phases(spec.mesh), x)
+    eye = np.eye(na)
+    out = np.empty_like(xk)
+    for k in range(nk):
+        out[k] = np.linalg.solve((eye + xk[k]).T, (eye - xk[k]).T).T
+    return np.ascontiguousarray(out)
