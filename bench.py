@@ -344,6 +344,37 @@ def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
                                               "n(n+1)/2 Coulomb multiply-adds per ERI pair row)",
                              "peak_source": "derived FP64 peak (152 SMs x 2 FMA/clk x 2 x 2070 MHz)"}}
 
+    # The DMET bath that produces such orbitals (dmet_emb_bath, FP64 kernels): the same cell and
+    # mesh, its n_AO LOs as the impurity and 8 of them as the valence columns of the SVD (the
+    # valence shell of a two-atom s/p cell), from a synthetic gapped mean field.
+    bath = None
+    if spec.n_spin == 1 and spec.nk > 1:
+        n_val = min(8, spec.n_ao)
+        bspec = synth.spec_with(spec, n_emb=spec.n_ao + n_val)
+        h = synth.mean_field_hamiltonian(bspec, spec.n_ao // 2)
+        gk = torch.from_numpy(synth.mean_field_density(h, spec.mesh, spec.n_ao // 2)).cuda()
+        Ulo = torch.from_numpy(synth.lo_rotation(bspec)).cuda()
+        val = list(range(0, spec.n_ao, max(1, spec.n_ao // n_val)))[:n_val]
+        Cb = torch.empty((spec.nk, spec.n_ao, bspec.n_emb), dtype=torch.complex128, device="cuda")
+        binfo = torch.zeros(n_val + 5, dtype=torch.float64, device="cuda")
+        bplan = dm.dmet_emb_plan(dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, bspec.n_emb), stream=stream.cuda_stream)
+        try:
+            for _ in range(3):
+                dm.dmet_emb_bath(bplan, gk, Ulo, val, Cb, binfo)
+            reps = 10
+            eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            eb0.record(stream)
+            for _ in range(reps):
+                dm.dmet_emb_bath(bplan, gk, Ulo, val, Cb, binfo)
+            eb1.record(stream)
+            torch.cuda.synchronize()
+            bi = binfo.cpu().numpy()
+            bath = {"ms": eb0.elapsed_time(eb1) / reps, "n_lo": spec.n_ao, "n_val": n_val,
+                    "launches_per_call": dm.dmet_emb_launch_count(bplan) // (reps + 3),
+                    "jacobi_sweeps": int(bi[n_val + 2]), "sigma_min_over_max": float(bi[n_val + 4])}
+        finally:
+            dm.dmet_emb_destroy(bplan)
+
     # End to end through the C ABI with host buffers: H2D of L and C, D2H of the ERI.
     e2e = None
     if not args.no_e2e:
@@ -379,6 +410,7 @@ def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
         "device_checks": {"status": int(st), "orthonormality": stats[0], "realness": stats[1],
                           "hermiticity_L": stats[2], "time_reversal_L": stats[3]},
         "embedding_fock": fock,
+        "dmet_bath": bath,
         "result": [o.cpu().numpy() for o in outs],
     }
 
@@ -518,6 +550,7 @@ def main():
         "device_checks": head["device_checks"],
         "tile_widths": head.get("tile_widths"),
         "embedding_fock": head.get("embedding_fock"),
+        "dmet_bath": head.get("dmet_bath"),
     }
     for p in precs[1:]:
         r = res[p]

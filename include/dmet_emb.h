@@ -171,6 +171,37 @@ DMET_API dmet_status_t dmet_emb_status(dmet_emb_plan_t plan, int32_t problem, do
 DMET_API dmet_status_t dmet_emb_fock(dmet_emb_plan_t plan, int32_t problem, const void* F, const void* C,
                                      const double* eri, const double* gamma, double* fock_out);
 
+/* The DMET bath and embedding orbitals of section 2.1, which produce the C input of
+ * dmet_emb_eri on the device. The impurity is the n_ao localized orbitals (LOs) of the
+ * reference cell R = 0. Steps:
+ *   1. gamma^{R,0} = (1/Nk) sum_k exp(+i k.R) gamma^k for every cell R != 0, on the impurity
+ *      valence columns val (Eq. "bath R SVD" with j restricted to the valence LOs);
+ *   2. the SVD of that ((Nk - 1) n_ao) x n_val block (real part; one-sided Jacobi rotations):
+ *      its left singular vectors B^R are the bath orbitals, in decreasing singular value, each
+ *      signed so that its largest-magnitude coefficient (the first in (R, i) order of equal
+ *      ones) is positive;
+ *   3. C^{R,LO,EO} = [[1, 0], [0, B^{R != 0}]] (Eq. "C loemb R"), impurity columns first;
+ *   4. C_out[k] = C^{k,AO,LO} sum_R exp(-i k.R) C^{R,LO,EO} (Eq. "C loemb k").
+ * The density convention: gamma^k = sum_R exp(+i k.R) g(R), g(R)_{ij} the element between LO i of
+ * cell 0 and LO j of cell R (as for the Fock matrix of dmet_emb_fock); a time-reversal-symmetric
+ * mean field (gamma^{-k} = conj gamma^k) makes the block real. Arguments:
+ *   problem, spin  which orbitals of the plan this builds; n_ao + n_val must equal n_emb[spin];
+ *   gamma_k  device complex128 [Nk][n_ao][n_ao], the mean-field density matrix in the LO basis;
+ *   C_lo     device complex128 [Nk][n_ao][n_ao], C^{k,AO,LO}[k][mu][i] (unitary at each k for
+ *            orthonormal AOs);
+ *   val      host int32 [n_val], distinct LO indices in [0, n_ao), 1 <= n_val <= min(n_ao, 128);
+ *   C_out    device complex128 [Nk][n_ao][n_ao + n_val], written (the layout dmet_emb_eri reads);
+ *   info     device double [n_val + 5] or NULL: the singular values (decreasing), then
+ *            max |Re| and max |Im| of the block, the Jacobi sweeps used (at most 40), the largest
+ *            pair cosine of the last sweep, and sigma_min / sigma_max. A zero singular value
+ *            leaves a zero bath column (the orthonormality check of dmet_emb_eri then fails).
+ * Needs Nk >= 2. FP64 throughout; queued on the plan's stream; grows a plan-owned scratch
+ * buffer on first use (about 16 (Nk - 1) n_ao n_val + 16 Nk n_ao n_val bytes). Invalid
+ * arguments return DMET_ERR_INVALID_ARG or DMET_ERR_ALIGNMENT before anything is queued. */
+DMET_API dmet_status_t dmet_emb_bath(dmet_emb_plan_t plan, int32_t problem, int32_t spin, const void* gamma_k,
+                                     const void* C_lo, const int32_t* val, int32_t n_val, void* C_out,
+                                     double* info);
+
 /* Frees the plan's device memory, events and tables. Safe on NULL. Waits for the stream. */
 DMET_API dmet_status_t dmet_emb_destroy(dmet_emb_plan_t plan);
 

@@ -109,6 +109,9 @@ def lib() -> ctypes.CDLL:
         L.dmet_emb_profile.restype = st
         L.dmet_emb_fock.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P]
         L.dmet_emb_fock.restype = st
+        L.dmet_emb_bath.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.c_int32, _P, _P]
+        L.dmet_emb_bath.restype = st
         L.dmet_emb_profile_count.argtypes = []
         L.dmet_emb_profile_count.restype = ctypes.c_int32
         L.dmet_emb_profile_read.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_char_p),
@@ -257,6 +260,13 @@ def dmet_emb_profile(plan, enable):
 def dmet_emb_fock(plan, F, C, eri, gamma, fock_out, problem=0):
     """Embedding Fock matrix with the double counting removed (device tensors; see dmet_emb_fock)."""
     _check(lib().dmet_emb_fock(_P(plan), problem, ptr(F), ptr(C), ptr(eri), ptr(gamma), ptr(fock_out)))
+
+
+def dmet_emb_bath(plan, gamma_k, C_lo, val, C_out, info=None, problem=0, spin=0):
+    """DMET bath and embedding orbitals C^{k,AO,EO} on the device (see dmet_emb_bath)."""
+    v = (ctypes.c_int32 * len(val))(*[int(x) for x in val])
+    _check(lib().dmet_emb_bath(_P(plan), problem, spin, ptr(gamma_k), ptr(C_lo), v, len(val), ptr(C_out),
+                               ptr(info) if info is not None else None))
 
 
 def dmet_emb_profile_count():

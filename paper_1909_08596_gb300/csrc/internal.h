@@ -77,6 +77,20 @@ cudaError_t launch_coulomb_exchange(const double* eri, const double* gamma, int 
                                     cudaStream_t st);
 cudaError_t launch_fock_combine(const double* F0, const double* J, const double* K, int n, double* out,
                                 cudaStream_t st);
+// Bath construction (bath.cu). The impurity columns that enter the SVD, by value.
+constexpr int kMaxBathCols = 128;
+struct BathCols {
+  int n;
+  int v[kMaxBathCols];
+};
+constexpr size_t kBathJacobiSmem = 200 * 1024;  // the SVD runs in shared memory up to this size
+cudaError_t launch_bath_offdiag(const double2* gk, const int mesh[3], int n_lo, const BathCols& val, double* A,
+                                double* stats, cudaStream_t st);
+size_t bath_jacobi_smem(int m, int n_val);
+cudaError_t launch_bath_jacobi(double* A, int m, int n_val, double* B, double* sigma, double* stats,
+                               cudaStream_t st);
+cudaError_t launch_bath_bloch(const double* B, const double2* Clo, const int mesh[3], int n_lo, int n_val,
+                              double2* Cb, double2* Cout, cudaStream_t st);
 cudaError_t launch_orth_reduce(const double2* Sg, int ng, int n, double s, double* stat, cudaStream_t st);
 cudaError_t launch_c_real_check(const double2* C, const int* neg, int nk, int nao, int n, double* stats,
                                 cudaStream_t st);

@@ -66,13 +66,15 @@ enum KernelClass {
   KC_TC_PACK,
   KC_TC_CONTRACT,
   KC_FOCK,
+  KC_BATH,
   KC_COUNT
 };
 const char* const kKcNames[KC_COUNT] = {"check_orbitals",      "check_L",          "gather_orbitals",
                                         "half_transform_1",    "half_transform_2", "pack_pairs",
                                         "contract_s8",         "contract_full",    "host_copy",
                                         "split_bf16x3",        "tc_half_transform_1", "tc_half_transform_2",
-                                        "tc_pack_split",       "tc_contract",      "embedding_fock"};
+                                        "tc_pack_split",       "tc_contract",      "embedding_fock",
+                                        "dmet_bath"};
 
 // ------------------------------------------------------------------------------------------
 // Scheduler: momentum-conserving pairs (k1, k1 + q), negation, q weights and the
@@ -258,6 +260,9 @@ struct dmet_emb_plan_s {
   // scratch of dmet_emb_fock (grown on demand)
   void* fock_ws = nullptr;
   size_t fock_ws_b = 0;
+  // scratch of dmet_emb_bath (grown on demand)
+  void* bath_ws = nullptr;
+  size_t bath_ws_b = 0;
   // Host L transferred block by block on its own stream: the problem being enqueued waits on
   // xev[b] (its contraction block b's pairs have landed) before its first read of L in block b.
   cudaStream_t xs = nullptr;
@@ -761,6 +766,7 @@ void destroy_plan(dmet_emb_plan_s* P) {
   cudaFree(P->stage_in);
   cudaFree(P->stage_out);
   cudaFree(P->fock_ws);
+  cudaFree(P->bath_ws);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   for (cudaStream_t st : P->side) cudaStreamDestroy(st);
   if (P->cap) cudaStreamDestroy(P->cap);
@@ -1873,6 +1879,79 @@ dmet_status_t dmet_emb_fock(dmet_emb_plan_t P, int32_t problem, const void* F, c
   CK(cudaMemsetAsync(K, 0, bM, P->cs));
   CK(launch_coulomb_exchange(eri, gamma, (int)n, J, K, P->cs));
   CK(launch_fock_combine(F0, J, K, (int)n, fock_out, P->cs));
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_bath(dmet_emb_plan_t P, int32_t problem, int32_t spin, const void* gamma_k, const void* C_lo,
+                            const int32_t* val, int32_t n_val, void* C_out, double* info) {
+  clear_error();
+  if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
+  if (problem < 0 || problem >= (int)P->probs.size()) return fail(DMET_ERR_INVALID_ARG, "problem %d", problem);
+  Prob& pr = P->probs[problem];
+  if (spin < 0 || spin >= pr.nspin) return fail(DMET_ERR_INVALID_ARG, "spin %d of a problem with %d", spin, pr.nspin);
+  if (!gamma_k || !C_lo || !val || !C_out) return fail(DMET_ERR_INVALID_ARG, "NULL pointer argument");
+  const int nk = pr.nk, nlo = pr.nao;
+  if (nk < 2) return fail(DMET_ERR_INVALID_ARG, "the bath needs an environment (Nk >= 2)");
+  if (n_val < 1 || n_val > nlo || n_val > kMaxBathCols)
+    return fail(DMET_ERR_INVALID_ARG, "n_val %d outside [1, min(n_ao %d, %d)]", n_val, nlo, kMaxBathCols);
+  if (nlo + n_val != pr.n[spin])
+    return fail(DMET_ERR_INVALID_ARG, "n_ao + n_val = %d, but the problem has n_emb = %d", nlo + n_val, pr.n[spin]);
+  BathCols cols;
+  cols.n = n_val;
+  {
+    std::vector<char> seen(nlo, 0);
+    for (int c = 0; c < n_val; ++c) {
+      if (val[c] < 0 || val[c] >= nlo) return fail(DMET_ERR_INVALID_ARG, "val[%d] = %d outside [0, %d)", c, val[c], nlo);
+      if (seen[val[c]]) return fail(DMET_ERR_INVALID_ARG, "val[%d] = %d repeats an earlier column", c, val[c]);
+      seen[val[c]] = 1;
+      cols.v[c] = val[c];
+    }
+  }
+  const void* ptrs[4] = {gamma_k, C_lo, C_out, info};
+  for (const void* q : ptrs)
+    if (q && !is_device_ptr(q)) return fail(DMET_ERR_INVALID_ARG, "dmet_emb_bath takes device pointers only");
+  if (!aligned16(gamma_k) || !aligned16(C_lo) || !aligned16(C_out))
+    return fail(DMET_ERR_ALIGNMENT, "gamma_k, C_lo or C_out not 16-byte aligned");
+  if ((uintptr_t)info & 7u) return fail(DMET_ERR_ALIGNMENT, "info not 8-byte aligned");
+  const long long m = (long long)(nk - 1) * nlo, nemb = nlo + n_val;
+  // scratch: A (column-major block, rotated in place), B (bath orbitals [m][n_val]), Cb (Bloch sum
+  // of the bath columns [k][i][b]), stats
+  const size_t bA = (size_t)(m * n_val) * 8, bC = (size_t)nk * nlo * n_val * 16;
+  const size_t oB = (bA + 255) & ~(size_t)255, oC = oB + ((bA + 255) & ~(size_t)255), oS = oC + bC;
+  P->cs = P->stream;
+  TRY(ensure(&P->bath_ws, &P->bath_ws_b, oS + 64));
+  char* w = (char*)P->bath_ws;
+  double* A = (double*)w;
+  double* B = (double*)(w + oB);
+  double2* Cb = (double2*)(w + oC);
+  double* stats = (double*)(w + oS);
+  Timed t(P, KC_BATH, 8.0 * nk * m * n_val + 4.0 * nk * m * n_val + 8.0 * nk * nlo * nlo * n_val,
+          16.0 * nk * nlo * n_val + 16.0 * nk * nlo * nlo + 16.0 * nk * nlo * nemb, 4);
+  CK(cudaMemsetAsync(stats, 0, 64, P->cs));
+  CK(launch_bath_offdiag((const double2*)gamma_k, pr.d.mesh, nlo, cols, A, stats, P->cs));
+  CK(launch_bath_jacobi(A, (int)m, n_val, B, info, stats, P->cs));
+  CK(launch_bath_bloch(B, (const double2*)C_lo, pr.d.mesh, nlo, n_val, Cb, (double2*)C_out, P->cs));
+  {
+    // bath columns: C_out[k][mu][n_lo + b] = sum_i C_lo[k][mu][i] Cb[k][i][b], as the product
+    // (b, mu) of opA(b, i) = Cb[k][i][b] and opB(i, mu) = C_lo[k][mu][i]
+    ZgemmArgs z = zargs();
+    z.A = Cb;
+    z.B = (const double2*)C_lo;
+    z.D = (double2*)C_out + nlo;
+    z.M = n_val;
+    z.N = nlo;
+    z.K = nlo;
+    z.lda = n_val;
+    z.ldb = nlo;
+    z.sA = (long long)nlo * n_val;
+    z.sB = (long long)nlo * nlo;
+    z.sD = (long long)nlo * nemb;
+    z.dm_lo = 1;
+    z.dn_lo = nemb;
+    z.batch = nk;
+    CK(launch_zgemm(z, A_KM, false, B_NK, P->cs));
+  }
+  if (info) CK(cudaMemcpyAsync(info + n_val, stats, 5 * sizeof(double), cudaMemcpyDeviceToDevice, P->cs));
   return DMET_OK;
 }
 
