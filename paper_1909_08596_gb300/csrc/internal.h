@@ -83,14 +83,16 @@ struct BathCols {
   int n;
   int v[kMaxBathCols];
 };
-constexpr size_t kBathJacobiSmem = 200 * 1024;  // the SVD runs in shared memory up to this size
-cudaError_t launch_bath_offdiag(const double2* gk, const int mesh[3], int n_lo, const BathCols& val, double* A,
-                                double* stats, cudaStream_t st);
+constexpr size_t kBathJacobiSmem = 200 * 1024;  // each CTA's rows stay in shared memory up to this size
+constexpr int kBathCluster = 8;                  // CTAs (SMs) of the Jacobi SVD's cluster
+cudaError_t launch_bath_twiddle(int nk, double2* tw, cudaStream_t st);
+cudaError_t launch_bath_offdiag(const double2* gk, const double2* tw, const int mesh[3], int n_lo, const BathCols& val,
+                                double* A, double* stats, cudaStream_t st);
 size_t bath_jacobi_smem(int m, int n_val);
 cudaError_t launch_bath_jacobi(double* A, int m, int n_val, double* B, double* sigma, double* stats,
                                cudaStream_t st);
-cudaError_t launch_bath_bloch(const double* B, const double2* Clo, const int mesh[3], int n_lo, int n_val,
-                              double2* Cb, double2* Cout, cudaStream_t st);
+cudaError_t launch_bath_bloch(const double* B, const double2* Clo, const double2* tw, const int mesh[3], int n_lo,
+                              int n_val, double2* Cb, double2* Cout, cudaStream_t st);
 cudaError_t launch_orth_reduce(const double2* Sg, int ng, int n, double s, double* stat, cudaStream_t st);
 cudaError_t launch_c_real_check(const double2* C, const int* neg, int nk, int nao, int n, double* stats,
                                 cudaStream_t st);

@@ -1915,22 +1915,24 @@ dmet_status_t dmet_emb_bath(dmet_emb_plan_t P, int32_t problem, int32_t spin, co
   if ((uintptr_t)info & 7u) return fail(DMET_ERR_ALIGNMENT, "info not 8-byte aligned");
   const long long m = (long long)(nk - 1) * nlo, nemb = nlo + n_val;
   // scratch: A (column-major block, rotated in place), B (bath orbitals [m][n_val]), Cb (Bloch sum
-  // of the bath columns [k][i][b]), stats
+  // of the bath columns [k][i][b]), stats, the table of the Nk roots of unity
   const size_t bA = (size_t)(m * n_val) * 8, bC = (size_t)nk * nlo * n_val * 16;
-  const size_t oB = (bA + 255) & ~(size_t)255, oC = oB + ((bA + 255) & ~(size_t)255), oS = oC + bC;
+  const size_t oB = (bA + 255) & ~(size_t)255, oC = oB + ((bA + 255) & ~(size_t)255), oS = oC + bC, oT = oS + 256;
   P->cs = P->stream;
-  TRY(ensure(&P->bath_ws, &P->bath_ws_b, oS + 64));
+  TRY(ensure(&P->bath_ws, &P->bath_ws_b, oT + (size_t)nk * 16));
   char* w = (char*)P->bath_ws;
   double* A = (double*)w;
   double* B = (double*)(w + oB);
   double2* Cb = (double2*)(w + oC);
   double* stats = (double*)(w + oS);
+  double2* tw = (double2*)(w + oT);
   Timed t(P, KC_BATH, 8.0 * nk * m * n_val + 4.0 * nk * m * n_val + 8.0 * nk * nlo * nlo * n_val,
-          16.0 * nk * nlo * n_val + 16.0 * nk * nlo * nlo + 16.0 * nk * nlo * nemb, 4);
+          16.0 * nk * nlo * n_val + 16.0 * nk * nlo * nlo + 16.0 * nk * nlo * nemb, 5);
   CK(cudaMemsetAsync(stats, 0, 64, P->cs));
-  CK(launch_bath_offdiag((const double2*)gamma_k, pr.d.mesh, nlo, cols, A, stats, P->cs));
+  CK(launch_bath_twiddle(nk, tw, P->cs));
+  CK(launch_bath_offdiag((const double2*)gamma_k, tw, pr.d.mesh, nlo, cols, A, stats, P->cs));
   CK(launch_bath_jacobi(A, (int)m, n_val, B, info, stats, P->cs));
-  CK(launch_bath_bloch(B, (const double2*)C_lo, pr.d.mesh, nlo, n_val, Cb, (double2*)C_out, P->cs));
+  CK(launch_bath_bloch(B, (const double2*)C_lo, tw, pr.d.mesh, nlo, n_val, Cb, (double2*)C_out, P->cs));
   {
     // bath columns: C_out[k][mu][n_lo + b] = sum_i C_lo[k][mu][i] Cb[k][i][b], as the product
     // (b, mu) of opA(b, i) = Cb[k][i][b] and opB(i, mu) = C_lo[k][mu][i]
