@@ -375,30 +375,50 @@ def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
         finally:
             dm.dmet_emb_destroy(bplan)
 
-    # End to end through the C ABI with host buffers: H2D of L and C, D2H of the ERI.
+    # End to end through the C ABI with host buffers: H2D of L and C, D2H of the ERI. A plan of its
+    # own, built with the q-block size capped (DMET_QBLOCK) so that L streams in small blocks.
     e2e = None
     if not args.no_e2e:
         Lh = torch.from_numpy(L).pin_memory()
         Ch = [torch.from_numpy(c).pin_memory() for c in Cs]
         Oh = [torch.empty(o.numel(), dtype=torch.float64).pin_memory() for o in outs]
-        dm.dmet_emb_eri(plan, [Lh], [Ch], [Oh])
-        torch.cuda.synchronize()
-        e2e_steps = args.e2e_steps if prec != "fp64" else 1
-        dm.dmet_emb_profile(plan, False)  # clears the counters (no events are recorded)
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            dm.dmet_emb_eri(plan, [Lh], [Ch], [Oh])
-        torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
-        # bytes the library moved between host and device (it transfers only the L blocks its schedule reads)
-        copy_b = sum(k["bytes"] for k in (dm.dmet_emb_profile_read(plan, i) for i in range(dm.dmet_emb_profile_count()))
-                     if k["name"] == "host_copy") / e2e_steps
+        old_qb = os.environ.get("DMET_QBLOCK")
+        if args.e2e_qblock > 0:
+            os.environ["DMET_QBLOCK"] = str(args.e2e_qblock)
+        try:
+            eplan = dm.dmet_emb_plan(desc, stream=stream.cuda_stream)
+        finally:
+            if old_qb is None:
+                os.environ.pop("DMET_QBLOCK", None)
+            else:
+                os.environ["DMET_QBLOCK"] = old_qb
+        try:
+            outs_e = [torch.empty_like(o) for o in outs]
+            if prec != "fp64" and not args.no_autotune:
+                dm.dmet_emb_autotune(eplan, [Ld], [Cd], [outs_e])
+            dm.dmet_emb_eri(eplan, [Ld], [Cd], [outs_e])  # the device result of this plan, for the check below
+            dm.dmet_emb_eri(eplan, [Lh], [Ch], [Oh])
+            torch.cuda.synchronize()
+            e2e_steps = args.e2e_steps if prec != "fp64" else 1
+            dm.dmet_emb_profile(eplan, False)  # clears the counters (no events are recorded)
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                dm.dmet_emb_eri(eplan, [Lh], [Ch], [Oh])
+            torch.cuda.synchronize()
+            e2e_s = (time.perf_counter() - t0) / e2e_steps
+            # bytes the library moved between host and device (it transfers only the L blocks its schedule reads)
+            copy_b = sum(k["bytes"] for k in (dm.dmet_emb_profile_read(eplan, i)
+                                              for i in range(dm.dmet_emb_profile_count()))
+                         if k["name"] == "host_copy") / e2e_steps
+        finally:
+            dm.dmet_emb_destroy(eplan)
         d2h_b = int(sum(o.numel() * 8 for o in Oh))
-        same = all(torch.equal(o.cpu(), h) for o, h in zip(outs, Oh))
+        same = all(torch.equal(o.cpu(), h) for o, h in zip(outs_e, Oh))
+        del outs_e
         e2e = {"value": world * fl_total / e2e_s / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(copy_b) - d2h_b, "d2h_bytes_per_step": d2h_b,
                "host_L_bytes": int(Lh.numel() * 16), "ms_per_step": e2e_s * 1e3,
-               "matches_device_result": bool(same)}
+               "qblock_cap": args.e2e_qblock, "matches_device_result": bool(same)}
     st, stats = dm.dmet_emb_status(plan, 0)
     dm.dmet_emb_destroy(plan)
     return {
@@ -497,6 +517,8 @@ def main():
     ap.add_argument("--only", action="store_true", help="measure the headline path only")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-qblock", type=int, default=1,
+                    help="q-block cap (DMET_QBLOCK) of the end-to-end plan; 0 = the plan's own choice")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the end-to-end measurement (it pins a host copy of L: for the largest workloads)")
