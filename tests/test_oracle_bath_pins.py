@@ -1,7 +1,8 @@
 """Pins of the bath oracle (section 2.1, Eqs. "bath R SVD", "C loemb R", "C loemb k") against
 results that do not go through it: the mean-field density matrix written out over the
 supercell with no k-points, the closed form of the singular values of an idempotent density
-matrix, and the Bloch sum of the synthetic-input generator."""
+matrix, the Bloch sum of the synthetic-input generator, and worked examples derived by hand
+(tests/golden/hand_bath.json)."""
 import numpy as np
 import pytest
 
@@ -118,3 +119,27 @@ def test_planted_fourier_sign_is_caught(monkeypatch):
     n = spec.n_ao
     err = max(np.abs(g0[r] - G[r * n:(r + 1) * n, :n]).max() for r in range(spec.nk))
     assert err > 1e-3
+
+
+def _hand_cases():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "hand_bath.json")
+    return json.load(open(path))["cases"]
+
+
+@pytest.mark.parametrize("case", _hand_cases(), ids=lambda c: c["name"])
+def test_hand_worked_examples(case):
+    mesh, val = tuple(case["mesh"]), case["val"]
+    gk = np.asarray(case["gamma_k"], dtype=np.complex128)
+    g0 = oracle.offdiag_density(gk, mesh)
+    g_rs = np.asarray(case["g_real_space"])
+    nk = g_rs.shape[0]
+    for r in range(nk):  # gamma^{R,0} = g(-R)
+        np.testing.assert_allclose(g0[r], g_rs[(-r) % nk], atol=1e-15)
+    B, s, _ = oracle.bath_svd(gk, mesh, val)
+    np.testing.assert_allclose(s, case["sigma"], rtol=1e-14)
+    np.testing.assert_allclose(B, np.asarray(case["bath"]), atol=1e-15)
+    c = oracle.embedding_orbitals_lo(B, mesh)
+    want = np.asarray(case["C_lo_eo_re"]) + 1j * np.asarray(case["C_lo_eo_im"])
+    np.testing.assert_allclose(c, want, atol=1e-15)
