@@ -144,3 +144,23 @@ def test_bath_rejects_bad_arguments(torch):
     with pytest.raises(B.DmetError) as e:
         dm.dmet_emb_plan(B.make_desc((1, 1, 1), 6, 9, 8), stream=torch.cuda.current_stream().cuda_stream)
     assert e.value.status == B.DMET_ERR_INVALID_ARG
+
+
+def _hand_cases():
+    import json
+    import os
+    return json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_bath.json")))["cases"]
+
+
+@pytest.mark.parametrize("case", _hand_cases(), ids=lambda c: c["name"])
+def test_bath_hand_worked_examples(torch, case):
+    """The device path against values derived by hand (C^{k,AO,LO} = 1, so C_out = C^{k,LO,EO})."""
+    mesh, val = tuple(case["mesh"]), case["val"]
+    gk = np.ascontiguousarray(np.asarray(case["gamma_k"], dtype=np.complex128))
+    nk, n_lo = gk.shape[0], gk.shape[1]
+    U = np.ascontiguousarray(np.broadcast_to(np.eye(n_lo, dtype=np.complex128), (nk, n_lo, n_lo)))
+    spec = synth.LatticeSpec(mesh, n_lo, 3, n_lo + len(val), 1, 0.6, 0.0, 0, "hand")
+    got, info = run_bath(torch, spec, gk, U, val)
+    want = np.asarray(case["C_lo_eo_re"]) + 1j * np.asarray(case["C_lo_eo_im"])
+    np.testing.assert_allclose(info[:len(val)], case["sigma"], rtol=1e-14)
+    np.testing.assert_allclose(got, want, atol=1e-14)

@@ -191,3 +191,21 @@ def test_mixed_pinned_host_inputs_match_device(torch):
             assert np.array_equal(dev[0], Oh[0].numpy())
     finally:
         dm.dmet_emb_destroy(plan)
+
+
+@pytest.mark.parametrize("qblock", [1, 3])
+def test_mixed_qblock_cap_matches_oracle(torch, monkeypatch, qblock):
+    """A plan built under DMET_QBLOCK (smaller q-blocks, more of them) gives the oracle's ERI from
+    device and from host inputs alike; the host inputs then stream in many pitched copies."""
+    spec = spec_of((4, 3, 1), 6, 11, 20)
+    L, Cs, _ = synth.make_problem(spec)
+    d = desc_of(spec)
+    ref = oracle.pack_s8(oracle.embedded_eri(L, Cs[0], spec.mesh).real)
+    base, st0, _ = run_eri(torch, d, L, Cs)
+    monkeypatch.setenv("DMET_QBLOCK", str(qblock))
+    dev, st1, _ = run_eri(torch, d, L, Cs)
+    host, st2, _ = run_eri(torch, d, L, Cs, host=True)
+    assert st0 == st1 == st2 == B.DMET_OK
+    assert np.array_equal(dev[0], host[0])
+    check(dev[0], ref)
+    assert rel_fro(dev[0], base[0]) < TOL
