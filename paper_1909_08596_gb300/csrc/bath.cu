@@ -369,7 +369,38 @@ __global__ void __launch_bounds__(128) bath_bloch_kernel(const double* __restric
   }
 }
 
+// The bath columns of C^{k,AO,EO}: C_out[k][mu][n_lo + b] = sum_i C_lo[k][mu][i] Cb[k][i][b], one
+// thread per output element (the products are n_lo x n_lo by n_lo x n_val per k: far too small
+// for a tiled GEMM, whose tiles would be mostly padding).
+__global__ void __launch_bounds__(128) bath_product_kernel(const double2* __restrict__ Clo, const double2* __restrict__ Cb,
+                                                           int nk, int n_lo, int n_val, double2* __restrict__ Cout) {
+  const int n_emb = n_lo + n_val;
+  const long long total = (long long)nk * n_lo * n_val;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total; x += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(x % n_val);
+    const long long kmu = x / n_val;  // k n_lo + mu
+    const int k = (int)(kmu / n_lo);
+    const double2* a = Clo + kmu * n_lo;
+    const double2* c = Cb + (long long)k * n_lo * n_val + b;
+    double re = 0.0, im = 0.0;
+    for (int i = 0; i < n_lo; ++i) {
+      const double2 u = a[i], v = c[(long long)i * n_val];
+      re = fma(u.x, v.x, fma(-u.y, v.y, re));
+      im = fma(u.x, v.y, fma(u.y, v.x, im));
+    }
+    Cout[kmu * n_emb + n_lo + b] = make_double2(re, im);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_bath_product(const double2* Clo, const double2* Cb, int nk, int n_lo, int n_val, double2* Cout,
+                                cudaStream_t st) {
+  const long long total = (long long)nk * n_lo * n_val;
+  const int blocks = (int)std::min<long long>((total + 127) / 128, 152LL * 16);
+  bath_product_kernel<<<blocks, 128, 0, st>>>(Clo, Cb, nk, n_lo, n_val, Cout);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_bath_twiddle(int nk, double2* tw, cudaStream_t st) {
   bath_twiddle_kernel<<<(nk + 255) / 256, 256, 0, st>>>(nk, tw);

@@ -91,6 +91,8 @@ cudaError_t launch_bath_offdiag(const double2* gk, const double2* tw, const int 
 size_t bath_jacobi_smem(int m, int n_val);
 cudaError_t launch_bath_jacobi(double* A, int m, int n_val, double* B, double* sigma, double* stats,
                                cudaStream_t st);
+cudaError_t launch_bath_product(const double2* Clo, const double2* Cb, int nk, int n_lo, int n_val, double2* Cout,
+                                cudaStream_t st);
 cudaError_t launch_bath_bloch(const double* B, const double2* Clo, const double2* tw, const int mesh[3], int n_lo,
                               int n_val, double2* Cb, double2* Cout, cudaStream_t st);
 cudaError_t launch_orth_reduce(const double2* Sg, int ng, int n, double s, double* stat, cudaStream_t st);

@@ -1956,26 +1956,7 @@ dmet_status_t dmet_emb_bath(dmet_emb_plan_t P, int32_t problem, int32_t spin, co
   CK(launch_bath_offdiag((const double2*)gamma_k, tw, pr.d.mesh, nlo, cols, A, stats, P->cs));
   CK(launch_bath_jacobi(A, (int)m, n_val, B, info, stats, P->cs));
   CK(launch_bath_bloch(B, (const double2*)C_lo, tw, pr.d.mesh, nlo, n_val, Cb, (double2*)C_out, P->cs));
-  {
-    // bath columns: C_out[k][mu][n_lo + b] = sum_i C_lo[k][mu][i] Cb[k][i][b], as the product
-    // (b, mu) of opA(b, i) = Cb[k][i][b] and opB(i, mu) = C_lo[k][mu][i]
-    ZgemmArgs z = zargs();
-    z.A = Cb;
-    z.B = (const double2*)C_lo;
-    z.D = (double2*)C_out + nlo;
-    z.M = n_val;
-    z.N = nlo;
-    z.K = nlo;
-    z.lda = n_val;
-    z.ldb = nlo;
-    z.sA = (long long)nlo * n_val;
-    z.sB = (long long)nlo * nlo;
-    z.sD = (long long)nlo * nemb;
-    z.dm_lo = 1;
-    z.dn_lo = nemb;
-    z.batch = nk;
-    CK(launch_zgemm(z, A_KM, false, B_NK, P->cs));
-  }
+  CK(launch_bath_product((const double2*)C_lo, Cb, nk, nlo, n_val, (double2*)C_out, P->cs));
   if (info) CK(cudaMemcpyAsync(info + n_val, stats, 5 * sizeof(double), cudaMemcpyDeviceToDevice, P->cs));
   return DMET_OK;
 }
