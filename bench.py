@@ -498,7 +498,7 @@ def run_batch(args):
             errs[p].append(float(np.linalg.norm(g - eri) / np.linalg.norm(eri)))
     for p in errs:
         out[p]["max_rel_fro_vs_oracle"] = max(errs[p])
-    line = {"metric": METRIC, "workload": "batch48 (48 uneven problems, see DESIGN.md)", "value": out["bf16x3"]["useful_tflops"],
+    line = {"metric": METRIC, "workload": "batch48 (48 uneven problems)", "value": out["bf16x3"]["useful_tflops"],
             "unit": "TFLOP/s", "problems": len(specs), **{p: out[p] for p in out},
             "speedup_bf16x3_over_fp64": out["fp64"]["ms_per_batch"] / out["bf16x3"]["ms_per_batch"]}
     print(json.dumps(line), flush=True)
