@@ -46,9 +46,9 @@ def run_bath(torch, spec, gamma_k, U, val):
 
 
 # (mesh, n_ao, n_occ, val): ragged and odd column counts, a single column, every impurity column,
-# a 3D mesh, an odd mesh, the h-BN-shaped cell (26 LOs, 8 valence) whose block is rotated in
-# shared memory, and the Si-shaped cell (52 LOs on 4x4x4, 16 valence) whose block (419 KB) is
-# rotated in global memory.
+# a 3D mesh, an odd mesh, the h-BN-shaped cell (26 LOs, 8 valence), the Si-shaped cell (52 LOs on
+# 4x4x4) with 16 and with all 52 columns, 70 columns (more pairs per round than warps), and a block
+# too large for shared memory.
 CASES = [
     ((2, 2, 1), 6, 3, [0, 2, 3, 5]),
     ((3, 2, 1), 8, 4, [7, 1, 4]),
@@ -56,6 +56,10 @@ CASES = [
     ((5, 1, 1), 5, 2, [3]),
     ((6, 6, 1), 26, 13, [0, 1, 2, 3, 13, 14, 15, 16]),
     ((4, 4, 4), 52, 26, [0, 13, 26, 39, 2, 6, 10, 14, 18, 22, 30, 34, 42, 46, 50, 51]),
+    ((4, 4, 4), 52, 26, list(range(52))),   # 26 pairs per round: two passes of the 16 warps
+    ((2, 2, 1), 70, 35, list(range(70))),   # 35 pairs per round: three passes
+    # 104 LOs on 4x4x4, 64 columns: each CTA's rows (819 x 64, 410 KB) stay in global memory
+    ((4, 4, 4), 104, 52, list(range(0, 104, 2)) + list(range(1, 24, 2))),
 ]
 
 
