@@ -37,14 +37,13 @@ METRIC = "embedded-ERI transform TFLOP/s and ms/problem at stated error vs FP64;
 SMS = 152
 DFMA_PER_SM_CLK = 2  # FP64 FMA lanes per SM per clock on GB300 (1.25 TFLOP/s nominal at 2.07 GHz)
 ORACLE_SAMPLE_ORBITALS = 24
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from the
-# ncu captures summarised under profiles/ (workload, path, kernel class) -> bytes.
-# DRAM bytes (read + write) per launch of the dominant kernels, averaged over the launches of one call, from an
-# ncu capture of the same revision (profiles/*_bf16x3_hbn_4x4x1.txt give the command); valid only for the
-# kernels as they are at that revision.
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the tensor kernels, averaged over the launches of
+# one call, from a one-pass ncu capture of the full h-BN bench command (profiles/launches_bf16x3_hbn_6x6x1.txt
+# gives the command and the figures); (workload, path, kernel class) -> bytes. Valid only for the kernels as
+# they were at that capture.
 TRAFFIC = {
-    ("hbn_6x6x1", "bf16x3", "tc_half_transform_1"): 1.489e9,
-    ("hbn_6x6x1", "bf16x3", "tc_half_transform_2"): 1.186e9,
+    ("hbn_6x6x1", "bf16x3", "tc_half_transform_1"): 1.424e9,
+    ("hbn_6x6x1", "bf16x3", "tc_half_transform_2"): 1.154e9,
     ("hbn_6x6x1", "bf16x3", "tc_contract"): 1.273e9,
 }
 

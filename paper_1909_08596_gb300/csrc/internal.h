@@ -111,6 +111,10 @@ namespace dmet {
 cudaError_t make_tmap_bf16_3d(CUtensorMap* map, const void* base, unsigned long long k_elems,
                               unsigned long long rows, unsigned long long slices, unsigned long long row_stride_elems,
                               unsigned long long slice_stride_elems, int box_k, int box_rows);
+// 4-D bf16 tensor map over a slice-interleaved operand [rows][K / 32][3 slices][32] with a
+// (32, 1, 1, box_rows) box: one slice of one 32-wide K block, swizzled as the 3-D maps (64 bytes).
+cudaError_t make_tmap_bf16_interleaved(CUtensorMap* map, const void* base, unsigned long long k_elems,
+                                       unsigned long long rows, int box_rows);
 }  // namespace dmet
 
 // ---- split-BF16 path (mixed.cu) ----
@@ -131,7 +135,7 @@ cudaError_t launch_pack_split(const void* ZT, int nq, int naux, int n, int nc, v
 cudaError_t launch_tc_pairs(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                             const tc::Segment* segs, void* out, long long ldo, unsigned int* err, cudaStream_t s);
 cudaError_t launch_tc_split_t(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                              const tc::Segment* segs, void* out, long long sstride, long long K2, int nao, int nemb,
+                              const tc::Segment* segs, void* out, long long K2, int nao, int nemb,
                               unsigned int* err, cudaStream_t s);
 cudaError_t launch_tc_rect(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                            const tc::Segment* segs, double* out, long long ldo, double scale, unsigned int* err,

@@ -195,15 +195,20 @@ __global__ void __launch_bounds__(256) pack_split_kernel(const float2* __restric
 }
 
 // Step-1 output functor: element (m = (P, mu) of entry e, n = (j, p)) -> bf16 slices of A2 at
-// row o2 + P * nemb + j, column o3 + 2 mu + p (o2 = slot * naux * nemb, o3 = r * 2 nao).
+// row o2 + P * nemb + j, column k = o3 + 2 mu + p (o2 = slot * naux * nemb, o3 = r * 2 nao).
+// A2 keeps the three slices of a row side by side in each 32-wide K block,
+// A2[row][k / 32][slice][k % 32] (a row is 3 K2 elements), so that the three slice values a lane
+// writes land in one 192-byte span: with the slices in three separate arrays the same bytes went
+// to three streams of 104-byte pieces and the step took a third longer. Step 2 reads the layout
+// through a 4D tensor map (one slice of one K block per box).
 struct EpiSplitT {
   struct Params {
     __nv_bfloat16* out;
-    long long sstride;
     long long K2;
     int nao, nemb;
   };
   static constexpr bool kStaged = false;  // lanes already write adjacent columns of one row
+  static constexpr bool kAInterleaved = false;
   template <int H>
   static __device__ __forceinline__ void store(const Params& p, const tc::TcJob& j, int row, int col0,
                                                const float* hi, const float* lo) {
@@ -217,16 +222,17 @@ struct EpiSplitT {
       const int jj = (j.o1 + col0 + c) >> 1;
       __nv_bfloat162 x0, x1, x2;  // (re, im) of slices 0, 1, 2
       split3f2(hi[c], lo[c], hi[c + 1], lo[c + 1], x0, x1, x2);
-      __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(p.out + (rbase + jj) * p.K2 + cidx);
-      o[0] = x0;
-      o[p.sstride / 2] = x1;
-      o[p.sstride] = x2;
+      __nv_bfloat16* o = p.out + (rbase + jj) * 3 * p.K2 + (cidx >> 5) * 96 + (cidx & 31);
+      *reinterpret_cast<__nv_bfloat162*>(o) = x0;
+      *reinterpret_cast<__nv_bfloat162*>(o + 32) = x1;
+      *reinterpret_cast<__nv_bfloat162*>(o + 64) = x2;
     }
   }
 };
 
 // Step-2 output functor: the two-float sum itself, out[(o0 + row) * ldo + o1 + col] = (hi, lo).
 struct EpiPairs {
+  static constexpr bool kAInterleaved = true;  // A = A2, written slice-interleaved by EpiSplitT
   struct Params {
     float2* out;
     long long ldo;
@@ -361,9 +367,9 @@ cudaError_t launch_pack_split(const void* ZT, int nq, int naux, int n, int nc, v
 }
 
 cudaError_t launch_tc_split_t(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                              const tc::Segment* segs, void* out, long long sstride, long long K2, int nao, int nemb,
+                              const tc::Segment* segs, void* out, long long K2, int nao, int nemb,
                               unsigned int* err, cudaStream_t s) {
-  EpiSplitT::Params p{(__nv_bfloat16*)out, sstride, K2, nao, nemb};
+  EpiSplitT::Params p{(__nv_bfloat16*)out, K2, nao, nemb};
   return launch_tc<EpiSplitT>(bn, A, B, jobs, njobs, segs, p, err, s);
 }
 

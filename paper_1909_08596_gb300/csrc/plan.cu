@@ -1030,13 +1030,13 @@ dmet_status_t mixed_maps(dmet_emb_plan_s* P, const Prob& pr, MixedMaps& mm) {
   const MixedPlan& m = pr.mx;
   const int BK = mixed_kblock(), T = tc::kTile;
   const long long nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
-  const long long cc_rows = (long long)pr.bq * 2 * nmax, a2_rows = (long long)pr.bq * pr.naux * nmax;
+  const long long cc_rows = (long long)pr.bq * 2 * nmax;
   CK(make_tmap_bf16_3d(&mm.Ls, P->W->Ls, m.K1, m.Ls_rows, 3, m.K1, m.Ls_rows * m.K1, BK, T));
   for (int s = 0; s < pr.nspin; ++s) {
     const long long n = pr.n[s];
     CK(make_tmap_bf16_3d(&mm.Cb[s], P->W->Cb[s], m.K1, pr.nk * 2 * n, 3, m.K1, pr.nk * 2 * n * m.K1, BK, m.bn1));
     CK(make_tmap_bf16_3d(&mm.Cc[s], P->W->Cc, m.K2, (long long)pr.bq * 2 * n, 3, m.K2, cc_rows * m.K2, BK, m.bn2));
-    CK(make_tmap_bf16_3d(&mm.A2[s], P->W->A2, m.K2, (long long)pr.bq * pr.naux * n, 3, m.K2, a2_rows * m.K2, BK, T));
+    CK(make_tmap_bf16_interleaved(&mm.A2[s], P->W->A2, m.K2, (long long)pr.bq * pr.naux * n, T));
     CK(make_tmap_bf16_3d(&mm.Xt[s], P->W->Xt[s], m.Rtot, pr.npair[s], 3, m.Rtot, pr.npair[s] * m.Rtot, BK, T));
   }
   return DMET_OK;
@@ -1047,7 +1047,7 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
   MixedMaps mm;
   TRY(mixed_maps(P, pr, mm));
   const long long nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
-  const long long cc_rows = (long long)pr.bq * 2 * nmax, a2_rows = (long long)pr.bq * pr.naux * nmax;
+  const long long cc_rows = (long long)pr.bq * 2 * nmax;
   int n1 = 0;
   for (int q : pr.con.order) n1 += pr.s.qw[q] == 1;
   const long long used1 = (long long)n1 * pr.naux, used2 = ((long long)pr.con.order.size() - n1) * 2 * pr.naux;
@@ -1089,7 +1089,7 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
         Timed t(P, KC_TC_TRANSFORM_1, 8.0 * n * (double)pr.naux * pr.nao * pr.nao * E, by, 1,
                 exec_flops(m, m.j1_off[s][bi], m.j1_cnt[s][bi], m.bn1));
         CK(launch_tc_split_t(m.bn1, mm.Ls, mm.Cb[s], m.d_jobs + m.j1_off[s][bi], m.j1_cnt[s][bi], m.d_segs, P->W->A2,
-                             a2_rows * m.K2, m.K2, pr.nao, n, P->derr, P->cs));
+                             m.K2, pr.nao, n, P->derr, P->cs));
       }
       {
         double fl = 0, by = 0;

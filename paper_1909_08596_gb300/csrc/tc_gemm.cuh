@@ -240,7 +240,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int k = sg.k0 + kb * Cfg::BK;
 #pragma unroll
           for (int t = 0; t < NSLICE; ++t) {
-            tma_load_3d(a_tile(s, t), &tmA, full(s), k, job.a_row0, t);
+            // A operands stored slice-interleaved ([row][K / 32][slice][32]) come through a 4D map
+            if constexpr (EPI::kAInterleaved)
+              tma_load_4d(a_tile(s, t), &tmA, full(s), 0, t, k / Cfg::BK, job.a_row0);
+            else
+              tma_load_3d(a_tile(s, t), &tmA, full(s), k, job.a_row0, t);
             tma_load_3d(b_tile(s, t), &tmB, full(s), k, job.b_row0, t);
           }
           ++issued;
@@ -398,6 +402,7 @@ __device__ __forceinline__ double scaled_pair(float hi, float lo, float sh, floa
 // A job with o2 != 0 is K part o3 of a split tile: it stores the unscaled pair (hi, lo) of
 // every element of the tile to part[o3][row][col] (128 x 128), for combine_parts to sum.
 struct EpiPacked {
+  static constexpr bool kAInterleaved = false;
   struct Params {
     double* out;
     float sh, sl;
@@ -422,6 +427,7 @@ struct EpiPacked {
 
 // Rectangular: out[(o0 + row) * ldo + o1 + col] = scale * (hi + lo), scale = sh + sl.
 struct EpiRect {
+  static constexpr bool kAInterleaved = false;
   struct Params {
     double* out;
     long long ldo;

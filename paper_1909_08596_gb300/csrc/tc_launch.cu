@@ -49,4 +49,20 @@ cudaError_t make_tmap_bf16_3d(CUtensorMap* map, const void* base, unsigned long 
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t make_tmap_bf16_interleaved(CUtensorMap* map, const void* base, unsigned long long k_elems,
+                                       unsigned long long rows, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  if (((uintptr_t)base & 15) || k_elems % 32) return cudaErrorInvalidValue;
+  // dims (innermost first): element in block, slice, K block, row
+  const cuuint64_t dims[4] = {32, 3, k_elems / 32, rows};
+  const cuuint64_t strides[3] = {32 * 2, 96 * 2, 3 * k_elems * 2};
+  const cuuint32_t box[4] = {32, 1, 1, (cuuint32_t)box_rows};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 }  // namespace dmet
