@@ -22,6 +22,6 @@ from .alg1 import embedded_3idx, embedded_eri, eri_entries
 from .supercell import (supercell_bath, supercell_density, supercell_eri, supercell_fock,
                         supercell_matrix)
 from .bath import bath_svd, embedding_orbitals, embedding_orbitals_lo, offdiag_density
-from .fock import coulomb_exchange, embedded_fock, fock_transform
+from .fock import coulomb_exchange, coulomb_exchange_df, embedded_fock, fock_transform
 from .checks import orthonormality_error, realness_error, pack_s8, pair_matrix, unpack_s8
 from .schedule import schedule

@@ -36,3 +36,22 @@ def embedded_fock(F0, eri, gamma):
     """Ftilde = F0 - (J - K / 2), Eq. "fock double counting"."""
     J, K = coulomb_exchange(eri, gamma)
     return F0 - (J - 0.5 * K)
+
+
+def coulomb_exchange_df(Lq, gamma, mesh):
+    """J and K straight from the density-fitted factors L^q (Algorithm 1's inner-loop output for
+    every q, [q][P][i][j]), without forming the ERI: with (ij|kl) = (1/Nk) sum_q sum_P
+    L^q_{P,ij} L^{-q}_{P,kl} (Algorithm 1's contraction),
+        J_ij = (1/Nk) sum_q sum_P L^q_{P,ij} tr(L^{-q}_P gamma),
+        K_ij = (1/Nk) sum_q sum_P (L^q_P gamma L^{-q}_P)_ij,
+    the density-fitted use the paper mentions for solvers that take the factors directly."""
+    from .mesh import k_neg
+    nk = Lq.shape[0]
+    J = np.zeros(gamma.shape, dtype=np.complex128)
+    K = np.zeros(gamma.shape, dtype=np.complex128)
+    for q in range(nk):
+        a, b = Lq[q], Lq[k_neg(q, mesh)]
+        for P in range(a.shape[0]):
+            J += a[P] * np.trace(b[P] @ gamma) / nk
+            K += a[P] @ gamma @ b[P] / nk
+    return J, K

@@ -51,19 +51,6 @@ def test_fock_planted_mistakes_fail_supercell_pin():
         assert np.abs(bad - ref).max() > 1e-3 * np.abs(ref).max()
 
 
-def _jk_3idx(Lq, gamma, mesh):
-    """J and K through the density-fitted factors: (ij|kl) = (1/Nk) sum_q sum_P Lq[q,P,ij] Lq[-q,P,kl]."""
-    nk = Lq.shape[0]
-    J = np.zeros(gamma.shape, dtype=np.complex128)
-    K = np.zeros(gamma.shape, dtype=np.complex128)
-    for q in range(nk):
-        a, b = Lq[q], Lq[k_neg(q, mesh)]
-        for P in range(a.shape[0]):
-            J += a[P] * np.trace(b[P] @ gamma) / nk
-            K += a[P] @ gamma @ b[P] / nk
-    return J, K
-
-
 @pytest.mark.parametrize("mesh,n_ao,n_emb", [((2, 1, 1), 3, 4), ((3, 1, 1), 3, 5), ((2, 2, 1), 2, 6)])
 def test_coulomb_exchange_match_density_fitted_route(mesh, n_ao, n_emb):
     spec = _spec(mesh, n_ao, 5, n_emb)
@@ -72,13 +59,39 @@ def test_coulomb_exchange_match_density_fitted_route(mesh, n_ao, n_emb):
     eri = oracle.embedded_eri(L, C, mesh, Lq_a=Lq).real
     gamma = synth.embedding_density(n_emb, 11)
     J, K = oracle.coulomb_exchange(eri, gamma)
-    J3, K3 = _jk_3idx(Lq, gamma, mesh)
+    J3, K3 = oracle.coulomb_exchange_df(Lq, gamma, mesh)
     scale = np.abs(J3).max()
     assert np.abs(J - J3).max() < 1e-12 * scale and np.abs(K - K3).max() < 1e-12 * scale
     assert np.abs(J - J.T).max() < 1e-12 * scale and np.abs(K - K.T).max() < 1e-12 * scale
     # planted: exchange contracted like Coulomb, (ij|kl) gamma_kl instead of (ik|lj) gamma_kl
     K_bad = np.einsum("ijkl,kl->ij", eri, gamma)
     assert np.abs(K_bad - K3).max() > 1e-6 * scale
+
+
+def test_density_fitted_jk_planted_momentum_mistake():
+    # pairing L^q with L^q instead of L^{-q} breaks the agreement with the ERI route
+    mesh = (3, 1, 1)
+    spec = _spec(mesh, 3, 5, 5)
+    L, (C,), _ = synth.make_problem(spec)
+    Lq = oracle.embedded_3idx(L, C, mesh)
+    gamma = synth.embedding_density(5, 11)
+    J, K = oracle.coulomb_exchange(oracle.embedded_eri(L, C, mesh, Lq_a=Lq).real, gamma)
+    Jb = sum(Lq[q][P] * np.trace(Lq[q][P] @ gamma) for q in range(3) for P in range(Lq.shape[1])) / 3
+    assert np.abs(Jb - J).max() > 1e-6 * np.abs(J).max()
+
+
+def test_density_fitted_jk_nk1_is_the_molecular_formula():
+    # one cell: J = sum_P B_P tr(B_P gamma), K = sum_P B_P gamma B_P with B_P = C^T L_P C (textbook DF)
+    mesh = (1, 1, 1)
+    spec = _spec(mesh, 4, 6, 3)
+    L, (C,), _ = synth.make_problem(spec)
+    Bp = np.einsum("mi,Pmn,nj->Pij", C[0].conj(), L[0, 0], C[0])
+    gamma = synth.embedding_density(3, 4)
+    J, K = oracle.coulomb_exchange_df(oracle.embedded_3idx(L, C, mesh), gamma, mesh)
+    Jt = sum(Bp[P] * np.trace(Bp[P] @ gamma) for P in range(Bp.shape[0]))
+    Kt = sum(Bp[P] @ gamma @ Bp[P] for P in range(Bp.shape[0]))
+    np.testing.assert_allclose(J, Jt, atol=1e-12)
+    np.testing.assert_allclose(K, Kt, atol=1e-12)
 
 
 def test_one_orbital_closed_form():
