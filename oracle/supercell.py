@@ -73,3 +73,27 @@ def supercell_bath(Gamma, n_lo, val):
     block = Gamma[n_lo:, :][:, list(val)]
     u, s, _ = np.linalg.svd(block, full_matrices=False)
     return u, s
+
+
+def supercell_eri_grid(chi_R, Csc, mesh, lattice, grid):
+    """(ij|kl) of the supercell orbitals psi_i(r) = sum_{R, mu} Csc[(R, mu), i] chi_R[R][mu](r), with
+    chi_R the AOs of every cell on the supercell grid (N_d g_d points along a_d): the periodic Coulomb
+    integral over the Born-von Karman supercell, Omega_sc sum_{G != 0} 4 pi / |G|^2 rho_ij(G) rho_kl(-G),
+    rho(G) = (1/N) sum_r exp(-i G.r) rho(r), with the supercell's own reciprocal vectors. No k-points."""
+    nk, na = chi_R.shape[0], chi_R.shape[1]
+    big = tuple(int(m) * int(g) for m, g in zip(mesh, grid))
+    npts = int(np.prod(big))
+    a_sc = np.asarray(lattice, dtype=np.float64) * np.asarray(mesh, dtype=np.float64)[:, None]
+    b_sc = 2.0 * np.pi * np.linalg.inv(a_sc).T
+    omega_sc = abs(np.linalg.det(a_sc))
+    psi = np.einsum("Rmi,Rmr->ir", Csc.reshape(nk, na, -1), chi_R)
+    n = psi.shape[0]
+    rho = psi.conj()[:, None, :] * psi[None, :, :]                     # [i][j][r]
+    hat = np.fft.fftn(rho.reshape((n, n) + big), axes=(2, 3, 4)) / npts
+    m = np.stack(np.meshgrid(*[np.fft.fftfreq(x) * x for x in big], indexing="ij"), -1)
+    gv = m @ b_sc
+    g2 = (gv * gv).sum(-1)
+    v = np.zeros(g2.shape)
+    v[g2 > 1e-12] = 4.0 * np.pi / g2[g2 > 1e-12]
+    neg = np.roll(np.flip(hat, axis=(2, 3, 4)), 1, axis=(2, 3, 4))    # rho(-G)
+    return omega_sc * np.einsum("ijG,klG->ijkl", (hat * v).reshape(n, n, -1), neg.reshape(n, n, -1))

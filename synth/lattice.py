@@ -331,3 +331,95 @@ def lo_rotation(spec: LatticeSpec, spin: int = 0, scale: float = 0.5) -> np.ndar
     for k in range(nk):
         out[k] = np.linalg.solve((eye + xk[k]).T, (eye - xk[k]).T).T
     return np.ascontiguousarray(out)
+
+
+# ---- inputs of the FFTDF variant (Appendix B, Algorithm 2): AO pair densities on a real-space grid ----
+
+_STREAM_FFTDF = 9 << 40
+
+
+@dataclasses.dataclass(frozen=True)
+class GridSpec:
+    """A cell with lattice vectors `lattice` (rows a_1, a_2, a_3), sampled on `grid` points per cell
+    (g_d points along a_d, even numbers), carrying n_ao Gaussian-shaped real AOs per cell."""
+
+    mesh: tuple
+    n_ao: int
+    grid: tuple
+    lattice: tuple = ((2.0, 0.0, 0.0), (0.3, 2.2, 0.0), (0.1, 0.2, 2.5))
+    n_emb: int = 4
+    seed: int = 0
+
+    @property
+    def nk(self) -> int:
+        return int(np.prod(self.mesh))
+
+
+def cell_grid_points(spec: GridSpec) -> np.ndarray:
+    """Cartesian points r = sum_d (j_d / g_d) a_d of the cell grid, C order, shape (N_g, 3)."""
+    g = np.asarray(spec.grid)
+    j = np.stack(np.meshgrid(*[np.arange(n) for n in g], indexing="ij"), -1).reshape(-1, 3)
+    return (j / g) @ np.asarray(spec.lattice)
+
+
+def ao_supercell(spec: GridSpec) -> np.ndarray:
+    """chi[mu][supercell grid point], real: AO mu of cell 0 on the grid of the whole Born-von Karman
+    supercell (N_d g_d points along a_d), a Gaussian exp(-alpha |r - c|^2) in the minimum-image
+    distance of the supercell, with its centre c inside cell 0 and alpha in [1.5, 3] drawn per AO.
+    The AO of cell R is this array shifted by R_d g_d points along each axis."""
+    g = np.asarray(spec.grid)
+    n = np.asarray(spec.mesh)
+    big = n * g
+    a = np.asarray(spec.lattice)
+    rng = _rng(spec.seed, _STREAM_FFTDF)
+    centres = rng.uniform(0.0, 1.0, (spec.n_ao, 3))      # fractional, in cell 0
+    alphas = rng.uniform(1.5, 3.0, spec.n_ao)
+    j = np.stack(np.meshgrid(*[np.arange(m) for m in big], indexing="ij"), -1).reshape(-1, 3)
+    frac = j / g                                           # in cell units
+    out = np.empty((spec.n_ao, len(j)))
+    for mu in range(spec.n_ao):
+        d = frac - centres[mu]
+        d -= n * np.round(d / n)                          # minimum image on the supercell
+        x = d @ a
+        out[mu] = np.exp(-alphas[mu] * (x * x).sum(-1))
+    return out
+
+
+def shift_cells(f: np.ndarray, spec: GridSpec, R: int) -> np.ndarray:
+    """f (on the supercell grid, last axis) translated by cell R (C-order index)."""
+    g = np.asarray(spec.grid)
+    n = np.asarray(spec.mesh)
+    big = tuple(n * g)
+    Rv = cell_vectors(spec.mesh)[R]
+    shaped = f.reshape(f.shape[:-1] + big)
+    return np.roll(shaped, tuple(Rv * g), axis=(-3, -2, -1)).reshape(f.shape)
+
+
+def pair_densities_k(spec: GridSpec) -> np.ndarray:
+    """rho[k1][k2][mu][nu][r] = conj(phi_{mu k1}(r)) phi_{nu k2}(r) on the grid of cell 0, with the
+    Bloch sums phi_{mu k}(r) = sum_R exp(+i k.R) chi_{mu R}(r) (the AO pair densities of Eq.
+    "FFTDF"; pair (k1, k2) carries momentum k2 - k1)."""
+    chi = ao_supercell(spec)
+    nk, na = spec.nk, spec.n_ao
+    ng = int(np.prod(spec.grid))
+    g = np.asarray(spec.grid)
+    big = np.asarray(spec.mesh) * g
+    # indices of the cell-0 grid inside the supercell grid (C order)
+    j = np.stack(np.meshgrid(*[np.arange(m) for m in g], indexing="ij"), -1).reshape(-1, 3)
+    flat = (j[:, 0] * big[1] + j[:, 1]) * big[2] + j[:, 2]
+    shifted = np.stack([shift_cells(chi, spec, R)[:, flat] for R in range(nk)])   # [R][mu][r]
+    ph = phases(spec.mesh).conj()                                               # exp(+i k.R) [k][R]
+    phi = np.einsum("kR,Rmr->kmr", ph, shifted)                                 # [k][mu][r]
+    rho = np.einsum("amr,bnr->abmnr", phi.conj(), phi)
+    assert rho.shape == (nk, nk, na, na, ng)
+    return np.ascontiguousarray(rho)
+
+
+def grid_orbitals(spec: GridSpec, spin: int = 0, complex_orbitals: bool = False) -> np.ndarray:
+    """Csc[(R, mu), i], orthonormal over the supercell (N(0,1) entries, or N(0,1) + i N(0,1), then QR),
+    n_emb columns."""
+    g = _rng(spec.seed + spin, _STREAM_FFTDF + 1)
+    a = g.standard_normal((spec.nk * spec.n_ao, spec.n_emb))
+    if complex_orbitals:
+        a = a + 1j * g.standard_normal((spec.nk * spec.n_ao, spec.n_emb))
+    return _orthonormalise(a)

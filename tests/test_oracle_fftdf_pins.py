@@ -1,0 +1,87 @@
+"""Pins of the FFTDF oracle (Appendix B, Algorithm 2 and Eq. "FFTDF") against results that do not go
+through it: the Coulomb integral of the real-space orbitals over the Born-von Karman supercell, done
+with the supercell's own FFT grid and no k-points; symmetries, realness and positivity of the ERI;
+planted mistakes in the oracle each fail the supercell pin."""
+import numpy as np
+import pytest
+
+import synth
+import oracle.fftdf as of
+from oracle.supercell import supercell_eri_grid
+
+# (mesh, grid): even and odd grids; N_d g_d odd on every axis in the last two
+CASES = [((1, 1, 1), (4, 4, 4)), ((2, 1, 1), (4, 4, 4)), ((2, 2, 1), (3, 4, 3)), ((3, 1, 1), (3, 5, 3)),
+         ((3, 3, 1), (3, 3, 5))]
+
+
+def _setup(mesh, grid, complex_orbitals=False, n_emb=3, seed=0):
+    spec = synth.GridSpec(tuple(mesh), 2, tuple(grid), n_emb=n_emb, seed=seed)
+    rho = synth.pair_densities_k(spec)
+    csc = synth.grid_orbitals(spec, complex_orbitals=complex_orbitals)
+    chi = synth.ao_supercell(spec)
+    chiR = np.stack([synth.shift_cells(chi, spec, R) for R in range(spec.nk)])
+    return spec, rho, csc, chiR
+
+
+@pytest.mark.parametrize("mesh,grid", CASES)
+@pytest.mark.parametrize("complex_orbitals", [False, True])
+@pytest.mark.parametrize("ck_norm", [0, 1])
+def test_fftdf_matches_supercell_coulomb(mesh, grid, complex_orbitals, ck_norm):
+    spec, rho, csc, chiR = _setup(mesh, grid, complex_orbitals)
+    C = synth.bloch_orbitals(csc, mesh, ck_norm)
+    eri = of.embedded_eri_fftdf(rho, C, mesh, spec.lattice, grid, ck_norm)
+    ref = supercell_eri_grid(chiR, csc, mesh, spec.lattice, grid)
+    assert np.abs(eri - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("mesh,grid", CASES[3:])
+def test_fftdf_real_symmetric_for_real_orbitals_on_odd_grids(mesh, grid):
+    # With N_d g_d odd the plane-wave set is symmetric under G -> -G, so real orbitals give a real,
+    # 8-fold symmetric ERI (with even sizes the Nyquist plane, present once, breaks that slightly in both
+    # routes alike).
+    spec, rho, csc, _ = _setup(mesh, grid)
+    eri = of.embedded_eri_fftdf(rho, synth.bloch_orbitals(csc, mesh), mesh, spec.lattice, grid)
+    scale = np.abs(eri).max()
+    assert np.abs(eri.imag).max() < 1e-14 * scale
+    e = eri.real
+    for perm in ("jikl", "ijlk", "klij", "lkji"):
+        assert np.abs(e - np.einsum("ijkl->" + perm, e)).max() < 1e-14 * scale
+
+
+@pytest.mark.parametrize("mesh,grid", CASES)
+def test_fftdf_pair_supermatrix_is_hermitian_psd(mesh, grid):
+    spec, rho, csc, _ = _setup(mesh, grid, complex_orbitals=True, n_emb=4)
+    eri = of.embedded_eri_fftdf(rho, synth.bloch_orbitals(csc, mesh), mesh, spec.lattice, grid)
+    n = eri.shape[0]
+    m = eri.transpose(0, 1, 3, 2).reshape(n * n, n * n)      # M[(ij),(lk)] = (ij|kl)
+    assert np.abs(m - m.conj().T).max() < 1e-13 * np.abs(m).max()
+    assert np.linalg.eigvalsh(0.5 * (m + m.conj().T)).min() > -1e-13 * np.abs(m).max()
+
+
+def _mutant_error(monkeypatch, name, value, mesh=(3, 1, 1), grid=(3, 5, 3)):
+    spec, rho, csc, chiR = _setup(mesh, grid)
+    ref = supercell_eri_grid(chiR, csc, mesh, spec.lattice, grid)
+    monkeypatch.setattr(of, name, value)
+    eri = of.embedded_eri_fftdf(rho, synth.bloch_orbitals(csc, mesh), mesh, spec.lattice, grid)
+    return np.abs(eri - ref).max() / np.abs(ref).max()
+
+
+def test_planted_no_bloch_phase_is_caught(monkeypatch):
+    # the pair's phase exp(i q.r) left in before the FFT
+    assert _mutant_error(monkeypatch, "_grid_frac", lambda grid: np.zeros((int(np.prod(grid)), 3))) > 1e-3
+
+
+def test_planted_kernel_without_q_is_caught(monkeypatch):
+    good = of.coulomb_kernel
+    assert _mutant_error(monkeypatch, "coulomb_kernel", lambda q, mesh, lat, grid: good(0, mesh, lat, grid)) > 1e-3
+
+
+def test_planted_second_factor_at_plus_q_is_caught(monkeypatch):
+    assert _mutant_error(monkeypatch, "k_neg", lambda q, mesh: q) > 1e-3
+
+
+def test_planted_kernel_sign_of_q_is_caught(monkeypatch):
+    good = of.coulomb_kernel
+    from oracle.mesh import k_neg
+    assert _mutant_error(monkeypatch, "coulomb_kernel",
+                         lambda q, mesh, lat, grid: good(k_neg(q, mesh), mesh, lat, grid)) > 1e-3
