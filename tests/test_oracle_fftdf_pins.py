@@ -85,3 +85,36 @@ def test_planted_kernel_sign_of_q_is_caught(monkeypatch):
     from oracle.mesh import k_neg
     assert _mutant_error(monkeypatch, "coulomb_kernel",
                          lambda q, mesh, lat, grid: good(k_neg(q, mesh), mesh, lat, grid)) > 1e-3
+
+
+@pytest.mark.parametrize("mesh,grid", CASES[3:])
+def test_plane_wave_gdf_form_reproduces_algorithm_2(mesh, grid):
+    # L^q_{G,ij} = (Omega v(q+G) / Nk)^(1/2) rho_hat^q_ij(G); the -q factor is taken at the plane wave
+    # opposite to q + G. Then (ij|kl) = sum_q sum_G L^q_{G,ij} L^{-q}_{G',kl} and L^{-q}_{G',kl} =
+    # conj L^q_{G,lk}: the form of Algorithm 1's contraction, with the plane waves as the aux set.
+    from oracle.mesh import k_neg, k_triplet
+    spec, rho, csc, _ = _setup(mesh, grid, complex_orbitals=True)
+    C = synth.bloch_orbitals(csc, mesh)
+    eri = of.embedded_eri_fftdf(rho, C, mesh, spec.lattice, grid)
+    nk, ng, n = spec.nk, int(np.prod(grid)), C.shape[2]
+    omega = abs(np.linalg.det(np.asarray(spec.lattice)))
+    frac = (np.stack(np.meshgrid(*[np.arange(g) for g in grid], indexing="ij"), -1).reshape(-1, 3)
+            / np.asarray(grid))
+    Lq = []
+    for q in range(nk):
+        t = np.asarray(k_triplet(q, mesh)) / np.asarray(mesh)
+        r = of.embedded_3idx_grid(rho, C, mesh, q) * np.exp(-2j * np.pi * (frac @ t))[:, None, None]
+        hat = np.fft.fftn(r.reshape(tuple(grid) + (n, n)), axes=(0, 1, 2)) / ng
+        v = of.coulomb_kernel(q, mesh, spec.lattice, grid)
+        Lq.append((np.sqrt(omega * v / nk)[..., None, None] * hat).reshape(ng, n, n))
+
+    def opposite(q):
+        t = k_triplet(q, mesh)
+        ax = [(-np.arange(g) - (1 if t[d] else 0)) % g for d, g in enumerate(grid)]
+        j = np.stack(np.meshgrid(*ax, indexing="ij"), -1).reshape(-1, 3)
+        return (j[:, 0] * grid[1] + j[:, 1]) * grid[2] + j[:, 2]
+
+    gdf = sum(np.einsum("Gij,Gkl->ijkl", Lq[q], Lq[k_neg(q, mesh)][opposite(q)]) for q in range(nk))
+    assert np.abs(gdf - eri).max() < 1e-13 * np.abs(eri).max()
+    for q in range(nk):
+        assert np.abs(Lq[k_neg(q, mesh)][opposite(q)] - Lq[q].transpose(0, 2, 1).conj()).max() < 1e-13 * np.abs(Lq[q]).max()
