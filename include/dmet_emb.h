@@ -222,6 +222,22 @@ DMET_API dmet_status_t dmet_emb_schedule(const dmet_emb_desc_t* desc, int32_t* k
                                 int32_t* q_weight, int32_t* n_rep, int32_t* rep_k1,
                                 int32_t* rep_half);
 
+/* Plane waves of the FFTDF variant (Appendix B, Eq. "FFTDF"; the auxiliary set of Algorithm 2) for
+ * momentum q of a Gamma-centred mesh, on a cell grid of grid[d] points along the lattice vectors a_d
+ * (lattice: 3 x 3, row-major, row d = a_d). Host-only; no GPU needed. For each FFT index j (C order over
+ * the grid; N_g = grid[0] grid[1] grid[2] entries, any output may be NULL):
+ *   m[3 j .. 3 j + 2]: the reciprocal-lattice triple of G (m_d = j_d mod grid[d]), chosen so that q + G is
+ *                      one of the signed FFT frequencies of the Born-von Karman supercell's grid
+ *                      (mesh[d] grid[d] points along a_d, Nyquist convention included);
+ *   v[j]:              the Coulomb kernel 4 pi / |q + G|^2, 0 at q + G = 0;
+ *   opposite[j]:       the FFT index j' at momentum -q whose plane wave is -(q + G) (the -q factor of
+ *                      Algorithm 2's contraction pairs with it), modulo the supercell grid: on an axis
+ *                      with mesh[d] grid[d] even, -(q + G) at the Nyquist frequency folds back onto it.
+ * Returns DMET_ERR_INVALID_ARG for sizes outside [1, 4096] per axis, Nk > 4096, N_g > 2^24, q outside
+ * [0, Nk) or a singular lattice. */
+DMET_API dmet_status_t dmet_fftdf_plane_waves(const int32_t* mesh, int32_t q, const int32_t* grid,
+                                              const double* lattice, int32_t* m, double* v, int32_t* opposite);
+
 /* Execution of the plan's problems (the batched form of Algorithm 1's loops; the paper runs
  * one embedding problem at a time). When every problem of a plan gets its own workspace
  * within the plan's workspace limit, dmet_emb_eri runs the problems concurrently on the

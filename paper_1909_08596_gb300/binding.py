@@ -112,6 +112,10 @@ def lib() -> ctypes.CDLL:
         L.dmet_emb_bath.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.c_int32, _P, _P]
         L.dmet_emb_bath.restype = st
+        L.dmet_fftdf_plane_waves.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                             _P, _P, _P]
+        L.dmet_fftdf_plane_waves.restype = st
         L.dmet_emb_profile_count.argtypes = []
         L.dmet_emb_profile_count.restype = ctypes.c_int32
         L.dmet_emb_profile_read.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_char_p),
@@ -267,6 +271,20 @@ def dmet_emb_bath(plan, gamma_k, C_lo, val, C_out, info=None, problem=0, spin=0)
     v = (ctypes.c_int32 * len(val))(*[int(x) for x in val])
     _check(lib().dmet_emb_bath(_P(plan), problem, spin, ptr(gamma_k), ptr(C_lo), v, len(val), ptr(C_out),
                                ptr(info) if info is not None else None))
+
+
+def dmet_fftdf_plane_waves(mesh, q, grid, lattice):
+    """(m [N_g, 3] int32, v [N_g] float64, opposite [N_g] int32) of the FFTDF plane waves at momentum q
+    (host-only; see dmet_fftdf_plane_waves)."""
+    ng = int(np.prod(grid))
+    m = np.zeros((ng, 3), dtype=np.int32)
+    v = np.zeros(ng, dtype=np.float64)
+    opp = np.zeros(ng, dtype=np.int32)
+    me = (ctypes.c_int32 * 3)(*[int(x) for x in mesh])
+    gr = (ctypes.c_int32 * 3)(*[int(x) for x in grid])
+    la = (ctypes.c_double * 9)(*[float(x) for x in np.asarray(lattice, dtype=np.float64).ravel()])
+    _check(lib().dmet_fftdf_plane_waves(me, int(q), gr, la, ptr(m), ptr(v), ptr(opp)))
+    return m, v, opp
 
 
 def dmet_emb_profile_count():

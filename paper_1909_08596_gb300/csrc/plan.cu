@@ -1245,6 +1245,83 @@ dmet_status_t dmet_emb_schedule(const dmet_emb_desc_t* desc, int32_t* k2_of, int
   return DMET_OK;
 }
 
+dmet_status_t dmet_fftdf_plane_waves(const int32_t* mesh, int32_t q, const int32_t* grid, const double* lattice,
+                                     int32_t* m_out, double* v_out, int32_t* opposite) {
+  clear_error();
+  if (!mesh || !grid || !lattice) return fail(DMET_ERR_INVALID_ARG, "NULL argument");
+  long long nk = 1, ng = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (mesh[d] < 1 || mesh[d] > 4096 || grid[d] < 1 || grid[d] > 4096)
+      return fail(DMET_ERR_INVALID_ARG, "mesh[%d] = %d, grid[%d] = %d", d, mesh[d], d, grid[d]);
+    nk *= mesh[d];
+    ng *= grid[d];
+  }
+  if (nk > 4096 || ng > (1LL << 24)) return fail(DMET_ERR_INVALID_ARG, "Nk = %lld or N_g = %lld too large", nk, ng);
+  if (q < 0 || q >= nk) return fail(DMET_ERR_INVALID_ARG, "q = %d outside [0, %lld)", q, nk);
+  // reciprocal vectors b_d (rows) with a_d . b_e = 2 pi delta: b = 2 pi (a^-1)^T
+  const double* a = lattice;
+  const double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                     a[2] * (a[3] * a[7] - a[4] * a[6]);
+  double scale = 0.0;
+  for (int i = 0; i < 9; ++i) scale = std::max(scale, std::fabs(a[i]));
+  if (!(std::fabs(det) > 1e-12 * scale * scale * scale)) return fail(DMET_ERR_INVALID_ARG, "singular lattice");
+  double b[9];
+  const double f = 2.0 * M_PI / det;
+  b[0] = f * (a[4] * a[8] - a[5] * a[7]);
+  b[1] = f * (a[5] * a[6] - a[3] * a[8]);
+  b[2] = f * (a[3] * a[7] - a[4] * a[6]);
+  b[3] = f * (a[2] * a[7] - a[1] * a[8]);
+  b[4] = f * (a[0] * a[8] - a[2] * a[6]);
+  b[5] = f * (a[1] * a[6] - a[0] * a[7]);
+  b[6] = f * (a[1] * a[5] - a[2] * a[4]);
+  b[7] = f * (a[2] * a[3] - a[0] * a[5]);
+  b[8] = f * (a[0] * a[4] - a[1] * a[3]);
+  // q's mesh triple (C order) and that of -q
+  const int n3[3] = {(int)(q / ((long long)mesh[1] * mesh[2])), (int)((q / mesh[2]) % mesh[1]), (int)(q % mesh[2])};
+  // per axis: m_d of each FFT index j_d (m_d = j_d mod g_d with n_d + N_d m_d a signed frequency of the
+  // supercell grid, N_d g_d points: [-floor(N g / 2), ceil(N g / 2) - 1]), and the opposite index
+  std::vector<int> mj[3], opp[3];
+  for (int d = 0; d < 3; ++d) {
+    const long long N = mesh[d], g = grid[d], Ng = N * g;
+    const long long lo = -(Ng / 2), hi = (Ng + 1) / 2 - 1;
+    mj[d].assign(g, 0);
+    opp[d].assign(g, 0);
+    for (long long j = 0; j < g; ++j) {
+      // m = j + g t for the integer t that puts s = n + N m in [lo, hi]
+      long long m = j;
+      while (n3[d] + N * m > hi) m -= g;
+      while (n3[d] + N * m < lo) m += g;
+      mj[d][j] = (int)m;
+      // -(q + G): s' = -s = n' + N m' with n' = (-n) mod N
+      const long long s_ = n3[d] + N * m;
+      const long long np = ((-n3[d]) % N + N) % N;
+      const long long mp = (-s_ - np) / N;
+      opp[d][j] = (int)(((mp % g) + g) % g);
+    }
+  }
+  const double t[3] = {(double)n3[0] / mesh[0], (double)n3[1] / mesh[1], (double)n3[2] / mesh[2]};
+  for (long long j0 = 0; j0 < grid[0]; ++j0)
+    for (long long j1 = 0; j1 < grid[1]; ++j1)
+      for (long long j2 = 0; j2 < grid[2]; ++j2) {
+        const long long idx = (j0 * grid[1] + j1) * grid[2] + j2;
+        const int mm[3] = {mj[0][j0], mj[1][j1], mj[2][j2]};
+        if (m_out) {
+          m_out[3 * idx] = mm[0];
+          m_out[3 * idx + 1] = mm[1];
+          m_out[3 * idx + 2] = mm[2];
+        }
+        if (v_out) {
+          double x[3] = {0.0, 0.0, 0.0};
+          for (int d = 0; d < 3; ++d)
+            for (int e = 0; e < 3; ++e) x[e] += (mm[d] + t[d]) * b[3 * d + e];
+          const double g2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+          v_out[idx] = g2 > 1e-12 ? 4.0 * M_PI / g2 : 0.0;
+        }
+        if (opposite) opposite[idx] = (int32_t)(((long long)opp[0][j0] * grid[1] + opp[1][j1]) * grid[2] + opp[2][j2]);
+      }
+  return DMET_OK;
+}
+
 dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, void* stream, size_t workspace_limit,
                             dmet_emb_plan_t* plan) {
   clear_error();
