@@ -423,3 +423,19 @@ def grid_orbitals(spec: GridSpec, spin: int = 0, complex_orbitals: bool = False)
     if complex_orbitals:
         a = a + 1j * g.standard_normal((spec.nk * spec.n_ao, spec.n_emb))
     return _orthonormalise(a)
+
+
+def make_L_pairs(spec: LatticeSpec, pairs, p_block: int = 64, out: np.ndarray | None = None) -> np.ndarray:
+    """L[e][P][mu][nu] = L^{k1_e, k2_e} for the listed pairs (pair index k1 Nk + k2), complex128, generated
+    P-block by P-block so that the full L is never held: the blocks a reduced input layout keeps (for
+    real-space-real inputs, the pairs the 8-fold schedule reads, about a quarter of all)."""
+    nk, na = spec.nk, spec.n_ao
+    pairs = np.asarray(pairs, dtype=np.int64)
+    if out is None:
+        out = np.empty((len(pairs), spec.n_aux, na, na), dtype=np.complex128)
+    k1, k2 = pairs // nk, pairs % nk
+    for p0 in range(0, spec.n_aux, p_block):
+        p1 = min(spec.n_aux, p0 + p_block)
+        blk = fourier_L(real_space_B(spec, p0, p1), spec.mesh)     # [k1][k2][P][mu][nu] of this P block
+        out[:, p0:p1] = blk[k1, k2]
+    return out

@@ -63,3 +63,20 @@ def test_reduced_pairs_rebuild_the_oracle(mesh):
             a = Lq[q]
             acc += w * (np.einsum("Pij,Pkl->ijkl", a.real, a.real) + np.einsum("Pij,Pkl->ijkl", a.imag, a.imag)) / nk
     assert np.abs(acc - eri.real).max() < 1e-13 * np.abs(eri).max()
+
+
+def test_pair_blocks_of_the_reduced_layout_match_full_L():
+    """The generator's per-pair L blocks (for a reduced input layout) equal the full L's blocks, for the
+    pairs the 8-fold schedule reads, generated P-block by P-block."""
+    import synth
+    spec = synth.spec_with(synth.CONFIGS["tiny_2x2x1"], mesh=(3, 2, 1), n_ao=3, n_aux=7)
+    from oracle.schedule import schedule
+    s = schedule(spec.mesh, real=True)
+    nk = spec.nk
+    pairs = sorted({int(k1) * nk + int(s["k2_of"][q][k1]) for q in range(nk) if s["q_weight"][q] > 0
+                    for k1 in s["rep_k1"][q][:s["n_rep"][q]]})
+    full = synth.make_L(spec)
+    red = synth.make_L_pairs(spec, pairs, p_block=3)
+    for e, p in enumerate(pairs):
+        np.testing.assert_array_equal(red[e], full[p // nk, p % nk])
+    assert len(pairs) < nk * nk / 2
