@@ -118,3 +118,23 @@ def test_plane_wave_gdf_form_reproduces_algorithm_2(mesh, grid):
     assert np.abs(gdf - eri).max() < 1e-13 * np.abs(eri).max()
     for q in range(nk):
         assert np.abs(Lq[k_neg(q, mesh)][opposite(q)] - Lq[q].transpose(0, 2, 1).conj()).max() < 1e-13 * np.abs(Lq[q]).max()
+
+
+def test_supercell_coulomb_closed_form_for_plane_waves():
+    # Orbitals psi_i = exp(i G_i . r) / sqrt(Omega): rho_ij has the single plane wave G_j - G_i, so
+    # (ij|kl) = 4 pi / (Omega |G_j - G_i|^2) when G_j - G_i = -(G_l - G_k) != 0, and 0 otherwise.
+    lat = np.asarray(((2.0, 0.0, 0.0), (0.3, 2.2, 0.0), (0.1, 0.2, 2.5)))
+    grid = (5, 5, 5)
+    b = 2.0 * np.pi * np.linalg.inv(lat).T
+    omega = abs(np.linalg.det(lat))
+    frac = np.stack(np.meshgrid(*[np.arange(g) for g in grid], indexing="ij"), -1).reshape(-1, 3) / np.asarray(grid)
+    ms = np.array([(0, 0, 0), (1, 0, 0), (0, -1, 1), (-1, 1, 0)])
+    chi = np.exp(2j * np.pi * (frac @ ms.T)).T / np.sqrt(omega)          # [i][r]
+    eri = supercell_eri_grid(chi[None], np.eye(len(ms)), (1, 1, 1), lat, grid)
+    want = np.zeros(eri.shape)
+    for i, j, k, l in np.ndindex(eri.shape):
+        d = ms[j] - ms[i]
+        if np.array_equal(d, -(ms[l] - ms[k])) and np.any(d != 0):
+            g = d @ b
+            want[i, j, k, l] = 4.0 * np.pi / (omega * (g @ g))
+    np.testing.assert_allclose(eri, want, atol=1e-12 * want.max())
