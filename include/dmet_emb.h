@@ -15,7 +15,8 @@
  * Memory conventions (every call):
  *  - Complex numbers are interleaved double pairs (re, im) ("complex128"), row-major.
  *  - L  : complex128 [Nk][Nk][n_aux][n_ao][n_ao], L[k1][k2][P][mu][nu] = (P | mu k1, nu k2)
- *         (Eq. "density fitting"; the aux index carries the implicit momentum k1 - k2).
+ *         (Eq. "density fitting"; the aux index carries the implicit momentum k1 - k2), or,
+ *         with l_layout = DMET_L_REDUCED, only the blocks listed by dmet_emb_l_pairs().
  *  - C  : complex128 [Nk][n_ao][n_emb] per spin, C[k][mu][i] = C^{k,AO,EO}_{mu i}.
  *  - Lq : complex128 [q_end - q_begin][n_aux][n_emb][n_emb].
  *  - ERI blocks: see dmet_emb_eri.
@@ -80,6 +81,18 @@ typedef enum {
                             the ERI is real with 8-fold symmetry */
 } dmet_sym_t;
 
+/* Layout of the L input (Eq. "density fitting"; section 2.1 loads L blockwise from disk, one
+ * block per k-point pair). */
+typedef enum {
+  DMET_L_FULL = 0,       /* complex128 [Nk][Nk][n_aux][n_ao][n_ao]: every (k1, k2) block */
+  DMET_L_REDUCED = 1     /* complex128 [n_pairs][n_aux][n_ao][n_ao]: only the blocks the
+                            8-fold schedule transforms (sym = REAL and S8 packing only), in the
+                            order of dmet_emb_l_pairs(); about a quarter of the full L (the
+                            others follow from L^{k2,k1} = conj(L^{k1,k2})^T and
+                            L^{-k1,-k2} = conj(L^{k1,k2})). With a shard (q_begin, q_end) only
+                            the shard's blocks. */
+} dmet_l_layout_t;
+
 typedef enum {
   DMET_PACK_AUTO = 0,    /* S8 for DMET_SYM_REAL, FULL otherwise */
   DMET_PACK_S8 = 1,      /* real, 8-fold packed (requires DMET_SYM_REAL) */
@@ -100,8 +113,14 @@ typedef struct {
   int32_t sym;          /* dmet_sym_t */
   int32_t eri_pack;     /* dmet_pack_t */
   int32_t check_l;      /* 1: also verify the symmetries of L on the device when sym = REAL
-                           (one extra pass over L; ~3 ms on a 3 GB L) */
-  int32_t reserved;     /* must be 0 */
+                           (one extra pass over L; ~3 ms on a 3 GB L); needs l_layout = FULL */
+  int32_t l_layout;     /* dmet_l_layout_t: how the caller stores L */
+  int32_t q_begin;      /* shard of the contraction (dmet_emb_eri): only the momentum transfers q */
+  int32_t q_end;        /* with q_begin <= rep(q) < q_end contribute, rep(q) = min(q, -q) for
+                           sym = REAL (q and -q stay together), rep(q) = q for sym = NONE.
+                           q_begin = q_end = 0 selects every q. The ERIs of disjoint shards that
+                           cover [0, Nk) add up to the full ERI (Algorithm 1's sum over k_L is
+                           a plain sum). */
   double ortho_tol;     /* <= 0 selects 1e-10 */
   double sym_tol;       /* relative; <= 0 selects 1e-10 */
 } dmet_emb_desc_t;
@@ -221,6 +240,16 @@ DMET_API dmet_status_t dmet_emb_destroy(dmet_emb_plan_t plan);
 DMET_API dmet_status_t dmet_emb_schedule(const dmet_emb_desc_t* desc, int32_t* k2_of, int32_t* neg,
                                 int32_t* q_weight, int32_t* n_rep, int32_t* rep_k1,
                                 int32_t* rep_half);
+
+/* The (k1, k2) blocks of L that dmet_emb_eri reads for a real-orbital, 8-fold packed problem
+ * (sym = REAL, S8 packing), in the order of the DMET_L_REDUCED layout: the contracted q values
+ * (those whose q_weight is nonzero and, with a shard, with q_begin <= q < q_end) with q = -q first
+ * and then q < -q, each in increasing order; within one q, its representative k1 of each orbit
+ * {k1, -k1-q} in increasing order (Algorithm 1's two loops with the symmetry reductions of
+ * dmet_emb_schedule). pairs[e] = k1 * Nk + k2 with k2 = k1 + q. Host-only; no GPU needed.
+ * *n_pairs receives the count; pairs may be NULL (count only). Other problems return
+ * DMET_ERR_UNSUPPORTED. */
+DMET_API dmet_status_t dmet_emb_l_pairs(const dmet_emb_desc_t* desc, int32_t* pairs, int64_t* n_pairs);
 
 /* Plane waves of the FFTDF variant (Appendix B, Eq. "FFTDF"; the auxiliary set of Algorithm 2) for
  * momentum q of a Gamma-centred mesh, on a cell grid of grid[d] points along the lattice vectors a_d

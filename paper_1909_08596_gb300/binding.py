@@ -35,6 +35,8 @@ STATUS_NAMES = {0: "DMET_OK", 1: "DMET_ERR_INVALID_ARG", 2: "DMET_ERR_ALIGNMENT"
 DMET_PREC_FP64, DMET_PREC_BF16X3 = 0, 1
 DMET_SYM_NONE, DMET_SYM_REAL = 0, 1
 DMET_PACK_AUTO, DMET_PACK_S8, DMET_PACK_FULL = 0, 1, 2
+# dmet_l_layout_t
+DMET_L_FULL, DMET_L_REDUCED = 0, 1
 
 
 class DmetError(RuntimeError):
@@ -55,21 +57,25 @@ class dmet_emb_desc_t(ctypes.Structure):
         ("sym", ctypes.c_int32),
         ("eri_pack", ctypes.c_int32),
         ("check_l", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("l_layout", ctypes.c_int32),
+        ("q_begin", ctypes.c_int32),
+        ("q_end", ctypes.c_int32),
         ("ortho_tol", ctypes.c_double),
         ("sym_tol", ctypes.c_double),
     ]
 
 
 def make_desc(mesh, n_ao, n_aux, n_emb, n_spin=1, prec=DMET_PREC_FP64, ck_norm=0, sym=DMET_SYM_REAL,
-              eri_pack=DMET_PACK_AUTO, check_l=0, ortho_tol=0.0, sym_tol=0.0) -> dmet_emb_desc_t:
+              eri_pack=DMET_PACK_AUTO, check_l=0, ortho_tol=0.0, sym_tol=0.0, l_layout=0, q_range=None
+              ) -> dmet_emb_desc_t:
     d = dmet_emb_desc_t()
     d.mesh[:] = list(mesh)
     d.n_ao, d.n_aux, d.n_spin = n_ao, n_aux, n_spin
     ne = list(n_emb) if isinstance(n_emb, (list, tuple)) else [n_emb, n_emb if n_spin == 2 else 0]
     d.n_emb[:] = ne + [0] * (2 - len(ne))
     d.prec, d.ck_norm, d.sym, d.eri_pack, d.check_l = prec, ck_norm, sym, eri_pack, check_l
-    d.reserved = 0
+    d.l_layout = l_layout
+    d.q_begin, d.q_end = (0, 0) if q_range is None else (int(q_range[0]), int(q_range[1]))
     d.ortho_tol, d.sym_tol = ortho_tol, sym_tol
     return d
 
@@ -105,6 +111,8 @@ def lib() -> ctypes.CDLL:
         ip = ctypes.POINTER(ctypes.c_int32)
         L.dmet_emb_schedule.argtypes = [ctypes.POINTER(dmet_emb_desc_t), ip, ip, ip, ip, ip, ip]
         L.dmet_emb_schedule.restype = st
+        L.dmet_emb_l_pairs.argtypes = [ctypes.POINTER(dmet_emb_desc_t), ip, ctypes.POINTER(ctypes.c_int64)]
+        L.dmet_emb_l_pairs.restype = st
         L.dmet_emb_profile.argtypes = [_P, ctypes.c_int32]
         L.dmet_emb_profile.restype = st
         L.dmet_emb_fock.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P]
@@ -255,6 +263,16 @@ def dmet_emb_schedule(desc):
     a["rep_k1"] = a["rep_k1"].reshape(nk, nk)
     a["rep_half"] = a["rep_half"].reshape(nk, nk)
     return a
+
+
+def dmet_emb_l_pairs(desc):
+    """The (k1 Nk + k2) blocks of the reduced L layout, in its order (int32 array)."""
+    n = ctypes.c_int64()
+    _check(lib().dmet_emb_l_pairs(ctypes.byref(desc), None, ctypes.byref(n)))
+    out = np.zeros(n.value, dtype=np.int32)
+    _check(lib().dmet_emb_l_pairs(ctypes.byref(desc), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  ctypes.byref(n)))
+    return out
 
 
 def dmet_emb_profile(plan, enable):

@@ -238,7 +238,7 @@ __global__ void pack_pairs_kernel(const double2* __restrict__ Z, double* __restr
 }
 
 __global__ void symmetrize_kernel(const double2* __restrict__ Z, double2* __restrict__ Lq, int nq, int naux,
-                                  int n, double s) {
+                                  int n, double s, double sim) {
   const long long nn = (long long)n * n;
   const long long total = (long long)nq * naux * nn;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
@@ -246,7 +246,7 @@ __global__ void symmetrize_kernel(const double2* __restrict__ Z, double2* __rest
     const long long base = x - x % nn;
     const int i = (int)((x % nn) / n), j = (int)(x % n);
     const double2 a = Z[x], b = Z[base + (long long)j * n + i];
-    Lq[x] = make_double2(s * (a.x + b.x), s * (a.y + b.y));
+    Lq[x] = make_double2(s * (a.x + b.x), sim * (a.y + b.y));
   }
 }
 
@@ -429,10 +429,10 @@ cudaError_t launch_pack_pairs(const double2* Z, double* X, int nq, int naux, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_symmetrize(const double2* Z, double2* Lq, int nq, int naux, int n, double sc,
+cudaError_t launch_symmetrize(const double2* Z, double2* Lq, int nq, int naux, int n, double sc, int conj,
                               cudaStream_t s) {
   const long long total = (long long)nq * naux * n * n;
-  symmetrize_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, s>>>(Z, Lq, nq, naux, n, sc);
+  symmetrize_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, s>>>(Z, Lq, nq, naux, n, sc, conj ? -sc : sc);
   return cudaGetLastError();
 }
 

@@ -63,8 +63,8 @@ cudaError_t launch_gather_orbitals(const double2* C, double2* Crep, const int4* 
 cudaError_t launch_pack_pairs(const double2* Z, double* X, int nq, int naux, int n, int nc, double s,
                               cudaStream_t st);
 
-// Real path 3-index output: Lq[q][P][i][j] = s * (Z_ij + Z_ji).
-cudaError_t launch_symmetrize(const double2* Z, double2* Lq, int nq, int naux, int n, double s,
+// Real path 3-index output: Lq[q][P][i][j] = s * (Z_ij + Z_ji), or its complex conjugate if conj.
+cudaError_t launch_symmetrize(const double2* Z, double2* Lq, int nq, int naux, int n, double s, int conj,
                               cudaStream_t st);
 
 // Checks. stats layout (doubles, raw maxima): [0] orthonormality, [1] |C^{-k} - conj C^k|,

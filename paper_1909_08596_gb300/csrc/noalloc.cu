@@ -151,8 +151,10 @@ extern "C" DMET_API dmet_status_t dmet_emb_eri_noalloc(const dmet_emb_desc_t* de
     if (d.mesh[i] < 1) return nfail(DMET_ERR_INVALID_ARG, "mesh[%d] = %d", i, d.mesh[i]);
   const long long nk = (long long)d.mesh[0] * d.mesh[1] * d.mesh[2];
   if (nk > kMaxNk) return nfail(DMET_ERR_UNSUPPORTED, "Nk = %lld exceeds the no-allocation limit %d", nk, kMaxNk);
-  if (d.n_ao < 1 || d.n_aux < 1 || (d.n_spin != 1 && d.n_spin != 2) || d.reserved != 0)
+  if (d.n_ao < 1 || d.n_aux < 1 || (d.n_spin != 1 && d.n_spin != 2))
     return nfail(DMET_ERR_INVALID_ARG, "invalid descriptor");
+  if (d.l_layout != DMET_L_FULL || d.q_begin != 0 || d.q_end != 0)
+    return nfail(DMET_ERR_UNSUPPORTED, "the no-allocation variant takes the full L layout and no shard");
   for (int s = 0; s < d.n_spin; ++s)
     if (d.n_emb[s] < 1 || (long long)d.n_emb[s] > nk * d.n_ao) return nfail(DMET_ERR_INVALID_ARG, "n_emb[%d]", s);
   if (d.prec != DMET_PREC_FP64 || d.sym != DMET_SYM_REAL ||

@@ -134,6 +134,20 @@ void build_schedule(const dmet_emb_desc_t& d, Sched& s) {
   }
 }
 
+// The contracted q values of an 8-fold packed problem in the library's order (q = -q first, then
+// q < -q, each increasing), restricted to the descriptor's shard; weights alongside.
+void contraction_order(const dmet_emb_desc_t& d, const Sched& s, std::vector<int>& order, std::vector<int>& wts) {
+  order.clear();
+  wts.clear();
+  const bool all = d.q_begin == 0 && d.q_end == 0;
+  for (int w = 1; w <= 2; ++w)
+    for (int q = 0; q < s.nk; ++q)
+      if (s.qw[q] == w && (all || (q >= d.q_begin && q < d.q_end))) {
+        order.push_back(q);
+        wts.push_back(w);
+      }
+}
+
 // Entry tables for one ordering of q values. Entry e = (q, r) for the r-th representative.
 struct Tables {
   std::vector<int> order;      // q values
@@ -201,6 +215,9 @@ struct Prob {
   double lq_scale;     // 1/Nk (Bloch sum) or 1 (unitary)
   double ortho_scale;  // same
   Tables nat, con;     // natural q order; contraction order (S8 only)
+  std::vector<char> nat_conj;  // per q: computed from -q and conjugated (reduced L layout)
+  std::vector<char> nat_ok;    // per q: its L blocks are in the caller's layout
+  long long n_lblocks = 0;     // (k1, k2) blocks of the caller's L
   std::vector<Block> con_blocks;
   int bq = 1;          // q slots per block
   int* d_neg = nullptr;
@@ -330,7 +347,19 @@ dmet_status_t validate_desc(const dmet_emb_desc_t& d, int idx) {
   if (d.eri_pack == DMET_PACK_S8 && d.sym != DMET_SYM_REAL)
     return fail(DMET_ERR_INVALID_ARG, "problem %d: 8-fold packing needs sym = DMET_SYM_REAL", idx);
   if (d.check_l != 0 && d.check_l != 1) return fail(DMET_ERR_INVALID_ARG, "problem %d: check_l = %d", idx, d.check_l);
-  if (d.reserved != 0) return fail(DMET_ERR_INVALID_ARG, "problem %d: reserved field must be 0", idx);
+  const int rpack = d.eri_pack == DMET_PACK_AUTO ? (d.sym == DMET_SYM_REAL ? DMET_PACK_S8 : DMET_PACK_FULL) : d.eri_pack;
+  if (d.l_layout != DMET_L_FULL && d.l_layout != DMET_L_REDUCED)
+    return fail(DMET_ERR_INVALID_ARG, "problem %d: l_layout = %d", idx, d.l_layout);
+  if (d.l_layout == DMET_L_REDUCED && (d.sym != DMET_SYM_REAL || rpack != DMET_PACK_S8))
+    return fail(DMET_ERR_INVALID_ARG, "problem %d: the reduced L layout needs sym = REAL and 8-fold packing", idx);
+  if (d.l_layout == DMET_L_REDUCED && d.check_l)
+    return fail(DMET_ERR_INVALID_ARG, "problem %d: check_l compares blocks the reduced L layout leaves out", idx);
+  if (!(d.q_begin == 0 && d.q_end == 0)) {
+    if (d.q_begin < 0 || d.q_end > nk || d.q_begin >= d.q_end)
+      return fail(DMET_ERR_INVALID_ARG, "problem %d: shard [%d, %d) not inside [0, %lld)", idx, d.q_begin, d.q_end, nk);
+    if (rpack != DMET_PACK_S8 && !(d.q_begin == 0 && d.q_end == nk))
+      return fail(DMET_ERR_UNSUPPORTED, "problem %d: a q shard needs the 8-fold packed output", idx);
+  }
   if (d.prec != DMET_PREC_FP64 && d.prec != DMET_PREC_BF16X3) return fail(DMET_ERR_INVALID_ARG, "problem %d: prec = %d", idx, d.prec);
   if (d.prec == DMET_PREC_BF16X3) {
     const int pack = d.eri_pack == DMET_PACK_AUTO ? (d.sym == DMET_SYM_REAL ? DMET_PACK_S8 : DMET_PACK_FULL) : d.eri_pack;
@@ -609,17 +638,20 @@ dmet_status_t run_half_transform(dmet_emb_plan_s* P, Prob& pr, const Tables& tb,
 dmet_status_t transform_range(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, int q_begin,
                               int q_end, double2* const* out) {
   const bool real = pr.d.sym == DMET_SYM_REAL;
-  for (int qa = q_begin; qa < q_end; qa += pr.bq) {
-    const int qb = std::min(q_end, qa + pr.bq);
+  // q-blocks of at most bq consecutive q with the same conjugation flag
+  for (int qa = q_begin; qa < q_end;) {
+    int qb = qa + 1;
+    while (qb < q_end && qb - qa < pr.bq && pr.nat_conj[qb] == pr.nat_conj[qa]) ++qb;
     for (int s = 0; s < pr.nspin; ++s) {
       const long long slot = (long long)pr.naux * pr.n[s] * pr.n[s];
       double2* dest = out[s] + (long long)(qa - q_begin) * slot;
       TRY(run_half_transform(P, pr, pr.nat, qa, qb, s, L, C[s], dest, qa));
       if (real) {
         Timed t(P, KC_PACK, 0.0, 32.0 * (qb - qa) * (double)slot);
-        CK(launch_symmetrize(P->W->Z, dest, qb - qa, pr.naux, pr.n[s], pr.lq_scale, P->cs));
+        CK(launch_symmetrize(P->W->Z, dest, qb - qa, pr.naux, pr.n[s], pr.lq_scale, pr.nat_conj[qa], P->cs));
       }
     }
+    qa = qb;
   }
   return DMET_OK;
 }
@@ -1245,6 +1277,26 @@ dmet_status_t dmet_emb_schedule(const dmet_emb_desc_t* desc, int32_t* k2_of, int
   return DMET_OK;
 }
 
+dmet_status_t dmet_emb_l_pairs(const dmet_emb_desc_t* desc, int32_t* pairs, int64_t* n_pairs) {
+  clear_error();
+  if (!desc || !n_pairs) return fail(DMET_ERR_INVALID_ARG, "desc or n_pairs is NULL");
+  TRY(validate_desc(*desc, 0));
+  const int pack = desc->eri_pack == DMET_PACK_AUTO ? (desc->sym == DMET_SYM_REAL ? DMET_PACK_S8 : DMET_PACK_FULL)
+                                                    : desc->eri_pack;
+  if (desc->sym != DMET_SYM_REAL || pack != DMET_PACK_S8)
+    return fail(DMET_ERR_UNSUPPORTED, "the reduced pair list exists for sym = REAL with 8-fold packing");
+  Sched s;
+  build_schedule(*desc, s);
+  std::vector<int> order, wts;
+  contraction_order(*desc, s, order, wts);
+  Tables t;
+  build_tables(s, order, desc->n_ao, t);
+  *n_pairs = (int64_t)t.t1.size();
+  if (pairs)
+    for (size_t e = 0; e < t.t1.size(); ++e) pairs[e] = t.t1[e].y;
+  return DMET_OK;
+}
+
 dmet_status_t dmet_fftdf_plane_waves(const int32_t* mesh, int32_t q, const int32_t* grid, const double* lattice,
                                      int32_t* m_out, double* v_out, int32_t* opposite) {
   clear_error();
@@ -1361,18 +1413,40 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     pr.lq_scale = pr.d.ck_norm == 0 ? 1.0 / pr.nk : 1.0;
     pr.orth_groups = orth_groups_for(pr.nk, pr.nao, std::max(pr.n[0], pr.n[1]));
     pr.ortho_scale = pr.lq_scale;
+    const bool reduced = pr.d.l_layout == DMET_L_REDUCED;
     std::vector<int> nat(pr.nk);
-    for (int q = 0; q < pr.nk; ++q) nat[q] = q;
+    pr.nat_conj.assign(pr.nk, 0);
+    for (int q = 0; q < pr.nk; ++q) {
+      // With the reduced layout a q whose contraction weight is 0 (q > -q) is computed from the
+      // blocks of -q: L^q_{P,ij} = conj(L^{-q}_{P,ji}) = conj(L^{-q}_{P,ij}) for real orbitals.
+      nat[q] = (reduced && pr.s.qw[q] == 0) ? pr.s.neg[q] : q;
+      pr.nat_conj[q] = nat[q] != q;
+    }
     build_tables(pr.s, nat, pr.nao, pr.nat);
     std::vector<int> con, wts;
     if (pr.pack == DMET_PACK_S8) {
-      for (int w = 1; w <= 2; ++w)
-        for (int q = 0; q < pr.nk; ++q)
-          if (pr.s.qw[q] == w) {
-            con.push_back(q);
-            wts.push_back(w);
-          }
+      contraction_order(pr.d, pr.s, con, wts);
       build_tables(pr.s, con, pr.nao, pr.con);
+    }
+    if (reduced) {
+      // Block e of the reduced layout is contraction entry e (dmet_emb_l_pairs lists the same pairs).
+      std::vector<int> red(pr.nk * pr.nk, -1);
+      for (size_t e = 0; e < pr.con.t1.size(); ++e) {
+        red[pr.con.t1[e].y] = (int)e;
+        pr.con.t1[e].y = (int)e;
+      }
+      pr.n_lblocks = (long long)pr.con.t1.size();
+      // transform_3idx reads the same blocks; a q outside the shard has none
+      pr.nat_ok.assign(pr.nk, 1);
+      for (int i = 0; i < pr.nk; ++i)
+        for (int e = pr.nat.start[i]; e < pr.nat.start[i + 1]; ++e) {
+          const int b = red[pr.nat.t1[e].y];
+          if (b < 0) pr.nat_ok[i] = 0;
+          pr.nat.t1[e].y = b < 0 ? 0 : b;
+        }
+    } else {
+      pr.n_lblocks = (long long)pr.nk * pr.nk;
+      pr.nat_ok.assign(pr.nk, 1);
     }
     // q-block size: the largest (<= 8, or <= DMET_QBLOCK, entries per launch <= 65535) whose
     // workspace fits.
@@ -1543,7 +1617,8 @@ dmet_status_t dmet_emb_destroy(dmet_emb_plan_t plan) {
 // symmetry check, which reads every block, is on).
 static dmet_status_t stage_inputs(dmet_emb_plan_s* P, const Prob& pr, const void* L, const void* const* C,
                                   const double2** Ld, const double2** Cd, bool subset = false) {
-  const size_t lb = (size_t)pr.nk * pr.nk * pr.naux * pr.nao * pr.nao * 16;
+  const size_t blk = (size_t)pr.naux * pr.nao * pr.nao * 16;  // one (k1, k2) block
+  const size_t lb = (size_t)pr.n_lblocks * blk;
   P->xpending = false;
   size_t need = 0;
   const bool lhost = L && !is_device_ptr(L);
@@ -1587,7 +1662,7 @@ static dmet_status_t stage_inputs(dmet_emb_plan_s* P, const Prob& pr, const void
       CK(cudaStreamWaitEvent(P->xs, P->xstart, 0));
       P->xsrc = (const char*)L;
       P->xdst = cur;
-      P->xbb = lb / ((size_t)pr.nk * pr.nk);
+      P->xbb = blk;
       P->xnext = 0;
       P->xpending = true;
       TRY(queue_block_copies(P, pr, 0));
@@ -1615,6 +1690,9 @@ dmet_status_t dmet_emb_transform_3idx(dmet_emb_plan_t P, int32_t problem, const 
     if (!aligned16(C[s]) || !aligned16(Lq_out[s])) return fail(DMET_ERR_ALIGNMENT, "spin %d pointer not 16-byte aligned", s);
   }
   if (q_begin == q_end) return DMET_OK;
+  for (int q = q_begin; q < q_end; ++q)
+    if (!pr.nat_ok[q])
+      return fail(DMET_ERR_INVALID_ARG, "q = %d: its L blocks are outside the shard of the reduced L layout", q);
   P->cs = P->stream;
   P->W = &P->ws[P->ws_of[problem]];
   const double2* Ld = nullptr;

@@ -22,8 +22,13 @@ Conventions (section 2.1, Eq. "C loemb k" and Eq. "density fitting"):
   "paper" normalisation, Nk^-1 sum_k C^k+ C^k = 1), or that times Nk^-1/2
   ("unitary" normalisation, sum_k C^k+ C^k = 1).
 
-Random numbers come from numpy's counter-based Philox generator keyed by
-(seed, stream, block), so any P-block of B regenerates identically on its own.
+Random numbers: the 3-index tensor B, the bulk of every input, is drawn from a counter-based
+generator defined here (SplitMix64 of Steele, Lea & Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014, used as a hash of (seed, stream, counter), with the Box-Muller
+transform), so that any P-block regenerates identically on its own and a device implementation
+of the same definition (synth.gpu, for workloads whose L is too large to draw on the host) gives
+the same numbers up to the last-bit rounding of log and cos. The orbitals and the other small
+inputs come from numpy's counter-based Philox generator keyed by (seed, stream).
 """
 from __future__ import annotations
 
@@ -121,21 +126,79 @@ def _rng(seed: int, stream: int) -> np.random.Generator:
     return np.random.Generator(np.random.Philox(key=[int(seed) & (2**64 - 1), int(stream)]))
 
 
+# SplitMix64 (Steele, Lea & Flood 2014): state increment and output mixing constants.
+SM_GAMMA = 0x9E3779B97F4A7C15
+SM_M1 = 0xBF58476D1CE4E5B9
+SM_M2 = 0x94D049BB133111EB
+_U64 = (1 << 64) - 1
+
+
+def _sm_mix_int(z: int) -> int:
+    z = ((z ^ (z >> 30)) * SM_M1) & _U64
+    z = ((z ^ (z >> 27)) * SM_M2) & _U64
+    return z ^ (z >> 31)
+
+
+def counter_key(seed: int, stream: int) -> int:
+    """Key of one stream: k0 = mix(seed + gamma), key = mix(k0 + (stream + 1) gamma), mod 2^64."""
+    k0 = _sm_mix_int((int(seed) + SM_GAMMA) & _U64)
+    return _sm_mix_int((k0 + (int(stream) + 1) * SM_GAMMA) & _U64)
+
+
+def counter_normals(seed: int, stream: int, start: int, count: int, out: np.ndarray | None = None,
+                    chunk: int = 1 << 20) -> np.ndarray:
+    """Normals t = start .. start + count - 1 of stream (seed, stream).
+
+    Normal t is the Box-Muller transform of the SplitMix64 outputs h(2t) and h(2t + 1), where
+    h(c) = mix(key + (c + 1) gamma) (mod 2^64) and mix is SplitMix64's output function:
+    u1 = (floor(h(2t) / 2^11) + 1) 2^-53 in (0, 1], u2 = floor(h(2t + 1) / 2^11) 2^-53 in [0, 1),
+    z = sqrt(-2 ln u1) cos(2 pi u2)."""
+    key = np.uint64(counter_key(seed, stream))
+    if out is None:
+        out = np.empty(count)
+    g, m1, m2 = np.uint64(SM_GAMMA), np.uint64(SM_M1), np.uint64(SM_M2)
+    for c0 in range(0, count, chunk):
+        m = min(chunk, count - c0)
+        t0 = start + c0
+        c = np.arange(2 * t0 + 1, 2 * (t0 + m) + 1, dtype=np.uint64)   # c + 1 for c = 2t, 2t + 1
+        c *= g
+        c += key
+        c ^= c >> np.uint64(30)
+        c *= m1
+        c ^= c >> np.uint64(27)
+        c *= m2
+        c ^= c >> np.uint64(31)
+        c >>= np.uint64(11)
+        f = c.view(np.int64).astype(np.float64).reshape(m, 2)
+        u1 = (f[:, 0] + 1.0) * 2.0 ** -53
+        r = np.log(u1)
+        r *= -2.0
+        np.sqrt(r, out=r)
+        u2 = f[:, 1] * (2.0 ** -53 * 2.0 * np.pi)
+        np.cos(u2, out=u2)
+        np.multiply(r, u2, out=out[c0:c0 + m])
+    return out
+
+
 def real_space_B(spec: LatticeSpec, p_begin: int = 0, p_end: int | None = None) -> np.ndarray:
     """B[P, mu, R1, nu, R2] for P in [p_begin, p_end), real, pair-symmetrised.
 
     Entries are N(0,1) * exp(-a (|R1| + |R2|)); then B <- (B + B^T_pair) / 2 with the
-    pair transpose (mu, R1) <-> (nu, R2). Each P is drawn from its own Philox stream.
+    pair transpose (mu, R1) <-> (nu, R2). Aux function P draws its N(0,1) numbers, in C order
+    over (mu, R1, nu, R2), from stream _STREAM_B + P of counter_normals.
     """
     p_end = spec.n_aux if p_end is None else p_end
     nk, na = spec.nk, spec.n_ao
     w = np.exp(-spec.decay * min_image_norm(spec.mesh))
+    per = na * nk * na * nk
     out = np.empty((p_end - p_begin, na, nk, na, nk))
+    b = np.empty(per)
     for p in range(p_begin, p_end):
-        b = _rng(spec.seed, _STREAM_B + p).standard_normal((na, nk, na, nk))
-        b *= w[None, :, None, None]
-        b *= w[None, None, None, :]
-        out[p - p_begin] = 0.5 * (b + b.transpose(2, 3, 0, 1))
+        counter_normals(spec.seed, _STREAM_B + p, 0, per, out=b)
+        g = b.reshape(na, nk, na, nk)
+        g *= w[None, :, None, None]
+        g *= w[None, None, None, :]
+        out[p - p_begin] = 0.5 * (g + g.transpose(2, 3, 0, 1))
     return out
 
 

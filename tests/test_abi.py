@@ -24,9 +24,9 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_desc_layout_matches_header():
-    # 13 int32 fields (mesh[3] counted as 3) then two doubles.
-    assert ctypes.sizeof(B.dmet_emb_desc_t) == 13 * 4 + 4 + 16  # 4 bytes of padding before the doubles
-    assert B.dmet_emb_desc_t.ortho_tol.offset == 56
+    # 16 int32 fields (mesh[3] counted as 3) then two doubles.
+    assert ctypes.sizeof(B.dmet_emb_desc_t) == 16 * 4 + 16
+    assert B.dmet_emb_desc_t.ortho_tol.offset == 64
 
 
 def test_eri_bytes():
@@ -75,6 +75,14 @@ BAD = {
     "s8_needs_real": dict(sym=0, eri_pack=1),
     "prec": dict(prec=9),
     "check_l": dict(check_l=3),
+    "l_layout": dict(l_layout=2),
+    "reduced_needs_real": dict(l_layout=1, sym=0),
+    "reduced_needs_s8": dict(l_layout=1, eri_pack=2),
+    "reduced_no_check_l": dict(l_layout=1, check_l=1),
+    "shard_empty": dict(q_range=(2, 2)),
+    "shard_reversed": dict(q_range=(3, 1)),
+    "shard_past_mesh": dict(q_range=(0, 5)),
+    "shard_negative": dict(q_range=(-1, 2)),
 }
 
 
@@ -89,12 +97,52 @@ def test_invalid_descriptor_rejected_on_host(name):
     assert dm.dmet_emb_eri_bytes(d, 0) == 0
 
 
-def test_reserved_field_must_be_zero():
-    d = dm.make_desc((2, 2, 1), 8, 40, 16)
-    d.reserved = 1
+def _reduced_pairs_from_oracle(mesh, q_range=None):
+    """The reduced layout's pair list written out from the oracle's schedule definition."""
+    s = oracle.schedule(mesh, True)
+    nk = int(np.prod(mesh))
+    lo, hi = (0, nk) if q_range is None else q_range
+    out = []
+    for w in (1, 2):
+        for q in range(nk):
+            if s["q_weight"][q] != w or not lo <= q < hi:
+                continue
+            for r in range(s["n_rep"][q]):
+                k1 = s["rep_k1"][q, r]
+                out.append(k1 * nk + s["k2_of"][q, k1])
+    return np.array(out, dtype=np.int32)
+
+
+@pytest.mark.parametrize("mesh", [(1, 1, 1), (2, 1, 1), (3, 1, 1), (2, 2, 1), (3, 3, 1), (2, 2, 2), (4, 4, 4),
+                                  (6, 6, 1), (5, 1, 2)])
+def test_reduced_pairs_match_schedule(mesh):
+    d = dm.make_desc(mesh, 2, 3, 1)
+    got = dm.dmet_emb_l_pairs(d)
+    assert np.array_equal(got, _reduced_pairs_from_oracle(mesh))
+    nk = int(np.prod(mesh))
+    # every (k1, k2) block is one of the listed blocks up to Hermiticity and time reversal
+    neg = oracle.schedule(mesh, True)["neg"]
+    listed = set(got.tolist())
+    for k1 in range(nk):
+        for k2 in range(nk):
+            images = {k1 * nk + k2, k2 * nk + k1, neg[k1] * nk + neg[k2], neg[k2] * nk + neg[k1]}
+            assert images & listed, (k1, k2)
+
+
+def test_reduced_pairs_of_shards_partition_the_list():
+    mesh = (4, 4, 4)
+    full = dm.dmet_emb_l_pairs(dm.make_desc(mesh, 2, 3, 1))
+    parts = [dm.dmet_emb_l_pairs(dm.make_desc(mesh, 2, 3, 1, q_range=r)) for r in ((0, 9), (9, 30), (30, 64))]
+    for r, p in zip(((0, 9), (9, 30), (30, 64)), parts):
+        assert np.array_equal(p, _reduced_pairs_from_oracle(mesh, r))
+    assert sorted(np.concatenate(parts).tolist()) == sorted(full.tolist())
+    assert sum(len(p) for p in parts) == len(full)
+
+
+def test_reduced_pairs_unsupported_for_complex_orbitals():
     with pytest.raises(B.DmetError) as e:
-        dm.dmet_emb_plan(d)
-    assert e.value.status == B.DMET_ERR_INVALID_ARG
+        dm.dmet_emb_l_pairs(dm.make_desc((2, 2, 1), 2, 3, 1, sym=B.DMET_SYM_NONE))
+    assert e.value.status == B.DMET_ERR_UNSUPPORTED
 
 
 def test_null_arguments():
