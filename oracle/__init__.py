@@ -19,7 +19,7 @@ closed forms, symmetries, positivity and unitary invariance); see tests/test_ora
 tests/test_oracle_fock_pins.py, tests/test_oracle_bath_pins.py and tests/test_oracle_fftdf_pins.py.
 """
 from .mesh import k_add, k_index, k_neg, k_triplet
-from .alg1 import embedded_3idx, embedded_eri, eri_entries
+from .alg1 import embedded_3idx, embedded_eri, embedded_eri_pblocks, eri_entries
 from .supercell import (supercell_bath, supercell_density, supercell_eri, supercell_eri_grid, supercell_fock,
                         supercell_matrix)
 from .bath import bath_svd, embedding_orbitals, embedding_orbitals_lo, offdiag_density

@@ -70,3 +70,41 @@ def eri_entries(Lq_a, Lq_b, mesh, idx):
         b = Lq_b[k_neg(q, mesh)][:, k, l]          # [P, m]
         total += (a * b).sum(0) / nk
     return total
+
+
+def _embedded_3idx_block(Lb, C, mesh, scale):
+    """Algorithm 1's inner loop for one block of aux functions: Lb[k1, k2, P, mu, nu] holds every
+    (k1, k2) pair of the block; returns [Nk (q), P, n, n]. The same sums as embedded_3idx, with the
+    block's P rows stacked into one matrix product per pair (a library GEMM per step)."""
+    nk, pb, na = Lb.shape[0], Lb.shape[2], Lb.shape[3]
+    n = C.shape[2]
+    out = np.zeros((nk, pb, n, n), dtype=np.complex128)
+    for q in range(nk):
+        for k1 in range(nk):
+            k2 = k_add(k1, q, mesh)
+            right = (Lb[k1, k2].reshape(pb * na, na) @ C[k2]).reshape(pb, na, n)       # [P, mu, j]
+            pair = C[k1].conj().T @ right.transpose(1, 0, 2).reshape(na, pb * n)      # [i, (P, j)]
+            out[q] += scale * pair.reshape(n, pb, n).transpose(1, 0, 2)
+    return out
+
+
+def embedded_eri_pblocks(L_blocks, Cs, mesh, ck_norm=0):
+    """Algorithm 1 with L supplied block by block over the aux index (section 2.1 loads the
+    3-index integrals from disk blockwise): the contraction sums over P, so each block's
+    transformed factors are contracted and added on their own.
+
+    L_blocks: iterable of arrays [Nk, Nk, Pb, n_ao, n_ao] (every (k1, k2) pair of a block of aux
+    functions; the blocks together cover every P once). Cs: orbitals per spin, [Nk, n_ao, n_s].
+    Returns {(sa, sb): complex [n_sa, n_sa, n_sb, n_sb]} for sa <= sb, (i j) of spin sa and (k l) of
+    spin sb."""
+    nk = int(np.prod(mesh))
+    scale = 1.0 / nk if ck_norm == 0 else 1.0
+    ns = len(Cs)
+    out = {(a, b): np.zeros((Cs[a].shape[2],) * 2 + (Cs[b].shape[2],) * 2, dtype=np.complex128)
+           for a in range(ns) for b in range(a, ns)}
+    for Lb in L_blocks:
+        lq = [_embedded_3idx_block(Lb, C, mesh, scale) for C in Cs]
+        for (a, b), eri in out.items():
+            for q in range(nk):
+                eri += np.tensordot(lq[a][q], lq[b][k_neg(q, mesh)], axes=([0], [0])) / nk
+    return out

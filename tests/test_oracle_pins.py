@@ -267,3 +267,57 @@ def test_planted_mistake_fails_a_pin(name):
     assert rel(eri, ref) > 1e-6, name
     # The unmutated oracle passes the same pin.
     assert rel(oracle.embedded_eri(L, C, spec.mesh), ref) < 1e-12
+
+
+# ---------------------------------------------------------------------------------------------
+# Algorithm 1 with L streamed in blocks of aux functions (used for the full-size checks).
+
+def _blocks(L, pb):
+    return (L[:, :, p0:p0 + pb] for p0 in range(0, L.shape[2], pb))
+
+
+@pytest.mark.parametrize("mesh", [(2, 2, 1), (3, 1, 1), (2, 3, 1)])
+@pytest.mark.parametrize("ck_norm", [0, 1])
+def test_pblocks_brute_force_unrestricted(mesh, ck_norm):
+    spec = small_spec(mesh, n_ao=3, n_aux=7, n_emb=5)
+    B = synth.real_space_B(spec)
+    ca, cb = synth.supercell_orbitals(spec, 0), synth.supercell_orbitals(spec, 1)
+    L = synth.fourier_L(B, spec.mesh)
+    Cs = [synth.bloch_orbitals(c, spec.mesh, ck_norm) for c in (ca, cb)]
+    got = oracle.embedded_eri_pblocks(_blocks(L, 3), Cs, spec.mesh, ck_norm=ck_norm)
+    assert sorted(got) == [(0, 0), (0, 1), (1, 1)]
+    assert rel(got[(0, 0)], oracle.supercell_eri(B, spec.mesh, ca)) < 1e-12
+    assert rel(got[(0, 1)], oracle.supercell_eri(B, spec.mesh, ca, cb)) < 1e-12
+    assert rel(got[(1, 1)], oracle.supercell_eri(B, spec.mesh, cb)) < 1e-12
+
+
+def test_pblocks_complex_orbitals():
+    spec = small_spec((3, 2, 1), n_ao=2, n_aux=5, n_emb=4)
+    B = synth.real_space_B(spec)
+    csc = synth.complex_supercell_orbitals(spec)
+    L = synth.fourier_L(B, spec.mesh)
+    got = oracle.embedded_eri_pblocks(_blocks(L, 2), [synth.bloch_orbitals(csc, spec.mesh)], spec.mesh)
+    assert rel(got[(0, 0)], oracle.supercell_eri(B, spec.mesh, csc)) < 1e-12
+
+
+BLOCK_MUTATIONS = {
+    "no_conj_on_bra": ("pair = C[k1].conj().T @", "pair = C[k1].T @"),
+    "bra_rows_not_restacked": ("right.transpose(1, 0, 2).reshape(na, pb * n)", "right.reshape(na, pb * n)"),
+    "result_not_untransposed": ("pair.reshape(n, pb, n).transpose(1, 0, 2)", "pair.reshape(pb, n, n)"),
+    "second_factor_same_q": ("lq[b][k_neg(q, mesh)]", "lq[b][q]"),
+    "ket_with_k1": ("@ C[k2]).reshape(pb, na, n)", "@ C[k1]).reshape(pb, na, n)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(BLOCK_MUTATIONS))
+def test_planted_mistake_in_block_form_fails(name):
+    ns = _mutated_alg1(*BLOCK_MUTATIONS[name])
+    spec = small_spec((2, 3, 1), n_ao=3, n_aux=4, n_emb=5, seed=5)
+    B = synth.real_space_B(spec)
+    csc = synth.supercell_orbitals(spec)
+    L = synth.fourier_L(B, spec.mesh)
+    C = synth.bloch_orbitals(csc, spec.mesh)
+    ref = oracle.supercell_eri(B, spec.mesh, csc)
+    eri = ns["embedded_eri_pblocks"](_blocks(L, 3), [C], spec.mesh)[(0, 0)]
+    assert rel(eri, ref) > 1e-6, name
+    assert rel(oracle.embedded_eri_pblocks(_blocks(L, 3), [C], spec.mesh)[(0, 0)], ref) < 1e-12
