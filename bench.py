@@ -1,19 +1,26 @@
 """Benchmark of the embedded-ERI transformation (Algorithm 1 of arXiv 1909.08596, section 2.1).
 
-One step = one call of dmet_emb_eri on one embedding problem: orbital and symmetry checks,
-the k-AO -> k-EO half transforms of every needed (k1, k1+q) pair, the Fourier sum to the
-reference cell, the contraction over the aux index and the sum over q into the 8-fold
-packed ERI. Inputs are synthetic (seeded) with the h-BN-shaped sizes of section 2.2
-(6x6x1 mesh, 26 AOs and 220 aux functions per cell, 104 embedding orbitals).
+One step = one call of dmet_emb_eri on one embedding problem: orbital checks, the k-AO -> k-EO
+half transforms of every needed (k1, k1+q) pair, the Fourier sum to the reference cell, the
+contraction over the aux index and the sum over q into the 8-fold packed ERI blocks.
 
-Prints one JSON line. `value` is useful TFLOP/s (the symmetry-reduced algorithmic flop
-count of the work the library does) with inputs resident in HBM; `e2e` is the same metric
-through the C ABI with host buffers (copies inside the timed region). The headline path is
-the split-BF16 tensor-core path; the plain FP64 path is measured in the same run and
-reported under "fp64", and both are compared with the FP64 oracle on an orbital subset.
+Default workload: the NiO-shaped unrestricted problem (section 3.3's AFM-II NiO cell on the
+4x4x4 mesh of section 2.2: 104 AOs and 900 aux functions per cell, 300 embedding orbitals per
+spin, alpha-alpha, alpha-beta and beta-beta blocks), with L in the reduced layout (the 1184
+(k1, k2) blocks the 8-fold schedule reads, 184 GB) generated on the device from the seeded
+generator. The inputs are synthetic stand-ins for the paper's GDF integrals and embedding
+orbitals (same shapes, seeded values; synth/lattice.py).
+
+Prints one JSON line. `value` is useful TFLOP/s (the symmetry-reduced algorithmic flop count
+of the work the library does) with inputs resident in HBM; `e2e` is the same metric through
+the C ABI with host buffers (copies inside the timed region). The headline path is the
+split-BF16 tensor-core path; the plain FP64 path is measured alongside where it finishes in
+reasonable time. The error of each result against the FP64 CPU oracle is measured on seeded
+orbital subsets (exact: an orbital-column subset of the ERI is the method applied to those
+columns), per spin block, with L streamed to the oracle in blocks of aux functions.
 
     python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference] [--workload NAME]
-                    [--prec bf16x3|fp64] [--only]
+                    [--prec bf16x3|fp64] [--only] [--check-orbitals N]
 """
 from __future__ import annotations
 
@@ -34,39 +41,59 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "embedded-ERI transform TFLOP/s and ms/problem at stated error vs FP64; % of roofline"
+DEFAULT_WORKLOAD = "nio_4x4x4_uhf"
 SMS = 152
 DFMA_PER_SM_CLK = 2  # FP64 FMA lanes per SM per clock on GB300 (1.25 TFLOP/s nominal at 2.07 GHz)
-ORACLE_SAMPLE_ORBITALS = 24
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the tensor kernels, averaged over the launches of
-# one call, from a one-pass ncu capture of the full h-BN bench command (profiles/launches_bf16x3_hbn_6x6x1.txt
-# gives the command and the figures); (workload, path, kernel class) -> bytes. Valid only for the kernels as
-# they were at that capture.
-TRAFFIC = {
-    ("hbn_6x6x1", "bf16x3", "tc_half_transform_1"): 1.424e9,
-    ("hbn_6x6x1", "bf16x3", "tc_half_transform_2"): 1.154e9,
-    ("hbn_6x6x1", "bf16x3", "tc_contract"): 1.273e9,
-}
+REF_SAMPLE_ORBITALS = 24
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of a tensor kernel, from an ncu capture of the
+# kernels as they are now: (workload, path, kernel class) -> bytes. Empty until such a capture exists; the
+# roofline's traffic is then null.
+TRAFFIC = {}
 
 
-def useful_flops(spec, n_list, desc_sym=1):
+def schedule_counts(mesh):
+    """Per q: the contraction weight (1 for q = -q, 2 for q < -q, 0 for q > -q) and the number of
+    transformed k1 (one per orbit {k1, -k1-q}), from their definition (section 2.1's loops with the
+    real-orbital symmetries; tests/test_bench_host.py checks them against the library's schedule)."""
+    n1, n2, n3 = mesh
+    nk = n1 * n2 * n3
+
+    def trip(k):
+        return k // (n2 * n3), (k // n3) % n2, k % n3
+
+    def idx(a, b, c):
+        return ((a % n1) * n2 + (b % n2)) * n3 + (c % n3)
+
+    neg = [idx(*(-x for x in trip(k))) for k in range(nk)]
+    qw, nrep = [], []
+    for q in range(nk):
+        qw.append(1 if q == neg[q] else (2 if q < neg[q] else 0))
+        tq = trip(q)
+        cnt = 0
+        for k1 in range(nk):
+            t1 = trip(k1)
+            partner = neg[idx(t1[0] + tq[0], t1[1] + tq[1], t1[2] + tq[2])]
+            cnt += k1 <= partner
+        nrep.append(cnt)
+    return qw, nrep
+
+
+def useful_flops(spec, n_list, n_aux=None):
     """Algorithmic flops of one problem with the symmetry reductions the library applies.
 
-    Transform (per spin, per computed pair): 8 n_aux (n_ao^2 n + n_ao n^2) (a complex MAC is
-    8 flops); contraction: npair (npair+1) K per same-spin block, 2 npair_a npair_b K for
+    Transform (per spin, per computed pair): 8 n_aux (n_ao^2 n + n_ao n^2) (a complex MAC is 8
+    flops); contraction: npair (npair+1) K per same-spin block, 2 npair_a npair_b K for
     alpha-beta, K = n_aux * (1 + [q != -q]) summed over the contracted q."""
-    import paper_1909_08596_gb300 as dm
-    d = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, n_list, n_spin=len(n_list), sym=desc_sym)
-    s = dm.dmet_emb_schedule(d)
-    nao, naux = spec.n_ao, spec.n_aux
+    qw, nrep = schedule_counts(spec.mesh)
+    nao, naux = spec.n_ao, spec.n_aux if n_aux is None else n_aux
     fl_t = 0.0
     K = 0
-    for q in range(spec.nk):
-        w = s["q_weight"][q]
+    for q, w in enumerate(qw):
         if not w:
             continue
         K += naux * (1 if w == 1 else 2)
         for n in n_list:
-            fl_t += s["n_rep"][q] * 8.0 * naux * (nao * nao * n + nao * n * n)
+            fl_t += nrep[q] * 8.0 * naux * (nao * nao * n + nao * n * n)
     pairs = [n * (n + 1) // 2 for n in n_list]
     fl_c = sum(p * (p + 1.0) * K for p in pairs)
     if len(n_list) == 2:
@@ -116,6 +143,7 @@ class ClockSampler:
         self.thread.join(timeout=5)
         sm = [float(r[0]) for r in self.rows if r[0].replace(".", "", 1).isdigit()]
         mx = [float(r[1]) for r in self.rows if r[1].replace(".", "", 1).isdigit()]
+        pw = [float(r[2]) for r in self.rows if r[2].replace(".", "", 1).isdigit()]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in self.rows:
@@ -123,7 +151,7 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
 def dist_env():
@@ -150,19 +178,6 @@ def job_tflops(world, flops_per_problem, steps, ms_total):
     return world * flops_per_problem * steps / (ms_total / 1e3) / 1e12
 
 
-def oracle_sample(spec, L, C, n_sub, seed=0):
-    """Runs the CPU oracle (Algorithm 1 as written: every q, every k1, dense contraction) on a
-    seeded subset of n_sub embedding orbitals; returns (seconds, useful flops, orbital subset,
-    ERI on the subset). Orbital-column subsets of the ERI are exact (same arithmetic per entry)."""
-    import oracle
-    rng = np.random.default_rng(seed)
-    S = np.sort(rng.choice(C.shape[2], n_sub, replace=False))
-    t0 = time.perf_counter()
-    eri = oracle.embedded_eri(L, np.ascontiguousarray(C[:, :, S]), spec.mesh)
-    dt = time.perf_counter() - t0
-    return dt, useful_flops(spec, [n_sub])[0], S, eri
-
-
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -170,42 +185,20 @@ def cpu_cores():
         return os.cpu_count()
 
 
-def run_reference(args):
-    rank, world, _ = dist_env()
-    if rank != 0:
-        return 0
-    spec = synth.CONFIGS[args.workload]
-    L, (C,), _ = synth.make_problem(spec)
-    times, fl = [], 0.0
-    for it in range(args.warmup + args.steps):
-        dt, fl, _, _ = oracle_sample(spec, L, C, ORACLE_SAMPLE_ORBITALS, seed=it)
-        if it >= args.warmup:
-            times.append(dt)
-    sec = float(np.mean(times))
-    value = fl / sec / 1e12
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": spec.name, "mesh": list(spec.mesh), "n_ao": spec.n_ao, "n_aux": spec.n_aux,
-                   "n_emb": spec.n_emb, "sample_orbitals": ORACLE_SAMPLE_ORBITALS},
-        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
-                         "sample": f"Algorithm 1 (all q, all k1, dense contraction) on {ORACLE_SAMPLE_ORBITALS} "
-                                   f"of {spec.n_emb} embedding orbitals per step; useful flops of that sub-problem"},
-        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
+def host_available_bytes():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
     return 0
 
 
-def measured_peaks():
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    try:
-        with open(path) as f:
-            d = json.load(f)
-        return d, "measured"
-    except (OSError, ValueError):
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+def subset_orbitals(spec, n_sub, seed=0):
+    rng = np.random.default_rng(seed)
+    return [np.sort(rng.choice(spec.n_emb, min(n_sub, spec.n_emb), replace=False)) for _ in range(spec.n_spin)]
 
 
 def s8_positions(S):
@@ -219,89 +212,129 @@ def s8_positions(S):
     return P * (P + 1) // 2 + Q
 
 
-def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
-    """Times args.steps calls of dmet_emb_eri on resident inputs, then the end-to-end form."""
-    n_list = [spec.n_emb] * spec.n_spin
-    fl_total, fl_t, fl_c = useful_flops(spec, n_list)
-    stream = torch.cuda.current_stream()
-    pcode = dm.binding.DMET_PREC_FP64 if prec == "fp64" else dm.binding.DMET_PREC_BF16X3
-    desc = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, n_list, n_spin=spec.n_spin, prec=pcode)
-    nblk = 1 if spec.n_spin == 1 else 3
-    outs = [torch.empty(dm.dmet_emb_eri_bytes(desc, b) // 8, dtype=torch.float64, device="cuda") for b in range(nblk)]
-    plan = dm.dmet_emb_plan(desc, stream=stream.cuda_stream)
-    tile_widths = None
-    if prec != "fp64" and not args.no_autotune:
-        # Tile widths of the transform GEMMs chosen by timing (outside the timed region).
-        dm.dmet_emb_autotune(plan, [Ld], [Cd], [outs])
-        tile_widths = dm.dmet_emb_tile_widths(plan, 0)
+def ab_positions(Sa, Sb, nb):
+    """Indices [IJ][KL] of the alpha-beta block for i, j in Sa (alpha) and k, l in Sb (beta)."""
+    i, j, k, l = np.meshgrid(np.arange(len(Sa)), np.arange(len(Sa)), np.arange(len(Sb)), np.arange(len(Sb)),
+                             indexing="ij")
+    ii, jj, kk, ll = Sa[i.ravel()], Sa[j.ravel()], Sb[k.ravel()], Sb[l.ravel()]
+    I, J = np.maximum(ii, jj), np.minimum(ii, jj)
+    K_, L_ = np.maximum(kk, ll), np.minimum(kk, ll)
+    npb = nb * (nb + 1) // 2
+    return (I * (I + 1) // 2 + J) * npb + (K_ * (K_ + 1) // 2 + L_)
 
-    def step():
-        dm.dmet_emb_eri(plan, [Ld], [Cd], [outs])
 
-    for _ in range(args.warmup):
-        step()
-    st, stats = dm.dmet_emb_status(plan, 0)
-    if st != dm.binding.DMET_OK:
-        raise RuntimeError(f"device status {st}: {dm.dmet_emb_last_error()} {stats}")
-    steps = args.steps if prec != "fp64" else min(args.steps, args.fp64_steps)
-    dm.dmet_emb_profile(plan, True)
-    launches0 = dm.dmet_emb_launch_count(plan)
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    launches = dm.dmet_emb_launch_count(plan) - launches0
-    kstats = [dm.dmet_emb_profile_read(plan, k) for k in range(dm.dmet_emb_profile_count())]
-    dm.dmet_emb_profile(plan, False)
-    ms_total = max_over_ranks(dist, ms_total, "cuda")
-    ms_step = ms_total / steps
-    value = job_tflops(world, fl_total, steps, ms_total)
+def block_positions(spec, S):
+    """Per output block b: the packed positions of the subset tensor (i j | k l), C order."""
+    if spec.n_spin == 1:
+        return [s8_positions(S[0])]
+    return [s8_positions(S[0]), ab_positions(S[0], S[1], spec.n_emb), s8_positions(S[1])]
 
+
+def block_spins(spec):
+    return [(0, 0)] if spec.n_spin == 1 else [(0, 0), (0, 1), (1, 1)]
+
+
+def error_stats(got, ref):
+    d = got - ref
+    return {"rel_fro": float(np.linalg.norm(d) / np.linalg.norm(ref)), "max_abs": float(np.abs(d).max()),
+            "max_abs_over_max": float(np.abs(d).max() / np.abs(ref).max()), "rms": float(np.sqrt(np.mean(d * d)))}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle (Algorithm 1 as written, every q and every k1, dense
+    contraction; L streamed over aux functions) on a bounded sample of the workload, on the host
+    cores. Uses only synth (host generator) and oracle; never the library under test."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    spec = synth.CONFIGS[args.workload]
+    # sample: REF_SAMPLE_ORBITALS orbitals per spin, the first p_ref aux functions (the host generator
+    # draws about 7.5e6 normals per second, so the sample's L is drawn in about 10 s at most)
+    per_p = (spec.n_ao * spec.nk) ** 2
+    p_ref = int(max(1, min(spec.n_aux, 75_000_000 // per_p)))
+    Lb = synth.fourier_L(synth.real_space_B(spec, 0, p_ref), spec.mesh)
+    _, Cs, _ = synth.make_problem(spec, with_L=False)
+    S = subset_orbitals(spec, REF_SAMPLE_ORBITALS)
+    Csub = [np.ascontiguousarray(C[:, :, s]) for C, s in zip(Cs, S)]
+    n_list = [len(s) for s in S]
+    fl = useful_flops(spec, n_list, n_aux=p_ref)[0]
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.embedded_eri_pblocks([Lb], Csub, spec.mesh)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    sec = float(np.mean(times))
+    value = fl / sec / 1e12
+    sample = (f"Algorithm 1 (all q, all k1, dense contraction) on {n_list[0]} of {spec.n_emb} embedding orbitals "
+              f"per spin and the first {p_ref} of {spec.n_aux} aux functions per step; useful flops of that "
+              f"sub-problem")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(spec, "fp64"),
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(spec, prec, layout=None):
+    return {"workload": spec.name, "mesh": list(spec.mesh), "n_ao": spec.n_ao, "n_aux": spec.n_aux,
+            "n_emb": spec.n_emb, "n_spin": spec.n_spin, "prec": prec, "pack": "s8",
+            **({"l_layout": layout} if layout else {})}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def roofline(spec, prec, kstats, sustained=False):
     peaks, peak_src = measured_peaks()
     top = max(kstats, key=lambda k: k["ms"])
     avg_ms = top["ms"] / max(top["launches"], 1)
     if prec == "fp64":
         peak = SMS * DFMA_PER_SM_CLK * 2 * 2070e6 / 1e12
         achieved = top["flops"] / (top["ms"] / 1e3) / 1e12 if top["ms"] > 0 else 0.0
-        roof = {"bound": "alu", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        return {"bound": "alu", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": TRAFFIC.get((spec.name, prec, top["name"])),
                 "flops_counted": "algorithmic FP64 flops",
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (FP64 runs on the CUDA cores)",
                 "avg_launch_ms": avg_ms}
-    else:
-        # A tensor kernel's roofline is whichever of its two floors is higher: executed tensor
-        # flops at the measured bf16 peak, or its algorithmic bytes at the measured HBM copy rate.
-        peak_t, peak_b = peaks["bf16_tflops"], peaks["hbm_gbs"]
-        secs = top["ms"] / 1e3 / max(top["launches"], 1)
-        fl_l = top["exec_flops"] / max(top["launches"], 1)
-        by_l = top["bytes"] / max(top["launches"], 1)
-        t_tensor, t_hbm = fl_l / (peak_t * 1e12), by_l / (peak_b * 1e9)
-        tensor = {"achieved": fl_l / secs / 1e12 if secs > 0 else 0.0, "peak": peak_t, "unit": "TFLOP/s"}
-        hbm = {"achieved": by_l / secs / 1e9 if secs > 0 else 0.0, "peak": peak_b, "unit": "GB/s"}
-        for d in (tensor, hbm):
-            d["frac"] = d["achieved"] / d["peak"]
-        main, other = (hbm, tensor) if t_hbm > t_tensor else (tensor, hbm)
-        roof = {"bound": "hbm" if main is hbm else "tensor", "kernel": top["name"], **main,
-                "traffic": TRAFFIC.get((spec.name, prec, top["name"])),
-                "other_bound": {"bound": "tensor" if main is hbm else "hbm", **other},
-                "flops_counted": "executed BF16 tensor flops (6 slice products per useful multiply-add, whole tiles)",
-                "bytes_counted": "algorithmic bytes per launch: operands read once, result written once",
-                "useful_achieved_tflops": top["flops"] / (top["ms"] / 1e3) / 1e12 if top["ms"] > 0 else 0.0,
-                "peak_source": f"{peak_src} bf16_tflops (burst; sustained {peaks.get('bf16_tflops_sustained')}) "
-                               f"and hbm_gbs",
-                "avg_launch_ms": avg_ms}
+    # A tensor kernel's roofline is whichever of its two floors is higher: executed tensor flops at
+    # the measured bf16 peak, or its algorithmic bytes at the measured HBM copy rate.
+    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+    peak_t, peak_b = peaks[key], peaks["hbm_gbs"]
+    secs = top["ms"] / 1e3 / max(top["launches"], 1)
+    fl_l = top["exec_flops"] / max(top["launches"], 1)
+    by_l = top["bytes"] / max(top["launches"], 1)
+    t_tensor, t_hbm = fl_l / (peak_t * 1e12), by_l / (peak_b * 1e9)
+    tensor = {"achieved": fl_l / secs / 1e12 if secs > 0 else 0.0, "peak": peak_t, "unit": "TFLOP/s"}
+    hbm = {"achieved": by_l / secs / 1e9 if secs > 0 else 0.0, "peak": peak_b, "unit": "GB/s"}
+    for d in (tensor, hbm):
+        d["frac"] = d["achieved"] / d["peak"]
+    main, other = (hbm, tensor) if t_hbm > t_tensor else (tensor, hbm)
+    useful = top["flops"] / (top["ms"] / 1e3) / 1e12 if top["ms"] > 0 else 0.0
+    return {"bound": "hbm" if main is hbm else "tensor", "kernel": top["name"], **main,
+            "traffic": TRAFFIC.get((spec.name, prec, top["name"])),
+            "other_bound": {"bound": "tensor" if main is hbm else "hbm", **other},
+            "flops_counted": "executed tensor flops (every slice product issued, whole tiles)",
+            "bytes_counted": "algorithmic bytes per launch: operands read once, result written once",
+            "useful_achieved_tflops": useful, "useful_frac": useful / peak_t,
+            "peak_source": f"{peak_src} {key} and hbm_gbs", "avg_launch_ms": avg_ms}
+
+
+def kernel_table(kstats):
     tot_ms = max(sum(x["ms"] for x in kstats), 1e-9)
     kernels = {}
     for k in kstats:
@@ -312,42 +345,116 @@ def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
             e["hbm_gbs"] = round(k["bytes"] / (k["ms"] / 1e3) / 1e9, 1)  # algorithmic bytes / time
         if k["ms"] > 0 and k["exec_flops"] > 0:
             e["exec_tflops"] = round(k["exec_flops"] / (k["ms"] / 1e3) / 1e12, 1)
+        if k["ms"] > 0 and k["flops"] > 0:
+            e["useful_tflops"] = round(k["flops"] / (k["ms"] / 1e3) / 1e12, 1)
         kernels[k["name"]] = e
+    return kernels
 
-    # The embedding one-particle Hamiltonian from this ERI (dmet_emb_fock, FP64 kernels): timed on
-    # its own, after the ERI, with a synthetic mean-field Fock matrix and embedding density.
-    fock = None
-    if spec.n_spin == 1:
+
+def measure(dm, torch, spec, desc, Ld, Cd, outs, steps, args, dist, world, local, ws_limit, autotune):
+    """Times `steps` calls of dmet_emb_eri on resident inputs (CUDA events on the plan's stream)."""
+    n_list = [spec.n_emb] * spec.n_spin
+    fl_total, fl_t, fl_c = useful_flops(spec, n_list)
+    stream = torch.cuda.current_stream()
+    plan = dm.dmet_emb_plan(desc, stream=stream.cuda_stream, workspace_limit=ws_limit)
+    try:
+        tile_widths = None
+        if autotune:
+            # Tile widths of the transform GEMMs chosen by timing (outside the timed region).
+            dm.dmet_emb_autotune(plan, [Ld], [Cd], [outs])
+            tile_widths = dm.dmet_emb_tile_widths(plan, 0)
+
+        def step():
+            dm.dmet_emb_eri(plan, [Ld], [Cd], [outs])
+
+        for _ in range(args.warmup):
+            step()
+        st, stats = dm.dmet_emb_status(plan, 0)
+        if st != dm.binding.DMET_OK:
+            raise RuntimeError(f"device status {st}: {dm.dmet_emb_last_error()} {stats}")
+        dm.dmet_emb_profile(plan, True)
+        launches0 = dm.dmet_emb_launch_count(plan)
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clk = clocks.stop()
+        ms_total = ev0.elapsed_time(ev1)
+        launches = dm.dmet_emb_launch_count(plan) - launches0
+        kstats = [dm.dmet_emb_profile_read(plan, k) for k in range(dm.dmet_emb_profile_count())]
+        dm.dmet_emb_profile(plan, False)
+        st, stats = dm.dmet_emb_status(plan, 0)
+    finally:
+        dm.dmet_emb_destroy(plan)
+    ms_total = max_over_ranks(dist, ms_total, "cuda")
+    ms_step = ms_total / steps
+    # a step of a second or more is a long timed region: the sustained peak applies
+    prec = "fp64" if desc.prec == dm.binding.DMET_PREC_FP64 else "bf16x3"
+    return {
+        "value": job_tflops(world, fl_total, steps, ms_total), "ms_per_step": ms_step,
+        "useful_tflop_per_problem": fl_total / 1e12,
+        "useful_split": {"transform": fl_t / 1e12, "contraction": fl_c / 1e12},
+        "roofline": roofline(spec, prec, kstats), "kernels": kernel_table(kstats), "gpu_launches": int(launches),
+        "clocks": clk, "steps": steps, "tile_widths": tile_widths,
+        "device_checks": {"status": int(st), "orthonormality": stats[0], "realness": stats[1],
+                          "hermiticity_L": stats[2], "time_reversal_L": stats[3]},
+    }
+
+
+def gather_subsets(torch, outs, positions):
+    """The GPU's packed values at the subset positions of every block (gathered on the device)."""
+    return [outs[b][torch.as_tensor(pos, device=outs[b].device)].cpu().numpy() for b, pos in enumerate(positions)]
+
+
+def measure_fock_and_bath(dm, torch, spec, Cd, eri0):
+    """The embedding one-particle Hamiltonian from this ERI (dmet_emb_fock) and the DMET bath that
+    produces such orbitals (dmet_emb_bath), FP64 kernels, timed on their own (restricted problems)."""
+    stream = torch.cuda.current_stream()
+    desc = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, spec.n_emb)
+    plan = dm.dmet_emb_plan(desc, stream=stream.cuda_stream, workspace_limit=1 << 30)
+    fock = bath = None
+    try:
         Fk = torch.from_numpy(synth.fock_k(synth.real_space_fock(spec), spec.mesh)).cuda()
         gam = torch.from_numpy(synth.embedding_density(spec.n_emb, spec.seed)).cuda()
         fo = torch.empty((spec.n_emb, spec.n_emb), dtype=torch.float64, device="cuda")
-        for _ in range(3):
-            dm.dmet_emb_fock(plan, Fk, Cd[0], outs[0], gam, fo)
-        dm.dmet_emb_profile(plan, True)
-        reps = 10
-        ef0, ef1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ef0.record(stream)
-        for _ in range(reps):
-            dm.dmet_emb_fock(plan, Fk, Cd[0], outs[0], gam, fo)
-        ef1.record(stream)
-        torch.cuda.synchronize()
-        fk = [k for k in (dm.dmet_emb_profile_read(plan, i) for i in range(dm.dmet_emb_profile_count()))
-              if k["name"] == "embedding_fock"][0]
-        dm.dmet_emb_profile(plan, False)
-        f_ms = ef0.elapsed_time(ef1) / reps
-        f_peak = SMS * DFMA_PER_SM_CLK * 2 * 2070e6 / 1e12
-        f_tf = fk["flops"] / reps / (f_ms / 1e3) / 1e12
-        fock = {"ms": f_ms, "launches_per_call": fk["launches"] // reps,
-                "roofline": {"bound": "alu", "achieved": f_tf, "peak": f_peak, "unit": "TFLOP/s", "frac": f_tf / f_peak,
-                             "flops_counted": "FP64 flops the kernels execute (transform GEMMs; 2 n^2 exchange and "
-                                              "n(n+1)/2 Coulomb multiply-adds per ERI pair row)",
-                             "peak_source": "derived FP64 peak (152 SMs x 2 FMA/clk x 2 x 2070 MHz)"}}
-
-    # The DMET bath that produces such orbitals (dmet_emb_bath, FP64 kernels): the same cell and
-    # mesh, its n_AO LOs as the impurity and 8 of them as the valence columns of the SVD (the
-    # valence shell of a two-atom s/p cell), from a synthetic gapped mean field.
-    bath = None
-    if spec.n_spin == 1 and spec.nk > 1:
+        if spec.n_emb <= 232:
+            for _ in range(3):
+                dm.dmet_emb_fock(plan, Fk, Cd[0], eri0, gam, fo)
+            dm.dmet_emb_profile(plan, True)
+            reps = 10
+            ef0, ef1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ef0.record(stream)
+            for _ in range(reps):
+                dm.dmet_emb_fock(plan, Fk, Cd[0], eri0, gam, fo)
+            ef1.record(stream)
+            torch.cuda.synchronize()
+            fk = [k for k in (dm.dmet_emb_profile_read(plan, i) for i in range(dm.dmet_emb_profile_count()))
+                  if k["name"] == "embedding_fock"][0]
+            dm.dmet_emb_profile(plan, False)
+            f_ms = ef0.elapsed_time(ef1) / reps
+            f_peak = SMS * DFMA_PER_SM_CLK * 2 * 2070e6 / 1e12
+            f_tf = fk["flops"] / reps / (f_ms / 1e3) / 1e12
+            fock = {"ms": f_ms, "launches_per_call": fk["launches"] // reps,
+                    "roofline": {"bound": "alu", "achieved": f_tf, "peak": f_peak, "unit": "TFLOP/s",
+                                 "frac": f_tf / f_peak,
+                                 "flops_counted": "FP64 flops the kernels execute (transform GEMMs; 2 n^2 exchange "
+                                                  "and n(n+1)/2 Coulomb multiply-adds per ERI pair row)",
+                                 "peak_source": "derived FP64 peak (152 SMs x 2 FMA/clk x 2 x 2070 MHz)"}}
+    finally:
+        dm.dmet_emb_destroy(plan)
+    # The bath: the same cell and mesh, its n_AO LOs as the impurity and 8 of them as the valence
+    # columns of the SVD (the valence shell of a two-atom s/p cell), from a synthetic gapped mean field.
+    if spec.nk > 1:
         n_val = min(8, spec.n_ao)
         bspec = synth.spec_with(spec, n_emb=spec.n_ao + n_val)
         h = synth.mean_field_hamiltonian(bspec, spec.n_ao // 2)
@@ -356,7 +463,8 @@ def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
         val = list(range(0, spec.n_ao, max(1, spec.n_ao // n_val)))[:n_val]
         Cb = torch.empty((spec.nk, spec.n_ao, bspec.n_emb), dtype=torch.complex128, device="cuda")
         binfo = torch.zeros(n_val + 5, dtype=torch.float64, device="cuda")
-        bplan = dm.dmet_emb_plan(dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, bspec.n_emb), stream=stream.cuda_stream)
+        bplan = dm.dmet_emb_plan(dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, bspec.n_emb),
+                                 stream=stream.cuda_stream, workspace_limit=1 << 30)
         try:
             for _ in range(3):
                 dm.dmet_emb_bath(bplan, gk, Ulo, val, Cb, binfo)
@@ -373,65 +481,101 @@ def measure(dm, torch, spec, L, Cs, Ld, Cd, prec, args, dist, world, local):
                     "jacobi_sweeps": int(bi[n_val + 2]), "sigma_min_over_max": float(bi[n_val + 4])}
         finally:
             dm.dmet_emb_destroy(bplan)
+    return fock, bath
 
-    # End to end through the C ABI with host buffers: H2D of L and C, D2H of the ERI. A plan of its
-    # own, built with the q-block size capped (DMET_QBLOCK) so that L streams in small blocks.
-    e2e = None
-    if not args.no_e2e:
-        Lh = torch.from_numpy(L).pin_memory()
-        Ch = [torch.from_numpy(c).pin_memory() for c in Cs]
-        Oh = [torch.empty(o.numel(), dtype=torch.float64).pin_memory() for o in outs]
-        old_qb = os.environ.get("DMET_QBLOCK")
-        if args.e2e_qblock > 0:
-            os.environ["DMET_QBLOCK"] = str(args.e2e_qblock)
-        try:
-            eplan = dm.dmet_emb_plan(desc, stream=stream.cuda_stream)
-        finally:
-            if old_qb is None:
-                os.environ.pop("DMET_QBLOCK", None)
-            else:
-                os.environ["DMET_QBLOCK"] = old_qb
-        try:
-            outs_e = [torch.empty_like(o) for o in outs]
-            if prec != "fp64" and not args.no_autotune:
-                dm.dmet_emb_autotune(eplan, [Ld], [Cd], [outs_e])
-            dm.dmet_emb_eri(eplan, [Ld], [Cd], [outs_e])  # the device result of this plan, for the check below
+
+def measure_e2e(dm, torch, desc, holder, Cs, positions, fl_total, world, args, ws_limit):
+    """End to end through the C ABI with host buffers: every step copies the (k1, k2) blocks of L the
+    schedule reads and C from pinned host memory to the device, runs the call and reads the ERI blocks
+    back. A plan of its own, built with the q-block size capped (DMET_QBLOCK) so that L streams in
+    small blocks. holder["Ld"] (the device L) is released once its host copy exists."""
+    Ld = holder["Ld"]
+    Lh = torch.empty(Ld.shape, dtype=Ld.dtype, pin_memory=True)
+    Lh.copy_(Ld)
+    holder["Ld"] = None
+    del Ld
+    torch.cuda.empty_cache()
+    Ch = [torch.from_numpy(c).pin_memory() for c in Cs]
+    nblk = 1 if desc.n_spin == 1 else 3
+    Oh = [torch.empty(dm.dmet_emb_eri_bytes(desc, b) // 8, dtype=torch.float64).pin_memory() for b in range(nblk)]
+    stream = torch.cuda.current_stream()
+    old_qb = os.environ.get("DMET_QBLOCK")
+    if args.e2e_qblock > 0:
+        os.environ["DMET_QBLOCK"] = str(args.e2e_qblock)
+    try:
+        eplan = dm.dmet_emb_plan(desc, stream=stream.cuda_stream, workspace_limit=ws_limit)
+    finally:
+        if old_qb is None:
+            os.environ.pop("DMET_QBLOCK", None)
+        else:
+            os.environ["DMET_QBLOCK"] = old_qb
+    try:
+        dm.dmet_emb_eri(eplan, [Lh], [Ch], [Oh])  # warm-up (allocates the staging buffers)
+        torch.cuda.synchronize()
+        dm.dmet_emb_profile(eplan, False)  # clears the counters (no events are recorded)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
             dm.dmet_emb_eri(eplan, [Lh], [Ch], [Oh])
-            torch.cuda.synchronize()
-            e2e_steps = args.e2e_steps if prec != "fp64" else 1
-            dm.dmet_emb_profile(eplan, False)  # clears the counters (no events are recorded)
-            t0 = time.perf_counter()
-            for _ in range(e2e_steps):
-                dm.dmet_emb_eri(eplan, [Lh], [Ch], [Oh])
-            torch.cuda.synchronize()
-            e2e_s = (time.perf_counter() - t0) / e2e_steps
-            # bytes the library moved between host and device (it transfers only the L blocks its schedule reads)
-            copy_b = sum(k["bytes"] for k in (dm.dmet_emb_profile_read(eplan, i)
-                                              for i in range(dm.dmet_emb_profile_count()))
-                         if k["name"] == "host_copy") / e2e_steps
-        finally:
-            dm.dmet_emb_destroy(eplan)
-        d2h_b = int(sum(o.numel() * 8 for o in Oh))
-        same = all(torch.equal(o.cpu(), h) for o, h in zip(outs_e, Oh))
-        del outs_e
-        e2e = {"value": world * fl_total / e2e_s / 1e12, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": int(copy_b) - d2h_b, "d2h_bytes_per_step": d2h_b,
-               "host_L_bytes": int(Lh.numel() * 16), "ms_per_step": e2e_s * 1e3,
-               "qblock_cap": args.e2e_qblock, "matches_device_result": bool(same)}
-    st, stats = dm.dmet_emb_status(plan, 0)
-    dm.dmet_emb_destroy(plan)
-    return {
-        "value": value, "ms_per_step": ms_step, "useful_tflop_per_problem": fl_total / 1e12,
-        "useful_split": {"transform": fl_t / 1e12, "contraction": fl_c / 1e12},
-        "roofline": roof, "kernels": kernels, "gpu_launches": int(launches), "clocks": clk, "steps": steps,
-        "tile_widths": tile_widths,
-        "e2e": e2e,
-        "device_checks": {"status": int(st), "orthonormality": stats[0], "realness": stats[1],
-                          "hermiticity_L": stats[2], "time_reversal_L": stats[3]},
-        "embedding_fock": fock,
-        "dmet_bath": bath,
-        "result": [o.cpu().numpy() for o in outs],
-    }
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        copy_b = sum(k["bytes"] for k in (dm.dmet_emb_profile_read(eplan, i)
+                                          for i in range(dm.dmet_emb_profile_count()))
+                     if k["name"] == "host_copy") / args.e2e_steps
+        st, _ = dm.dmet_emb_status(eplan, 0)
+    finally:
+        dm.dmet_emb_destroy(eplan)
+    d2h_b = int(sum(o.numel() * 8 for o in Oh))
+    sub = [Oh[b].numpy()[pos] for b, pos in enumerate(positions)]
+    return {"value": world * fl_total / e2e_s / 1e12, "unit": "TFLOP/s",
+            "h2d_bytes_per_step": int(copy_b) - d2h_b, "d2h_bytes_per_step": d2h_b,
+            "host_L_bytes": int(Lh.numel() * 16), "ms_per_step": e2e_s * 1e3, "steps": args.e2e_steps,
+            "qblock_cap": args.e2e_qblock, "status": int(st)}, sub
+
+
+def oracle_check(torch, spec, Cs, S, p_block, baseline_s=12.0):
+    """The FP64 oracle's (ij|kl) on the orbital subsets S, per spin block (the real part, in the order of
+    block_positions), with every aux function's L streamed to the oracle from the device generator
+    P-block by P-block; plus the oracle's own rate on the first blocks (about baseline_s seconds) as
+    the CPU baseline."""
+    import oracle
+    from synth import gpu as sgpu
+    Csub = [np.ascontiguousarray(C[:, :, s]) for C, s in zip(Cs, S)]
+    n_list = [len(s) for s in S]
+    acc = None
+    t_oracle, p_timed, t_base, p_base = 0.0, 0, None, 0
+    gen_check = None
+    t_all = time.perf_counter()
+    for p0 in range(0, spec.n_aux, p_block):
+        p1 = min(spec.n_aux, p0 + p_block)
+        blk = sgpu.L_blocks_device(torch, spec, p0, p1).cpu().numpy()
+        torch.cuda.empty_cache()
+        if gen_check is None:
+            # the device generator against the host one on this block's first aux function
+            h = synth.fourier_L(synth.real_space_B(spec, p0, p0 + 1), spec.mesh)
+            gen_check = float(np.abs(blk[:, :, :1] - h).max() / np.abs(h).max())
+        t0 = time.perf_counter()
+        part = oracle.embedded_eri_pblocks([blk], Csub, spec.mesh)
+        t_oracle += time.perf_counter() - t0
+        p_timed += p1 - p0
+        if t_base is None and t_oracle >= baseline_s:
+            t_base, p_base = t_oracle, p_timed
+        if acc is None:
+            acc = part
+        else:
+            for k in acc:
+                acc[k] += part[k]
+        del blk
+    if t_base is None:
+        t_base, p_base = t_oracle, p_timed
+    refs = [acc[k].real.ravel() for k in block_spins(spec)]
+    imag = max(float(np.abs(acc[k].imag).max() / np.abs(acc[k].real).max()) for k in block_spins(spec))
+    fl_base = useful_flops(spec, n_list, n_aux=p_base)[0]
+    base = {"value": fl_base / t_base / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"Algorithm 1 (all q, all k1, dense contraction; L streamed over aux functions) on {n_list[0]} "
+                      f"of {spec.n_emb} embedding orbitals per spin and the first {p_base} of {spec.n_aux} aux "
+                      f"functions ({t_base:.1f} s); useful flops of that sub-problem"}
+    return refs, base, {"oracle_s": t_oracle, "wall_s": time.perf_counter() - t_all,
+                        "device_vs_host_generator_max_rel": gen_check, "oracle_max_imag_over_max": imag}
 
 
 def run_batch(args):
@@ -510,17 +654,21 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hbn_6x6x1")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "fp64"],
                     help="path of the headline number; the other path is measured alongside unless --only")
     ap.add_argument("--only", action="store_true", help="measure the headline path only")
-    ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--l-layout", default="auto", choices=["auto", "full", "reduced"],
+                    help="auto: reduced when the full L would exceed 32 GB")
+    ap.add_argument("--fp64-steps", type=int, default=-1,
+                    help="timed steps of the FP64 path (-1: 3, or 0 when one FP64 call would exceed a minute)")
+    ap.add_argument("--e2e-steps", type=int, default=-1, help="timed end-to-end steps (-1: 3, or 2 above 100 GB)")
     ap.add_argument("--e2e-qblock", type=int, default=1,
                     help="q-block cap (DMET_QBLOCK) of the end-to-end plan; 0 = the plan's own choice")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true",
-                    help="skip the end-to-end measurement (it pins a host copy of L: for the largest workloads)")
+    ap.add_argument("--check-orbitals", type=int, default=48,
+                    help="orbitals per spin of the seeded subset on which the oracle checks every result")
+    ap.add_argument("--no-check", action="store_true", help="skip the oracle check and the CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -533,6 +681,7 @@ def main():
     import torch
     import paper_1909_08596_gb300 as dm
     from paper_1909_08596_gb300 import build as libbuild
+    from synth import gpu as sgpu
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -545,21 +694,85 @@ def main():
     base = synth.CONFIGS[args.workload]
     # Weak scaling: every rank transforms its own problem (a different seed); no data exchange.
     spec = rank_spec(base, rank)
-    L, Cs, _ = synth.make_problem(spec)
-    Ld = torch.from_numpy(L).cuda()
+    n_list = [spec.n_emb] * spec.n_spin
+    fl_total = useful_flops(spec, n_list)[0]
+    full_L_bytes = spec.nk ** 2 * spec.n_aux * spec.n_ao ** 2 * 16
+    reduced = args.l_layout == "reduced" or (args.l_layout == "auto" and full_L_bytes > (32 << 30))
+    layout = dm.binding.DMET_L_REDUCED if reduced else dm.binding.DMET_L_FULL
+    big = full_L_bytes > (32 << 30)
+
+    # Inputs: C on the host (QR over the supercell), L drawn on the device by the seeded generator.
+    _, Cs, _ = synth.make_problem(spec, with_L=False)
     Cd = [torch.from_numpy(c).cuda() for c in Cs]
+    desc_kw = dict(n_spin=spec.n_spin, l_layout=layout)
+    probe = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, n_list, **desc_kw)
+    pairs = dm.dmet_emb_l_pairs(probe) if reduced else np.arange(spec.nk * spec.nk)
+    t0 = time.perf_counter()
+    holder = {"Ld": sgpu.make_L_pairs_device(torch, spec, pairs)}
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    gen_s = time.perf_counter() - t0
+    L_bytes = holder["Ld"].numel() * 16
+
+    S = subset_orbitals(spec, args.check_orbitals)
+    positions = block_positions(spec, S)
+    nblk = len(positions)
 
     precs = [args.prec] + ([] if args.only else [p for p in ("bf16x3", "fp64") if p != args.prec])
-    res = {p: measure(dm, torch, spec, L, Cs, Ld, Cd, p, args, dist, world, local) for p in precs}
+    res, subs = {}, {}
+    for prec in precs:
+        pcode = dm.binding.DMET_PREC_FP64 if prec == "fp64" else dm.binding.DMET_PREC_BF16X3
+        desc = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, n_list, prec=pcode, **desc_kw)
+        if prec == "fp64":
+            steps = args.fp64_steps if args.fp64_steps >= 0 else (0 if big else 3)
+            if steps == 0:
+                res[prec] = {"skipped": "one FP64 call on this workload takes minutes (the FP64 pipe runs at "
+                                        "1/64 of the FP32 rate); measured on the smaller workloads"}
+                continue
+        else:
+            steps = args.steps
+        outs = [torch.empty(dm.dmet_emb_eri_bytes(desc, b) // 8, dtype=torch.float64, device="cuda")
+                for b in range(nblk)]
+        free, _ = torch.cuda.mem_get_info()
+        ws_limit = max(1 << 30, free - (4 << 30))
+        r = measure(dm, torch, spec, desc, holder["Ld"], Cd, outs, steps, args, dist, world, local, ws_limit,
+                    autotune=(prec != "fp64" and not args.no_autotune and not big))
+        subs[prec] = gather_subsets(torch, outs, positions)
+        if prec == args.prec and spec.n_spin == 1:
+            r["embedding_fock"], r["dmet_bath"] = measure_fock_and_bath(dm, torch, spec, Cd, outs[0])
+        res[prec] = r
+        del outs
+        torch.cuda.empty_cache()
     head = res[args.prec]
+
+    e2e = None
+    if not args.no_e2e:
+        need = L_bytes + sum(dm.dmet_emb_eri_bytes(probe, b) for b in range(nblk))
+        avail = host_available_bytes()
+        if avail and need * 1.25 > avail:
+            e2e = {"skipped": f"host memory: {need / 1e9:.0f} GB of pinned buffers wanted, {avail / 1e9:.0f} GB "
+                              f"available"}
+        else:
+            args.e2e_steps = args.e2e_steps if args.e2e_steps > 0 else (2 if L_bytes > 100e9 else 3)
+            pcode = dm.binding.DMET_PREC_FP64 if args.prec == "fp64" else dm.binding.DMET_PREC_BF16X3
+            desc = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, n_list, prec=pcode, **desc_kw)
+            # the device L is released once its host copy exists; the plan's staging buffers then take
+            # its place (L and the output blocks), so the workspace gets what is free now less the outputs
+            free, _ = torch.cuda.mem_get_info()
+            out_b = sum(dm.dmet_emb_eri_bytes(desc, b) for b in range(nblk))
+            e2e, e2e_sub = measure_e2e(dm, torch, desc, holder, Cs, positions, fl_total, world, args,
+                                       ws_limit=max(1 << 30, free - out_b - (8 << 30)))
+            e2e["matches_device_result"] = bool(all(np.array_equal(a, b) for a, b in zip(e2e_sub, subs[args.prec])))
+    holder["Ld"] = None
+    torch.cuda.empty_cache()
 
     line = {
         "metric": METRIC, "value": head["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": head["steps"],
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "bf16x3", "data": "synthetic",
-        "config": {"workload": spec.name, "mesh": list(spec.mesh), "n_ao": spec.n_ao, "n_aux": spec.n_aux,
-                   "n_emb": spec.n_emb, "n_spin": spec.n_spin, "prec": args.prec, "pack": "s8",
-                   "problems_per_step": world, "l2": f"inputs larger than L2 (L = {L.nbytes / 1e9:.2f} GB)"},
+        "config": {**workload_config(spec, args.prec, "reduced" if reduced else "full"),
+                   "problems_per_step": world,
+                   "l2": f"inputs larger than L2 (L = {L_bytes / 1e9:.2f} GB)"},
         "ms_per_problem": head["ms_per_step"],
         "useful_tflop_per_problem": head["useful_tflop_per_problem"],
         "useful_split": head["useful_split"],
@@ -567,36 +780,34 @@ def main():
         "kernels": head["kernels"],
         "gpu_launches": head["gpu_launches"],
         "clocks": head["clocks"],
-        "e2e": head["e2e"],
+        "e2e": e2e,
         "device_checks": head["device_checks"],
         "tile_widths": head.get("tile_widths"),
-        "embedding_fock": head.get("embedding_fock"),
-        "dmet_bath": head.get("dmet_bath"),
+        "input_generation_s": gen_s,
     }
+    if "embedding_fock" in head:
+        line["embedding_fock"], line["dmet_bath"] = head["embedding_fock"], head["dmet_bath"]
     for p in precs[1:]:
         r = res[p]
-        line[p] = {k: r[k] for k in ("value", "ms_per_step", "roofline", "kernels", "gpu_launches", "clocks", "e2e")}
+        if "skipped" in r:
+            line[p] = r
+            continue
+        line[p] = {k: r[k] for k in ("value", "ms_per_step", "roofline", "kernels", "gpu_launches", "clocks")}
         line[p]["dtype"] = "f64" if p == "fp64" else "bf16x3"
-    if "fp64" in res and "bf16x3" in res:
+    if "value" in res.get("fp64", {}) and "value" in res.get("bf16x3", {}):
         line["speedup_bf16x3_over_fp64"] = res["fp64"]["ms_per_step"] / res["bf16x3"]["ms_per_step"]
 
-    if rank == 0 and not args.no_cpu_baseline:
-        # CPU baseline: the oracle as it stands on a bounded sample (orbital subset) of this
-        # workload, which also gives the error of each GPU result on that subset.
-        dt, fl_s, S, eri_s = oracle_sample(spec, L, Cs[0], 32)
-        pos = s8_positions(S)
-        ref = eri_s.real.ravel()
-        line["cpu_baseline"] = {"value": fl_s / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
-                                "sample": f"Algorithm 1 (all q, all k1, dense contraction) on 32 of {spec.n_emb} "
-                                          f"embedding orbitals; {dt:.1f} s; useful flops of that sub-problem"}
-        errs = {}
-        for p, r in res.items():
-            g = r["result"][0][pos]
-            errs[p] = {"rel_fro": float(np.linalg.norm(g - ref) / np.linalg.norm(ref)),
-                       "max_abs": float(np.abs(g - ref).max()),
-                       "max_abs_over_max": float(np.abs(g - ref).max() / np.abs(ref).max()),
-                       "rms": float(np.sqrt(np.mean((g - ref) ** 2)))}
-        line["error_vs_fp64_oracle"] = {"sample": "all (ij|kl) on a seeded 32-orbital subset", **errs}
+    if rank == 0 and not args.no_check:
+        # The oracle on the seeded orbital subsets (every aux function, streamed): the error of each GPU
+        # result per spin block, and the oracle's own rate on the first blocks as the CPU baseline.
+        pb = max(1, min(spec.n_aux, (6 << 30) // (spec.nk ** 2 * spec.n_ao ** 2 * 16)))
+        refs, base, info = oracle_check(torch, spec, Cs, S, pb)
+        names = {(0, 0): "aa" if spec.n_spin == 2 else "s8", (0, 1): "ab", (1, 1): "bb"}
+        errs_all = {p: {names[k]: error_stats(subs[p][b], refs[b]) for b, k in enumerate(block_spins(spec))}
+                    for p in subs}
+        line["cpu_baseline"] = base
+        line["error_vs_fp64_oracle"] = {"sample": f"all (ij|kl) of every spin block on seeded {len(S[0])}-orbital "
+                                                  f"subsets per spin", **errs_all, "oracle": info}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -116,11 +116,13 @@ typedef struct {
                            (one extra pass over L; ~3 ms on a 3 GB L); needs l_layout = FULL */
   int32_t l_layout;     /* dmet_l_layout_t: how the caller stores L */
   int32_t q_begin;      /* shard of the contraction (dmet_emb_eri): only the momentum transfers q */
-  int32_t q_end;        /* with q_begin <= rep(q) < q_end contribute, rep(q) = min(q, -q) for
-                           sym = REAL (q and -q stay together), rep(q) = q for sym = NONE.
-                           q_begin = q_end = 0 selects every q. The ERIs of disjoint shards that
-                           cover [0, Nk) add up to the full ERI (Algorithm 1's sum over k_L is
-                           a plain sum). */
+  int32_t q_end;        /* with q_begin <= min(q, -q) < q_end contribute (q and -q stay together:
+                           their imaginary parts cancel in the sum). q_begin = q_end = 0 selects
+                           every q. The ERIs of disjoint shards that cover [0, Nk) add up to the
+                           full ERI (Algorithm 1's sum over k_L is a plain sum), so a problem can
+                           be split over GPUs with one FP64 sum of the packed blocks. A partial
+                           shard needs sym = REAL and 8-fold packing (else DMET_ERR_UNSUPPORTED).
+                           dmet_emb_transform_3idx ignores the shard. */
   double ortho_tol;     /* <= 0 selects 1e-10 */
   double sym_tol;       /* relative; <= 0 selects 1e-10 */
 } dmet_emb_desc_t;
@@ -293,6 +295,17 @@ DMET_API dmet_status_t dmet_emb_autotune(dmet_emb_plan_t plan, const void* const
 /* The tile widths in use for `problem`: bn[0] (half transform 1), bn[1] (half transform 2). */
 DMET_API dmet_status_t dmet_emb_tile_widths(dmet_emb_plan_t plan, int32_t problem, int32_t* bn);
 
+/* Bounded waits. Every spin-wait of the tensor-core kernels (on an mbarrier: a stage loaded, a stage
+ * or accumulator free, an accumulator ready) gives up after wait_ns nanoseconds of the GPU's global
+ * timer (0 restores the default, 4 s); the kernel then records which kind of wait expired in the
+ * plan's device error word, lets its copies in flight land, frees its tensor memory and returns, so
+ * the context stays usable, and the next dmet_emb_status returns DMET_ERR_TIMEOUT (once; the word
+ * is then cleared). test_withhold_loads != 0 is a test hook with no counterpart in the paper: the
+ * producer thread of every later tensor-core launch of this plan issues no copies, so the waits for
+ * loaded stages and ready accumulators expire with no copy and no MMA in flight (the results are
+ * then meaningless). A captured graph is discarded. */
+DMET_API dmet_status_t dmet_emb_wait_limit(dmet_emb_plan_t plan, uint64_t wait_ns, int32_t test_withhold_loads);
+
 /* Per-kernel timing with CUDA events on the plan's stream. enable != 0 starts recording
  * (and clears the counters); 0 stops. */
 DMET_API dmet_status_t dmet_emb_profile(dmet_emb_plan_t plan, int32_t enable);
@@ -326,11 +339,15 @@ DMET_API int64_t dmet_emb_launch_count(dmet_emb_plan_t plan);
  * which every GPU that loads the library holds until the process exits. The caller passes
  * device pointers (L, C[s], eri_out[b]) laid out as for dmet_emb_eri, and `stream`, a
  * cudaStream_t (NULL = legacy default stream).
- * Supported: prec = FP64, sym = REAL, 8-fold packing (AUTO or S8), Nk <= 64; a problem whose
- * scratch would exceed the array is rejected with DMET_ERR_OOM and a message giving both
- * sizes, before any work is queued. Host pointers are rejected (staging would allocate).
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current) and caches it; make that first call before any stream capture.
+ * Supported: prec = FP64, sym = REAL, 8-fold packing (AUTO or S8), the full L layout, no
+ * shard, Nk <= 64 (each mesh dimension <= 64); descriptor fields outside dmet_emb_plan's bounds
+ * are rejected before any size is computed, and a problem whose scratch would exceed the array
+ * is rejected with DMET_ERR_OOM and a message giving both sizes, before any work is queued.
+ * Host pointers are rejected (staging would allocate). Every call looks up the array's address
+ * on the current device (cudaGetSymbolAddress, which allocates nothing: in host code the array's
+ * name is only a host-side stand-in); the first call on a device loads the library's device code
+ * there, so make it before any stream capture. The host-side tables live in one static
+ * structure that a mutex guards for the whole call.
  * Calls share the array and leave their contents in it; the call clears what must start at
  * zero (its check maxima and the output blocks) itself. Two calls whose work overlaps on the
  * GPU (other streams, other host threads on the same device) race on the array: serialise

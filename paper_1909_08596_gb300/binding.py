@@ -140,6 +140,8 @@ def lib() -> ctypes.CDLL:
         L.dmet_emb_autotune.restype = st
         L.dmet_emb_tile_widths.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.dmet_emb_tile_widths.restype = st
+        L.dmet_emb_wait_limit.argtypes = [_P, ctypes.c_uint64, ctypes.c_int32]
+        L.dmet_emb_wait_limit.restype = st
         L.dmet_emb_launch_count.argtypes = [_P]
         L.dmet_emb_launch_count.restype = ctypes.c_int64
         L.dmet_emb_eri_noalloc.argtypes = [ctypes.POINTER(dmet_emb_desc_t), _P, ctypes.POINTER(_P),
@@ -327,6 +329,10 @@ def dmet_emb_problem_ms(plan, problem):
     ms = ctypes.c_double()
     _check(lib().dmet_emb_problem_ms(_P(plan), problem, ctypes.byref(ms)))
     return ms.value
+
+
+def dmet_emb_wait_limit(plan, wait_ns, test_withhold_loads=False):
+    _check(lib().dmet_emb_wait_limit(_P(plan), int(wait_ns), 1 if test_withhold_loads else 0))
 
 
 def dmet_emb_launch_count(plan):

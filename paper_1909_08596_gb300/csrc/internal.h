@@ -122,6 +122,7 @@ namespace dmet {
 namespace tc {
 struct TcJob;
 struct Segment;
+struct TcCtl;
 }
 int mixed_kblock();
 cudaError_t launch_split_L(const double2* L, const int4* t1, int e0, int E, int nk, int naux, int nao, int K1,
@@ -133,15 +134,15 @@ cudaError_t launch_build_Cc(const double2* C, const int4* gather, const int4* t2
 cudaError_t launch_pack_split(const void* ZT, int nq, int naux, int n, int nc, void* Xt, long long sstride,
                               long long Rtot, long long row_base, cudaStream_t s);
 cudaError_t launch_tc_pairs(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                            const tc::Segment* segs, void* out, long long ldo, unsigned int* err, cudaStream_t s);
+                            const tc::Segment* segs, void* out, long long ldo, const tc::TcCtl& ctl, cudaStream_t s);
 cudaError_t launch_tc_split_t(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                               const tc::Segment* segs, void* out, long long K2, int nao, int nemb,
-                              unsigned int* err, cudaStream_t s);
+                              const tc::TcCtl& ctl, cudaStream_t s);
 cudaError_t launch_tc_rect(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                           const tc::Segment* segs, double* out, long long ldo, double scale, unsigned int* err,
+                           const tc::Segment* segs, double* out, long long ldo, double scale, const tc::TcCtl& ctl,
                            cudaStream_t s);
 cudaError_t launch_tc_packed(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                             const tc::Segment* segs, double* out, double scale, void* part, unsigned int* err,
+                             const tc::Segment* segs, double* out, double scale, void* part, const tc::TcCtl& ctl,
                              cudaStream_t s);
 // Sums the K parts of the split tiles of a packed contraction (the parts' jobs: jobs[0 .. ntiles * f)).
 cudaError_t launch_combine_parts(const tc::TcJob* jobs, int ntiles, int f, const void* part, double* out, double scale,

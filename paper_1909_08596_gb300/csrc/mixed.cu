@@ -251,7 +251,7 @@ struct EpiPairs {
 
 template <int BN, class EPI>
 cudaError_t launch_tc_bn(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                         const tc::Segment* segs, const typename EPI::Params& ep, unsigned int* err, cudaStream_t s) {
+                         const tc::Segment* segs, const typename EPI::Params& ep, const tc::TcCtl& ctl, cudaStream_t s) {
   using Cfg = tc::TcCfg<3, 64, BN, EPI::kStaged>;
   static bool attr = false;
   if (!attr) {
@@ -275,17 +275,17 @@ cudaError_t launch_tc_bn(const CUtensorMap& A, const CUtensorMap& B, const tc::T
     if (e != cudaSuccess) return e;
   }
   const int grid = njobs < nsm ? njobs : nsm;
-  tc::tc_gemm_kernel<3, 64, BN, EPI><<<grid, tc::kThreads, Cfg::SMEM, s>>>(A, B, jobs, njobs, segs, ep, err);
+  tc::tc_gemm_kernel<3, 64, BN, EPI><<<grid, tc::kThreads, Cfg::SMEM, s>>>(A, B, jobs, njobs, segs, ep, ctl);
   return cudaGetLastError();
 }
 
 template <class EPI>
 cudaError_t launch_tc(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                      const tc::Segment* segs, const typename EPI::Params& ep, unsigned int* err, cudaStream_t s) {
+                      const tc::Segment* segs, const typename EPI::Params& ep, const tc::TcCtl& ctl, cudaStream_t s) {
   switch (bn) {
-    case 128: return launch_tc_bn<128, EPI>(A, B, jobs, njobs, segs, ep, err, s);
-    case 112: return launch_tc_bn<112, EPI>(A, B, jobs, njobs, segs, ep, err, s);
-    case 96: return launch_tc_bn<96, EPI>(A, B, jobs, njobs, segs, ep, err, s);
+    case 128: return launch_tc_bn<128, EPI>(A, B, jobs, njobs, segs, ep, ctl, s);
+    case 112: return launch_tc_bn<112, EPI>(A, B, jobs, njobs, segs, ep, ctl, s);
+    case 96: return launch_tc_bn<96, EPI>(A, B, jobs, njobs, segs, ep, ctl, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -368,31 +368,31 @@ cudaError_t launch_pack_split(const void* ZT, int nq, int naux, int n, int nc, v
 
 cudaError_t launch_tc_split_t(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                               const tc::Segment* segs, void* out, long long K2, int nao, int nemb,
-                              unsigned int* err, cudaStream_t s) {
+                              const tc::TcCtl& ctl, cudaStream_t s) {
   EpiSplitT::Params p{(__nv_bfloat16*)out, K2, nao, nemb};
-  return launch_tc<EpiSplitT>(bn, A, B, jobs, njobs, segs, p, err, s);
+  return launch_tc<EpiSplitT>(bn, A, B, jobs, njobs, segs, p, ctl, s);
 }
 
 cudaError_t launch_tc_rect(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                           const tc::Segment* segs, double* out, long long ldo, double scale, unsigned int* err,
+                           const tc::Segment* segs, double* out, long long ldo, double scale, const tc::TcCtl& ctl,
                            cudaStream_t s) {
   const float sh = (float)scale;
   tc::EpiRect::Params p{out, ldo, sh, (float)(scale - (double)sh)};
-  return launch_tc<tc::EpiRect>(128, A, B, jobs, njobs, segs, p, err, s);
+  return launch_tc<tc::EpiRect>(128, A, B, jobs, njobs, segs, p, ctl, s);
 }
 
 cudaError_t launch_tc_pairs(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                            const tc::Segment* segs, void* out, long long ldo, unsigned int* err, cudaStream_t s) {
+                            const tc::Segment* segs, void* out, long long ldo, const tc::TcCtl& ctl, cudaStream_t s) {
   EpiPairs::Params p{(float2*)out, ldo};
-  return launch_tc<EpiPairs>(bn, A, B, jobs, njobs, segs, p, err, s);
+  return launch_tc<EpiPairs>(bn, A, B, jobs, njobs, segs, p, ctl, s);
 }
 
 cudaError_t launch_tc_packed(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                             const tc::Segment* segs, double* out, double scale, void* part, unsigned int* err,
+                             const tc::Segment* segs, double* out, double scale, void* part, const tc::TcCtl& ctl,
                              cudaStream_t s) {
   const float sh = (float)scale;
   tc::EpiPacked::Params p{out, sh, (float)(scale - (double)sh), (unsigned long long*)part};
-  return launch_tc<tc::EpiPacked>(128, A, B, jobs, njobs, segs, p, err, s);
+  return launch_tc<tc::EpiPacked>(128, A, B, jobs, njobs, segs, p, ctl, s);
 }
 
 }  // namespace dmet

@@ -3,7 +3,7 @@
 // half transforms per q, pair packing and the 8-fold packed contraction), but every scratch
 // buffer is carved out of one file-scope __device__ array, so the call allocates nothing:
 // no cudaMalloc, no cudaFree, no allocating library routine, and no host heap either (its
-// schedule tables are built in fixed-size thread-local host arrays).
+// schedule tables are built in one fixed-size static host structure).
 //
 // Who needs this: a caller whose device memory is entirely owned by another allocator
 // (for example a framework's caching pool that must see every byte), or one that must not
@@ -13,16 +13,20 @@
 //
 // The array (DMET_EMB_NOALLOC_SCRATCH_BYTES) is part of the library's device image: every
 // GPU on which the library's kernels are loaded holds it until the process exits. Its
-// device address is looked up with cudaGetSymbolAddress the first time the entry point runs
-// on a device (with that device current) and cached; that first call should therefore be
-// made before any stream capture. All calls share the array and leave their contents in
-// it, so two calls whose work overlaps on the GPU (different streams, or different host
-// threads on one device) race on it: serialise them.
+// device address is looked up with cudaGetSymbolAddress on every call, with the caller's
+// device current (no cached address can outlive a context that was torn down and created
+// again); the first call on a device loads the library's device code there, so make it
+// before any stream capture. All calls share the array and leave their contents in it, so
+// two calls whose work overlaps on the GPU (different streams, or different host threads on
+// one device) race on it: serialise them. The host side keeps its schedule tables in one
+// static structure guarded by a mutex for the whole call, so calls from several host
+// threads take turns there.
 
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <climits>
+#include <cstdint>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -37,10 +41,8 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_scratch[DMET_EMB_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
 constexpr int kMaxNk = 64;  // the schedule tables below are sized for this mesh bound
-void* g_scratch_addr[kMaxDevices] = {};
-std::mutex g_scratch_mutex;
+std::mutex g_mutex;         // guards g_tab for a whole call
 
 dmet_status_t nfail(dmet_status_t st, const char* fmt, ...) {
   va_list ap;
@@ -68,7 +70,7 @@ struct NoAllocTables {
   int4 gather[kMaxNk * kMaxNk];
   int4 t2[kMaxNk];
 };
-thread_local NoAllocTables t_tab;
+NoAllocTables g_tab;
 
 int kmod(int a, int n) { return ((a % n) + n) % n; }
 
@@ -120,6 +122,14 @@ void build_noalloc_tables(const dmet_emb_desc_t& d, NoAllocTables& t) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Scratch layout arithmetic that reports overflow instead of wrapping: off = align256(off + a * b).
+bool grow(size_t& off, size_t a, size_t b) {
+  size_t p = 0, q = 0;
+  if (__builtin_mul_overflow(a, b, &p) || __builtin_add_overflow(off, p, &q) || q > (SIZE_MAX - 255)) return false;
+  off = align256(q);
+  return true;
+}
+
 ZgemmArgs zdefault() {
   ZgemmArgs z;
   std::memset(&z, 0, sizeof(z));
@@ -148,11 +158,14 @@ extern "C" DMET_API dmet_status_t dmet_emb_eri_noalloc(const dmet_emb_desc_t* de
   const dmet_emb_desc_t& d = *desc;
   // The same descriptor rules as dmet_emb_plan, narrowed to what this variant runs.
   for (int i = 0; i < 3; ++i)
-    if (d.mesh[i] < 1) return nfail(DMET_ERR_INVALID_ARG, "mesh[%d] = %d", i, d.mesh[i]);
+    if (d.mesh[i] < 1 || d.mesh[i] > kMaxNk) return nfail(DMET_ERR_INVALID_ARG, "mesh[%d] = %d", i, d.mesh[i]);
   const long long nk = (long long)d.mesh[0] * d.mesh[1] * d.mesh[2];
   if (nk > kMaxNk) return nfail(DMET_ERR_UNSUPPORTED, "Nk = %lld exceeds the no-allocation limit %d", nk, kMaxNk);
-  if (d.n_ao < 1 || d.n_aux < 1 || (d.n_spin != 1 && d.n_spin != 2))
-    return nfail(DMET_ERR_INVALID_ARG, "invalid descriptor");
+  if (d.n_ao < 1 || d.n_ao > 4096 || d.n_aux < 1 || d.n_aux > 65536 || (d.n_spin != 1 && d.n_spin != 2))
+    return nfail(DMET_ERR_INVALID_ARG, "invalid descriptor (n_ao %d, n_aux %d, n_spin %d)", d.n_ao, d.n_aux, d.n_spin);
+  if (d.check_l != 0 && d.check_l != 1) return nfail(DMET_ERR_INVALID_ARG, "check_l = %d", d.check_l);
+  for (int s = 0; s < d.n_spin; ++s)
+    if (d.n_emb[s] > 2047) return nfail(DMET_ERR_UNSUPPORTED, "n_emb[%d] = %d > 2047", s, d.n_emb[s]);
   if (d.l_layout != DMET_L_FULL || d.q_begin != 0 || d.q_end != 0)
     return nfail(DMET_ERR_UNSUPPORTED, "the no-allocation variant takes the full L layout and no shard");
   for (int s = 0; s < d.n_spin; ++s)
@@ -160,8 +173,15 @@ extern "C" DMET_API dmet_status_t dmet_emb_eri_noalloc(const dmet_emb_desc_t* de
   if (d.prec != DMET_PREC_FP64 || d.sym != DMET_SYM_REAL ||
       (d.eri_pack != DMET_PACK_AUTO && d.eri_pack != DMET_PACK_S8) || (d.ck_norm != 0 && d.ck_norm != 1))
     return nfail(DMET_ERR_UNSUPPORTED, "the no-allocation variant runs FP64, sym = REAL, 8-fold packing only");
+  {
+    // the per-launch 32-bit sizes of the kernels (as in dmet_emb_plan)
+    const long long nm = std::max(d.n_emb[0], d.n_spin == 2 ? d.n_emb[1] : 0);
+    if ((long long)d.n_aux * nm > INT_MAX / 2 || (long long)d.n_aux * d.n_ao > INT_MAX / 2)
+      return nfail(DMET_ERR_UNSUPPORTED, "n_aux*n too large for one launch");
+  }
   const int nblk = d.n_spin == 1 ? 1 : 3;
-  NoAllocTables& tb = t_tab;
+  std::lock_guard<std::mutex> lock(g_mutex);
+  NoAllocTables& tb = g_tab;
   build_noalloc_tables(d, tb);
   const int nao = d.n_ao, naux = d.n_aux, nspin = d.n_spin;
   const int n[2] = {d.n_emb[0], nspin == 2 ? d.n_emb[1] : 0};
@@ -176,31 +196,35 @@ extern "C" DMET_API dmet_status_t dmet_emb_eri_noalloc(const dmet_emb_desc_t* de
       break;
     }
 
-  // Scratch layout (256-byte aligned pieces), one q at a time.
+  // Scratch layout (256-byte aligned pieces), one q at a time. Every size is a product of bounded
+  // descriptor fields; grow() still checks each step for overflow.
   size_t off = 0;
+  bool fits = true;
   const size_t o_stats = off;
-  off = align256(off + 8 * sizeof(double));
+  fits = fits && grow(off, 8, sizeof(double));
   const size_t o_neg = off;
-  off = align256(off + nk * sizeof(int));
+  fits = fits && grow(off, (size_t)nk, sizeof(int));
   const size_t o_t1 = off;
-  off = align256(off + (size_t)tb.start[tb.nq] * sizeof(int4));
+  fits = fits && grow(off, (size_t)tb.start[tb.nq], sizeof(int4));
   const size_t o_gather = off;
-  off = align256(off + (size_t)tb.start[tb.nq] * sizeof(int4));
+  fits = fits && grow(off, (size_t)tb.start[tb.nq], sizeof(int4));
   const size_t o_t2 = off;
-  off = align256(off + (size_t)tb.nq * sizeof(int4));
+  fits = fits && grow(off, (size_t)tb.nq, sizeof(int4));
   const size_t o_S = off;
-  off = align256(off + (size_t)ng * nmax * nmax * 16);
+  fits = fits && grow(off, (size_t)ng * nmax, (size_t)nmax * 16);
   const size_t o_crep = off;
-  off = align256(off + (size_t)emax * nao * nmax * 16);
+  fits = fits && grow(off, (size_t)emax * nao, (size_t)nmax * 16);
   const size_t o_T = off;
-  off = align256(off + (size_t)emax * nao * naux * nmax * 16);
+  fits = fits && grow(off, (size_t)emax * nao * naux, (size_t)nmax * 16);
   const size_t o_Z = off;
-  off = align256(off + (size_t)naux * nmax * nmax * 16);
+  fits = fits && grow(off, (size_t)naux * nmax, (size_t)nmax * 16);
   size_t o_X[2];
   for (int s = 0; s < 2; ++s) {
     o_X[s] = off;
-    off = align256(off + (s < nspin ? (size_t)naux * 2 * npair[s] * 8 : 0));
+    fits = fits && grow(off, s < nspin ? (size_t)naux * 2 : 0, (size_t)npair[s] * 8);
   }
+  if (!fits) return nfail(DMET_ERR_OOM, "problem's scratch size overflows; the static scratch holds %zu bytes",
+                          (size_t)DMET_EMB_NOALLOC_SCRATCH_BYTES);
   if (off > (size_t)DMET_EMB_NOALLOC_SCRATCH_BYTES)
     return nfail(DMET_ERR_OOM, "problem needs %zu bytes of scratch; the static scratch holds %zu", off,
                  (size_t)DMET_EMB_NOALLOC_SCRATCH_BYTES);
@@ -216,18 +240,13 @@ extern "C" DMET_API dmet_status_t dmet_emb_eri_noalloc(const dmet_emb_desc_t* de
   }
 
 
-  int dev = 0;
-  NCK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return nfail(DMET_ERR_UNSUPPORTED, "device ordinal %d", dev);
+  // The array's address on the current device (host code cannot use the symbol itself: in host
+  // code it names a host-side stand-in). Looked up on every call; it allocates nothing.
   unsigned char* base = nullptr;
   {
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
-      void* p = nullptr;
-      NCK(cudaGetSymbolAddress(&p, g_scratch));
-      g_scratch_addr[dev] = p;
-    }
-    base = (unsigned char*)g_scratch_addr[dev];
+    void* p = nullptr;
+    NCK(cudaGetSymbolAddress(&p, g_scratch));
+    base = (unsigned char*)p;
   }
   cudaStream_t st = (cudaStream_t)stream;
   double* stats = (double*)(base + o_stats);

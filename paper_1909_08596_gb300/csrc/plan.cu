@@ -303,6 +303,10 @@ struct dmet_emb_plan_s {
   KStat ks[KC_COUNT];
   std::vector<cudaEvent_t> pool;
   long long launches = 0;
+  // bounded waits of the tensor-core kernels
+  unsigned long long wait_ns = tc::kWaitLimitNs;
+  int withhold_loads = 0;
+  tc::TcCtl ctl() const { return tc::TcCtl{derr, wait_ns, withhold_loads}; }
 };
 
 
@@ -636,12 +640,12 @@ dmet_status_t run_half_transform(dmet_emb_plan_s* P, Prob& pr, const Tables& tb,
 }
 
 dmet_status_t transform_range(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, int q_begin,
-                              int q_end, double2* const* out) {
+                              int q_end, double2* const* out, int bq) {
   const bool real = pr.d.sym == DMET_SYM_REAL;
   // q-blocks of at most bq consecutive q with the same conjugation flag
   for (int qa = q_begin; qa < q_end;) {
     int qb = qa + 1;
-    while (qb < q_end && qb - qa < pr.bq && pr.nat_conj[qb] == pr.nat_conj[qa]) ++qb;
+    while (qb < q_end && qb - qa < bq && pr.nat_conj[qb] == pr.nat_conj[qa]) ++qb;
     for (int s = 0; s < pr.nspin; ++s) {
       const long long slot = (long long)pr.naux * pr.n[s] * pr.n[s];
       double2* dest = out[s] + (long long)(qa - q_begin) * slot;
@@ -698,7 +702,7 @@ dmet_status_t eri_s8(dmet_emb_plan_s* P, Prob& pr, const double2* L, const doubl
 
 dmet_status_t eri_full(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, void* const* out) {
   double2* lq[2] = {P->W->lq_all[0], P->W->lq_all[1]};
-  TRY(transform_range(P, pr, L, C, 0, pr.nk, lq));
+  TRY(transform_range(P, pr, L, C, 0, pr.nk, lq, pr.bq));
   for (int blk = 0; blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
     const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
     const long long na2 = (long long)pr.n[sa] * pr.n[sa], nb2 = (long long)pr.n[sb] * pr.n[sb];
@@ -760,12 +764,15 @@ WsSizes ws_for(const Prob& pr, int bq) {
   WsSizes w;
   std::memset(&w, 0, sizeof(w));
   const int nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
+  w.S = (size_t)pr.orth_groups * nmax * nmax * 16;
+  // The split-BF16 path needs only the orthonormality product here; dmet_emb_transform_3idx (FP64)
+  // grows its transform buffers on first use (mixed_transform_ws).
+  if (pr.mixed) return w;
   int E = max_entries(pr.nat, bq);
   if (pr.pack == DMET_PACK_S8) E = std::max(E, max_entries(pr.con, bq));
   w.crep = (size_t)E * pr.nao * nmax * 16;
   w.T = (size_t)E * pr.nao * pr.naux * nmax * 16;
   w.Z = pr.d.sym == DMET_SYM_REAL ? (size_t)bq * pr.naux * nmax * nmax * 16 : 0;
-  w.S = (size_t)pr.orth_groups * nmax * nmax * 16;
   for (int s = 0; s < pr.nspin; ++s) {
     if (pr.pack == DMET_PACK_S8) w.X[s] = (size_t)bq * pr.naux * 2 * pr.npair[s] * 8;
     else w.lq_all[s] = (size_t)pr.nk * pr.naux * pr.n[s] * pr.n[s] * 16;
@@ -1121,7 +1128,7 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
         Timed t(P, KC_TC_TRANSFORM_1, 8.0 * n * (double)pr.naux * pr.nao * pr.nao * E, by, 1,
                 exec_flops(m, m.j1_off[s][bi], m.j1_cnt[s][bi], m.bn1));
         CK(launch_tc_split_t(m.bn1, mm.Ls, mm.Cb[s], m.d_jobs + m.j1_off[s][bi], m.j1_cnt[s][bi], m.d_segs, P->W->A2,
-                             m.K2, pr.nao, n, P->derr, P->cs));
+                             m.K2, pr.nao, n, P->ctl(), P->cs));
       }
       {
         double fl = 0, by = 0;
@@ -1133,7 +1140,7 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
         }
         Timed t(P, KC_TC_TRANSFORM_2, fl, by, 1, exec_flops(m, m.j2_off[s][bi], m.j2_cnt[s][bi], m.bn2));
         CK(launch_tc_pairs(m.bn2, mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs, P->W->ZT, 2LL * n,
-                           P->derr, P->cs));
+                           P->ctl(), P->cs));
       }
       {
         const int nc = bl.w == 1 ? 1 : 2;
@@ -1158,10 +1165,10 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
     Timed t(P, KC_TC_CONTRACT, fl, by, nsplit ? 2 : 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk], tc::kTile));
     if (blk == 1) {
       CK(launch_tc_rect(mm.Xt[0], mm.Xt[1], m.d_jobs + m.jc_off[1], m.jc_cnt[1], m.d_segs, (double*)out[1],
-                        pr.npair[1], oscale, P->derr, P->cs));
+                        pr.npair[1], oscale, P->ctl(), P->cs));
     } else {
       CK(launch_tc_packed(mm.Xt[sa], mm.Xt[sa], m.d_jobs + m.jc_off[blk], m.jc_cnt[blk], m.d_segs, (double*)out[blk],
-                          oscale, P->W->ZT, P->derr, P->cs));
+                          oscale, P->W->ZT, P->ctl(), P->cs));
       if (nsplit)
         CK(launch_combine_parts(m.d_jobs + m.jc_off[blk] + m.jc_cnt[blk] - nsplit * f, nsplit, f, P->W->ZT,
                                 (double*)out[blk], oscale, P->cs));
@@ -1719,7 +1726,17 @@ dmet_status_t dmet_emb_transform_3idx(dmet_emb_plan_t P, int32_t problem, const 
         cur += ob[s];
       }
   }
-  TRY(transform_range(P, pr, Ld, Cd, q_begin, q_end, out));
+  int bq = pr.bq;
+  if (pr.mixed) {
+    // FP64 transform buffers of a split-BF16 plan, grown on first use, one q at a time
+    bq = 1;
+    const int nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
+    const size_t E = (size_t)max_entries(pr.nat, 1);
+    TRY(ensure((void**)&P->W->crep, &P->W->crep_b, E * pr.nao * nmax * 16));
+    TRY(ensure((void**)&P->W->T, &P->W->T_b, E * pr.nao * pr.naux * nmax * 16));
+    TRY(ensure((void**)&P->W->Z, &P->W->Z_b, (size_t)pr.naux * nmax * nmax * 16));
+  }
+  TRY(transform_range(P, pr, Ld, Cd, q_begin, q_end, out, bq));
   if (need) {
     for (int s = 0; s < pr.nspin; ++s)
       if (ohost[s]) {
@@ -2137,7 +2154,12 @@ dmet_status_t dmet_emb_status(dmet_emb_plan_t P, int32_t problem, double* stats)
   }
   unsigned int werr = 0;
   if (P->derr) CK(cudaMemcpy(&werr, P->derr, sizeof(werr), cudaMemcpyDeviceToHost));
-  if (werr) return fail(DMET_ERR_TIMEOUT, "a bounded device wait expired (flags 0x%x)", werr);
+  if (werr) {
+    // reported once: the word is cleared for the plan's later calls
+    CK(cudaMemset(P->derr, 0, sizeof(unsigned int)));
+    return fail(DMET_ERR_TIMEOUT, "a bounded device wait expired (flags 0x%x: 1 stage free, 2 accumulator free, "
+                "4 stage loaded, 8 accumulator ready, 16 MMAs done, 32 copies landed)", werr);
+  }
   if (!(h[0] <= pr.d.ortho_tol))
     return fail(DMET_ERR_NOT_ORTHONORMAL, "problem %d: orthonormality error %.3e > %.3e", problem, h[0], pr.d.ortho_tol);
   if (real && !(rc <= pr.d.sym_tol))
@@ -2145,6 +2167,21 @@ dmet_status_t dmet_emb_status(dmet_emb_plan_t P, int32_t problem, double* stats)
   if (lchk && !(herm <= pr.d.sym_tol && tr <= pr.d.sym_tol))
     return fail(DMET_ERR_SYMMETRY, "problem %d: L symmetry violated (hermiticity %.3e, time reversal %.3e)", problem,
                 herm, tr);
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_wait_limit(dmet_emb_plan_t P, uint64_t wait_ns, int32_t test_withhold_loads) {
+  clear_error();
+  if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
+  P->wait_ns = wait_ns ? (unsigned long long)wait_ns : tc::kWaitLimitNs;
+  P->withhold_loads = test_withhold_loads != 0;
+  if (P->gexec) {
+    // a captured graph holds the old launch parameters
+    CK(cudaStreamSynchronize(P->stream));
+    CK(cudaGraphExecDestroy(P->gexec));
+    P->gexec = nullptr;
+    P->gkey.clear();
+  }
   return DMET_OK;
 }
 

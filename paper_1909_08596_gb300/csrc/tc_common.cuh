@@ -8,8 +8,9 @@
 namespace dmet {
 namespace tc {
 
-// Every spin-wait gives up after this many nanoseconds of %globaltimer, records where it
-// gave up in the kernel's error word and lets the kernel wind down.
+// Every spin-wait gives up after a limit in nanoseconds of %globaltimer (a kernel parameter;
+// this is its default), records where it gave up in the kernel's error word and lets the
+// kernel wind down.
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -64,15 +65,16 @@ __device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Waits for the phase with the given parity to complete. Returns false (and sets bit `code`
-// of *err) if the wait exceeded kWaitLimitNs. The first check is the non-blocking test: on a
+// of *err) if the wait exceeded limit_ns. The first check is the non-blocking test: on a
 // phase that has already completed it returns sooner than try_wait, which matters to the MMA
 // thread (the tensor pipe holds about one MMA, so its waits are pipe bubbles).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned int* err, unsigned int code) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned int* err, unsigned int code,
+                                          unsigned long long limit_ns) {
   if (mbar_test_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer() - t0 > kWaitLimitNs) {
+    if (globaltimer() - t0 > limit_ns) {
       if (err) atomicOr(err, code);
       return false;
     }

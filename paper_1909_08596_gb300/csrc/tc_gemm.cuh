@@ -68,6 +68,14 @@ struct TcJob {
   int o0, o1, o2, o3;  // output-functor parameters (tile origin in the output's own indexing)
 };
 
+// Run-time controls of one launch.
+struct TcCtl {
+  unsigned int* err;           // error word: one bit per kind of bounded wait that expired
+  unsigned long long wait_ns;  // limit of every bounded wait
+  int withhold_loads;          // test hook: the producer issues no copies, so the MMA thread's and
+                               // the epilogue's waits expire with no copy or MMA in flight
+};
+
 constexpr int kTile = 128;
 constexpr int kEpiGroups = 2;                    // epilogue warpgroups
 constexpr int kEpiWarps = 4 * kEpiGroups;
@@ -170,7 +178,7 @@ template <int NSLICE, int ROWB, int BN, class EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcJob* __restrict__ jobs, int njobs, const Segment* __restrict__ segs,
-                   const typename EPI::Params ep, unsigned int* err) {
+                   const typename EPI::Params ep, const TcCtl ctl) {
   using Cfg = TcCfg<NSLICE, ROWB, BN, EPI::kStaged>;
   constexpr int S = Cfg::STAGES;
   constexpr int H = Cfg::PART;
@@ -185,6 +193,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned long long* staging = (unsigned long long*)(smem + S * Cfg::STAGE_BYTES + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned int* const err = ctl.err;
+  const unsigned long long lim = ctl.wait_ns;
 
   auto full = [&](int s) { return smem_u32(bars + s); };
   auto empty = [&](int s) { return smem_u32(bars + S + s); };
@@ -225,14 +235,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---------------- TMA producer ----------------
       prefetch_tmap(&tmA);
       prefetch_tmap(&tmB);
-      bool ok = true;
+      bool ok = !ctl.withhold_loads;
       for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x) {
       const TcJob job = jobs[jb];
       for (int g = 0; g < job.nseg && ok; ++g) {
         const Segment sg = segs[job.seg0 + g];
         for (int kb = 0; kb < sg.nkb; ++kb) {
           const int s = issued % S, ph = (issued / S) & 1;
-          if (!mbar_wait(empty(s), ph ^ 1, err, 1u)) {
+          if (!mbar_wait(empty(s), ph ^ 1, err, 1u, lim)) {
             ok = false;
             break;
           }
@@ -265,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // The buffer of segment gs - 2 is free once the epilogue has read it; the epilogue
         // reads a run's correction sum before it releases the run's last segment, so this
         // also frees the correction buffer of run `run - 1` (every run has >= 1 segment).
-        if (!mbar_wait(acce(b), (u & 1) ^ 1, err, 2u)) break;
+        if (!mbar_wait(acce(b), (u & 1) ^ 1, err, 2u, lim)) break;
         tc_fence_after();
         const Segment sg = segs[job.seg0 + g];
         const bool first = g == 0 || (sg.flags & kRunFirst);
@@ -275,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nkb = sg.nkb;
         for (int kb = 0; kb < nkb; ++kb) {
           const int s = it % S, ph = (it / S) & 1;
-          if (!mbar_wait(full(s), ph, err, 4u)) {
+          if (!mbar_wait(full(s), ph, err, 4u, lim)) {
             ok = false;
             break;
           }
@@ -300,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // Every MMA issued above must be complete before the accumulators are released.
       umma_commit(done_bar);
-      mbar_wait(done_bar, 0, err, 16u);
+      mbar_wait(done_bar, 0, err, 16u, lim);
     }
   } else {
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kEpiRegs));
@@ -314,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const TcJob job = jobs[jb];
       for (int g = 0; g < job.nseg; ++g, ++gs) {
         const int b = gs & 1, u = gs >> 1;
-        if (!mbar_wait(accf(b), u & 1, err, 8u)) {
+        if (!mbar_wait(accf(b), u & 1, err, 8u, lim)) {
           ok = false;
           break;
         }
@@ -375,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 0 && lane == 0) {
     // Copies issued but never consumed (only after an expired wait) must land before exit.
-    for (int i = *consumed; i < issued; ++i) mbar_wait(full(i % S), (i / S) & 1, err, 32u);
+    for (int i = *consumed; i < issued; ++i) mbar_wait(full(i % S), (i / S) & 1, err, 32u, lim);
   }
   __syncthreads();
   if (warp == 1) {

@@ -162,3 +162,24 @@ def test_plan_without_gpu_reports_cuda_error():
     with pytest.raises(B.DmetError) as e:
         dm.dmet_emb_plan(dm.make_desc((2, 2, 1), 8, 40, 16))
     assert e.value.status == B.DMET_ERR_CUDA
+
+
+@pytest.mark.parametrize("fields", [
+    dict(n_ao=1 << 20, n_aux=1 << 20, n_emb=(1 << 26, 0)),   # products that would wrap a 64-bit size
+    dict(n_ao=4096, n_aux=65536, n_emb=(2047, 0)),          # within the bounds, far beyond the scratch
+    dict(mesh=(65, 1, 1)),
+    dict(check_l=2),
+    dict(l_layout=1),
+    dict(q_range=(0, 1)),
+])
+def test_noalloc_rejects_descriptors_before_touching_the_gpu(fields):
+    """No CUDA call happens for these: the bounds and the scratch size are checked first."""
+    kw = dict(mesh=(2, 2, 1), n_ao=8, n_aux=40, n_emb=16)
+    kw.update({k: v for k, v in fields.items() if k != "n_emb"})
+    d = dm.make_desc(**kw)
+    if "n_emb" in fields:
+        d.n_emb[:] = list(fields["n_emb"])
+    buf = np.zeros(4)
+    with pytest.raises(B.DmetError) as e:
+        B.dmet_emb_eri_noalloc(d, buf, [buf], [buf])
+    assert e.value.status in (B.DMET_ERR_INVALID_ARG, B.DMET_ERR_UNSUPPORTED, B.DMET_ERR_OOM)

@@ -1,0 +1,50 @@
+"""Host-side pieces of bench.py: its closed-form schedule counts (used to count useful flops without
+the library, so the reference arm never loads it) against the library's schedule, and the packed
+positions it compares with the oracle."""
+import numpy as np
+import pytest
+
+import bench
+import oracle
+import paper_1909_08596_gb300 as dm
+
+
+@pytest.mark.parametrize("mesh", [(1, 1, 1), (2, 1, 1), (3, 1, 1), (2, 2, 1), (3, 3, 1), (2, 2, 2), (4, 4, 4),
+                                  (6, 6, 1), (3, 3, 3), (5, 1, 2)])
+def test_schedule_counts_match_library(mesh):
+    qw, nrep = bench.schedule_counts(mesh)
+    s = dm.dmet_emb_schedule(dm.make_desc(mesh, 2, 3, 1))
+    assert qw == s["q_weight"].tolist()
+    assert nrep == s["n_rep"].tolist()
+
+
+def test_reduced_pair_count_of_nio_shape():
+    # 8 self-conjugate q with 36 orbit representatives each, 28 q < -q with 32 each
+    qw, nrep = bench.schedule_counts((4, 4, 4))
+    assert sum(r for w, r in zip(qw, nrep) if w) == 1184
+    assert len(dm.dmet_emb_l_pairs(dm.make_desc((4, 4, 4), 104, 900, 300, n_spin=2))) == 1184
+
+
+def test_block_positions_match_pair_matrix():
+    import synth
+    spec = synth.spec_with(synth.CONFIGS["tiny_2x2x1"], n_spin=2, n_emb=6)
+    rng = np.random.default_rng(3)
+    ea = rng.standard_normal((6, 6, 6, 6))
+    ea = ea + ea.transpose(1, 0, 2, 3)
+    ea = ea + ea.transpose(0, 1, 3, 2)
+    eb = ea + ea.transpose(2, 3, 0, 1)  # 8-fold symmetric
+    S = [np.array([0, 2, 5]), np.array([1, 4, 5])]
+    pos = bench.block_positions(spec, S)
+    packed = oracle.pack_s8(eb)
+    sub = eb[np.ix_(S[0], S[0], S[0], S[0])].ravel()
+    assert np.array_equal(packed[pos[0]], sub)
+    ab = oracle.pair_matrix(ea).ravel()   # [IJ][KL] over alpha pairs x beta pairs
+    assert np.array_equal(ab[pos[1]], ea[np.ix_(S[0], S[0], S[1], S[1])].ravel())
+
+
+def test_useful_flops_nio_shape():
+    import synth
+    spec = synth.CONFIGS["nio_4x4x4_uhf"]
+    tot, t, c = bench.useful_flops(spec, [300, 300])
+    assert abs(c - 470e12) / 470e12 < 0.01      # aa + bb SYRK and the ab GEMM at K = 57 600
+    assert 150e12 < t < 250e12
