@@ -45,6 +45,11 @@ DEFAULT_WORKLOAD = "nio_4x4x4_uhf"
 SMS = 152
 DFMA_PER_SM_CLK = 2  # FP64 FMA lanes per SM per clock on GB300 (1.25 TFLOP/s nominal at 2.07 GHz)
 REF_SAMPLE_ORBITALS = 24
+# dmet_prec_t codes, and each tensor-core precision's tensor rate relative to dense bf16 (the recipe's
+# nominal figures: fp16 = bf16, tf32 = half of bf16); the measured bf16 peak times that ratio is the peak
+PREC_CODES = {"fp64": 0, "bf16x3": 1, "tf32": 2, "tf32x3": 3, "fp16x2": 4}
+PEAK_RATIO = {"bf16x3": 1.0, "fp16x2": 1.0, "tf32": 0.5, "tf32x3": 0.5}
+PREC_DTYPE = {"fp64": "f64", "bf16x3": "bf16x3", "fp16x2": "fp16x2", "tf32": "tf32", "tf32x3": "tf32x3"}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of a tensor kernel, from an ncu capture of the
 # kernels as they are now: (workload, path, kernel class) -> bytes. Empty until such a capture exists; the
 # roofline's traffic is then null.
@@ -171,6 +176,43 @@ def max_over_ranks(dist, ms, device):
     t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def shard_ranges(mesh, n_ao, n_emb_list, world):
+    """A q shard per rank for splitting one problem over `world` GPUs (strong scaling): contiguous
+    ranges of the contracted q (q and -q stay together, as min(q, -q) is the contracted one) whose
+    costs (the transforms of the q's representative pairs plus its share of the contraction) are as
+    equal as the q granularity allows. Returns [(q_begin, q_end)] covering [0, Nk)."""
+    qw, nrep = schedule_counts(mesh)
+    nk = len(qw)
+    cost = [0.0] * nk
+    for q in range(nk):
+        if qw[q]:
+            cost[q] = sum(nrep[q] * (n_ao * n_ao * n + n_ao * n * n) for n in n_emb_list) + \
+                qw[q] * sum(n * n * n * n for n in n_emb_list) / 8.0
+    total = sum(cost)
+    out, lo, acc = [], 0, 0.0
+    for r in range(world - 1):
+        target = total * (r + 1) / world
+        hi = lo
+        while hi < nk and acc + cost[hi] <= target:
+            acc += cost[hi]
+            hi += 1
+        hi = max(hi, lo + 1) if any(cost[lo:]) else hi
+        out.append((lo, hi))
+        lo = hi
+    out.append((lo, nk))
+    return out
+
+
+def sum_over_ranks(dist, tensors):
+    """The one exchange step of a q-sharded problem: the FP64 sum of every rank's partial packed ERI
+    blocks (Algorithm 1's sum over the aux momentum, split across ranks), in place on every rank."""
+    if not dist:
+        return tensors
+    for t in tensors:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return tensors
 
 
 def job_tflops(world, flops_per_problem, steps, ms_total):
@@ -312,9 +354,10 @@ def roofline(spec, prec, kstats, sustained=False):
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (FP64 runs on the CUDA cores)",
                 "avg_launch_ms": avg_ms}
     # A tensor kernel's roofline is whichever of its two floors is higher: executed tensor flops at
-    # the measured bf16 peak, or its algorithmic bytes at the measured HBM copy rate.
+    # the precision's peak (the measured bf16 peak times the nominal ratio), or its algorithmic bytes
+    # at the measured HBM copy rate.
     key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
-    peak_t, peak_b = peaks[key], peaks["hbm_gbs"]
+    peak_t, peak_b = peaks[key] * PEAK_RATIO[prec], peaks["hbm_gbs"]
     secs = top["ms"] / 1e3 / max(top["launches"], 1)
     fl_l = top["exec_flops"] / max(top["launches"], 1)
     by_l = top["bytes"] / max(top["launches"], 1)
@@ -331,7 +374,7 @@ def roofline(spec, prec, kstats, sustained=False):
             "flops_counted": "executed tensor flops (every slice product issued, whole tiles)",
             "bytes_counted": "algorithmic bytes per launch: operands read once, result written once",
             "useful_achieved_tflops": useful, "useful_frac": useful / peak_t,
-            "peak_source": f"{peak_src} {key} and hbm_gbs", "avg_launch_ms": avg_ms}
+            "peak_source": f"{peak_src} {key} x {PEAK_RATIO[prec]} ({prec}) and hbm_gbs", "avg_launch_ms": avg_ms}
 
 
 def kernel_table(kstats):
@@ -351,8 +394,11 @@ def kernel_table(kstats):
     return kernels
 
 
-def measure(dm, torch, spec, desc, Ld, Cd, outs, steps, args, dist, world, local, ws_limit, autotune):
-    """Times `steps` calls of dmet_emb_eri on resident inputs (CUDA events on the plan's stream)."""
+def measure(dm, torch, spec, desc, Ld, Cd, outs, steps, args, dist, world, local, ws_limit, autotune,
+            qshard=False):
+    """Times `steps` calls of dmet_emb_eri on resident inputs (CUDA events on the plan's stream). With
+    qshard, every rank computes its q shard of one problem and each step ends with the FP64 sum of the
+    partial ERI blocks over the ranks (NCCL), inside the timed region."""
     n_list = [spec.n_emb] * spec.n_spin
     fl_total, fl_t, fl_c = useful_flops(spec, n_list)
     stream = torch.cuda.current_stream()
@@ -366,6 +412,8 @@ def measure(dm, torch, spec, desc, Ld, Cd, outs, steps, args, dist, world, local
 
         def step():
             dm.dmet_emb_eri(plan, [Ld], [Cd], [outs])
+            if qshard:
+                sum_over_ranks(dist, outs)
 
         for _ in range(args.warmup):
             step()
@@ -398,10 +446,9 @@ def measure(dm, torch, spec, desc, Ld, Cd, outs, steps, args, dist, world, local
         dm.dmet_emb_destroy(plan)
     ms_total = max_over_ranks(dist, ms_total, "cuda")
     ms_step = ms_total / steps
-    # a step of a second or more is a long timed region: the sustained peak applies
-    prec = "fp64" if desc.prec == dm.binding.DMET_PREC_FP64 else "bf16x3"
+    prec = {v: k for k, v in PREC_CODES.items()}[desc.prec]
     return {
-        "value": job_tflops(world, fl_total, steps, ms_total), "ms_per_step": ms_step,
+        "value": job_tflops(1 if qshard else world, fl_total, steps, ms_total), "ms_per_step": ms_step,
         "useful_tflop_per_problem": fl_total / 1e12,
         "useful_split": {"transform": fl_t / 1e12, "contraction": fl_c / 1e12},
         "roofline": roofline(spec, prec, kstats), "kernels": kernel_table(kstats), "gpu_launches": int(launches),
@@ -655,8 +702,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "fp64"],
-                    help="path of the headline number; the other path is measured alongside unless --only")
+    ap.add_argument("--prec", default="bf16x3", choices=sorted(PREC_CODES),
+                    help="path of the headline number")
+    ap.add_argument("--precs", default="fp64",
+                    help="comma-separated paths measured alongside the headline (errors included)")
     ap.add_argument("--only", action="store_true", help="measure the headline path only")
     ap.add_argument("--l-layout", default="auto", choices=["auto", "full", "reduced"],
                     help="auto: reduced when the full L would exceed 32 GB")
@@ -670,6 +719,9 @@ def main():
     ap.add_argument("--no-check", action="store_true", help="skip the oracle check and the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--multi", default="weak", choices=["weak", "qshard"],
+                    help="N > 1: weak = one problem per rank (no exchange); qshard = one problem split into q "
+                         "shards over the ranks, with an FP64 sum of the partial ERIs (strong scaling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -692,9 +744,12 @@ def main():
     libbuild.build()
 
     base = synth.CONFIGS[args.workload]
+    qshard = world > 1 and args.multi == "qshard"
     # Weak scaling: every rank transforms its own problem (a different seed); no data exchange.
-    spec = rank_spec(base, rank)
+    # q shards: every rank takes its share of the contracted q of the same problem (strong scaling).
+    spec = base if qshard else rank_spec(base, rank)
     n_list = [spec.n_emb] * spec.n_spin
+    q_range = shard_ranges(spec.mesh, spec.n_ao, n_list, world)[rank] if qshard else None
     fl_total = useful_flops(spec, n_list)[0]
     full_L_bytes = spec.nk ** 2 * spec.n_aux * spec.n_ao ** 2 * 16
     reduced = args.l_layout == "reduced" or (args.l_layout == "auto" and full_L_bytes > (32 << 30))
@@ -704,9 +759,12 @@ def main():
     # Inputs: C on the host (QR over the supercell), L drawn on the device by the seeded generator.
     _, Cs, _ = synth.make_problem(spec, with_L=False)
     Cd = [torch.from_numpy(c).cuda() for c in Cs]
-    desc_kw = dict(n_spin=spec.n_spin, l_layout=layout)
+    desc_kw = dict(n_spin=spec.n_spin, l_layout=layout, q_range=q_range)
     probe = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, n_list, **desc_kw)
-    pairs = dm.dmet_emb_l_pairs(probe) if reduced else np.arange(spec.nk * spec.nk)
+    if reduced:
+        pairs = dm.dmet_emb_l_pairs(probe)   # with a q shard, the shard's blocks only
+    else:
+        pairs = np.arange(spec.nk * spec.nk)
     t0 = time.perf_counter()
     holder = {"Ld": sgpu.make_L_pairs_device(torch, spec, pairs)}
     torch.cuda.synchronize()
@@ -718,10 +776,14 @@ def main():
     positions = block_positions(spec, S)
     nblk = len(positions)
 
-    precs = [args.prec] + ([] if args.only else [p for p in ("bf16x3", "fp64") if p != args.prec])
+    extra = [] if args.only else [p for p in args.precs.split(",") if p and p != args.prec]
+    for p in extra:
+        if p not in PREC_CODES:
+            raise SystemExit(f"unknown precision {p}")
+    precs = [args.prec] + extra
     res, subs = {}, {}
     for prec in precs:
-        pcode = dm.binding.DMET_PREC_FP64 if prec == "fp64" else dm.binding.DMET_PREC_BF16X3
+        pcode = PREC_CODES[prec]
         desc = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, n_list, prec=pcode, **desc_kw)
         if prec == "fp64":
             steps = args.fp64_steps if args.fp64_steps >= 0 else (0 if big else 3)
@@ -736,7 +798,7 @@ def main():
         free, _ = torch.cuda.mem_get_info()
         ws_limit = max(1 << 30, free - (4 << 30))
         r = measure(dm, torch, spec, desc, holder["Ld"], Cd, outs, steps, args, dist, world, local, ws_limit,
-                    autotune=(prec != "fp64" and not args.no_autotune and not big))
+                    autotune=(prec != "fp64" and not args.no_autotune and not big), qshard=qshard)
         subs[prec] = gather_subsets(torch, outs, positions)
         if prec == args.prec and spec.n_spin == 1:
             r["embedding_fock"], r["dmet_bath"] = measure_fock_and_bath(dm, torch, spec, Cd, outs[0])
@@ -746,7 +808,9 @@ def main():
     head = res[args.prec]
 
     e2e = None
-    if not args.no_e2e:
+    if qshard and not args.no_e2e:
+        e2e = {"skipped": "the q-shard mode times resident inputs only"}
+    elif not args.no_e2e:
         need = L_bytes + sum(dm.dmet_emb_eri_bytes(probe, b) for b in range(nblk))
         avail = host_available_bytes()
         if avail and need * 1.25 > avail:
@@ -754,8 +818,7 @@ def main():
                               f"available"}
         else:
             args.e2e_steps = args.e2e_steps if args.e2e_steps > 0 else (2 if L_bytes > 100e9 else 3)
-            pcode = dm.binding.DMET_PREC_FP64 if args.prec == "fp64" else dm.binding.DMET_PREC_BF16X3
-            desc = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, n_list, prec=pcode, **desc_kw)
+            desc = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, n_list, prec=PREC_CODES[args.prec], **desc_kw)
             # the device L is released once its host copy exists; the plan's staging buffers then take
             # its place (L and the output blocks), so the workspace gets what is free now less the outputs
             free, _ = torch.cuda.mem_get_info()
@@ -768,10 +831,13 @@ def main():
 
     line = {
         "metric": METRIC, "value": head["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": head["steps"],
-        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "bf16x3", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "strong" if qshard else "weak",
+        "vs_baseline": None, "dtype": PREC_DTYPE[args.prec], "data": "synthetic",
         "config": {**workload_config(spec, args.prec, "reduced" if reduced else "full"),
-                   "problems_per_step": world,
+                   "problems_per_step": 1 if qshard else world,
+                   "parallelism": f"q shards over {world} GPUs, FP64 sum of the partial ERIs" if qshard else
+                   (f"one problem per GPU ({world})" if world > 1 else "1 GPU"),
                    "l2": f"inputs larger than L2 (L = {L_bytes / 1e9:.2f} GB)"},
         "ms_per_problem": head["ms_per_step"],
         "useful_tflop_per_problem": head["useful_tflop_per_problem"],
@@ -793,9 +859,10 @@ def main():
             line[p] = r
             continue
         line[p] = {k: r[k] for k in ("value", "ms_per_step", "roofline", "kernels", "gpu_launches", "clocks")}
-        line[p]["dtype"] = "f64" if p == "fp64" else "bf16x3"
-    if "value" in res.get("fp64", {}) and "value" in res.get("bf16x3", {}):
-        line["speedup_bf16x3_over_fp64"] = res["fp64"]["ms_per_step"] / res["bf16x3"]["ms_per_step"]
+        line[p]["dtype"] = PREC_DTYPE[p]
+    if "value" in res.get("fp64", {}):
+        line["speedup_over_fp64"] = {p: res["fp64"]["ms_per_step"] / res[p]["ms_per_step"]
+                                     for p in res if p != "fp64" and "value" in res[p]}
 
     if rank == 0 and not args.no_check:
         # The oracle on the seeded orbital subsets (every aux function, streamed): the error of each GPU

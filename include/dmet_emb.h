@@ -67,10 +67,19 @@ typedef enum {
   DMET_ERR_SYMMETRY = 8         /* device check: inputs violate the declared symmetry */
 } dmet_status_t;
 
+/* Arithmetic of the transforms and the contraction. The tensor-core precisions split every FP64
+ * operand into slices the tensor cores (tcgen05) multiply exactly, accumulate in FP32 within short
+ * K segments and across segments in an exact two-float sum, and write FP64 results; they need
+ * sym = REAL and 8-fold packing. Errors against FP64 (relative Frobenius, measured): see the
+ * library's documentation; BF16X3 and FP16X2 meet 1e-6, TF32 does not. */
 typedef enum {
   DMET_PREC_FP64 = 0,    /* every product and sum in IEEE FP64 */
-  DMET_PREC_BF16X3 = 1   /* split-BF16 products on tcgen05, FP32 accumulation per q block,
-                            FP64 cross-q accumulation */
+  DMET_PREC_BF16X3 = 1,  /* three bf16 slices per operand, six slice products per multiply-add */
+  DMET_PREC_TF32 = 2,    /* one TF32 slice, one product (about 2^-11 relative per product) */
+  DMET_PREC_TF32X3 = 3,  /* two TF32 slices, three products (about 2^-22), half the 16-bit rate */
+  DMET_PREC_FP16X2 = 4   /* two fp16 slices of each operand times an exact power-of-two scale
+                            computed on the device from the inputs' largest components, three
+                            products (about 2^-22): half the products of BF16X3 */
 } dmet_prec_t;
 
 typedef enum {

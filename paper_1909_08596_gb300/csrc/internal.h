@@ -106,44 +106,61 @@ cudaError_t launch_l_check(const double2* L, const int* neg, int nk, int naux, i
 // ---- tensor maps for the tcgen05 kernels (tc_launch.cu) ----
 #include <cuda.h>
 namespace dmet {
-// 3-D bf16 tensor map over [slices][rows][K] (K contiguous) with a (box_k, box_rows, 1) box,
-// swizzled to match the UMMA descriptors (box_k * 2 bytes = 64 or 128).
-cudaError_t make_tmap_bf16_3d(CUtensorMap* map, const void* base, unsigned long long k_elems,
-                              unsigned long long rows, unsigned long long slices, unsigned long long row_stride_elems,
-                              unsigned long long slice_stride_elems, int box_k, int box_rows);
-// 4-D bf16 tensor map over a slice-interleaved operand [rows][K / 32][3 slices][32] with a
-// (32, 1, 1, box_rows) box: one slice of one 32-wide K block, swizzled as the 3-D maps (64 bytes).
-cudaError_t make_tmap_bf16_interleaved(CUtensorMap* map, const void* base, unsigned long long k_elems,
-                                       unsigned long long rows, int box_rows);
+// Tensor maps over the operand slices of precision `prec` (dmet_prec_t; element type bf16, fp16 or
+// fp32 for TF32), swizzled to match the UMMA descriptors (64-byte rows):
+// 3-D over [slices][rows][K] (K contiguous) with a (64 bytes of K, box_rows, 1) box;
+cudaError_t make_tmap_3d(CUtensorMap* map, int prec, const void* base, unsigned long long k_elems,
+                         unsigned long long rows, unsigned long long slices, unsigned long long row_stride_elems,
+                         unsigned long long slice_stride_elems, int box_rows);
+// 4-D over a slice-interleaved operand [rows][K / BK][slices][BK] (BK = 64 bytes of elements) with a
+// (BK, 1, 1, box_rows) box: one slice of one K block.
+cudaError_t make_tmap_interleaved(CUtensorMap* map, int prec, const void* base, unsigned long long k_elems,
+                                  unsigned long long rows, int slices, int box_rows);
 }  // namespace dmet
 
-// ---- split-BF16 path (mixed.cu) ----
+// ---- mixed-precision paths (mixed.cu) ----
 namespace dmet {
 namespace tc {
 struct TcJob;
 struct Segment;
 struct TcCtl;
 }
-int mixed_kblock();
-cudaError_t launch_split_L(const double2* L, const int4* t1, int e0, int E, int nk, int naux, int nao, int K1,
-                           void* Ls, long long sstride, cudaStream_t s);
-cudaError_t launch_build_Cb(const double2* C, int nk, int nao, int n, int K1, void* Cb, long long sstride,
-                            cudaStream_t s);
-cudaError_t launch_build_Cc(const double2* C, const int4* gather, const int4* t2, int b0, int nq, int nao, int n,
-                            int K2, void* Cc, long long sstride, cudaStream_t s);
-cudaError_t launch_pack_split(const void* ZT, int nq, int naux, int n, int nc, void* Xt, long long sstride,
-                              long long Rtot, long long row_base, cudaStream_t s);
-cudaError_t launch_tc_pairs(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                            const tc::Segment* segs, void* out, long long ldo, const tc::TcCtl& ctl, cudaStream_t s);
-cudaError_t launch_tc_split_t(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                              const tc::Segment* segs, void* out, long long K2, int nao, int nemb,
-                              const tc::TcCtl& ctl, cudaStream_t s);
-cudaError_t launch_tc_rect(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+// Operand scales of the FP16 precision (powers of two; all 1 for the other precisions), computed on
+// the device from the maxima mx (float bits) of |L| and |C_s|: Ls = L sL, Cb = Cc = C sC[s],
+// A2 = T sT[s] = (step-1 result) f1[s], Z = (step-2 result) f2[s], Xt = (Z + Z^T) sX[s], and block b of
+// the contraction = (its result) fc[b].
+struct MixScales {
+  float sL, sC[2], sT[2], f1[2], f2[2], sX[2], fc[3];
+  unsigned int mx[3];
+};
+int mixed_kblock();             // K padding unit of every operand (elements)
+bool prec_scaled(int prec);
+int prec_slices(int prec);
+int prec_products(int prec);
+int prec_elem_bytes(int prec);
+cudaError_t launch_mix_scales(int prec, const double2* L, const int4* t1, int E, long long per_block,
+                              const double2* const* C, const long long* c_elems, int nspin, int nao, int nrep_max,
+                              MixScales* sc, cudaStream_t s);
+cudaError_t launch_split_L(int prec, const double2* L, const int4* t1, int e0, int E, int naux, int nao, int K1,
+                           void* Ls, long long sstride, const MixScales* sc, cudaStream_t s);
+cudaError_t launch_build_Cb(int prec, const double2* C, int nk, int nao, int n, int K1, void* Cb, long long sstride,
+                            const float* sc, cudaStream_t s);
+cudaError_t launch_build_Cc(int prec, const double2* C, const int4* gather, const int4* t2, int b0, int nq, int nao,
+                            int n, int K2, void* Cc, long long sstride, const float* sc, cudaStream_t s);
+cudaError_t launch_pack_split(int prec, const void* ZT, int nq, int naux, int n, int nc, void* Xt, long long sstride,
+                              long long Rtot, long long row_base, const float* sx, cudaStream_t s);
+cudaError_t launch_tc_pairs(int prec, int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs,
+                            int njobs, const tc::Segment* segs, void* out, long long ldo, const tc::TcCtl& ctl,
+                            const float* fac, cudaStream_t s);
+cudaError_t launch_tc_split_t(int prec, int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs,
+                              int njobs, const tc::Segment* segs, void* out, long long K2, int nao, int nemb,
+                              const tc::TcCtl& ctl, const float* fac, cudaStream_t s);
+cudaError_t launch_tc_rect(int prec, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                            const tc::Segment* segs, double* out, long long ldo, double scale, const tc::TcCtl& ctl,
-                           cudaStream_t s);
-cudaError_t launch_tc_packed(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+                           const float* fac, cudaStream_t s);
+cudaError_t launch_tc_packed(int prec, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                              const tc::Segment* segs, double* out, double scale, void* part, const tc::TcCtl& ctl,
-                             cudaStream_t s);
+                             const float* fac, cudaStream_t s);
 // Sums the K parts of the split tiles of a packed contraction (the parts' jobs: jobs[0 .. ntiles * f)).
 cudaError_t launch_combine_parts(const tc::TcJob* jobs, int ntiles, int f, const void* part, double* out, double scale,
                                  cudaStream_t s);

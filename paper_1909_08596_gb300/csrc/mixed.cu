@@ -1,22 +1,31 @@
-// Split-BF16 (mixed-precision) path of the embedded-ERI transformation: the operand
-// splitting kernels and the tcgen05 GEMM instantiations with their output functors.
+// Mixed-precision paths of the embedded-ERI transformation: the operand splitting kernels, the
+// operand scales of the FP16 precision and the tcgen05 GEMM instantiations with their output
+// functors, for every operand precision of prec.cuh (BF16x3, FP16x2, TF32, TF32x3).
 //
-// Every FP64 operand x is split into three bf16 slices x = x0 + x1 + x2 + O(2^-26 |x|),
-// each slice the round-to-nearest bf16 of what the previous ones left over (the error-free
-// splitting of Ozaki et al., applied per element, computed from a two-float form of x so
-// that no FP64 arithmetic is needed; see split.cuh). Complex products are written as real
-// GEMMs over interleaved (re, im) K indices; the orbital operands carry the signs.
+// Every FP64 operand x is split into slices x = x_0 + x_1 (+ x_2) of the precision's element type,
+// each slice the round-to-nearest of what the previous ones left over (the error-free splitting of
+// Ozaki et al., applied per element, computed from a two-float form of x so that no FP64
+// arithmetic is needed; see split.cuh and prec.cuh). Complex products are written as real GEMMs
+// over interleaved (re, im) K indices; the orbital operands carry the signs.
 //
 // Step 1 (ket side):  T_e[(P,mu)][(j,p)] = sum_(nu,c) L_e[(P,mu)][(nu,c)] Cb^{k2}[(j,p)][(nu,c)]
 //   with Cb rows (j, re) = (Cr, -Ci), (j, im) = (Ci, Cr) over (nu, c), so T = L C^{k2}.
 // Step 2 (bra side + Fourier sum): Z_q[(P,j)][(i,p)] = sum_(r,mu,c) T[(P,j)][(r,mu,c)] Cc[(i,p)][(r,mu,c)]
 //   with Cc rows (i, re) = w_r (Cr, Ci), (i, im) = w_r (-Ci, Cr), so Z = sum_r w_r C^{k1_r +} T_r.
 // Contraction: X[(q,P,c)][IJ] = Re/Im of s (Z_ij + Z_ji); (ij|kl) = (1/Nk) sum w_q X^T X.
+//
+// Scales (FP16x2 only; 1 otherwise): L and C are scaled by powers of two sL, sC that put their
+// largest components at or below 2^14; T and X by sT, sX derived from rigorous bounds on their
+// magnitudes (a sum of K products is at most K times the largest product); each GEMM's results are
+// multiplied back by the exact power of two its operands' scales leave.
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "../../include/dmet_emb.h"
 #include "internal.h"
+#include "prec.cuh"
 #include "split.cuh"
 #include "tc_gemm.cuh"
 
@@ -24,25 +33,46 @@ namespace dmet {
 
 namespace {
 
+using tc::PrecBF16x3;
+using tc::PrecFP16x2;
+using tc::PrecTF32;
+using tc::PrecTF32x3;
+
 inline int grid_for(long long total, int threads, int cap) {
   long long g = (total + threads - 1) / threads;
   if (g < 1) g = 1;
   return (int)(g < cap ? g : cap);
 }
 
-// Ls[t][(e - e0) * naux * nao + P * nao + mu][col] for col < K1: L^{k1,k2}_{P, mu, nu}.(re|im)
+template <class T>
+struct __align__(2 * sizeof(T)) Pair2 {
+  T a, b;
+};
+
+// x * s as a two-float (hi, lo): the two-float form of the double x, scaled exactly.
+__device__ __forceinline__ float2 scaled_ff(double x, float s) {
+  const float2 p = d2ff(x);
+  return make_float2(p.x * s, p.y * s);
+}
+
+// Ls[t][(e - e0) * naux * nao + P * nao + mu][col] for col < K1: L^{k1,k2}_{P, mu, nu}.(re|im) * sL
 // at col = 2 nu + c, zero for col >= 2 nao. One thread per (row, nu): it reads the complex
-// element (16 bytes; a warp reads a row's run of nu) and writes one bf16 (re, im) pair per
-// slice. blockIdx.y is the entry; all index arithmetic within an entry is 32-bit.
+// element (16 bytes; a warp reads a row's run of nu) and writes one (re, im) pair per slice.
+// blockIdx.y is the entry; all index arithmetic within an entry is 32-bit.
+template <class PREC>
 __global__ void __launch_bounds__(256) split_L_kernel(const double2* __restrict__ L, const int4* __restrict__ t1,
                                                       int e0, int naux, int nao, int K1,
-                                                      __nv_bfloat162* __restrict__ Ls, long long sstride2) {
+                                                      typename PREC::T* __restrict__ Ls, long long sstride,
+                                                      const MixScales* __restrict__ sc) {
+  using T = typename PREC::T;
+  const float s = PREC::kScaled ? sc->sL : 1.f;
   const int el = blockIdx.y;
   const int rows_e = naux * nao, half = K1 >> 1;
   const int total = rows_e * half;
-  const long long pair = t1[e0 + el].y;  // k1 * nk + k2
+  const long long pair = t1[e0 + el].y;  // block of L
   const double2* src = L + pair * rows_e * nao;
-  __nv_bfloat162* dst = Ls + (long long)el * total;
+  Pair2<T>* dst = reinterpret_cast<Pair2<T>*>(Ls) + (long long)el * total;
+  const long long ss = sstride / 2;
   // Four elements per trip, all loads issued before the first conversion (memory-level parallelism).
   const int stride = gridDim.x * blockDim.x;
   for (int x0 = blockIdx.x * blockDim.x + threadIdx.x; x0 < total; x0 += 4 * stride) {
@@ -58,20 +88,22 @@ __global__ void __launch_bounds__(256) split_L_kernel(const double2* __restrict_
     for (int u = 0; u < 4; ++u) {
       const int x = x0 + u * stride;
       if (x >= total) break;
-      const float2 re = d2ff(v[u].x), im = d2ff(v[u].y);
-      __nv_bfloat162 a, b, c;
-      split3f2(re.x, re.y, im.x, im.y, a, b, c);
-      dst[x] = a;
-      dst[x + sstride2] = b;
-      dst[x + 2 * sstride2] = c;
+      const float2 re = scaled_ff(v[u].x, s), im = scaled_ff(v[u].y, s);
+      T a[3], b[3];
+      PREC::split(re.x, re.y, a);
+      PREC::split(im.x, im.y, b);
+#pragma unroll
+      for (int t = 0; t < PREC::kSlices; ++t) dst[x + t * ss] = Pair2<T>{a[t], b[t]};
     }
   }
 }
 
 // Cb[t][k * 2n + 2j + p][col], col = 2 nu + c < 2 nao:
-//   p = 0: (Cr, -Ci)[c];  p = 1: (Ci, Cr)[c]   of C^k_{nu j}.
+//   p = 0: (Cr, -Ci)[c];  p = 1: (Ci, Cr)[c]   of C^k_{nu j} (times sC).
+template <class PREC>
 __global__ void build_Cb_kernel(const double2* __restrict__ C, int nk, int nao, int n, int K1,
-                                __nv_bfloat16* __restrict__ Cb, long long sstride) {
+                                typename PREC::T* __restrict__ Cb, long long sstride, const float* __restrict__ psc) {
+  const float sc = PREC::kScaled ? *psc : 1.f;
   const long long total = (long long)nk * 2 * n * K1;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
        x += (long long)gridDim.x * blockDim.x) {
@@ -86,19 +118,21 @@ __global__ void build_Cb_kernel(const double2* __restrict__ C, int nk, int nao, 
       const double2 z = C[((long long)k * nao + nu) * n + j];
       v = p == 0 ? (c == 0 ? z.x : -z.y) : (c == 0 ? z.y : z.x);
     }
-    __nv_bfloat16 a, b, cc;
-    split3d(v, a, b, cc);
-    Cb[x] = a;
-    Cb[x + sstride] = b;
-    Cb[x + 2 * sstride] = cc;
+    const float2 f = scaled_ff(v, sc);
+    typename PREC::T a[3];
+    PREC::split(f.x, f.y, a);
+#pragma unroll
+    for (int t = 0; t < PREC::kSlices; ++t) Cb[x + t * sstride] = a[t];
   }
 }
 
 // Cc[t][slot * 2n + 2i + p][col], col = r * 2nao + 2 mu + c for r < nrep(slot):
-//   p = 0: w_r (Cr, Ci)[c];  p = 1: w_r (-Ci, Cr)[c]  of C^{k1_r}_{mu i}; zero elsewhere.
+//   p = 0: w_r (Cr, Ci)[c];  p = 1: w_r (-Ci, Cr)[c]  of C^{k1_r}_{mu i} (times sC); zero elsewhere.
+template <class PREC>
 __global__ void build_Cc_kernel(const double2* __restrict__ C, const int4* __restrict__ gather,
                                 const int4* __restrict__ t2, int b0, int nq, int nao, int n, int K2,
-                                __nv_bfloat16* __restrict__ Cc, long long sstride) {
+                                typename PREC::T* __restrict__ Cc, long long sstride, const float* __restrict__ psc) {
+  const float sc = PREC::kScaled ? *psc : 1.f;
   const long long total = (long long)nq * 2 * n * K2;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
        x += (long long)gridDim.x * blockDim.x) {
@@ -117,21 +151,24 @@ __global__ void build_Cc_kernel(const double2* __restrict__ C, const int4* __res
       const double2 z = C[((long long)g.x * nao + mu) * n + i];
       v = w * (p == 0 ? (c == 0 ? z.x : z.y) : (c == 0 ? -z.y : z.x));
     }
-    __nv_bfloat16 a, b, cc;
-    split3d(v, a, b, cc);
-    Cc[x] = a;
-    Cc[x + sstride] = b;
-    Cc[x + 2 * sstride] = cc;
+    const float2 f = scaled_ff(v, sc);
+    typename PREC::T a[3];
+    PREC::split(f.x, f.y, a);
+#pragma unroll
+    for (int t = 0; t < PREC::kSlices; ++t) Cc[x + t * sstride] = a[t];
   }
 }
 
-// Xt[t][IJ][row_base + (slot * naux + P) * nc + c] = split of (Z_ij + Z_ji).c for i >= j, where
+// Xt[t][IJ][row_base + (slot * naux + P) * nc + c] = split of sX (Z_ij + Z_ji).c for i >= j, where
 // each real component of Z_ij (complex) is a two-float pair ZT[slot][(P n + j) 2n + 2i + (re|im)].
 // (The factor s of L^q = s (Z + Z^T) is applied, squared, to the contraction's output.)
 constexpr int PK_P = 64, PK_B = 4;
+template <class PREC>
 __global__ void __launch_bounds__(256) pack_split_kernel(const float2* __restrict__ ZT, int naux, int n, int nc,
-                                                         __nv_bfloat16* __restrict__ Xt, long long sstride,
-                                                         long long Rtot, long long row_base) {
+                                                         typename PREC::T* __restrict__ Xt, long long sstride,
+                                                         long long Rtot, long long row_base,
+                                                         const float* __restrict__ psx) {
+  const float sx = PREC::kScaled ? *psx : 1.f;
   // (re.hi, re.lo, im.hi, im.lo) of (pl, ii, jj) at [pl][ii * PK_B + jj]; the odd row pitch puts
   // consecutive pl (the lanes of the write phase) in different banks.
   constexpr int kPitch = PK_B * PK_B + 1;
@@ -186,24 +223,27 @@ __global__ void __launch_bounds__(256) pack_split_kernel(const float2* __restric
     const float sl = ((ah - (sh - bv)) + (bh - bv)) + (al + bl);
     const long long IJ = (long long)i * (i + 1) / 2 + j;
     const long long idx = IJ * Rtot + row_base + ((long long)slot * naux + P) * nc + c;
-    __nv_bfloat16 x0, x1, x2;
-    split3f(sh, sl, x0, x1, x2);
-    Xt[idx] = x0;
-    Xt[idx + sstride] = x1;
-    Xt[idx + 2 * sstride] = x2;
+    typename PREC::T x[3];
+    PREC::split(sh * sx, sl * sx, x);
+#pragma unroll
+    for (int q = 0; q < PREC::kSlices; ++q) Xt[idx + q * sstride] = x[q];
   }
 }
 
-// Step-1 output functor: element (m = (P, mu) of entry e, n = (j, p)) -> bf16 slices of A2 at
+// Step-1 output functor: element (m = (P, mu) of entry e, n = (j, p)) -> slices of A2 at
 // row o2 + P * nemb + j, column k = o3 + 2 mu + p (o2 = slot * naux * nemb, o3 = r * 2 nao).
-// A2 keeps the three slices of a row side by side in each 32-wide K block,
-// A2[row][k / 32][slice][k % 32] (a row is 3 K2 elements), so that the three slice values a lane
-// writes land in one 192-byte span: with the slices in three separate arrays the same bytes went
-// to three streams of 104-byte pieces and the step took a third longer. Step 2 reads the layout
-// through a 4D tensor map (one slice of one K block per box).
+// A2 keeps the slices of a row side by side in each K block of BK elements,
+// A2[row][k / BK][slice][k % BK] (a row is kSlices * K2 elements), so that the slice values a lane
+// writes land in one span: with the slices in separate arrays the same bytes went to separate
+// streams of short pieces and the step took a third longer. Step 2 reads the layout through a 4D
+// tensor map (one slice of one K block per box).
+template <class PREC>
 struct EpiSplitT {
+  using T = typename PREC::T;
+  static constexpr int NS = PREC::kSlices;
+  static constexpr int BK = tc::kblock_elems<PREC>();
   struct Params {
-    __nv_bfloat16* out;
+    T* out;
     long long K2;
     int nao, nemb;
   };
@@ -220,12 +260,12 @@ struct EpiSplitT {
     for (int c = 0; c < H; c += 2) {
       if (col0 + c >= j.n_valid) break;
       const int jj = (j.o1 + col0 + c) >> 1;
-      __nv_bfloat162 x0, x1, x2;  // (re, im) of slices 0, 1, 2
-      split3f2(hi[c], lo[c], hi[c + 1], lo[c + 1], x0, x1, x2);
-      __nv_bfloat16* o = p.out + (rbase + jj) * 3 * p.K2 + (cidx >> 5) * 96 + (cidx & 31);
-      *reinterpret_cast<__nv_bfloat162*>(o) = x0;
-      *reinterpret_cast<__nv_bfloat162*>(o + 32) = x1;
-      *reinterpret_cast<__nv_bfloat162*>(o + 64) = x2;
+      T a[3], b[3];  // (re, im) of each slice
+      PREC::split(hi[c], lo[c], a);
+      PREC::split(hi[c + 1], lo[c + 1], b);
+      T* o = p.out + (rbase + jj) * NS * p.K2 + (cidx / BK) * (NS * BK) + (cidx % BK);
+#pragma unroll
+      for (int t = 0; t < NS; ++t) *reinterpret_cast<Pair2<T>*>(o + t * BK) = Pair2<T>{a[t], b[t]};
     }
   }
 };
@@ -249,19 +289,20 @@ struct EpiPairs {
   }
 };
 
-template <int BN, class EPI>
+template <class PREC, int BN, class EPI>
 cudaError_t launch_tc_bn(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                         const tc::Segment* segs, const typename EPI::Params& ep, const tc::TcCtl& ctl, cudaStream_t s) {
-  using Cfg = tc::TcCfg<3, 64, BN, EPI::kStaged>;
+                         const tc::Segment* segs, const typename EPI::Params& ep, const tc::TcCtl& ctl, const float* fac,
+                         cudaStream_t s) {
+  using Cfg = tc::TcCfg<PREC, BN, EPI::kStaged>;
   static bool attr = false;
   if (!attr) {
     // The register split inside the kernel assumes exactly kLaunchRegs registers per thread at
     // launch; with fewer, setmaxnreg.inc could never be satisfied, so refuse to launch.
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, tc::tc_gemm_kernel<3, 64, BN, EPI>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, tc::tc_gemm_kernel<PREC, BN, EPI>);
     if (e != cudaSuccess) return e;
     if (fa.numRegs != tc::kLaunchRegs) return cudaErrorInvalidKernelImage;
-    e = cudaFuncSetAttribute(tc::tc_gemm_kernel<3, 64, BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(tc::tc_gemm_kernel<PREC, BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              Cfg::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
@@ -275,17 +316,30 @@ cudaError_t launch_tc_bn(const CUtensorMap& A, const CUtensorMap& B, const tc::T
     if (e != cudaSuccess) return e;
   }
   const int grid = njobs < nsm ? njobs : nsm;
-  tc::tc_gemm_kernel<3, 64, BN, EPI><<<grid, tc::kThreads, Cfg::SMEM, s>>>(A, B, jobs, njobs, segs, ep, ctl);
+  tc::tc_gemm_kernel<PREC, BN, EPI><<<grid, tc::kThreads, Cfg::SMEM, s>>>(A, B, jobs, njobs, segs, ep, ctl, fac);
   return cudaGetLastError();
 }
 
-template <class EPI>
+template <class PREC, class EPI>
 cudaError_t launch_tc(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                      const tc::Segment* segs, const typename EPI::Params& ep, const tc::TcCtl& ctl, cudaStream_t s) {
+                      const tc::Segment* segs, const typename EPI::Params& ep, const tc::TcCtl& ctl, const float* fac,
+                      cudaStream_t s) {
   switch (bn) {
-    case 128: return launch_tc_bn<128, EPI>(A, B, jobs, njobs, segs, ep, ctl, s);
-    case 112: return launch_tc_bn<112, EPI>(A, B, jobs, njobs, segs, ep, ctl, s);
-    case 96: return launch_tc_bn<96, EPI>(A, B, jobs, njobs, segs, ep, ctl, s);
+    case 128: return launch_tc_bn<PREC, 128, EPI>(A, B, jobs, njobs, segs, ep, ctl, fac, s);
+    case 112: return launch_tc_bn<PREC, 112, EPI>(A, B, jobs, njobs, segs, ep, ctl, fac, s);
+    case 96: return launch_tc_bn<PREC, 96, EPI>(A, B, jobs, njobs, segs, ep, ctl, fac, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Runs f(PREC{}) for the precision code (dmet_prec_t, tensor-core values only).
+template <class F>
+cudaError_t with_prec(int prec, F&& f) {
+  switch (prec) {
+    case DMET_PREC_BF16X3: return f(PrecBF16x3{});
+    case DMET_PREC_TF32: return f(PrecTF32{});
+    case DMET_PREC_TF32X3: return f(PrecTF32x3{});
+    case DMET_PREC_FP16X2: return f(PrecFP16x2{});
     default: return cudaErrorInvalidValue;
   }
 }
@@ -313,6 +367,76 @@ __global__ void __launch_bounds__(256) combine_parts_kernel(const tc::TcJob* __r
   }
 }
 
+// Largest |component| of the L blocks t1[e0 .. e0 + E).y, as float bits (atomicMax on the bits of a
+// non-negative float orders like the value).
+__global__ void __launch_bounds__(256) absmax_L_kernel(const double2* __restrict__ L, const int4* __restrict__ t1,
+                                                       int e0, long long per_block, unsigned int* __restrict__ out) {
+  const double2* src = L + (long long)t1[e0 + blockIdx.y].y * per_block;
+  double m = 0.0;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < per_block;
+       x += (long long)gridDim.x * blockDim.x) {
+    const double2 v = src[x];
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
+  float mf = (float)m;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mf = fmaxf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mf));
+}
+
+__global__ void __launch_bounds__(256) absmax_kernel(const double* __restrict__ x, long long n,
+                                                     unsigned int* __restrict__ out) {
+  double m = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[i]));
+  float mf = (float)m;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mf = fmaxf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mf));
+}
+
+// Power of two s = 2^e with b * s < 2^14 (b >= 0; s = 1 for b = 0), e clamped to FP32's range.
+__device__ int scale_exp(double b) {
+  if (!(b > 0.0)) return 0;
+  int k = 0;
+  frexp(b, &k);  // b = m 2^k, 0.5 <= m < 1, so b < 2^k
+  const int e = 14 - k;
+  return e < -120 ? -120 : (e > 120 ? 120 : e);
+}
+
+__device__ float pow2f(int e) {
+  e = e < -126 ? -126 : (e > 127 ? 127 : e);
+  return __uint_as_float((unsigned int)(e + 127) << 23);
+}
+
+// The FP16 precision's scales from the maxima in sc->mx: |L| <= mL, |C_s| <= mC_s component-wise;
+// |T_s| <= 2 nao mL mC_s (a sum of 2 nao products); |Z_s| <= 2 nrep nao |T_s| mC_s (2 nrep nao
+// products, orbital weights <= 1); |X_s| <= 2 |Z_s|.
+__global__ void make_scales_kernel(MixScales* sc, int nao, int nrep_max, int nspin) {
+  if (threadIdx.x || blockIdx.x) return;
+  const double mL = (double)__uint_as_float(sc->mx[0]);
+  const int eL = scale_exp(mL);
+  int eC[2] = {0, 0}, eT[2] = {0, 0}, eX[2] = {0, 0};
+  for (int s = 0; s < nspin; ++s) {
+    const double mC = (double)__uint_as_float(sc->mx[1 + s]);
+    const double bT = 2.0 * nao * mL * mC;
+    const double bX = 2.0 * (2.0 * nrep_max * nao * bT * mC);
+    eC[s] = scale_exp(mC);
+    eT[s] = scale_exp(bT);
+    eX[s] = scale_exp(bX);
+  }
+  sc->sL = pow2f(eL);
+  for (int s = 0; s < 2; ++s) {
+    sc->sC[s] = pow2f(eC[s]);
+    sc->sT[s] = pow2f(eT[s]);
+    sc->f1[s] = pow2f(eT[s] - eL - eC[s]);
+    sc->f2[s] = pow2f(-eT[s] - eC[s]);
+    sc->sX[s] = pow2f(eX[s]);
+  }
+  const int sa[3] = {0, 0, 1}, sb[3] = {0, 1, 1};
+  for (int b = 0; b < 3; ++b) sc->fc[b] = pow2f(-eX[sa[b]] - eX[nspin == 2 ? sb[b] : 0]);
+}
+
 }  // namespace
 
 cudaError_t launch_combine_parts(const tc::TcJob* jobs, int ntiles, int f, const void* part, double* out, double scale,
@@ -324,10 +448,37 @@ cudaError_t launch_combine_parts(const tc::TcJob* jobs, int ntiles, int f, const
   return cudaGetLastError();
 }
 
-int mixed_kblock() { return tc::TcCfg<3, 64, 128, true>::BK; }
+int mixed_kblock() { return 32; }
 
-cudaError_t launch_split_L(const double2* L, const int4* t1, int e0, int E, int nk, int naux, int nao, int K1,
-                           void* Ls, long long sstride, cudaStream_t s) {
+bool prec_scaled(int prec) { return prec == DMET_PREC_FP16X2; }
+int prec_slices(int prec) {
+  return prec == DMET_PREC_BF16X3 ? 3 : (prec == DMET_PREC_TF32 ? 1 : 2);
+}
+int prec_products(int prec) {
+  return prec == DMET_PREC_BF16X3 ? 6 : (prec == DMET_PREC_TF32 ? 1 : 3);
+}
+int prec_elem_bytes(int prec) { return (prec == DMET_PREC_TF32 || prec == DMET_PREC_TF32X3) ? 4 : 2; }
+
+cudaError_t launch_mix_scales(int prec, const double2* L, const int4* t1, int E, long long per_block,
+                              const double2* const* C, const long long* c_elems, int nspin, int nao, int nrep_max,
+                              MixScales* sc, cudaStream_t s) {
+  if (!prec_scaled(prec)) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(sc->mx, 0, sizeof(sc->mx), s);
+  if (e != cudaSuccess) return e;
+  for (int e0 = 0; e0 < E; e0 += 65535) {
+    const int n = E - e0 < 65535 ? E - e0 : 65535;
+    const long long gx = (152LL * 8 + n - 1) / n;
+    absmax_L_kernel<<<dim3((unsigned)(gx > 1 ? gx : 1), (unsigned)n), 256, 0, s>>>(L, t1, e0, per_block, &sc->mx[0]);
+  }
+  for (int sp = 0; sp < nspin; ++sp)
+    absmax_kernel<<<grid_for(2 * c_elems[sp], 256, 152 * 4), 256, 0, s>>>((const double*)C[sp], 2 * c_elems[sp],
+                                                                           &sc->mx[1 + sp]);
+  make_scales_kernel<<<1, 32, 0, s>>>(sc, nao, nrep_max, nspin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_L(int prec, const double2* L, const int4* t1, int e0, int E, int naux, int nao, int K1,
+                           void* Ls, long long sstride, const MixScales* sc, cudaStream_t s) {
   if (E <= 0) return cudaSuccess;
   if ((long long)naux * nao * (K1 / 2) >= (1LL << 30) || E > 65535) return cudaErrorInvalidValue;
   // about 16 blocks of 256 threads per SM over all entries, at least one per entry
@@ -336,63 +487,88 @@ cudaError_t launch_split_L(const double2* L, const int4* t1, int e0, int E, int 
   const long long need = (per_entry + 1023) / 1024;  // four elements per thread at least
   if (gx > need) gx = need;
   if (gx < 1) gx = 1;
-  split_L_kernel<<<dim3((unsigned)gx, (unsigned)E), 256, 0, s>>>(L, t1, e0, naux, nao, K1, (__nv_bfloat162*)Ls,
-                                                                sstride / 2);
-  (void)nk;
-  return cudaGetLastError();
+  return with_prec(prec, [&](auto tag) -> cudaError_t {
+    using P = decltype(tag);
+    split_L_kernel<P><<<dim3((unsigned)gx, (unsigned)E), 256, 0, s>>>(L, t1, e0, naux, nao, K1,
+                                                                       (typename P::T*)Ls, sstride, sc);
+    return cudaGetLastError();
+  });
 }
 
-cudaError_t launch_build_Cb(const double2* C, int nk, int nao, int n, int K1, void* Cb, long long sstride,
-                            cudaStream_t s) {
+cudaError_t launch_build_Cb(int prec, const double2* C, int nk, int nao, int n, int K1, void* Cb, long long sstride,
+                            const float* sc, cudaStream_t s) {
   const long long total = (long long)nk * 2 * n * K1;
-  build_Cb_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, s>>>(C, nk, nao, n, K1, (__nv_bfloat16*)Cb, sstride);
-  return cudaGetLastError();
+  return with_prec(prec, [&](auto tag) -> cudaError_t {
+    using P = decltype(tag);
+    build_Cb_kernel<P><<<grid_for(total, 256, 152 * 16), 256, 0, s>>>(C, nk, nao, n, K1, (typename P::T*)Cb, sstride,
+                                                                      sc);
+    return cudaGetLastError();
+  });
 }
 
-cudaError_t launch_build_Cc(const double2* C, const int4* gather, const int4* t2, int b0, int nq, int nao, int n,
-                            int K2, void* Cc, long long sstride, cudaStream_t s) {
+cudaError_t launch_build_Cc(int prec, const double2* C, const int4* gather, const int4* t2, int b0, int nq, int nao,
+                            int n, int K2, void* Cc, long long sstride, const float* sc, cudaStream_t s) {
   const long long total = (long long)nq * 2 * n * K2;
-  build_Cc_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, s>>>(C, gather, t2, b0, nq, nao, n, K2,
-                                                                (__nv_bfloat16*)Cc, sstride);
-  return cudaGetLastError();
+  return with_prec(prec, [&](auto tag) -> cudaError_t {
+    using P = decltype(tag);
+    build_Cc_kernel<P><<<grid_for(total, 256, 152 * 16), 256, 0, s>>>(C, gather, t2, b0, nq, nao, n, K2,
+                                                                      (typename P::T*)Cc, sstride, sc);
+    return cudaGetLastError();
+  });
 }
 
-cudaError_t launch_pack_split(const void* ZT, int nq, int naux, int n, int nc, void* Xt, long long sstride,
-                              long long Rtot, long long row_base, cudaStream_t s) {
+cudaError_t launch_pack_split(int prec, const void* ZT, int nq, int naux, int n, int nc, void* Xt, long long sstride,
+                              long long Rtot, long long row_base, const float* sx, cudaStream_t s) {
   const long long nb = (n + PK_B - 1) / PK_B;
   const dim3 grid((unsigned)(nb * (nb + 1) / 2), (naux + PK_P - 1) / PK_P, nq);
-  pack_split_kernel<<<grid, 256, 0, s>>>((const float2*)ZT, naux, n, nc, (__nv_bfloat16*)Xt, sstride, Rtot,
-                                         row_base);
-  return cudaGetLastError();
+  return with_prec(prec, [&](auto tag) -> cudaError_t {
+    using P = decltype(tag);
+    pack_split_kernel<P><<<grid, 256, 0, s>>>((const float2*)ZT, naux, n, nc, (typename P::T*)Xt, sstride, Rtot,
+                                              row_base, sx);
+    return cudaGetLastError();
+  });
 }
 
-cudaError_t launch_tc_split_t(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                              const tc::Segment* segs, void* out, long long K2, int nao, int nemb,
-                              const tc::TcCtl& ctl, cudaStream_t s) {
-  EpiSplitT::Params p{(__nv_bfloat16*)out, K2, nao, nemb};
-  return launch_tc<EpiSplitT>(bn, A, B, jobs, njobs, segs, p, ctl, s);
+cudaError_t launch_tc_split_t(int prec, int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs,
+                              int njobs, const tc::Segment* segs, void* out, long long K2, int nao, int nemb,
+                              const tc::TcCtl& ctl, const float* fac, cudaStream_t s) {
+  return with_prec(prec, [&](auto tag) -> cudaError_t {
+    using P = decltype(tag);
+    typename EpiSplitT<P>::Params p{(typename P::T*)out, K2, nao, nemb};
+    return launch_tc<P, EpiSplitT<P>>(bn, A, B, jobs, njobs, segs, p, ctl, fac, s);
+  });
 }
 
-cudaError_t launch_tc_rect(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+cudaError_t launch_tc_pairs(int prec, int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs,
+                            int njobs, const tc::Segment* segs, void* out, long long ldo, const tc::TcCtl& ctl,
+                            const float* fac, cudaStream_t s) {
+  EpiPairs::Params p{(float2*)out, ldo};
+  return with_prec(prec, [&](auto tag) -> cudaError_t {
+    using P = decltype(tag);
+    return launch_tc<P, EpiPairs>(bn, A, B, jobs, njobs, segs, p, ctl, fac, s);
+  });
+}
+
+cudaError_t launch_tc_rect(int prec, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                            const tc::Segment* segs, double* out, long long ldo, double scale, const tc::TcCtl& ctl,
-                           cudaStream_t s) {
+                           const float* fac, cudaStream_t s) {
   const float sh = (float)scale;
   tc::EpiRect::Params p{out, ldo, sh, (float)(scale - (double)sh)};
-  return launch_tc<tc::EpiRect>(128, A, B, jobs, njobs, segs, p, ctl, s);
+  return with_prec(prec, [&](auto tag) -> cudaError_t {
+    using P = decltype(tag);
+    return launch_tc_bn<P, 128, tc::EpiRect>(A, B, jobs, njobs, segs, p, ctl, fac, s);
+  });
 }
 
-cudaError_t launch_tc_pairs(int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
-                            const tc::Segment* segs, void* out, long long ldo, const tc::TcCtl& ctl, cudaStream_t s) {
-  EpiPairs::Params p{(float2*)out, ldo};
-  return launch_tc<EpiPairs>(bn, A, B, jobs, njobs, segs, p, ctl, s);
-}
-
-cudaError_t launch_tc_packed(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+cudaError_t launch_tc_packed(int prec, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                              const tc::Segment* segs, double* out, double scale, void* part, const tc::TcCtl& ctl,
-                             cudaStream_t s) {
+                             const float* fac, cudaStream_t s) {
   const float sh = (float)scale;
   tc::EpiPacked::Params p{out, sh, (float)(scale - (double)sh), (unsigned long long*)part};
-  return launch_tc<tc::EpiPacked>(128, A, B, jobs, njobs, segs, p, ctl, s);
+  return with_prec(prec, [&](auto tag) -> cudaError_t {
+    using P = decltype(tag);
+    return launch_tc_bn<P, 128, tc::EpiPacked>(A, B, jobs, njobs, segs, p, ctl, fac, s);
+  });
 }
 
 }  // namespace dmet

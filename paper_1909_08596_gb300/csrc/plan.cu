@@ -72,7 +72,7 @@ enum KernelClass {
 const char* const kKcNames[KC_COUNT] = {"check_orbitals",      "check_L",          "gather_orbitals",
                                         "half_transform_1",    "half_transform_2", "pack_pairs",
                                         "contract_s8",         "contract_full",    "host_copy",
-                                        "split_bf16x3",        "tc_half_transform_1", "tc_half_transform_2",
+                                        "split_operands",      "tc_half_transform_1", "tc_half_transform_2",
                                         "tc_pack_split",       "tc_contract",      "embedding_fock",
                                         "dmet_bath"};
 
@@ -188,7 +188,10 @@ struct Block {
 
 // Split-BF16 path: tables built at plan time (they depend on shapes only).
 struct MixedPlan {
-  int K1 = 0, K2 = 0, kseg = 128;
+  int prec = DMET_PREC_BF16X3;         // operand precision (dmet_prec_t)
+  int ns = 3, esz = 2, nprod = 6;      // slices per operand, bytes per slice element, slice products
+  int K1 = 0, K2 = 0, kseg = 128, kseg1 = 0, crun = 0;
+  int kseg_def = 128, kseg1_def = 0, crun_def = 0;  // defaults of the segment knobs
   int bn1 = 128, bn2 = 128;            // output tile widths of the two transform GEMMs
   long long Rtot = 0, R1 = 0;
   std::vector<Block> blocks;           // contraction order, q-blocks within one weight class
@@ -250,7 +253,8 @@ struct Workspace {
   void* A2 = nullptr;
   double* ZT = nullptr;
   void* Xt[2] = {nullptr, nullptr};
-  size_t Ls_b = 0, Cb_b[2] = {0, 0}, Cc_b = 0, A2_b = 0, ZT_b = 0, Xt_b[2] = {0, 0};
+  MixScales* sc = nullptr;
+  size_t Ls_b = 0, Cb_b[2] = {0, 0}, Cc_b = 0, A2_b = 0, ZT_b = 0, Xt_b[2] = {0, 0}, sc_b = 0;
 };
 
 struct dmet_emb_plan_s {
@@ -364,11 +368,12 @@ dmet_status_t validate_desc(const dmet_emb_desc_t& d, int idx) {
     if (rpack != DMET_PACK_S8 && !(d.q_begin == 0 && d.q_end == nk))
       return fail(DMET_ERR_UNSUPPORTED, "problem %d: a q shard needs the 8-fold packed output", idx);
   }
-  if (d.prec != DMET_PREC_FP64 && d.prec != DMET_PREC_BF16X3) return fail(DMET_ERR_INVALID_ARG, "problem %d: prec = %d", idx, d.prec);
-  if (d.prec == DMET_PREC_BF16X3) {
+  if (d.prec < DMET_PREC_FP64 || d.prec > DMET_PREC_FP16X2)
+    return fail(DMET_ERR_INVALID_ARG, "problem %d: prec = %d", idx, d.prec);
+  if (d.prec != DMET_PREC_FP64) {
     const int pack = d.eri_pack == DMET_PACK_AUTO ? (d.sym == DMET_SYM_REAL ? DMET_PACK_S8 : DMET_PACK_FULL) : d.eri_pack;
     if (d.sym != DMET_SYM_REAL || pack != DMET_PACK_S8)
-      return fail(DMET_ERR_UNSUPPORTED, "problem %d: the split-BF16 path needs sym = REAL and 8-fold packing", idx);
+      return fail(DMET_ERR_UNSUPPORTED, "problem %d: the tensor-core paths need sym = REAL and 8-fold packing", idx);
   }
   const long long nmax = std::max(d.n_emb[0], d.n_spin == 2 ? d.n_emb[1] : 0);
   if ((long long)d.n_aux * nmax > INT_MAX / 2 || (long long)d.n_aux * d.n_ao > INT_MAX / 2)
@@ -800,7 +805,7 @@ void free_tables(Tables& t) {
 
 void free_workspace(Workspace& w) {
   void* ptrs[] = {w.crep, w.T, w.Z, w.S, w.X[0], w.X[1], w.lq_all[0], w.lq_all[1],
-                  w.Ls, w.Cb[0], w.Cb[1], w.Cc, w.A2, w.ZT, w.Xt[0], w.Xt[1]};
+                  w.Ls, w.Cb[0], w.Cb[1], w.Cc, w.A2, w.ZT, w.Xt[0], w.Xt[1], w.sc};
   for (void* q : ptrs) cudaFree(q);
   w = Workspace();
 }
@@ -881,12 +886,22 @@ long long zt_bytes(const Prob& pr) {
 void build_mixed(Prob& pr) {
   MixedPlan& m = pr.mx;
   const int BK = mixed_kblock();
-  // K elements per FP32 segment (a multiple of the K block); DMET_TC_KSEG overrides.
-  m.kseg = 128;
-  if (const char* e = std::getenv("DMET_TC_KSEG")) {
+  m.prec = pr.d.prec;
+  m.ns = prec_slices(m.prec);
+  m.esz = prec_elem_bytes(m.prec);
+  m.nprod = prec_products(m.prec);
+  // K elements per FP32 segment (a multiple of the K block) of the second transform and the
+  // contraction (DMET_TC_KSEG), of the first transform (DMET_TC_KSEG1; 0 = one segment), and the most
+  // segments one correction-sum run spans (DMET_TC_CRUN; 0 = no limit).
+  auto knob = [](const char* name, int def, int lo, int hi, int mult) {
+    const char* e = std::getenv(name);
+    if (!e) return def;
     const int v = std::atoi(e);
-    if (v >= BK && v % BK == 0 && v <= 4096) m.kseg = v;
-  }
+    return (v >= lo && v <= hi && (mult <= 1 || v % mult == 0)) ? v : def;
+  };
+  m.kseg = knob("DMET_TC_KSEG", m.kseg_def, BK, 4096, BK);
+  m.kseg1 = knob("DMET_TC_KSEG1", m.kseg1_def, 0, 4096, BK);
+  m.crun = knob("DMET_TC_CRUN", m.crun_def, 0, 1 << 20, 1);
   const int nk = pr.nk, nao = pr.nao, naux = pr.naux;
   m.K1 = (int)padk(2LL * nao);
   int nrep_max = 1;
@@ -902,8 +917,10 @@ void build_mixed(Prob& pr) {
     m.row_base.push_back(b.w == 1 ? (long long)b.b0 * naux : m.R1 + (long long)(b.b0 - n1) * 2 * naux);
   m.segs.clear();
   m.jobs.clear();
-  // segment 0: the single K range of step 1
-  m.segs.push_back({0, m.K1 / BK, 1.0f, 0});
+  // segments [0, n1seg): the K range of step 1
+  const int seg1 = m.kseg1 > 0 ? m.kseg1 : m.K1;
+  for (int k0 = 0; k0 < m.K1; k0 += seg1) m.segs.push_back({k0, std::min(m.K1 - k0, seg1), 1.0f, 0});
+  const int n1seg = (int)m.segs.size();
   // step 2: per contraction slot, chunks of kseg over its K
   const int nslots = (int)pr.con.order.size();
   std::vector<int> s2_off(nslots), s2_cnt(nslots);
@@ -911,22 +928,29 @@ void build_mixed(Prob& pr) {
     const long long K = padk(2LL * pr.s.nrep[pr.con.order[i]] * nao);
     s2_off[i] = (int)m.segs.size();
     for (long long k0 = 0; k0 < K; k0 += m.kseg)
-      m.segs.push_back({(int)k0, (int)((std::min<long long>(K - k0, m.kseg)) / BK), 1.0f, 0});
+      m.segs.push_back({(int)k0, (int)std::min<long long>(K - k0, m.kseg), 1.0f, 0});
     s2_cnt[i] = (int)m.segs.size() - s2_off[i];
   }
   // contraction: class 1 (weight 1) rows [0, R1), class 2 (weight 2) rows [R1, Rtot)
   const int sc_off = (int)m.segs.size();
   for (long long k0 = 0; k0 < m.R1; k0 += m.kseg)
-    m.segs.push_back({(int)k0, (int)(std::min<long long>(m.R1 - k0, m.kseg) / BK), 1.0f, 0});
+    m.segs.push_back({(int)k0, (int)std::min<long long>(m.R1 - k0, m.kseg), 1.0f, 0});
   for (long long k0 = m.R1; k0 < m.Rtot; k0 += m.kseg)
-    m.segs.push_back({(int)k0, (int)(std::min<long long>(m.Rtot - k0, m.kseg) / BK), 2.0f, 0});
+    m.segs.push_back({(int)k0, (int)std::min<long long>(m.Rtot - k0, m.kseg), 2.0f, 0});
   const int sc_cnt = (int)m.segs.size() - sc_off;
-  // A correction-sum run never spans a change of weight.
+  // A correction-sum run never spans a change of weight, nor more than crun segments of one list.
+  auto bound = [&](size_t i) {  // a run ends at segment i - 1 and the next starts at i
+    m.segs[i - 1].flags |= tc::kRunLast;
+    m.segs[i].flags |= tc::kRunFirst;
+  };
   for (size_t i = 1; i < m.segs.size(); ++i)
-    if (m.segs[i].w != m.segs[i - 1].w) {
-      m.segs[i - 1].flags |= tc::kRunLast;
-      m.segs[i].flags |= tc::kRunFirst;
-    }
+    if (m.segs[i].w != m.segs[i - 1].w) bound(i);
+  if (m.crun > 0) {
+    std::vector<std::pair<int, int>> lists = {{0, n1seg}, {sc_off, (int)m.segs.size()}};
+    for (int i = 0; i < nslots; ++i) lists.push_back({s2_off[i], s2_off[i] + s2_cnt[i]});
+    for (auto& l : lists)
+      for (int i = l.first + m.crun; i < l.second; i += m.crun) bound((size_t)i);
+  }
 
   auto cdiv = [](long long a, long long b) { return (int)((a + b - 1) / b); };
   const int T = tc::kTile;
@@ -951,7 +975,7 @@ void build_mixed(Prob& pr) {
               const int r = e - pr.con.start[slot], el = e - e0, k2 = pr.con.t1[e].x;
               m.jobs.push_back({el * naux * nao + mt * T, k2 * 2 * n + nt * B1,
                                 (int)std::min<long long>(T, (long long)naux * nao - mt * T),
-                                (int)std::min<long long>(B1, 2LL * n - nt * B1), 0, 1, mt * T, nt * B1,
+                                (int)std::min<long long>(B1, 2LL * n - nt * B1), 0, n1seg, mt * T, nt * B1,
                                 (slot - bl.b0) * naux * n, r * 2 * nao});
             }
       m.j1_cnt[sp].push_back((int)m.jobs.size() - m.j1_off[sp].back());
@@ -1032,51 +1056,55 @@ void build_mixed(Prob& pr) {
   (void)nk;
 }
 
-// Tensor flops a job range issues: 6 slice products of 128 x bn x K tiles.
+// Tensor flops a job range issues: the precision's slice products of 128 x bn x K tiles.
 double exec_flops(const MixedPlan& m, int off, int cnt, int bn) {
   double f = 0;
   for (int i = off; i < off + cnt; ++i) {
     const tc::TcJob& j = m.jobs[i];
     long long k = 0;
-    for (int g = j.seg0; g < j.seg0 + j.nseg; ++g) k += (long long)m.segs[g].nkb * mixed_kblock();
-    f += 6.0 * 2.0 * tc::kTile * bn * (double)k;
+    for (int g = j.seg0; g < j.seg0 + j.nseg; ++g) k += (long long)m.segs[g].nk;
+    f += (double)m.nprod * 2.0 * tc::kTile * bn * (double)k;
   }
   return f;
 }
 
 struct MixedWs {
-  size_t Ls, Cb[2], Cc, A2, ZT, Xt[2];
+  size_t Ls, Cb[2], Cc, A2, ZT, Xt[2], sc;
 };
 
 MixedWs mixed_ws(const Prob& pr) {
   const MixedPlan& m = pr.mx;
   const long long nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
   MixedWs w;
-  w.Ls = (size_t)3 * m.Ls_rows * m.K1 * 2;
+  const size_t se = (size_t)m.ns * m.esz;  // bytes of all slices of one element
+  w.Ls = se * m.Ls_rows * m.K1;
   for (int s = 0; s < 2; ++s) {
-    w.Cb[s] = s < pr.nspin ? (size_t)3 * pr.nk * 2 * pr.n[s] * m.K1 * 2 : 0;
-    w.Xt[s] = s < pr.nspin ? (size_t)3 * pr.npair[s] * m.Rtot * 2 : 0;
+    w.Cb[s] = s < pr.nspin ? se * pr.nk * 2 * pr.n[s] * m.K1 : 0;
+    w.Xt[s] = s < pr.nspin ? se * pr.npair[s] * m.Rtot : 0;
   }
-  w.Cc = (size_t)3 * pr.bq * 2 * nmax * m.K2 * 2;
-  w.A2 = (size_t)3 * pr.bq * pr.naux * nmax * m.K2 * 2;
+  w.Cc = se * pr.bq * 2 * nmax * m.K2;
+  w.A2 = se * pr.bq * pr.naux * nmax * m.K2;
   w.ZT = (size_t)zt_bytes(pr);
+  w.sc = sizeof(MixScales);
   return w;
 }
 
-size_t mixed_total(const MixedWs& w) { return w.Ls + w.Cb[0] + w.Cb[1] + w.Cc + w.A2 + w.ZT + w.Xt[0] + w.Xt[1]; }
+size_t mixed_total(const MixedWs& w) {
+  return w.Ls + w.Cb[0] + w.Cb[1] + w.Cc + w.A2 + w.ZT + w.Xt[0] + w.Xt[1] + w.sc;
+}
 
 dmet_status_t mixed_maps(dmet_emb_plan_s* P, const Prob& pr, MixedMaps& mm) {
   const MixedPlan& m = pr.mx;
-  const int BK = mixed_kblock(), T = tc::kTile;
+  const int T = tc::kTile, pc = m.prec, ns = m.ns;
   const long long nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
   const long long cc_rows = (long long)pr.bq * 2 * nmax;
-  CK(make_tmap_bf16_3d(&mm.Ls, P->W->Ls, m.K1, m.Ls_rows, 3, m.K1, m.Ls_rows * m.K1, BK, T));
+  CK(make_tmap_3d(&mm.Ls, pc, P->W->Ls, m.K1, m.Ls_rows, ns, m.K1, m.Ls_rows * m.K1, T));
   for (int s = 0; s < pr.nspin; ++s) {
     const long long n = pr.n[s];
-    CK(make_tmap_bf16_3d(&mm.Cb[s], P->W->Cb[s], m.K1, pr.nk * 2 * n, 3, m.K1, pr.nk * 2 * n * m.K1, BK, m.bn1));
-    CK(make_tmap_bf16_3d(&mm.Cc[s], P->W->Cc, m.K2, (long long)pr.bq * 2 * n, 3, m.K2, cc_rows * m.K2, BK, m.bn2));
-    CK(make_tmap_bf16_interleaved(&mm.A2[s], P->W->A2, m.K2, (long long)pr.bq * pr.naux * n, T));
-    CK(make_tmap_bf16_3d(&mm.Xt[s], P->W->Xt[s], m.Rtot, pr.npair[s], 3, m.Rtot, pr.npair[s] * m.Rtot, BK, T));
+    CK(make_tmap_3d(&mm.Cb[s], pc, P->W->Cb[s], m.K1, pr.nk * 2 * n, ns, m.K1, pr.nk * 2 * n * m.K1, m.bn1));
+    CK(make_tmap_3d(&mm.Cc[s], pc, P->W->Cc, m.K2, (long long)pr.bq * 2 * n, ns, m.K2, cc_rows * m.K2, m.bn2));
+    CK(make_tmap_interleaved(&mm.A2[s], pc, P->W->A2, m.K2, (long long)pr.bq * pr.naux * n, ns, T));
+    CK(make_tmap_3d(&mm.Xt[s], pc, P->W->Xt[s], m.Rtot, pr.npair[s], ns, m.Rtot, pr.npair[s] * m.Rtot, T));
   }
   return DMET_OK;
 }
@@ -1090,18 +1118,32 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
   int n1 = 0;
   for (int q : pr.con.order) n1 += pr.s.qw[q] == 1;
   const long long used1 = (long long)n1 * pr.naux, used2 = ((long long)pr.con.order.size() - n1) * 2 * pr.naux;
+  const int pc = m.prec;
+  const double se = (double)m.ns * m.esz;  // bytes of all slices of one operand element
+  MixScales* sc = P->W->sc;
+  const bool scaled = prec_scaled(pc);
+  if (scaled) {
+    // the FP16 operand scales, from the maxima of the L blocks this call reads and of C
+    const int E_all = (int)pr.con.t1.size();
+    int nrep_max = 1;
+    for (int q : pr.con.order) nrep_max = std::max(nrep_max, pr.s.nrep[q]);
+    const long long c_el[2] = {(long long)pr.nk * pr.nao * pr.n[0], (long long)pr.nk * pr.nao * pr.n[1]};
+    Timed t(P, KC_SPLIT, 0.0, 16.0 * E_all * pr.naux * pr.nao * pr.nao + 16.0 * (c_el[0] + c_el[1]), 2 + pr.nspin);
+    CK(launch_mix_scales(pc, L, pr.con.d_t1, E_all, (long long)pr.naux * pr.nao * pr.nao, C, c_el, pr.nspin, pr.nao,
+                         nrep_max, sc, P->cs));
+  }
   for (int s = 0; s < pr.nspin; ++s) {
     // padding rows of the contraction operand read as zeros
-    const size_t pitch = (size_t)m.Rtot * 2;
-    const long long h = 3 * pr.npair[s];
+    const size_t pitch = (size_t)m.Rtot * m.esz;
+    const long long h = (long long)m.ns * pr.npair[s];
     if (m.R1 > used1)
-      CK(cudaMemset2DAsync((char*)P->W->Xt[s] + used1 * 2, pitch, 0, (size_t)(m.R1 - used1) * 2, h, P->cs));
+      CK(cudaMemset2DAsync((char*)P->W->Xt[s] + used1 * m.esz, pitch, 0, (size_t)(m.R1 - used1) * m.esz, h, P->cs));
     if (m.Rtot - m.R1 > used2)
-      CK(cudaMemset2DAsync((char*)P->W->Xt[s] + (m.R1 + used2) * 2, pitch, 0, (size_t)(m.Rtot - m.R1 - used2) * 2, h,
-                           P->cs));
-    Timed t(P, KC_SPLIT, 0.0, 16.0 * pr.nk * pr.nao * pr.n[s] + 6.0 * pr.nk * 2 * pr.n[s] * m.K1);
-    CK(launch_build_Cb(C[s], pr.nk, pr.nao, pr.n[s], m.K1, P->W->Cb[s], (long long)pr.nk * 2 * pr.n[s] * m.K1,
-                       P->cs));
+      CK(cudaMemset2DAsync((char*)P->W->Xt[s] + (m.R1 + used2) * m.esz, pitch, 0,
+                           (size_t)(m.Rtot - m.R1 - used2) * m.esz, h, P->cs));
+    Timed t(P, KC_SPLIT, 0.0, 16.0 * pr.nk * pr.nao * pr.n[s] + se * pr.nk * 2 * pr.n[s] * m.K1);
+    CK(launch_build_Cb(pc, C[s], pr.nk, pr.nao, pr.n[s], m.K1, P->W->Cb[s], (long long)pr.nk * 2 * pr.n[s] * m.K1,
+                       &sc->sC[s], P->cs));
   }
   for (size_t bi = 0; bi < m.blocks.size(); ++bi) {
     const Block& bl = m.blocks[bi];
@@ -1112,23 +1154,23 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
     }
     {
       const double rows = (double)E * pr.naux * pr.nao;
-      Timed t(P, KC_SPLIT, 0.0, rows * (16.0 * pr.nao + 6.0 * m.K1));
-      CK(launch_split_L(L, pr.con.d_t1, e0, E, pr.nk, pr.naux, pr.nao, m.K1, P->W->Ls, m.Ls_rows * m.K1, P->cs));
+      Timed t(P, KC_SPLIT, 0.0, rows * (16.0 * pr.nao + se * m.K1));
+      CK(launch_split_L(pc, L, pr.con.d_t1, e0, E, pr.naux, pr.nao, m.K1, P->W->Ls, m.Ls_rows * m.K1, sc, P->cs));
     }
     for (int s = 0; s < pr.nspin; ++s) {
       const int n = pr.n[s];
       {
-        Timed t(P, KC_SPLIT, 0.0, 6.0 * nq * 2 * n * m.K2);
-        CK(launch_build_Cc(C[s], pr.con.d_gather, pr.con.d_t2, bl.b0, nq, pr.nao, n, m.K2, P->W->Cc, cc_rows * m.K2,
-                           P->cs));
+        Timed t(P, KC_SPLIT, 0.0, se * nq * 2 * n * m.K2);
+        CK(launch_build_Cc(pc, C[s], pr.con.d_gather, pr.con.d_t2, bl.b0, nq, pr.nao, n, m.K2, P->W->Cc,
+                           cc_rows * m.K2, &sc->sC[s], P->cs));
       }
       {
-        // algorithmic bytes: the L slices read once, T written once as three bf16 slices
-        const double by = 6.0 * E * pr.naux * pr.nao * (m.K1 + 2.0 * n);
+        // algorithmic bytes: the L slices read once, T written once as slices
+        const double by = se * E * pr.naux * pr.nao * (m.K1 + 2.0 * n);
         Timed t(P, KC_TC_TRANSFORM_1, 8.0 * n * (double)pr.naux * pr.nao * pr.nao * E, by, 1,
                 exec_flops(m, m.j1_off[s][bi], m.j1_cnt[s][bi], m.bn1));
-        CK(launch_tc_split_t(m.bn1, mm.Ls, mm.Cb[s], m.d_jobs + m.j1_off[s][bi], m.j1_cnt[s][bi], m.d_segs, P->W->A2,
-                             m.K2, pr.nao, n, P->ctl(), P->cs));
+        CK(launch_tc_split_t(pc, m.bn1, mm.Ls, mm.Cb[s], m.d_jobs + m.j1_off[s][bi], m.j1_cnt[s][bi], m.d_segs,
+                             P->W->A2, m.K2, pr.nao, n, P->ctl(), scaled ? &sc->f1[s] : nullptr, P->cs));
       }
       {
         double fl = 0, by = 0;
@@ -1136,17 +1178,17 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
           fl += 8.0 * n * (double)pr.naux * n * pr.con.t2[i].w;
           // the slot's T slices (K = its padded 2 n_rep n_AO) read once, Z written as two-float pairs
           const double K = (double)padk(2LL * pr.s.nrep[pr.con.order[i]] * pr.nao);
-          by += 6.0 * pr.naux * n * K + 6.0 * 2 * n * K + 8.0 * pr.naux * n * 2.0 * n;
+          by += se * pr.naux * n * K + se * 2 * n * K + 8.0 * pr.naux * n * 2.0 * n;
         }
         Timed t(P, KC_TC_TRANSFORM_2, fl, by, 1, exec_flops(m, m.j2_off[s][bi], m.j2_cnt[s][bi], m.bn2));
-        CK(launch_tc_pairs(m.bn2, mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs, P->W->ZT, 2LL * n,
-                           P->ctl(), P->cs));
+        CK(launch_tc_pairs(pc, m.bn2, mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs,
+                           P->W->ZT, 2LL * n, P->ctl(), scaled ? &sc->f2[s] : nullptr, P->cs));
       }
       {
         const int nc = bl.w == 1 ? 1 : 2;
-        Timed t(P, KC_TC_PACK, 0.0, 16.0 * nq * pr.naux * (double)n * n + 6.0 * nq * pr.naux * nc * pr.npair[s]);
-        CK(launch_pack_split(P->W->ZT, nq, pr.naux, n, nc, P->W->Xt[s], pr.npair[s] * m.Rtot, m.Rtot, m.row_base[bi],
-                             P->cs));
+        Timed t(P, KC_TC_PACK, 0.0, 16.0 * nq * pr.naux * (double)n * n + se * nq * pr.naux * nc * pr.npair[s]);
+        CK(launch_pack_split(pc, P->W->ZT, nq, pr.naux, n, nc, P->W->Xt[s], pr.npair[s] * m.Rtot, m.Rtot,
+                             m.row_base[bi], &sc->sX[s], P->cs));
       }
     }
   }
@@ -1159,16 +1201,16 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
     const double fl = blk == 1 ? 2.0 * pr.npair[0] * (double)pr.npair[1] * K
                                : (double)pr.npair[sa] * (pr.npair[sa] + 1.0) * K;
     // algorithmic bytes: both operands' slices read once, the packed FP64 result written once
-    const double by = 6.0 * m.Rtot * (double)(pr.npair[sa] + (blk == 1 ? pr.npair[sb] : 0)) +
+    const double by = se * m.Rtot * (double)(pr.npair[sa] + (blk == 1 ? pr.npair[sb] : 0)) +
                       8.0 * (blk == 1 ? (double)pr.npair[sa] * pr.npair[sb] : pr.npair[sa] * (pr.npair[sa] + 1.0) / 2);
     const int nsplit = m.jc_split_n[blk], f = m.jc_split_f[blk];
     Timed t(P, KC_TC_CONTRACT, fl, by, nsplit ? 2 : 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk], tc::kTile));
     if (blk == 1) {
-      CK(launch_tc_rect(mm.Xt[0], mm.Xt[1], m.d_jobs + m.jc_off[1], m.jc_cnt[1], m.d_segs, (double*)out[1],
-                        pr.npair[1], oscale, P->ctl(), P->cs));
+      CK(launch_tc_rect(pc, mm.Xt[0], mm.Xt[1], m.d_jobs + m.jc_off[1], m.jc_cnt[1], m.d_segs, (double*)out[1],
+                        pr.npair[1], oscale, P->ctl(), scaled ? &sc->fc[1] : nullptr, P->cs));
     } else {
-      CK(launch_tc_packed(mm.Xt[sa], mm.Xt[sa], m.d_jobs + m.jc_off[blk], m.jc_cnt[blk], m.d_segs, (double*)out[blk],
-                          oscale, P->W->ZT, P->ctl(), P->cs));
+      CK(launch_tc_packed(pc, mm.Xt[sa], mm.Xt[sa], m.d_jobs + m.jc_off[blk], m.jc_cnt[blk], m.d_segs,
+                          (double*)out[blk], oscale, P->W->ZT, P->ctl(), scaled ? &sc->fc[blk] : nullptr, P->cs));
       if (nsplit)
         CK(launch_combine_parts(m.d_jobs + m.jc_off[blk] + m.jc_cnt[blk] - nsplit * f, nsplit, f, P->W->ZT,
                                 (double*)out[blk], oscale, P->cs));
@@ -1457,7 +1499,7 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     }
     // q-block size: the largest (<= 8, or <= DMET_QBLOCK, entries per launch <= 65535) whose
     // workspace fits.
-    pr.mixed = pr.d.prec == DMET_PREC_BF16X3;
+    pr.mixed = pr.d.prec != DMET_PREC_FP64;
     if (pr.mixed) tune_cache_lookup(pr, pr.mx.bn1, pr.mx.bn2);
     auto total_for = [&](int b) {
       size_t t = ws_for(pr, b).total();
@@ -1517,6 +1559,7 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     c.Cc = std::max(c.Cc, d.Cc);
     c.A2 = std::max(c.A2, d.A2);
     c.ZT = std::max(c.ZT, d.ZT);
+    c.sc = std::max(c.sc, d.sc);
     for (int s = 0; s < 2; ++s) {
       a.X[s] = std::max(a.X[s], b.X[s]);
       a.lq_all[s] = std::max(a.lq_all[s], b.lq_all[s]);
@@ -1544,6 +1587,7 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     alloc(&W.Cc, &W.Cc_b, mn.Cc);
     alloc(&W.A2, &W.A2_b, mn.A2);
     alloc((void**)&W.ZT, &W.ZT_b, mn.ZT);
+    alloc((void**)&W.sc, &W.sc_b, mn.sc);
     for (int s = 0; s < 2; ++s) {
       alloc(&W.Cb[s], &W.Cb_b[s], mn.Cb[s]);
       alloc(&W.Xt[s], &W.Xt_b[s], mn.Xt[s]);

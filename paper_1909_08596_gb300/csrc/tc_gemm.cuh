@@ -41,6 +41,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "prec.cuh"
 #include "split.cuh"
 #include "tc_common.cuh"
 
@@ -48,8 +49,8 @@ namespace dmet {
 namespace tc {
 
 struct Segment {
-  int k0;     // first K element (a multiple of the K block)
-  int nkb;    // number of K blocks
+  int k0;     // first K element (a multiple of 32, so of every precision's K block)
+  int nk;     // number of K elements (a multiple of 32)
   float w;    // weight of this segment (a power of two, so the scaling is exact)
   int flags;  // kRunFirst / kRunLast: bounds of a correction-sum run inside a job
 };
@@ -89,22 +90,25 @@ static_assert(128 * kCtrlRegs + 128 * kEpiGroups * kEpiRegs <= kThreads * kLaunc
               "the register split must fit in what the CTA launches with");
 static_assert(kCtrlRegs + kEpiGroups * kEpiRegs <= 512, "per sub-partition register file");
 
-// BN: output columns per tile (the UMMA N), 128, 112 or 96. Each of the four accumulators
-// (two buffers of leading + correction sums) starts on a 128-column boundary of TMEM.
-// STAGED: the output functor stores through the shared-memory transpose. The stage ring
-// takes what the 227 KB of shared memory leave (4 to 6 stages).
-template <int NSLICE, int ROWB, int BN, bool STAGED>
+// PREC: the operand precision (prec.cuh). BN: output columns per tile (the UMMA N), 128, 112 or
+// 96. Each of the four accumulators (two buffers of leading + correction sums) starts on a
+// 128-column boundary of TMEM. STAGED: the output functor stores through the shared-memory
+// transpose. The stage ring takes what the 227 KB of shared memory leave (4 to 8 stages).
+// Operand rows are 64 bytes per K block (64-byte swizzle).
+template <class PREC, int BN, bool STAGED>
 struct TcCfg {
   static_assert(BN % 32 == 16 || BN % 32 == 0, "BN must be a multiple of 16");
   static_assert(BN <= 128 && BN >= 64, "4 BN TMEM columns must fit");
-  static constexpr int BK = ROWB / 2;                           // bf16 elements per K block
+  static constexpr int ROWB = 64;
+  static constexpr int NSLICE = PREC::kSlices;
+  static constexpr int BK = kblock_elems<PREC>();               // elements per K block
   static constexpr int A_BYTES = kTile * ROWB;                  // one A slice tile
   static constexpr int B_BYTES = BN * ROWB;                     // one B slice tile
   static constexpr int STAGE_BYTES = NSLICE * (A_BYTES + B_BYTES);
-  static constexpr int NPROD = NSLICE == 3 ? 6 : 1;
+  static constexpr int NPROD = PREC::kProducts;
   static constexpr int STAGING = STAGED ? kEpiWarps * 32 * 8 * 8 : 0;  // epilogue transpose: 32 x 8 words per warp
   static constexpr int RING = 232448 - 1024 - 256 - STAGING;    // 227 KB less alignment, barriers, staging
-  static constexpr int STAGES = RING / STAGE_BYTES > 6 ? 6 : RING / STAGE_BYTES;
+  static constexpr int STAGES = RING / STAGE_BYTES > 8 ? 8 : RING / STAGE_BYTES;
   static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 256 + STAGING;
   static_assert(STAGES >= 2 && SMEM <= 232448, "shared memory");
   static constexpr int PART = BN / kEpiGroups;                  // columns per epilogue warp
@@ -174,12 +178,16 @@ __device__ __forceinline__ void staged_store(const typename EPI::Params& ep, con
 // row = tile-local row (< 128) and columns col0 .. col0+H-1, or (kStaged) give the 8-byte
 // value of an element, EPI::value(params, job, hi, lo), and write it, EPI::put(params, job, row,
 // col, v), skipping elements outside the job's valid region.
-template <int NSLICE, int ROWB, int BN, class EPI>
+// fac (device, or null for 1): a power of two that multiplies every result before the output functor
+// sees it (it undoes the operand scaling of the FP16 precision).
+template <class PREC, int BN, class EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcJob* __restrict__ jobs, int njobs, const Segment* __restrict__ segs,
-                   const typename EPI::Params ep, const TcCtl ctl) {
-  using Cfg = TcCfg<NSLICE, ROWB, BN, EPI::kStaged>;
+                   const typename EPI::Params ep, const TcCtl ctl, const float* __restrict__ fac) {
+  using Cfg = TcCfg<PREC, BN, EPI::kStaged>;
+  constexpr int NSLICE = Cfg::NSLICE;
+  constexpr int ROWB = Cfg::ROWB;
   constexpr int S = Cfg::STAGES;
   constexpr int H = Cfg::PART;
   constexpr int kChunk = 32;  // TMEM columns per load round trip
@@ -240,7 +248,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const TcJob job = jobs[jb];
       for (int g = 0; g < job.nseg && ok; ++g) {
         const Segment sg = segs[job.seg0 + g];
-        for (int kb = 0; kb < sg.nkb; ++kb) {
+        const int nkb = sg.nk / Cfg::BK;
+        for (int kb = 0; kb < nkb; ++kb) {
           const int s = issued % S, ph = (issued / S) & 1;
           if (!mbar_wait(empty(s), ph ^ 1, err, 1u, lim)) {
             ok = false;
@@ -263,9 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     } else if (warp == 1 && lane == 0) {
       // ---------------- MMA issuer ----------------
-      constexpr uint32_t idesc = idesc_bf16_f32(kTile, BN);
-      constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
-      constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
+      constexpr uint32_t idesc = idesc_f32acc(PREC::kFormat, kTile, BN);
       int it = 0, gs = 0, run = -1;  // K blocks, segments and correction runs so far (across jobs)
       bool ok = true;
       for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x) {
@@ -282,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         run += first;
         // 128-column aligned: leading sums at 0 / 128, correction sums at 256 / 384
         const uint32_t d_main = tmem + b * kTile, d_corr = tmem + (2 + (run & 1)) * kTile;
-        const int nkb = sg.nkb;
+        const int nkb = sg.nk / Cfg::BK;
         for (int kb = 0; kb < nkb; ++kb) {
           const int s = it % S, ph = (it / S) & 1;
           if (!mbar_wait(full(s), ph, err, 4u, lim)) {
@@ -291,14 +298,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           // (TMA wrote the stage and the MMAs read it, both through the async proxy; the
           // mbarrier's phase completion orders them, so no tcgen05 fence belongs here.)
+          // each MMA takes 32 bytes of K from every operand row
 #pragma unroll
-          for (int kk = 0; kk < Cfg::BK / 16; ++kk) {
+          for (int kk = 0; kk < ROWB / 32; ++kk) {
 #pragma unroll
             for (int p = 0; p < Cfg::NPROD; ++p) {
-              const uint64_t ad = smem_desc<ROWB>(a_tile(s, pa[p]) + kk * 32);
-              const uint64_t bd = smem_desc<ROWB>(b_tile(s, pb[p]) + kk * 32);
-              if (p == 0) umma_bf16(d_main, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
-              else umma_bf16(d_corr, ad, bd, idesc, (!first || (kb | kk) != 0 || p > 1) ? 1u : 0u);
+              const uint64_t ad = smem_desc<ROWB>(a_tile(s, PREC::prod_a(p)) + kk * 32);
+              const uint64_t bd = smem_desc<ROWB>(b_tile(s, PREC::prod_b(p)) + kk * 32);
+              if (p == 0) umma<PREC::kKind>(d_main, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+              else umma<PREC::kKind>(d_corr, ad, bd, idesc, (!first || (kb | kk) != 0 || p > 1) ? 1u : 0u);
             }
           }
           umma_commit(empty(s));
@@ -317,6 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue ----------------
     const int quad = warp & 3, half = (warp - 4) >> 2;  // (half: this warp's column share)
     const int row = quad * 32 + lane;
+    const float f = fac ? *fac : 1.f;
     float hi[H], lo[H];
     bool ok = true;
     int gs = 0, run = -1;
@@ -332,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const Segment sg = segs[job.seg0 + g];
         const float w = sg.w;
         run += g == 0 || (sg.flags & kRunFirst);
-        const bool last = NSLICE == 3 && (g == job.nseg - 1 || (sg.flags & kRunLast));
+        const bool last = Cfg::NPROD > 1 && (g == job.nseg - 1 || (sg.flags & kRunLast));
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + half * H;
         const uint32_t tm_main = lane_base + b * kTile, tm_corr = lane_base + (2 + (run & 1)) * kTile;
         // Up to kChunk columns per round trip: all loads, then one wait.
@@ -374,6 +383,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acce(b));
+      }
+      if (f != 1.f) {
+#pragma unroll
+        for (int c = 0; c < H; ++c) {
+          hi[c] *= f;
+          lo[c] *= f;
+        }
       }
       if constexpr (EPI::kStaged) {
         if (ok) staged_store<H, EPI>(ep, job, quad * 32, half * H, hi, lo, staging + (warp - 4) * 256, lane);
