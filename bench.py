@@ -867,7 +867,8 @@ def main():
     if rank == 0 and not args.no_check:
         # The oracle on the seeded orbital subsets (every aux function, streamed): the error of each GPU
         # result per spin block, and the oracle's own rate on the first blocks as the CPU baseline.
-        pb = max(1, min(spec.n_aux, (6 << 30) // (spec.nk ** 2 * spec.n_ao ** 2 * 16)))
+        # blocks of aux functions of about 24 GB of L (larger blocks: larger GEMMs in the oracle)
+        pb = max(1, min(spec.n_aux, (24 << 30) // (spec.nk ** 2 * spec.n_ao ** 2 * 16)))
         refs, base, info = oracle_check(torch, spec, Cs, S, pb)
         names = {(0, 0): "aa" if spec.n_spin == 2 else "s8", (0, 1): "ab", (1, 1): "bb"}
         errs_all = {p: {names[k]: error_stats(subs[p][b], refs[b]) for b, k in enumerate(block_spins(spec))}

