@@ -164,6 +164,9 @@ DMET_API dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_pro
  * k-AO -> k-EO transform of every momentum-conserving pair, then the Fourier sum to the
  * reference cell; the paper notes that a density-fitting solver can consume these
  * directly and skip the contraction). C[s] and Lq_out[s] for s < n_spin.
+ * The transforms run in the problem's precision: FP64 kernels for DMET_PREC_FP64, the
+ * tensor-core half transforms of the contraction path otherwise (then the q must belong to the
+ * descriptor's shard; L^q is summed from the FP32 two-float results exactly in FP64).
  * Also runs the orbital checks (orthonormality; realness when sym = REAL). */
 DMET_API dmet_status_t dmet_emb_transform_3idx(dmet_emb_plan_t plan, int32_t problem, const void* L,
                                       const void* const* C, int32_t q_begin, int32_t q_end,
@@ -234,6 +237,22 @@ DMET_API dmet_status_t dmet_emb_fock(dmet_emb_plan_t plan, int32_t problem, cons
 DMET_API dmet_status_t dmet_emb_bath(dmet_emb_plan_t plan, int32_t problem, int32_t spin, const void* gamma_k,
                                      const void* C_lo, const int32_t* val, int32_t n_val, void* C_out,
                                      double* info);
+
+/* Coulomb and exchange of an embedding density straight from the density-fitted factors, without
+ * forming the ERI (section 2.1: a solver that supports density fitting takes the factors and skips
+ * Algorithm 1's contraction). With (ij|kl) = (1/Nk) sum_q sum_P L^q_{P,ij} L^{-q}_{P,kl}:
+ *     J_ij = (1/Nk) sum_q sum_P L^q_{P,ij} tr(L^{-q}_P gamma),
+ *     K_ij = (1/Nk) sum_q sum_P (L^q_P gamma L^{-q}_P)_ij,
+ * i.e. J_ij = sum_kl (ij|kl) gamma_lk and K_ij = sum_kl (ik|lj) gamma_kl, the two terms of Eq.
+ * "fock double counting". Device pointers only (16-byte aligned):
+ *   Lq     complex128 [Nk][n_aux][n][n], L^q of spin `spin` for every q (as dmet_emb_transform_3idx
+ *          writes them for q in [0, Nk));
+ *   gamma  complex128 [n][n], the embedding density;
+ *   J, K   complex128 [n][n], written (real for real orbitals and a real gamma).
+ * FP64 throughout (batched complex GEMMs over the (q, P) entries in chunks, and reductions); queued
+ * on the plan's stream; grows a plan-owned scratch buffer of at most about 1 GiB on first use. */
+DMET_API dmet_status_t dmet_emb_jk_df(dmet_emb_plan_t plan, int32_t problem, int32_t spin, const void* Lq,
+                                      const void* gamma, void* J, void* K);
 
 /* Frees the plan's device memory, events and tables. Safe on NULL. Waits for the stream. */
 DMET_API dmet_status_t dmet_emb_destroy(dmet_emb_plan_t plan);

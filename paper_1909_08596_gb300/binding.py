@@ -120,6 +120,8 @@ def lib() -> ctypes.CDLL:
         L.dmet_emb_bath.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.c_int32, _P, _P]
         L.dmet_emb_bath.restype = st
+        L.dmet_emb_jk_df.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P]
+        L.dmet_emb_jk_df.restype = st
         L.dmet_fftdf_plane_waves.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
                                              _P, _P, _P]
@@ -291,6 +293,11 @@ def dmet_emb_bath(plan, gamma_k, C_lo, val, C_out, info=None, problem=0, spin=0)
     v = (ctypes.c_int32 * len(val))(*[int(x) for x in val])
     _check(lib().dmet_emb_bath(_P(plan), problem, spin, ptr(gamma_k), ptr(C_lo), v, len(val), ptr(C_out),
                                ptr(info) if info is not None else None))
+
+
+def dmet_emb_jk_df(plan, Lq, gamma, J, K, problem=0, spin=0):
+    """Density-fitted Coulomb and exchange of gamma from the factors L^q (device tensors; see dmet_emb_jk_df)."""
+    _check(lib().dmet_emb_jk_df(_P(plan), problem, spin, ptr(Lq), ptr(gamma), ptr(J), ptr(K)))
 
 
 def dmet_fftdf_plane_waves(mesh, q, grid, lattice):

@@ -92,6 +92,59 @@ inline int blocks_for(long long total, int threads, int cap) {
   return (int)(b < 1 ? 1 : (b < cap ? b : cap));
 }
 
+// v[z] = tr(L^{-q}_P gamma) = sum_{k,l} Lm[z][k][l] gamma[l][k] for the batch entries z = (q, P) of a
+// chunk: Lm[z] = Lq[tab[z].y] (the -q factor). One block per z.
+__global__ void __launch_bounds__(256) jk_trace_kernel(const double2* __restrict__ Lq, const int4* __restrict__ tab,
+                                                       int n, const double2* __restrict__ gamma, double2* __restrict__ v) {
+  const long long nn = (long long)n * n;
+  const double2* m = Lq + (long long)tab[blockIdx.x].y * nn;
+  double re = 0.0, im = 0.0;
+  for (long long x = threadIdx.x; x < nn; x += blockDim.x) {
+    const int k = (int)(x / n), l = (int)(x % n);
+    const double2 a = m[x], g = gamma[(long long)l * n + k];
+    re = fma(a.x, g.x, fma(-a.y, g.y, re));
+    im = fma(a.x, g.y, fma(a.y, g.x, im));
+  }
+  __shared__ double sr[8], si[8];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sr[threadIdx.x >> 5] = re;
+    si[threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += sr[w];
+      b += si[w];
+    }
+    v[blockIdx.x] = make_double2(a, b);
+  }
+}
+
+// J[x] += s sum_z v[z] Lq[tab[z].x][x] and K[x] += s sum_z Kb[z][x] over the nz entries of a chunk.
+__global__ void __launch_bounds__(256) jk_accumulate_kernel(const double2* __restrict__ Lq, const int4* __restrict__ tab,
+                                                            const double2* __restrict__ v, const double2* __restrict__ Kb,
+                                                            int nz, long long nn, double s, double2* __restrict__ J,
+                                                            double2* __restrict__ K) {
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < nn; x += (long long)gridDim.x * blockDim.x) {
+    double jr = 0.0, ji = 0.0, kr = 0.0, ki = 0.0;
+    for (int z = 0; z < nz; ++z) {
+      const double2 a = Lq[(long long)tab[z].x * nn + x], w = v[z], b = Kb[(long long)z * nn + x];
+      jr = fma(a.x, w.x, fma(-a.y, w.y, jr));
+      ji = fma(a.x, w.y, fma(a.y, w.x, ji));
+      kr += b.x;
+      ki += b.y;
+    }
+    J[x] = make_double2(J[x].x + s * jr, J[x].y + s * ji);
+    K[x] = make_double2(K[x].x + s * kr, K[x].y + s * ki);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_fock_reduce(const double2* G, int nk, int n, double s, double* F0, cudaStream_t st) {
@@ -118,6 +171,22 @@ cudaError_t launch_coulomb_exchange(const double* eri, const double* gamma, int 
 cudaError_t launch_fock_combine(const double* F0, const double* J, const double* K, int n, double* out,
                                 cudaStream_t st) {
   fock_combine_kernel<<<blocks_for((long long)n * n, 256, 152 * 8), 256, 0, st>>>(F0, J, K, n * n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jk_trace(const double2* Lq, const int4* tab, int nz, int n, const double2* gamma, double2* v,
+                            cudaStream_t st) {
+  if (nz <= 0) return cudaSuccess;
+  jk_trace_kernel<<<nz, 256, 0, st>>>(Lq, tab, n, gamma, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jk_accumulate(const double2* Lq, const int4* tab, const double2* v, const double2* Kb, int nz, int n,
+                                 double s, double2* J, double2* K, cudaStream_t st) {
+  const long long nn = (long long)n * n;
+  long long blocks = (nn + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  jk_accumulate_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, st>>>(Lq, tab, v, Kb, nz, nn, s, J, K);
   return cudaGetLastError();
 }
 

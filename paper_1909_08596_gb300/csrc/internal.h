@@ -77,6 +77,13 @@ cudaError_t launch_coulomb_exchange(const double* eri, const double* gamma, int 
                                     cudaStream_t st);
 cudaError_t launch_fock_combine(const double* F0, const double* J, const double* K, int n, double* out,
                                 cudaStream_t st);
+// Density-fitted J and K from the factors L^q (fock.cu), per chunk of z = (q, P) batch entries with
+// tab[z] = {z-th factor's index in Lq, the -q factor's index, z, n}:
+// v[z] = tr(L^{-q}_P gamma); J += s sum_z v[z] L^q_P; K += s sum_z Kb[z] (Kb[z] = L^q_P gamma L^{-q}_P).
+cudaError_t launch_jk_trace(const double2* Lq, const int4* tab, int nz, int n, const double2* gamma, double2* v,
+                            cudaStream_t st);
+cudaError_t launch_jk_accumulate(const double2* Lq, const int4* tab, const double2* v, const double2* Kb, int nz, int n,
+                                 double s, double2* J, double2* K, cudaStream_t st);
 // Bath construction (bath.cu). The impurity columns that enter the SVD, by value.
 constexpr int kMaxBathCols = 128;
 struct BathCols {
@@ -161,6 +168,8 @@ cudaError_t launch_tc_rect(int prec, const CUtensorMap& A, const CUtensorMap& B,
 cudaError_t launch_tc_packed(int prec, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                              const tc::Segment* segs, double* out, double scale, void* part, const tc::TcCtl& ctl,
                              const float* fac, cudaStream_t s);
+// L^q of one slot from the step-2 output (two-float pairs): s (Z + Z^T), conjugated if conj.
+cudaError_t launch_lq_from_pairs(const void* ZT, int naux, int n, double s, int conj, double2* Lq, cudaStream_t st);
 // Sums the K parts of the split tiles of a packed contraction (the parts' jobs: jobs[0 .. ntiles * f)).
 cudaError_t launch_combine_parts(const tc::TcJob* jobs, int ntiles, int f, const void* part, double* out, double scale,
                                  cudaStream_t s);

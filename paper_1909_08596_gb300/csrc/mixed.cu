@@ -437,7 +437,30 @@ __global__ void make_scales_kernel(MixScales* sc, int nao, int nrep_max, int nsp
   for (int b = 0; b < 3; ++b) sc->fc[b] = pow2f(-eX[sa[b]] - eX[nspin == 2 ? sb[b] : 0]);
 }
 
+// Lq[P][i][j] = s (Z_ij + Z_ji) (conj: its complex conjugate) from the step-2 output of one slot,
+// Z_ij = (re, im), each a two-float (hi, lo) at ZT[(P n + j) n + i] (a float4), summed exactly in FP64.
+__global__ void lq_from_pairs_kernel(const float4* __restrict__ ZT, int naux, int n, double s, double sim,
+                                     double2* __restrict__ Lq) {
+  const long long nn = (long long)n * n, total = (long long)naux * nn;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+       x += (long long)gridDim.x * blockDim.x) {
+    const long long P = x / nn;
+    const int i = (int)((x % nn) / n), j = (int)(x % n);
+    const float4 a = ZT[(P * n + j) * n + i], b = ZT[(P * n + i) * n + j];
+    const double re = ((double)a.x + (double)a.y) + ((double)b.x + (double)b.y);
+    const double im = ((double)a.z + (double)a.w) + ((double)b.z + (double)b.w);
+    Lq[x] = make_double2(s * re, sim * im);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_lq_from_pairs(const void* ZT, int naux, int n, double s, int conj, double2* Lq, cudaStream_t st) {
+  const long long total = (long long)naux * n * n;
+  lq_from_pairs_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, st>>>((const float4*)ZT, naux, n, s, conj ? -s : s,
+                                                                        Lq);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_combine_parts(const tc::TcJob* jobs, int ntiles, int f, const void* part, double* out, double scale,
                                  cudaStream_t s) {

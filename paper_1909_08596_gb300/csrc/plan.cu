@@ -67,6 +67,7 @@ enum KernelClass {
   KC_TC_CONTRACT,
   KC_FOCK,
   KC_BATH,
+  KC_JK_DF,
   KC_COUNT
 };
 const char* const kKcNames[KC_COUNT] = {"check_orbitals",      "check_L",          "gather_orbitals",
@@ -74,7 +75,7 @@ const char* const kKcNames[KC_COUNT] = {"check_orbitals",      "check_L",       
                                         "contract_s8",         "contract_full",    "host_copy",
                                         "split_operands",      "tc_half_transform_1", "tc_half_transform_2",
                                         "tc_pack_split",       "tc_contract",      "embedding_fock",
-                                        "dmet_bath"};
+                                        "dmet_bath",           "jk_density_fitted"};
 
 // ------------------------------------------------------------------------------------------
 // Scheduler: momentum-conserving pairs (k1, k1 + q), negation, q weights and the
@@ -290,6 +291,9 @@ struct dmet_emb_plan_s {
   // scratch of dmet_emb_bath (grown on demand)
   void* bath_ws = nullptr;
   size_t bath_ws_b = 0;
+  // scratch of dmet_emb_jk_df (grown on demand)
+  void* jk_ws = nullptr;
+  size_t jk_ws_b = 0;
   // Host L transferred block by block on its own stream: the problem being enqueued waits on
   // xev[b] (its contraction block b's pairs have landed) before its first read of L in block b.
   cudaStream_t xs = nullptr;
@@ -835,6 +839,7 @@ void destroy_plan(dmet_emb_plan_s* P) {
   cudaFree(P->stage_out);
   cudaFree(P->fock_ws);
   cudaFree(P->bath_ws);
+  cudaFree(P->jk_ws);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   for (cudaStream_t st : P->side) cudaStreamDestroy(st);
   if (P->cap) cudaStreamDestroy(P->cap);
@@ -1115,7 +1120,21 @@ dmet_status_t mixed_maps(dmet_emb_plan_s* P, const Prob& pr, MixedMaps& mm) {
   return DMET_OK;
 }
 
-dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, void* const* out) {
+// What dmet_emb_transform_3idx asks of the tensor-core path: L^q for q in [q_begin, q_end) of every
+// spin, from the contraction slot slot[q - q_begin] (conjugated where conj[q - q_begin]).
+struct Lq3Req {
+  int q_begin = 0, q_end = 0;
+  std::vector<int> slot;
+  std::vector<char> conj;
+  double2* const* out = nullptr;
+};
+
+// The tensor-core path of Algorithm 1: the operand scales and the orbital operands, then block by
+// block the split of L, the two half transforms and the pair packing, then the contraction. With
+// `req`, only the blocks that hold requested q run, their L^q are written out, and nothing is
+// packed or contracted (dmet_emb_transform_3idx).
+dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, void* const* out,
+                        const Lq3Req* req = nullptr) {
   MixedPlan& m = pr.mx;
   MixedMaps mm;
   TRY(mixed_maps(P, pr, mm));
@@ -1142,9 +1161,9 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
     // padding rows of the contraction operand read as zeros
     const size_t pitch = (size_t)m.Rtot * m.esz;
     const long long h = (long long)m.ns * pr.npair[s];
-    if (m.R1 > used1)
+    if (!req && m.R1 > used1)
       CK(cudaMemset2DAsync((char*)P->W->Xt[s] + used1 * m.esz, pitch, 0, (size_t)(m.R1 - used1) * m.esz, h, P->cs));
-    if (m.Rtot - m.R1 > used2)
+    if (!req && m.Rtot - m.R1 > used2)
       CK(cudaMemset2DAsync((char*)P->W->Xt[s] + (m.R1 + used2) * m.esz, pitch, 0,
                            (size_t)(m.Rtot - m.R1 - used2) * m.esz, h, P->cs));
     Timed t(P, KC_SPLIT, 0.0, 16.0 * pr.nk * pr.nao * pr.n[s] + se * pr.nk * 2 * pr.n[s] * m.K1);
@@ -1154,6 +1173,11 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
   for (size_t bi = 0; bi < m.blocks.size(); ++bi) {
     const Block& bl = m.blocks[bi];
     const int e0 = pr.con.start[bl.b0], E = pr.con.start[bl.b1] - e0, nq = bl.b1 - bl.b0;
+    if (req) {
+      bool any = false;
+      for (int sl : req->slot) any |= sl >= bl.b0 && sl < bl.b1;
+      if (!any) continue;
+    }
     if (P->xpending) {
       TRY(queue_block_copies(P, pr, (int)bi));
       CK(cudaStreamWaitEvent(P->cs, P->xev[bi], 0));
@@ -1190,6 +1214,17 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
         CK(launch_tc_pairs(pc, m.bn2, mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs,
                            P->W->ZT, 2LL * n, P->ctl(), scaled ? &sc->f2[s] : nullptr, P->cs));
       }
+      if (req) {
+        for (int i = 0; i < req->q_end - req->q_begin; ++i) {
+          const int sl = req->slot[i];
+          if (sl < bl.b0 || sl >= bl.b1) continue;
+          const long long slot_el = (long long)pr.naux * n * n;
+          Timed t(P, KC_PACK, 0.0, 16.0 * slot_el + 16.0 * slot_el);
+          CK(launch_lq_from_pairs((const char*)P->W->ZT + (size_t)(sl - bl.b0) * slot_el * 2 * sizeof(float2), pr.naux,
+                                  n, pr.lq_scale, req->conj[i], req->out[s] + i * slot_el, P->cs));
+        }
+        continue;
+      }
       {
         const int nc = bl.w == 1 ? 1 : 2;
         Timed t(P, KC_TC_PACK, 0.0, 16.0 * nq * pr.naux * (double)n * n + se * nq * pr.naux * nc * pr.npair[s]);
@@ -1198,6 +1233,7 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
       }
     }
   }
+  if (req) return DMET_OK;
   long long K = 0;
   for (int q : pr.con.order) K += (long long)pr.naux * (pr.s.qw[q] == 1 ? 1 : 2);
   // The operand holds Z + Z^T; L^q = s (Z + Z^T), so the product carries s^2, and 1/Nk.
@@ -1776,17 +1812,25 @@ dmet_status_t dmet_emb_transform_3idx(dmet_emb_plan_t P, int32_t problem, const 
         cur += ob[s];
       }
   }
-  int bq = pr.bq;
   if (pr.mixed) {
-    // FP64 transform buffers of a split-BF16 plan, grown on first use, one q at a time
-    bq = 1;
-    const int nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
-    const size_t E = (size_t)max_entries(pr.nat, 1);
-    TRY(ensure((void**)&P->W->crep, &P->W->crep_b, E * pr.nao * nmax * 16));
-    TRY(ensure((void**)&P->W->T, &P->W->T_b, E * pr.nao * pr.naux * nmax * 16));
-    TRY(ensure((void**)&P->W->Z, &P->W->Z_b, (size_t)pr.naux * nmax * nmax * 16));
+    // the tensor-core transforms of the plan's precision, for the contraction slots that hold the q
+    // (q of zero contraction weight: from -q, conjugated; real orbitals, section 2.1)
+    Lq3Req req;
+    req.q_begin = q_begin;
+    req.q_end = q_end;
+    req.out = out;
+    for (int q = q_begin; q < q_end; ++q) {
+      const int qe = pr.s.qw[q] > 0 ? q : pr.s.neg[q];
+      const auto it = std::find(pr.con.order.begin(), pr.con.order.end(), qe);
+      if (it == pr.con.order.end())
+        return fail(DMET_ERR_INVALID_ARG, "q = %d is outside the plan's q shard", q);
+      req.slot.push_back((int)(it - pr.con.order.begin()));
+      req.conj.push_back(qe != q);
+    }
+    TRY(eri_mixed(P, pr, Ld, Cd, nullptr, &req));
+  } else {
+    TRY(transform_range(P, pr, Ld, Cd, q_begin, q_end, out, pr.bq));
   }
-  TRY(transform_range(P, pr, Ld, Cd, q_begin, q_end, out, bq));
   if (need) {
     for (int s = 0; s < pr.nspin; ++s)
       if (ohost[s]) {
@@ -2180,6 +2224,98 @@ dmet_status_t dmet_emb_bath(dmet_emb_plan_t P, int32_t problem, int32_t spin, co
   CK(launch_bath_bloch(B, (const double2*)C_lo, tw, pr.d.mesh, nlo, n_val, Cb, (double2*)C_out, P->cs));
   CK(launch_bath_product((const double2*)C_lo, Cb, nk, nlo, n_val, (double2*)C_out, P->cs));
   if (info) CK(cudaMemcpyAsync(info + n_val, stats, 5 * sizeof(double), cudaMemcpyDeviceToDevice, P->cs));
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_jk_df(dmet_emb_plan_t P, int32_t problem, int32_t spin, const void* Lq, const void* gamma,
+                             void* J, void* K) {
+  clear_error();
+  if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
+  if (problem < 0 || problem >= (int)P->probs.size()) return fail(DMET_ERR_INVALID_ARG, "problem %d", problem);
+  Prob& pr = P->probs[problem];
+  if (spin < 0 || spin >= pr.nspin) return fail(DMET_ERR_INVALID_ARG, "spin %d of a problem with %d", spin, pr.nspin);
+  if (!Lq || !gamma || !J || !K) return fail(DMET_ERR_INVALID_ARG, "NULL pointer argument");
+  const void* ptrs[4] = {Lq, gamma, J, K};
+  for (const void* q : ptrs) {
+    if (!is_device_ptr(q)) return fail(DMET_ERR_INVALID_ARG, "dmet_emb_jk_df takes device pointers only");
+    if (!aligned16(q)) return fail(DMET_ERR_ALIGNMENT, "a pointer is not 16-byte aligned");
+  }
+  const int nk = pr.nk, naux = pr.naux, n = pr.n[spin];
+  const long long nn = (long long)n * n, nz_all = (long long)nk * naux;
+  // batch entries z = (q, P) in chunks whose two n x n scratch matrices per entry stay within 1 GiB
+  const long long per = 2 * nn * 16 + 16 + 2 * (long long)sizeof(int4);
+  const int chunk = (int)std::max(1LL, std::min({nz_all, (1LL << 30) / per, 65535LL}));
+  const size_t oW = 0, oKb = oW + (size_t)chunk * nn * 16, ov = oKb + (size_t)chunk * nn * 16,
+               ot1 = ov + ((size_t)chunk * 16 + 255) / 256 * 256, ot2 = ot1 + (size_t)chunk * sizeof(int4);
+  P->cs = P->stream;
+  TRY(ensure(&P->jk_ws, &P->jk_ws_b, ot2 + (size_t)chunk * sizeof(int4)));
+  char* w = (char*)P->jk_ws;
+  double2* W = (double2*)(w + oW);
+  double2* Kb = (double2*)(w + oKb);
+  double2* v = (double2*)(w + ov);
+  int4* d1 = (int4*)(w + ot1);
+  int4* d2 = (int4*)(w + ot2);
+  const double2* L = (const double2*)Lq;
+  // 8 flops per complex multiply-add: two n^3 products and the two n^2 reductions per entry
+  const int nchunks = (int)((nz_all + chunk - 1) / chunk);
+  Timed t(P, KC_JK_DF, 8.0 * nz_all * (2.0 * nn * n + 2.0 * nn), 16.0 * nz_all * nn * 5, 4 * nchunks);
+  CK(cudaMemsetAsync(J, 0, (size_t)nn * 16, P->cs));
+  CK(cudaMemsetAsync(K, 0, (size_t)nn * 16, P->cs));
+  std::vector<int4> t1(chunk), t2(chunk);
+  for (long long z0 = 0; z0 < nz_all; z0 += chunk) {
+    const int nz = (int)std::min<long long>(chunk, nz_all - z0);
+    for (int i = 0; i < nz; ++i) {
+      const long long z = z0 + i;
+      const int q = (int)(z / naux), Pp = (int)(z % naux);
+      const int mz = pr.s.neg[q] * naux + Pp;  // the -q factor of the same aux function
+      t1[i] = make_int4((int)z, mz, i, n);
+      t2[i] = make_int4(i, mz, i, n);
+    }
+    CK(cudaMemcpyAsync(d1, t1.data(), nz * sizeof(int4), cudaMemcpyHostToDevice, P->cs));
+    CK(cudaMemcpyAsync(d2, t2.data(), nz * sizeof(int4), cudaMemcpyHostToDevice, P->cs));
+    {
+      // W[i] = L^q_P gamma
+      ZgemmArgs z = zargs();
+      z.A = L;
+      z.B = (const double2*)gamma;
+      z.D = W;
+      z.tab = d1;
+      z.M = n;
+      z.N = n;
+      z.K = n;
+      z.lda = n;
+      z.ldb = n;
+      z.sA = nn;
+      z.sB = 0;
+      z.sD = nn;
+      z.dm_lo = n;
+      z.dn_lo = 1;
+      z.batch = nz;
+      CK(launch_zgemm(z, A_MK, false, B_KN, P->cs));
+    }
+    {
+      // Kb[i] = W[i] L^{-q}_P
+      ZgemmArgs z = zargs();
+      z.A = W;
+      z.B = L;
+      z.D = Kb;
+      z.tab = d2;
+      z.M = n;
+      z.N = n;
+      z.K = n;
+      z.lda = n;
+      z.ldb = n;
+      z.sA = nn;
+      z.sB = nn;
+      z.sD = nn;
+      z.dm_lo = n;
+      z.dn_lo = 1;
+      z.batch = nz;
+      CK(launch_zgemm(z, A_MK, false, B_KN, P->cs));
+    }
+    CK(launch_jk_trace(L, d1, nz, n, (const double2*)gamma, v, P->cs));
+    CK(launch_jk_accumulate(L, d1, v, Kb, nz, n, 1.0 / nk, (double2*)J, (double2*)K, P->cs));
+  }
   return DMET_OK;
 }
 

@@ -119,3 +119,24 @@ def test_precision_close_to_bf16x3(torch, name, layout):
     (b,), st1, _ = run_eri(torch, d1, Lin, Cs)
     assert st0 == st1 == B.DMET_OK
     assert rel_fro(b, a) < 5e-6
+
+
+@pytest.mark.parametrize("name", ["bf16x3", "fp16x2", "tf32x3"])
+@pytest.mark.parametrize("layout", [B.DMET_L_FULL, B.DMET_L_REDUCED])
+def test_precision_transform_3idx_matches_oracle(torch, name, layout):
+    """dmet_emb_transform_3idx of a tensor-core plan: the half transforms of that precision (every q,
+    including the q of zero contraction weight, which the reduced layout takes from -q conjugated)."""
+    import paper_1909_08596_gb300 as dm
+    from gpu_helpers import run_3idx
+    codes = {"bf16x3": (B.DMET_PREC_BF16X3, 1e-6), "fp16x2": (B.DMET_PREC_FP16X2, 5e-6),
+             "tf32x3": (B.DMET_PREC_TF32X3, 5e-6)}
+    code, tol = codes[name]
+    spec = spec_of((3, 2, 1), 6, 11, 20, n_spin=2)
+    L, Cs, _ = synth.make_problem(spec)
+    d = B.make_desc(spec.mesh, 6, 11, [20, 20], n_spin=2, prec=code, l_layout=layout)
+    Lin = synth.make_L_pairs(spec, dm.dmet_emb_l_pairs(d)) if layout == B.DMET_L_REDUCED else L
+    got, st, _ = run_3idx(torch, d, Lin, Cs, 0, spec.nk)
+    assert st == B.DMET_OK
+    for s in range(2):
+        ref = oracle.embedded_3idx(L, Cs[s], spec.mesh)
+        assert rel_fro(got[s], ref) < tol, (name, s, rel_fro(got[s], ref))
