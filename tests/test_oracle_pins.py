@@ -321,3 +321,55 @@ def test_planted_mistake_in_block_form_fails(name):
     eri = ns["embedded_eri_pblocks"](_blocks(L, 3), [C], spec.mesh)[(0, 0)]
     assert rel(eri, ref) > 1e-6, name
     assert rel(oracle.embedded_eri_pblocks(_blocks(L, 3), [C], spec.mesh)[(0, 0)], ref) < 1e-12
+
+
+# ---------------------------------------------------------------------------------------------
+# 4-fold packing of a complex ERI: the layout's definition fixed by a table worked out by hand for two
+# orbitals (pairs 00 -> 0, 10 -> 1, 11 -> 2; block A at IJ(IJ+1)/2 + KL; block B after the 6 entries of
+# A, its only entry (10|01)); (position, stored as the conjugate?).
+S4_HAND_N2 = {
+    (0, 0, 0, 0): (0, False), (0, 0, 0, 1): (1, True), (0, 0, 1, 0): (1, False), (0, 0, 1, 1): (3, False),
+    (0, 1, 0, 0): (1, True), (0, 1, 0, 1): (2, True), (0, 1, 1, 0): (6, False), (0, 1, 1, 1): (4, True),
+    (1, 0, 0, 0): (1, False), (1, 0, 0, 1): (6, False), (1, 0, 1, 0): (2, False), (1, 0, 1, 1): (4, False),
+    (1, 1, 0, 0): (3, False), (1, 1, 0, 1): (4, True), (1, 1, 1, 0): (4, False), (1, 1, 1, 1): (5, False),
+}
+
+
+def test_s4_layout_hand_table():
+    from oracle import checks
+    assert checks.s4_size(2) == 7
+    for idx, want in S4_HAND_N2.items():
+        assert checks._s4_home(*idx, 2) == want, idx
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_s4_every_slot_holds_one_orbit(n):
+    """Each packed slot is the home of the 1, 2 or 4 entries of one symmetry orbit, and of nothing else."""
+    from oracle import checks
+    members = {}
+    for idx in np.ndindex(n, n, n, n):
+        p, c = checks._s4_home(*idx, n)
+        members.setdefault(p, []).append((idx, c))
+    assert sorted(members) == list(range(checks.s4_size(n)))
+    for p, m in members.items():
+        i, j, k, l = m[0][0]
+        orbit = {(i, j, k, l), (k, l, i, j), (j, i, l, k), (l, k, j, i)}
+        assert {x for x, _ in m} == orbit, (p, m)
+        # the swap keeps the conjugation flag, the pair transposition flips it
+        flags = dict(m)
+        assert flags[(i, j, k, l)] == flags[(k, l, i, j)] != flags[(j, i, l, k)] or (i, j, k, l) == (j, i, l, k) \
+            or (i, j, k, l) == (l, k, j, i)
+
+
+@pytest.mark.parametrize("mesh,n,complex_orbitals", [((3, 2, 1), 4, True), ((2, 2, 1), 5, True), ((3, 1, 1), 3, False)])
+def test_s4_roundtrip_of_the_oracle_eri(mesh, n, complex_orbitals):
+    from oracle import checks
+    spec = small_spec(mesh, n_ao=3, n_aux=5, n_emb=n)
+    L = synth.make_L(spec)
+    csc = synth.complex_supercell_orbitals(spec) if complex_orbitals else synth.supercell_orbitals(spec)
+    eri = oracle.embedded_eri(L, synth.bloch_orbitals(csc, mesh), mesh)
+    packed = checks.pack_s4(eri)
+    assert len(packed) == checks.s4_size(n)
+    assert rel(checks.unpack_s4(packed, n), eri) < 1e-13
+    if complex_orbitals:
+        assert np.abs(packed.imag).max() > 1e-3 * np.abs(packed).max()
