@@ -468,7 +468,7 @@ def measure_fock_and_bath(dm, torch, spec, Cd, eri0):
     produces such orbitals (dmet_emb_bath), FP64 kernels, timed on their own (restricted problems)."""
     stream = torch.cuda.current_stream()
     desc = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, spec.n_emb)
-    plan = dm.dmet_emb_plan(desc, stream=stream.cuda_stream, workspace_limit=1 << 30)
+    plan = dm.dmet_emb_plan(desc, stream=stream.cuda_stream, workspace_limit=16 << 30)
     fock = bath = None
     try:
         Fk = torch.from_numpy(synth.fock_k(synth.real_space_fock(spec), spec.mesh)).cuda()

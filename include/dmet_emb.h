@@ -105,7 +105,8 @@ typedef enum {
 typedef enum {
   DMET_PACK_AUTO = 0,    /* S8 for DMET_SYM_REAL, FULL otherwise */
   DMET_PACK_S8 = 1,      /* real, 8-fold packed (requires DMET_SYM_REAL) */
-  DMET_PACK_FULL = 2     /* complex128 [n][n][n][n] */
+  DMET_PACK_FULL = 2,    /* complex128 [n][n][n][n] */
+  DMET_PACK_S4 = 3       /* complex, 4-fold packed: (ij|kl) = (kl|ij) = conj((ji|lk)) (FP64 path) */
 } dmet_pack_t;
 
 /* One embedding problem. Sizes follow section 2.1/2.2: a Gamma-centred mesh, n_ao AOs and
@@ -145,6 +146,15 @@ typedef struct {
  *       IJ = i(i+1)/2 + j (i >= j), element IJ(IJ+1)/2 + KL (IJ >= KL).
  *   S8, alpha-beta block: double[npair_a][npair_b], element [IJ][KL].
  *   FULL: complex128 [n_a][n_a][n_b][n_b], element [i][j][k][l].
+ *   S4, same-spin block: complex128, every entry stored once (possibly as the conjugate of the
+ *       stored value) using (ij|kl) = (kl|ij) and (ij|kl) = conj((ji|lk)):
+ *       block A: i >= j, k >= l, IJ >= KL (IJ = i(i+1)/2 + j) at IJ(IJ+1)/2 + KL;
+ *       block B: i > j, k < l, a >= b (a = i(i-1)/2 + j, b = l(l-1)/2 + k) at nA + a(a+1)/2 + b,
+ *       nA = npair(npair+1)/2, npair = n(n+1)/2. Any other entry: (ij|kl) = (kl|ij) brings an
+ *       ordered pair first; a reversed first pair is conj((ji|lk)); (ii|kl) with k < l is
+ *       conj((ii|lk)); in block B, a < b is conj((lk|ji)) stored at nA + b(b+1)/2 + a.
+ *   S4, alpha-beta block: complex128 [npair_a][n_b][n_b], element [IJ][k][l] for i >= j (the
+ *       others: (ij|kl) = conj((ji|lk))).
  * Returns the number of BYTES of block `block` of `desc`, or 0 for an invalid request. */
 DMET_API size_t dmet_emb_eri_bytes(const dmet_emb_desc_t* desc, int32_t block);
 

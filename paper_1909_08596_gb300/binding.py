@@ -34,7 +34,7 @@ STATUS_NAMES = {0: "DMET_OK", 1: "DMET_ERR_INVALID_ARG", 2: "DMET_ERR_ALIGNMENT"
 # dmet_prec_t, dmet_sym_t, dmet_pack_t
 DMET_PREC_FP64, DMET_PREC_BF16X3, DMET_PREC_TF32, DMET_PREC_TF32X3, DMET_PREC_FP16X2 = 0, 1, 2, 3, 4
 DMET_SYM_NONE, DMET_SYM_REAL = 0, 1
-DMET_PACK_AUTO, DMET_PACK_S8, DMET_PACK_FULL = 0, 1, 2
+DMET_PACK_AUTO, DMET_PACK_S8, DMET_PACK_FULL, DMET_PACK_S4 = 0, 1, 2, 3
 # dmet_l_layout_t
 DMET_L_FULL, DMET_L_REDUCED = 0, 1
 

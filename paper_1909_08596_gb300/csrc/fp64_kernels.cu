@@ -385,6 +385,47 @@ inline int grid_for(long long total, int threads, int cap) {
   return (int)(g < cap ? g : cap);
 }
 
+// Largest t with t(t+1)/2 <= x (the row of a lower-triangle index), exact for x < 2^50.
+__device__ __forceinline__ long long tri_row(long long x) {
+  long long t = (long long)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
+  while (t * (t + 1) / 2 > x) --t;
+  while ((t + 1) * (t + 2) / 2 <= x) ++t;
+  return t;
+}
+
+// out[pos] = full[i][j][k][l] for the (i, j, k, l) that packed position pos stands for.
+__global__ void pack_s4_kernel(const double2* __restrict__ full, int na, int nb, int rect, double2* __restrict__ out) {
+  const long long np = (long long)na * (na + 1) / 2, ns = (long long)na * (na - 1) / 2;
+  const long long nA = np * (np + 1) / 2;
+  const long long total = rect ? np * nb * nb : nA + ns * (ns + 1) / 2;
+  const long long nb2 = (long long)nb * nb;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+       x += (long long)gridDim.x * blockDim.x) {
+    long long i, j, k, l;
+    if (rect) {
+      const long long I = x / nb2, kl = x % nb2;
+      i = tri_row(I);
+      j = I - i * (i + 1) / 2;
+      k = kl / nb;
+      l = kl % nb;
+    } else if (x < nA) {
+      const long long I = tri_row(x), K = x - I * (I + 1) / 2;
+      i = tri_row(I);
+      j = I - i * (i + 1) / 2;
+      k = tri_row(K);
+      l = K - k * (k + 1) / 2;
+    } else {
+      // a = i(i-1)/2 + j with i > j, b = l(l-1)/2 + k with l > k
+      const long long y = x - nA, a = tri_row(y), b = y - a * (a + 1) / 2;
+      i = tri_row(a) + 1;
+      j = a - i * (i - 1) / 2;
+      l = tri_row(b) + 1;
+      k = b - l * (l - 1) / 2;
+    }
+    out[x] = full[((i * na + j) * nb + k) * nb + l];
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_zgemm(const ZgemmArgs& a, int a_layout, bool conj_a, int b_layout, cudaStream_t s) {
@@ -453,6 +494,13 @@ cudaError_t launch_l_check(const double2* L, const int* neg, int nk, int naux, i
   const long long pchunks = (naux + LCHK_P - 1) / LCHK_P;
   const long long nwork = (long long)nk * nk * pchunks;
   l_check_kernel<<<(unsigned)(nwork < (1LL << 30) ? nwork : (1LL << 30)), 256, 0, s>>>(L, neg, nk, naux, nao, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_s4(const double2* full, int na, int nb, int rect, double2* out, cudaStream_t st) {
+  const long long np = (long long)na * (na + 1) / 2, ns = (long long)na * (na - 1) / 2;
+  const long long total = rect ? np * nb * nb : np * (np + 1) / 2 + ns * (ns + 1) / 2;
+  pack_s4_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, st>>>(full, na, nb, rect, out);
   return cudaGetLastError();
 }
 

@@ -63,6 +63,9 @@ cudaError_t launch_gather_orbitals(const double2* C, double2* Crep, const int4* 
 cudaError_t launch_pack_pairs(const double2* Z, double* X, int nq, int naux, int n, int nc, double s,
                               cudaStream_t st);
 
+// 4-fold packing of a complex ERI block full[i][j][k][l] (the layout of dmet_emb_eri_bytes): a
+// same-spin block (rect = 0, na == nb) or the alpha-beta block (rect = 1, rows i >= j, all (k, l)).
+cudaError_t launch_pack_s4(const double2* full, int na, int nb, int rect, double2* out, cudaStream_t st);
 // Real path 3-index output: Lq[q][P][i][j] = s * (Z_ij + Z_ji), or its complex conjugate if conj.
 cudaError_t launch_symmetrize(const double2* Z, double2* Lq, int nq, int naux, int n, double s, int conj,
                               cudaStream_t st);

@@ -252,7 +252,8 @@ struct Workspace {
   double2* S = nullptr;
   double* X[2] = {nullptr, nullptr};
   double2* lq_all[2] = {nullptr, nullptr};
-  size_t crep_b = 0, T_b = 0, Z_b = 0, S_b = 0, X_b[2] = {0, 0}, lq_all_b[2] = {0, 0};
+  double2* full = nullptr;  // one complex ERI block before 4-fold packing
+  size_t crep_b = 0, T_b = 0, Z_b = 0, S_b = 0, X_b[2] = {0, 0}, lq_all_b[2] = {0, 0}, full_b = 0;
   // split-BF16 operands
   void* Ls = nullptr;
   void* Cb[2] = {nullptr, nullptr};
@@ -343,6 +344,11 @@ size_t eri_bytes_of(const dmet_emb_desc_t& d, int block) {
     if (block == 1) return (size_t)(pa * pb) * 8;
     return (size_t)(pa * (pa + 1) / 2) * 8;
   }
+  if (pack == DMET_PACK_S4) {
+    const long long pa = a * (a + 1) / 2, sa = a * (a - 1) / 2;
+    if (block == 1) return (size_t)(pa * b * b) * 16;
+    return (size_t)(pa * (pa + 1) / 2 + sa * (sa + 1) / 2) * 16;
+  }
   return (size_t)(a * a * b * b) * 16;
 }
 
@@ -361,7 +367,7 @@ dmet_status_t validate_desc(const dmet_emb_desc_t& d, int idx) {
   }
   if (d.ck_norm != 0 && d.ck_norm != 1) return fail(DMET_ERR_INVALID_ARG, "problem %d: ck_norm = %d", idx, d.ck_norm);
   if (d.sym != DMET_SYM_NONE && d.sym != DMET_SYM_REAL) return fail(DMET_ERR_INVALID_ARG, "problem %d: sym = %d", idx, d.sym);
-  if (d.eri_pack < 0 || d.eri_pack > 2) return fail(DMET_ERR_INVALID_ARG, "problem %d: eri_pack = %d", idx, d.eri_pack);
+  if (d.eri_pack < 0 || d.eri_pack > 3) return fail(DMET_ERR_INVALID_ARG, "problem %d: eri_pack = %d", idx, d.eri_pack);
   if (d.eri_pack == DMET_PACK_S8 && d.sym != DMET_SYM_REAL)
     return fail(DMET_ERR_INVALID_ARG, "problem %d: 8-fold packing needs sym = DMET_SYM_REAL", idx);
   if (d.check_l != 0 && d.check_l != 1) return fail(DMET_ERR_INVALID_ARG, "problem %d: check_l = %d", idx, d.check_l);
@@ -718,15 +724,19 @@ dmet_status_t eri_s8(dmet_emb_plan_s* P, Prob& pr, const double2* L, const doubl
 dmet_status_t eri_full(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, void* const* out) {
   double2* lq[2] = {P->W->lq_all[0], P->W->lq_all[1]};
   TRY(transform_range(P, pr, L, C, 0, pr.nk, lq, pr.bq));
+  const bool s4 = pr.pack == DMET_PACK_S4;
   for (int blk = 0; blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
     const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
     const long long na2 = (long long)pr.n[sa] * pr.n[sa], nb2 = (long long)pr.n[sb] * pr.n[sb];
+    // S4: the block's full ERI in the workspace first, then packed
+    double2* dst = s4 ? P->W->full : (double2*)out[blk];
+    if (s4) CK(cudaMemsetAsync(dst, 0, (size_t)na2 * nb2 * 16, P->cs));
     for (int q = 0; q < pr.nk; ++q) {
       // (ij|kl) += (1/Nk) sum_P L^q_{P,ij} L^{-q}_{P,kl}
       ZgemmArgs z = zargs();
       z.A = lq[sa] + (long long)q * pr.naux * na2;
       z.B = lq[sb] + (long long)pr.s.neg[q] * pr.naux * nb2;
-      z.D = (double2*)out[blk];
+      z.D = dst;
       z.M = (int)na2;
       z.N = (int)nb2;
       z.K = pr.naux;
@@ -739,14 +749,18 @@ dmet_status_t eri_full(dmet_emb_plan_s* P, Prob& pr, const double2* L, const dou
       Timed t(P, KC_CONTRACT_FULL, 8.0 * (double)na2 * nb2 * pr.naux, 0.0);
       CK(launch_zgemm(z, A_KM, false, B_KN, P->cs));
     }
+    if (s4) {
+      Timed t(P, KC_PACK, 0.0, 16.0 * (double)na2 * nb2 + (double)eri_bytes_of(pr.d, blk));
+      CK(launch_pack_s4(P->W->full, pr.n[sa], pr.n[sb], blk == 1, (double2*)out[blk], P->cs));
+    }
   }
   return DMET_OK;
 }
 
 // Workspace for a q-block size bq.
 struct WsSizes {
-  size_t crep, T, Z, S, X[2], lq_all[2];
-  size_t total() const { return crep + T + Z + S + X[0] + X[1] + lq_all[0] + lq_all[1]; }
+  size_t crep, T, Z, S, X[2], lq_all[2], full;
+  size_t total() const { return crep + T + Z + S + X[0] + X[1] + lq_all[0] + lq_all[1] + full; }
 };
 
 void partition(const Prob& pr, const Tables& t, const std::vector<int>& wts, int bq, std::vector<Block>& out) {
@@ -792,6 +806,7 @@ WsSizes ws_for(const Prob& pr, int bq) {
     if (pr.pack == DMET_PACK_S8) w.X[s] = (size_t)bq * pr.naux * 2 * pr.npair[s] * 8;
     else w.lq_all[s] = (size_t)pr.nk * pr.naux * pr.n[s] * pr.n[s] * 16;
   }
+  if (pr.pack == DMET_PACK_S4) w.full = (size_t)nmax * nmax * nmax * nmax * 16;
   return w;
 }
 
@@ -814,7 +829,7 @@ void free_tables(Tables& t) {
 }
 
 void free_workspace(Workspace& w) {
-  void* ptrs[] = {w.crep, w.T, w.Z, w.S, w.X[0], w.X[1], w.lq_all[0], w.lq_all[1],
+  void* ptrs[] = {w.crep, w.T, w.Z, w.S, w.X[0], w.X[1], w.lq_all[0], w.lq_all[1], w.full,
                   w.Ls, w.Cb[0], w.Cb[1], w.Cc, w.A2, w.ZT, w.Xt[0], w.Xt[1], w.sc};
   for (void* q : ptrs) cudaFree(q);
   w = Workspace();
@@ -1595,6 +1610,7 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     a.T = std::max(a.T, b.T);
     a.Z = std::max(a.Z, b.Z);
     a.S = std::max(a.S, b.S);
+    a.full = std::max(a.full, b.full);
     MixedWs& c = msz[i];
     const MixedWs& d = mneed[p];
     c.Ls = std::max(c.Ls, d.Ls);
@@ -1621,6 +1637,7 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     alloc((void**)&W.T, &W.T_b, need.T);
     alloc((void**)&W.Z, &W.Z_b, need.Z);
     alloc((void**)&W.S, &W.S_b, need.S);
+    alloc((void**)&W.full, &W.full_b, need.full);
     for (int s = 0; s < 2; ++s) {
       alloc((void**)&W.X[s], &W.X_b[s], need.X[s]);
       alloc((void**)&W.lq_all[s], &W.lq_all_b[s], need.lq_all[s]);

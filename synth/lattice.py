@@ -75,6 +75,9 @@ CONFIGS = {
     "hbn_4x4x1": LatticeSpec((4, 4, 1), 26, 220, 104, 1, 0.5, 0.0, 1100, "hbn_4x4x1"),
     "si_4x4x4": LatticeSpec((4, 4, 4), 52, 400, 200, 1, 0.6, 4.0, 2000, "si_4x4x4"),
     "nio_4x4x4_uhf": LatticeSpec((4, 4, 4), 104, 900, 300, 2, 0.6, 0.0, 3000, "nio_4x4x4_uhf"),
+    # a few GB on the device with the NiO-shaped aux basis (900 per cell, K = 14 400): the case the
+    # profiler captures kernel by kernel in place of the 270 GB NiO-shaped run
+    "nio_proxy_4x4x1": LatticeSpec((4, 4, 1), 52, 900, 128, 1, 0.6, 0.0, 3500, "nio_proxy_4x4x1"),
 }
 
 

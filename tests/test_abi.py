@@ -43,6 +43,11 @@ def test_eri_bytes():
     assert dm.dmet_emb_eri_bytes(d, 2) == pb * (pb + 1) // 2 * 8
     d = dm.make_desc((2, 2, 1), 8, 40, (5, 7), n_spin=2, eri_pack=B.DMET_PACK_FULL)
     assert dm.dmet_emb_eri_bytes(d, 1) == 25 * 49 * 16
+    d = dm.make_desc((2, 2, 1), 8, 40, (5, 7), n_spin=2, sym=B.DMET_SYM_NONE, eri_pack=B.DMET_PACK_S4)
+    from oracle import checks
+    assert dm.dmet_emb_eri_bytes(d, 0) == checks.s4_size(5) * 16
+    assert dm.dmet_emb_eri_bytes(d, 1) == 15 * 49 * 16
+    assert dm.dmet_emb_eri_bytes(d, 2) == checks.s4_size(7) * 16
 
 
 @pytest.mark.parametrize("mesh", [(1, 1, 1), (2, 1, 1), (3, 1, 1), (2, 2, 1), (3, 2, 1), (2, 2, 2), (6, 6, 1),
@@ -183,3 +188,10 @@ def test_noalloc_rejects_descriptors_before_touching_the_gpu(fields):
     with pytest.raises(B.DmetError) as e:
         B.dmet_emb_eri_noalloc(d, buf, [buf], [buf])
     assert e.value.status in (B.DMET_ERR_INVALID_ARG, B.DMET_ERR_UNSUPPORTED, B.DMET_ERR_OOM)
+
+
+def test_partial_shard_needs_s8():
+    d = dm.make_desc((2, 2, 1), 8, 40, 16, sym=B.DMET_SYM_NONE, eri_pack=B.DMET_PACK_S4, q_range=(0, 1))
+    with pytest.raises(B.DmetError) as e:
+        dm.dmet_emb_plan(d)
+    assert e.value.status == B.DMET_ERR_UNSUPPORTED
