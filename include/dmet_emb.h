@@ -264,6 +264,26 @@ DMET_API dmet_status_t dmet_emb_bath(dmet_emb_plan_t plan, int32_t problem, int3
 DMET_API dmet_status_t dmet_emb_jk_df(dmet_emb_plan_t plan, int32_t problem, int32_t spin, const void* Lq,
                                       const void* gamma, void* J, void* K);
 
+/* Embedded ERIs with FFTDF (Appendix B, Algorithm 2, Eq. "FFTDF"): the auxiliary set is the plane
+ * waves of the cell's real-space grid. The problem's n_aux must be the number of grid points N_g =
+ * grid[0] grid[1] grid[2] (prec = FP64, FULL packing, full L layout). Arguments (device pointers):
+ *   rho      complex128 [Nk][Nk][N_g][n_ao][n_ao], rho[k1][k2][r][mu][nu] = conj(phi_{mu k1}(r))
+ *            phi_{nu k2}(r), the AO pair densities on the reference cell's grid (r in C order over
+ *            the grid points sum_d (j_d / g_d) a_d) in place of L;
+ *   C        the orbitals per spin, as for dmet_emb_eri;
+ *   grid     host int32 [3], points per lattice vector;  lattice  host double [3][3], rows a_d;
+ *   eri_out  complex128 [n_a][n_a][n_b][n_b] per block (FULL layout of dmet_emb_eri).
+ * For every q: (r|0i 0j) = s_C sum_k1 C^{k1+} rho^{k1,k1+q}(r) C^{k1+q} (the half transforms of
+ * dmet_emb_eri), then exp(-i q.r), the forward DFT over the grid, the Coulomb kernel 4 pi / |q + G|^2
+ * (the plane waves and kernel of dmet_fftdf_plane_waves, 0 at q + G = 0), the inverse DFT,
+ * exp(+i q.r), and (ij|kl) += Omega / (N_g Nk) sum_r w(r)_ij (r|0k 0l)^{-q} with the inverse DFT
+ * normalised by 1/N_g (Omega the cell volume). The DFTs are dense per grid axis (batched complex
+ * GEMMs). FP64 throughout; queued on the plan's stream; grows a plan-owned scratch buffer on first use
+ * (2 N_g n^2 complex values). */
+DMET_API dmet_status_t dmet_emb_eri_fftdf(dmet_emb_plan_t plan, int32_t problem, const void* rho,
+                                          const void* const* C, const int32_t* grid, const double* lattice,
+                                          void* const* eri_out);
+
 /* Frees the plan's device memory, events and tables. Safe on NULL. Waits for the stream. */
 DMET_API dmet_status_t dmet_emb_destroy(dmet_emb_plan_t plan);
 

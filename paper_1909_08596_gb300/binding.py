@@ -122,6 +122,9 @@ def lib() -> ctypes.CDLL:
         L.dmet_emb_bath.restype = st
         L.dmet_emb_jk_df.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P]
         L.dmet_emb_jk_df.restype = st
+        L.dmet_emb_eri_fftdf.argtypes = [_P, ctypes.c_int32, _P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_P)]
+        L.dmet_emb_eri_fftdf.restype = st
         L.dmet_fftdf_plane_waves.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
                                              _P, _P, _P]
@@ -298,6 +301,15 @@ def dmet_emb_bath(plan, gamma_k, C_lo, val, C_out, info=None, problem=0, spin=0)
 def dmet_emb_jk_df(plan, Lq, gamma, J, K, problem=0, spin=0):
     """Density-fitted Coulomb and exchange of gamma from the factors L^q (device tensors; see dmet_emb_jk_df)."""
     _check(lib().dmet_emb_jk_df(_P(plan), problem, spin, ptr(Lq), ptr(gamma), ptr(J), ptr(K)))
+
+
+def dmet_emb_eri_fftdf(plan, rho, C, grid, lattice, eri_out, problem=0):
+    """FFTDF embedded ERIs (Algorithm 2) from pair densities rho [Nk][Nk][N_g][n_ao][n_ao] (device tensors)."""
+    cs = (_P * len(C))(*[ptr(c) for c in C])
+    outs = (_P * len(eri_out))(*[ptr(o) for o in eri_out])
+    gr = (ctypes.c_int32 * 3)(*[int(x) for x in grid])
+    la = (ctypes.c_double * 9)(*[float(x) for x in np.asarray(lattice, dtype=np.float64).ravel()])
+    _check(lib().dmet_emb_eri_fftdf(_P(plan), problem, _P(ptr(rho)), cs, gr, la, outs))
 
 
 def dmet_fftdf_plane_waves(mesh, q, grid, lattice):

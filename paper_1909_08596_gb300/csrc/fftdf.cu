@@ -1,0 +1,62 @@
+// The FFTDF variant of the embedded-ERI transformation (Appendix B, Algorithm 2): the pointwise
+// steps around the Fourier transforms of the transformed pair densities. The transforms themselves
+// are dense DFTs along each grid axis, run as batched complex GEMMs (zgemm_fp64_kernel); FP64.
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace dmet {
+
+namespace {
+
+inline int grid_for(long long total, int threads, int cap) {
+  long long g = (total + threads - 1) / threads;
+  if (g < 1) g = 1;
+  return (int)(g < cap ? g : cap);
+}
+
+// dst[r][x] = s exp(sign * i q.r) src[r][x], q.r = 2 pi sum_d (j_d / g_d)(n_d / N_d) for grid point
+// r = (j_1, j_2, j_3) (C order) and the mesh triple n of q.
+__global__ void fftdf_phase_kernel(const double2* __restrict__ src, double2* __restrict__ dst, int g0, int g1, int g2,
+                                   double f0, double f1, double f2, double sign, double s, long long nx) {
+  const long long total = (long long)g0 * g1 * g2 * nx;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t / nx;
+    const int j2 = (int)(r % g2), j1 = (int)((r / g2) % g1), j0 = (int)(r / ((long long)g1 * g2));
+    // exp(sign * 2 pi i (j0 f0 + j1 f1 + j2 f2)), f_d = n_d / (N_d g_d)
+    double sn, cs;
+    sincospi(2.0 * sign * (j0 * f0 + j1 * f1 + j2 * f2), &sn, &cs);
+    const double2 a = src[t];
+    dst[t] = make_double2(s * (a.x * cs - a.y * sn), s * (a.x * sn + a.y * cs));
+  }
+}
+
+// buf[G][x] *= v[G]
+__global__ void fftdf_kernel_mul(double2* __restrict__ buf, const double* __restrict__ v, long long ng, long long nx) {
+  const long long total = ng * nx;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double w = v[t / nx];
+    buf[t] = make_double2(buf[t].x * w, buf[t].y * w);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_fftdf_phase(const double2* src, double2* dst, const int grid[3], const int nq[3], const int mesh[3],
+                               double sign, double s, long long nx, cudaStream_t st) {
+  const long long total = (long long)grid[0] * grid[1] * grid[2] * nx;
+  fftdf_phase_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, st>>>(
+      src, dst, grid[0], grid[1], grid[2], (double)nq[0] / ((double)mesh[0] * grid[0]),
+      (double)nq[1] / ((double)mesh[1] * grid[1]), (double)nq[2] / ((double)mesh[2] * grid[2]), sign, s, nx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fftdf_kernel_mul(double2* buf, const double* v, long long ng, long long nx, cudaStream_t st) {
+  fftdf_kernel_mul<<<grid_for(ng * nx, 256, 152 * 16), 256, 0, st>>>(buf, v, ng, nx);
+  return cudaGetLastError();
+}
+
+}  // namespace dmet

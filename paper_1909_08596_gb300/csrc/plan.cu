@@ -68,6 +68,7 @@ enum KernelClass {
   KC_FOCK,
   KC_BATH,
   KC_JK_DF,
+  KC_FFTDF,
   KC_COUNT
 };
 const char* const kKcNames[KC_COUNT] = {"check_orbitals",      "check_L",          "gather_orbitals",
@@ -75,7 +76,7 @@ const char* const kKcNames[KC_COUNT] = {"check_orbitals",      "check_L",       
                                         "contract_s8",         "contract_full",    "host_copy",
                                         "split_operands",      "tc_half_transform_1", "tc_half_transform_2",
                                         "tc_pack_split",       "tc_contract",      "embedding_fock",
-                                        "dmet_bath",           "jk_density_fitted"};
+                                        "dmet_bath",           "jk_density_fitted", "fftdf_grid"};
 
 // ------------------------------------------------------------------------------------------
 // Scheduler: momentum-conserving pairs (k1, k1 + q), negation, q weights and the
@@ -295,6 +296,9 @@ struct dmet_emb_plan_s {
   // scratch of dmet_emb_jk_df (grown on demand)
   void* jk_ws = nullptr;
   size_t jk_ws_b = 0;
+  // scratch of dmet_emb_eri_fftdf (grown on demand)
+  void* fft_ws = nullptr;
+  size_t fft_ws_b = 0;
   // Host L transferred block by block on its own stream: the problem being enqueued waits on
   // xev[b] (its contraction block b's pairs have landed) before its first read of L in block b.
   cudaStream_t xs = nullptr;
@@ -855,6 +859,7 @@ void destroy_plan(dmet_emb_plan_s* P) {
   cudaFree(P->fock_ws);
   cudaFree(P->bath_ws);
   cudaFree(P->jk_ws);
+  cudaFree(P->fft_ws);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   for (cudaStream_t st : P->side) cudaStreamDestroy(st);
   if (P->cap) cudaStreamDestroy(P->cap);
@@ -2333,6 +2338,141 @@ dmet_status_t dmet_emb_jk_df(dmet_emb_plan_t P, int32_t problem, int32_t spin, c
     CK(launch_jk_trace(L, d1, nz, n, (const double2*)gamma, v, P->cs));
     CK(launch_jk_accumulate(L, d1, v, Kb, nz, n, 1.0 / nk, (double2*)J, (double2*)K, P->cs));
   }
+  return DMET_OK;
+}
+
+// out[o][k][x] = sum_j F[k][j] in[o][j][x] for o < outer (a dense DFT along one grid axis of length g,
+// as one batched complex GEMM).
+static dmet_status_t dft_axis(dmet_emb_plan_s* P, const double2* F, int g, long long outer, long long inner,
+                              const double2* in, double2* out) {
+  if (inner > INT_MAX || outer > 65535) return fail(DMET_ERR_UNSUPPORTED, "FFTDF grid too large for one DFT launch");
+  ZgemmArgs z = zargs();
+  z.A = F;
+  z.B = in;
+  z.D = out;
+  z.M = g;
+  z.N = (int)inner;
+  z.K = g;
+  z.lda = g;
+  z.ldb = inner;
+  z.sA = 0;
+  z.sB = (long long)g * inner;
+  z.sD = (long long)g * inner;
+  z.dm_lo = inner;
+  z.dn_lo = 1;
+  z.batch = (int)outer;
+  CK(launch_zgemm(z, A_MK, false, B_KN, P->cs));
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_eri_fftdf(dmet_emb_plan_t P, int32_t problem, const void* rho, const void* const* C,
+                                 const int32_t* grid, const double* lattice, void* const* eri_out) {
+  clear_error();
+  if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
+  if (problem < 0 || problem >= (int)P->probs.size()) return fail(DMET_ERR_INVALID_ARG, "problem %d", problem);
+  Prob& pr = P->probs[problem];
+  if (!rho || !C || !grid || !lattice || !eri_out) return fail(DMET_ERR_INVALID_ARG, "NULL pointer argument");
+  if (pr.mixed || pr.pack != DMET_PACK_FULL || pr.d.l_layout != DMET_L_FULL)
+    return fail(DMET_ERR_UNSUPPORTED, "problem %d: the FFTDF ERI needs prec = FP64, FULL packing and the full layout",
+                problem);
+  long long ng = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (grid[d] < 1 || grid[d] > 4096) return fail(DMET_ERR_INVALID_ARG, "grid[%d] = %d", d, grid[d]);
+    ng *= grid[d];
+  }
+  if (ng != pr.naux)
+    return fail(DMET_ERR_INVALID_ARG, "problem %d: n_aux = %d must be the grid's %lld points", problem, pr.naux, ng);
+  const int nblk = pr.nspin == 1 ? 1 : 3;
+  std::vector<const void*> ptrs = {rho};
+  for (int s = 0; s < pr.nspin; ++s) ptrs.push_back(C[s]);
+  for (int b = 0; b < nblk; ++b) ptrs.push_back(eri_out[b]);
+  for (const void* q : ptrs) {
+    if (!q || !is_device_ptr(q)) return fail(DMET_ERR_INVALID_ARG, "dmet_emb_eri_fftdf takes device pointers only");
+    if (!aligned16(q)) return fail(DMET_ERR_ALIGNMENT, "a pointer is not 16-byte aligned");
+  }
+  const int nk = pr.nk;
+  const int nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
+  const long long nx_max = (long long)nmax * nmax;
+  // host tables: DFT matrices per axis (forward, then inverse = conjugate), the Coulomb kernel per q
+  std::vector<double2> F;
+  size_t f_off[3][2];
+  for (int d = 0; d < 3; ++d)
+    for (int inv = 0; inv < 2; ++inv) {
+      f_off[d][inv] = F.size();
+      const int g = grid[d];
+      for (int k = 0; k < g; ++k)
+        for (int j = 0; j < g; ++j) {
+          const double a = 2.0 * M_PI * (double)((long long)j * k % g) / g;
+          F.push_back(make_double2(std::cos(a), inv ? std::sin(a) : -std::sin(a)));
+        }
+    }
+  std::vector<double> vq((size_t)nk * ng);
+  for (int q = 0; q < nk; ++q)
+    TRY(dmet_fftdf_plane_waves(pr.d.mesh, q, grid, lattice, nullptr, vq.data() + (size_t)q * ng, nullptr));
+  const double a0[3] = {lattice[0], lattice[1], lattice[2]}, a1[3] = {lattice[3], lattice[4], lattice[5]},
+               a2[3] = {lattice[6], lattice[7], lattice[8]};
+  const double omega = std::fabs(a0[0] * (a1[1] * a2[2] - a1[2] * a2[1]) - a0[1] * (a1[0] * a2[2] - a1[2] * a2[0]) +
+                                 a0[2] * (a1[0] * a2[1] - a1[1] * a2[0]));
+  // scratch: two [grid][n^2] buffers, the DFT matrices, the kernels
+  const size_t bbuf = (size_t)ng * nx_max * 16, oF = 2 * bbuf, oV = oF + (F.size() * 16 + 255) / 256 * 256;
+  P->cs = P->stream;
+  TRY(ensure(&P->fft_ws, &P->fft_ws_b, oV + vq.size() * 8));
+  char* w = (char*)P->fft_ws;
+  double2* buf0 = (double2*)w;
+  double2* buf1 = (double2*)(w + bbuf);
+  double2* dF = (double2*)(w + oF);
+  double* dV = (double*)(w + oV);
+  CK(cudaMemcpyAsync(dF, F.data(), F.size() * 16, cudaMemcpyHostToDevice, P->cs));
+  CK(cudaMemcpyAsync(dV, vq.data(), vq.size() * 8, cudaMemcpyHostToDevice, P->cs));
+  // Step 1 of Algorithm 2 for every q and spin: (r|0i 0j) = s sum_k1 C^{k1+} rho^{k1,k1+q}(r) C^{k1+q}
+  const double2* Cd[2] = {(const double2*)C[0], pr.nspin == 2 ? (const double2*)C[1] : nullptr};
+  P->W = &P->ws[P->ws_of[problem]];
+  CK(cudaMemsetAsync(P->dstats + 8 * problem, 0, 8 * sizeof(double), P->cs));
+  TRY(run_orbital_checks(P, pr, problem, Cd));
+  double2* lq[2] = {P->W->lq_all[0], P->W->lq_all[1]};
+  TRY(transform_range(P, pr, (const double2*)rho, Cd, 0, nk, lq, pr.bq));
+  for (int b = 0; b < nblk; ++b) CK(cudaMemsetAsync(eri_out[b], 0, eri_bytes_of(pr.d, b), P->cs));
+  const long long g0 = grid[0], g1 = grid[1], g2 = grid[2];
+  for (int sa = 0; sa < pr.nspin; ++sa) {
+    const long long nx = (long long)pr.n[sa] * pr.n[sa];
+    for (int q = 0; q < nk; ++q) {
+      const int nq[3] = {(int)(q / (pr.d.mesh[1] * pr.d.mesh[2])), (int)((q / pr.d.mesh[2]) % pr.d.mesh[1]),
+                         (int)(q % pr.d.mesh[2])};
+      const double2* rq = lq[sa] + (long long)q * ng * nx;
+      Timed t(P, KC_FFTDF, 8.0 * ng * nx * 2.0 * (g0 + g1 + g2), 16.0 * ng * nx * 14, 9);
+      // 2. exp(-i q.r), forward DFT, 4 pi / |q + G|^2, inverse DFT, exp(+i q.r)
+      CK(launch_fftdf_phase(rq, buf0, grid, nq, pr.d.mesh, -1.0, 1.0, nx, P->cs));
+      TRY(dft_axis(P, dF + f_off[0][0], (int)g0, 1, g1 * g2 * nx, buf0, buf1));
+      TRY(dft_axis(P, dF + f_off[1][0], (int)g1, g0, g2 * nx, buf1, buf0));
+      TRY(dft_axis(P, dF + f_off[2][0], (int)g2, g0 * g1, nx, buf0, buf1));
+      CK(launch_fftdf_kernel_mul(buf1, dV + (size_t)q * ng, ng, nx, P->cs));
+      TRY(dft_axis(P, dF + f_off[0][1], (int)g0, 1, g1 * g2 * nx, buf1, buf0));
+      TRY(dft_axis(P, dF + f_off[1][1], (int)g1, g0, g2 * nx, buf0, buf1));
+      TRY(dft_axis(P, dF + f_off[2][1], (int)g2, g0 * g1, nx, buf1, buf0));
+      CK(launch_fftdf_phase(buf0, buf1, grid, nq, pr.d.mesh, 1.0, 1.0, nx, P->cs));
+      // 4. (ij|kl) += Omega / (N_g^2 Nk) sum_r w^q(r)_ij (r|0k 0l)^{-q} (one 1/N_g is the unnormalised DFTs')
+      for (int sb = sa; sb < pr.nspin; ++sb) {
+        const long long nxb = (long long)pr.n[sb] * pr.n[sb];
+        const int blk = pr.nspin == 1 ? 0 : (sa == 0 ? (sb == 0 ? 0 : 1) : 2);
+        ZgemmArgs z = zargs();
+        z.A = buf1;
+        z.B = lq[sb] + (long long)pr.s.neg[q] * ng * nxb;
+        z.D = (double2*)eri_out[blk];
+        z.M = (int)nx;
+        z.N = (int)nxb;
+        z.K = (int)ng;
+        z.lda = nx;
+        z.ldb = nxb;
+        z.dm_lo = nxb;
+        z.dn_lo = 1;
+        z.alpha = omega / ((double)ng * ng * nk);
+        z.beta = 1;
+        Timed tc(P, KC_FFTDF, 8.0 * (double)nx * nxb * ng, 0.0);
+        CK(launch_zgemm(z, A_KM, false, B_KN, P->cs));
+      }
+    }
+  }
+  CK(cudaGetLastError());
   return DMET_OK;
 }
 
