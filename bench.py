@@ -657,7 +657,7 @@ def run_batch(args):
             dm.dmet_emb_graph(plan, True)
             for _ in range(args.warmup):
                 dm.dmet_emb_eri(plan, Ls, Cds, outs)
-            steps = args.steps if prec != "fp64" else min(args.steps, args.fp64_steps)
+            steps = args.steps if prec != "fp64" else min(args.steps, args.fp64_steps if args.fp64_steps > 0 else 3)
             l0 = dm.dmet_emb_launch_count(plan)
             stream.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -2268,38 +2268,44 @@ dmet_status_t dmet_emb_jk_df(dmet_emb_plan_t P, int32_t problem, int32_t spin, c
   const long long per = 2 * nn * 16 + 16 + 2 * (long long)sizeof(int4);
   const int chunk = (int)std::max(1LL, std::min({nz_all, (1LL << 30) / per, 65535LL}));
   const size_t oW = 0, oKb = oW + (size_t)chunk * nn * 16, ov = oKb + (size_t)chunk * nn * 16,
-               ot1 = ov + ((size_t)chunk * 16 + 255) / 256 * 256, ot2 = ot1 + (size_t)chunk * sizeof(int4);
+               ot1 = ov + ((size_t)chunk * 16 + 255) / 256 * 256, ot2 = ot1 + (size_t)chunk * sizeof(int4),
+               ot3 = ot2 + (size_t)chunk * sizeof(int4);
   P->cs = P->stream;
-  TRY(ensure(&P->jk_ws, &P->jk_ws_b, ot2 + (size_t)chunk * sizeof(int4)));
+  TRY(ensure(&P->jk_ws, &P->jk_ws_b, ot3 + (size_t)chunk * sizeof(int4)));
   char* w = (char*)P->jk_ws;
   double2* W = (double2*)(w + oW);
   double2* Kb = (double2*)(w + oKb);
   double2* v = (double2*)(w + ov);
   int4* d1 = (int4*)(w + ot1);
   int4* d2 = (int4*)(w + ot2);
+  int4* d3 = (int4*)(w + ot3);
   const double2* L = (const double2*)Lq;
   // 8 flops per complex multiply-add: two n^3 products and the two n^2 reductions per entry
   const int nchunks = (int)((nz_all + chunk - 1) / chunk);
   Timed t(P, KC_JK_DF, 8.0 * nz_all * (2.0 * nn * n + 2.0 * nn), 16.0 * nz_all * nn * 5, 4 * nchunks);
   CK(cudaMemsetAsync(J, 0, (size_t)nn * 16, P->cs));
   CK(cudaMemsetAsync(K, 0, (size_t)nn * 16, P->cs));
-  std::vector<int4> t1(chunk), t2(chunk);
+  // (the batched GEMMs are written transposed: the FP64 GEMM kernel takes A K-major)
+  std::vector<int4> t1(chunk), t2(chunk), t3(chunk);
   for (long long z0 = 0; z0 < nz_all; z0 += chunk) {
     const int nz = (int)std::min<long long>(chunk, nz_all - z0);
     for (int i = 0; i < nz; ++i) {
       const long long z = z0 + i;
       const int q = (int)(z / naux), Pp = (int)(z % naux);
       const int mz = pr.s.neg[q] * naux + Pp;  // the -q factor of the same aux function
-      t1[i] = make_int4((int)z, mz, i, n);
-      t2[i] = make_int4(i, mz, i, n);
+      t1[i] = make_int4(0, (int)z, i, n);       // W: A = gamma (shared), B = L^q_P, D = W[i]
+      t2[i] = make_int4(mz, i, i, n);           // Kb: A = L^{-q}_P, B = W[i], D = Kb[i]
+      t3[i] = make_int4((int)z, mz, i, n);      // trace and sums: L^q_P, L^{-q}_P
     }
     CK(cudaMemcpyAsync(d1, t1.data(), nz * sizeof(int4), cudaMemcpyHostToDevice, P->cs));
     CK(cudaMemcpyAsync(d2, t2.data(), nz * sizeof(int4), cudaMemcpyHostToDevice, P->cs));
+    CK(cudaMemcpyAsync(d3, t3.data(), nz * sizeof(int4), cudaMemcpyHostToDevice, P->cs));
     {
-      // W[i] = L^q_P gamma
+      // W[i][a][b] = (L^q_P gamma)_ab, as W^T = gamma^T (L^q_P)^T: m = b, n = a, k = l;
+      // opA(b, l) = gamma[l][b], opB(l, a) = L[a][l], stored at a n + b
       ZgemmArgs z = zargs();
-      z.A = L;
-      z.B = (const double2*)gamma;
+      z.A = (const double2*)gamma;
+      z.B = L;
       z.D = W;
       z.tab = d1;
       z.M = n;
@@ -2307,19 +2313,20 @@ dmet_status_t dmet_emb_jk_df(dmet_emb_plan_t P, int32_t problem, int32_t spin, c
       z.K = n;
       z.lda = n;
       z.ldb = n;
-      z.sA = nn;
-      z.sB = 0;
+      z.sA = 0;
+      z.sB = nn;
       z.sD = nn;
-      z.dm_lo = n;
-      z.dn_lo = 1;
+      z.dm_lo = 1;
+      z.dn_lo = n;
       z.batch = nz;
-      CK(launch_zgemm(z, A_MK, false, B_KN, P->cs));
+      CK(launch_zgemm(z, A_KM, false, B_NK, P->cs));
     }
     {
-      // Kb[i] = W[i] L^{-q}_P
+      // Kb[i][a][b] = (W[i] L^{-q}_P)_ab, as Kb^T = (L^{-q}_P)^T W[i]^T: m = b, n = a, k = l;
+      // opA(b, l) = L^{-q}[l][b], opB(l, a) = W[a][l], stored at a n + b
       ZgemmArgs z = zargs();
-      z.A = W;
-      z.B = L;
+      z.A = L;
+      z.B = W;
       z.D = Kb;
       z.tab = d2;
       z.M = n;
@@ -2330,38 +2337,39 @@ dmet_status_t dmet_emb_jk_df(dmet_emb_plan_t P, int32_t problem, int32_t spin, c
       z.sA = nn;
       z.sB = nn;
       z.sD = nn;
-      z.dm_lo = n;
-      z.dn_lo = 1;
+      z.dm_lo = 1;
+      z.dn_lo = n;
       z.batch = nz;
-      CK(launch_zgemm(z, A_MK, false, B_KN, P->cs));
+      CK(launch_zgemm(z, A_KM, false, B_NK, P->cs));
     }
-    CK(launch_jk_trace(L, d1, nz, n, (const double2*)gamma, v, P->cs));
-    CK(launch_jk_accumulate(L, d1, v, Kb, nz, n, 1.0 / nk, (double2*)J, (double2*)K, P->cs));
+    CK(launch_jk_trace(L, d3, nz, n, (const double2*)gamma, v, P->cs));
+    CK(launch_jk_accumulate(L, d3, v, Kb, nz, n, 1.0 / nk, (double2*)J, (double2*)K, P->cs));
   }
   return DMET_OK;
 }
 
 // out[o][k][x] = sum_j F[k][j] in[o][j][x] for o < outer (a dense DFT along one grid axis of length g,
-// as one batched complex GEMM).
+// as one batched complex GEMM with m = x, n = k, k = j: opA(x, j) = in[o][j][x] (K-major),
+// opB(j, k) = F[k][j], stored at out[o][k][x]).
 static dmet_status_t dft_axis(dmet_emb_plan_s* P, const double2* F, int g, long long outer, long long inner,
                               const double2* in, double2* out) {
   if (inner > INT_MAX || outer > 65535) return fail(DMET_ERR_UNSUPPORTED, "FFTDF grid too large for one DFT launch");
   ZgemmArgs z = zargs();
-  z.A = F;
-  z.B = in;
+  z.A = in;
+  z.B = F;
   z.D = out;
-  z.M = g;
-  z.N = (int)inner;
+  z.M = (int)inner;
+  z.N = g;
   z.K = g;
-  z.lda = g;
-  z.ldb = inner;
-  z.sA = 0;
-  z.sB = (long long)g * inner;
+  z.lda = inner;
+  z.ldb = g;
+  z.sA = (long long)g * inner;
+  z.sB = 0;
   z.sD = (long long)g * inner;
-  z.dm_lo = inner;
-  z.dn_lo = 1;
+  z.dm_lo = 1;
+  z.dn_lo = inner;
   z.batch = (int)outer;
-  CK(launch_zgemm(z, A_MK, false, B_KN, P->cs));
+  CK(launch_zgemm(z, A_KM, false, B_NK, P->cs));
   return DMET_OK;
 }
 
