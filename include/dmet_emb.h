@@ -69,9 +69,13 @@ typedef enum {
 
 /* Arithmetic of the transforms and the contraction. The tensor-core precisions split every FP64
  * operand into slices the tensor cores (tcgen05) multiply exactly, accumulate in FP32 within short
- * K segments and across segments in an exact two-float sum, and write FP64 results; they need
- * sym = REAL and 8-fold packing. Errors against FP64 (relative Frobenius, measured): see the
- * library's documentation; BF16X3 and FP16X2 meet 1e-6, TF32 does not. */
+ * K segments and across segments in an exact two-float sum, and write FP64 results. Real orbitals
+ * (sym = REAL) need 8-fold packing; general orbitals (sym = NONE) take FULL or S4 packing, every q
+ * contracted as one real GEMM of the bra rows (Re, Im of L^q_ij) against the ket rows of
+ * L^{-q}_kl arranged so that output column 2 kl + c is component c of (ij|kl), only for kl <= ij
+ * in the same-spin blocks ((kl|ij) = (ij|kl) supplies the rest). Errors against FP64 (relative
+ * Frobenius, measured): see the library's documentation; BF16X3 and FP16X2 meet 1e-6, TF32 does
+ * not. */
 typedef enum {
   DMET_PREC_FP64 = 0,    /* every product and sum in IEEE FP64 */
   DMET_PREC_BF16X3 = 1,  /* three bf16 slices per operand, six slice products per multiply-add */

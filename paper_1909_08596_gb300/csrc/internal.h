@@ -176,8 +176,19 @@ cudaError_t launch_tc_rect(int prec, const CUtensorMap& A, const CUtensorMap& B,
 cudaError_t launch_tc_packed(int prec, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                              const tc::Segment* segs, double* out, double scale, void* part, const tc::TcCtl& ctl,
                              const float* fac, cudaStream_t s);
-// L^q of one slot from the step-2 output (two-float pairs): s (Z + Z^T), conjugated if conj.
-cudaError_t launch_lq_from_pairs(const void* ZT, int naux, int n, double s, int conj, double2* Lq, cudaStream_t st);
+// L^q of one slot from the step-2 output (two-float pairs): s (Z + Z^T) (pair = 1, real orbitals) or
+// s Z (pair = 0), conjugated if conj.
+cudaError_t launch_lq_from_pairs(const void* ZT, int naux, int n, double s, int conj, int pair, double2* Lq,
+                                 cudaStream_t st);
+// The contraction operand of general (complex) orbitals from the step-2 output of slots q0 .. q0+nq-1
+// (bra rows ij in the K block of q, ket rows n^2 + 2 kl + c in the K block of -q; mixed.cu).
+cudaError_t launch_pack_cplx(int prec, const void* ZT, int nq, int naux, int n, int q0, const int* neg, void* Xt,
+                             long long sstride, long long Rtot, const float* sx, cudaStream_t s);
+// One same-spin block of complex ERIs, (ij|kl) as (re, im) doubles at out[ij * 2 n2 + 2 kl + c], from
+// the tiles with kl <= ij (the others by (kl|ij) = (ij|kl)).
+cudaError_t launch_tc_herm(int prec, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+                           const tc::Segment* segs, double* out, long long n2, double scale, const tc::TcCtl& ctl,
+                           const float* fac, cudaStream_t s);
 // Sums the K parts of the split tiles of a packed contraction (the parts' jobs: jobs[0 .. ntiles * f)).
 cudaError_t launch_combine_parts(const tc::TcJob* jobs, int ntiles, int f, const void* part, double* out, double scale,
                                  cudaStream_t s);

@@ -230,6 +230,72 @@ __global__ void __launch_bounds__(256) pack_split_kernel(const float2* __restric
   }
 }
 
+// General (complex) orbitals: the contraction operand of spin s holds 3 n^2 rows of Rtot columns.
+// Rows ij = i n + j (the bra side) carry, in the K block of q (q * 2 naux), Re L^q_{P,ij} at P and
+// Im L^q_{P,ij} at naux + P. Rows n^2 + 2 kl + c (the ket side) carry, in the K block of -q, the
+// row of L^q_{P,kl} = y that turns the real dot product into component c of x y for the bra value
+// x = L^{-q}: (Re y, -Im y) for c = 0 and (Im y, Re y) for c = 1, since Re(x y) = xr yr - xi yi and
+// Im(x y) = xr yi + xi yr. Then (ij|kl) = (1/Nk) sum_q sum_P L^q_ij L^{-q}_kl is one real GEMM of
+// the bra rows against the ket rows, whose output row ij is (ij|kl) as (re, im) doubles over kl.
+// Z_ij of slot sl is the two-float pair ZT[sl][(P n + j) n + i] (re.hi, re.lo, im.hi, im.lo); the
+// factor s of L^q = s Z is applied, squared, to the contraction's output. One block stages a tile
+// of 32 P x 32 i at one j (reads coalesced over i), then writes runs of 32 consecutive P per row.
+__device__ __forceinline__ float neg_of(float x) { return -x; }
+__device__ __forceinline__ __half neg_of(__half x) { return __hneg(x); }
+__device__ __forceinline__ __nv_bfloat16 neg_of(__nv_bfloat16 x) { return __hneg(x); }
+
+constexpr int PC_T = 32;
+template <class PREC>
+__global__ void __launch_bounds__(256) pack_cplx_kernel(const float4* __restrict__ ZT, int naux, int n, int nq,
+                                                        int q0, const int* __restrict__ neg,
+                                                        typename PREC::T* __restrict__ Xt, long long sstride,
+                                                        long long Rtot, const float* __restrict__ psx) {
+  using T = typename PREC::T;
+  const float sx = PREC::kScaled ? *psx : 1.f;
+  __shared__ float4 z[PC_T][PC_T + 1];  // [i][P]
+  const int itiles = (n + PC_T - 1) / PC_T;
+  const int i0 = (blockIdx.x % itiles) * PC_T, j = blockIdx.x / itiles;
+  const int P0 = blockIdx.y * PC_T;
+  const int sl = blockIdx.z;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const float4* zs = ZT + (long long)sl * naux * n * n;
+#pragma unroll
+  for (int r = 0; r < PC_T / 8; ++r) {
+    const int pl = ty + r * 8, P = P0 + pl, i = i0 + tx;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (P < naux && i < n) v = zs[((long long)P * n + j) * n + i];
+    z[tx][pl] = v;
+  }
+  __syncthreads();
+  const int q = q0 + sl, P = P0 + tx;
+  if (P >= naux) return;
+  const long long kb = (long long)q * 2 * naux + P, kn = (long long)neg[q] * 2 * naux + P;
+  const long long n2 = (long long)n * n;
+#pragma unroll
+  for (int r = 0; r < PC_T / 8; ++r) {
+    const int il = ty + r * 8, i = i0 + il;
+    if (i >= n) break;
+    const float4 v = z[il][tx];
+    T re[3], im[3];
+    PREC::split(v.x * sx, v.y * sx, re);
+    PREC::split(v.z * sx, v.w * sx, im);
+    const long long ij = (long long)i * n + j;
+    T* a = Xt + ij * Rtot;
+    T* b0 = Xt + (n2 + 2 * ij) * Rtot;
+    T* b1 = b0 + Rtot;
+#pragma unroll
+    for (int t = 0; t < PREC::kSlices; ++t) {
+      const long long o = t * sstride;
+      a[o + kb] = re[t];
+      a[o + kb + naux] = im[t];
+      b0[o + kn] = re[t];
+      b0[o + kn + naux] = neg_of(im[t]);
+      b1[o + kn] = im[t];
+      b1[o + kn + naux] = re[t];
+    }
+  }
+}
+
 // Step-1 output functor: element (m = (P, mu) of entry e, n = (j, p)) -> slices of A2 at
 // row o2 + P * nemb + j, column k = o3 + 2 mu + p (o2 = slot * naux * nemb, o3 = r * 2 nao).
 // A2 keeps the slices of a row side by side in each K block of BK elements,
@@ -439,14 +505,15 @@ __global__ void make_scales_kernel(MixScales* sc, int nao, int nrep_max, int nsp
 
 // Lq[P][i][j] = s (Z_ij + Z_ji) (conj: its complex conjugate) from the step-2 output of one slot,
 // Z_ij = (re, im), each a two-float (hi, lo) at ZT[(P n + j) n + i] (a float4), summed exactly in FP64.
-__global__ void lq_from_pairs_kernel(const float4* __restrict__ ZT, int naux, int n, double s, double sim,
+__global__ void lq_from_pairs_kernel(const float4* __restrict__ ZT, int naux, int n, double s, double sim, int pair,
                                      double2* __restrict__ Lq) {
   const long long nn = (long long)n * n, total = (long long)naux * nn;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
        x += (long long)gridDim.x * blockDim.x) {
     const long long P = x / nn;
     const int i = (int)((x % nn) / n), j = (int)(x % n);
-    const float4 a = ZT[(P * n + j) * n + i], b = ZT[(P * n + i) * n + j];
+    const float4 a = ZT[(P * n + j) * n + i];
+    const float4 b = pair ? ZT[(P * n + i) * n + j] : make_float4(0.f, 0.f, 0.f, 0.f);
     const double re = ((double)a.x + (double)a.y) + ((double)b.x + (double)b.y);
     const double im = ((double)a.z + (double)a.w) + ((double)b.z + (double)b.w);
     Lq[x] = make_double2(s * re, sim * im);
@@ -455,10 +522,11 @@ __global__ void lq_from_pairs_kernel(const float4* __restrict__ ZT, int naux, in
 
 }  // namespace
 
-cudaError_t launch_lq_from_pairs(const void* ZT, int naux, int n, double s, int conj, double2* Lq, cudaStream_t st) {
+cudaError_t launch_lq_from_pairs(const void* ZT, int naux, int n, double s, int conj, int pair, double2* Lq,
+                                 cudaStream_t st) {
   const long long total = (long long)naux * n * n;
   lq_from_pairs_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, st>>>((const float4*)ZT, naux, n, s, conj ? -s : s,
-                                                                        Lq);
+                                                                        pair, Lq);
   return cudaGetLastError();
 }
 
@@ -552,6 +620,19 @@ cudaError_t launch_pack_split(int prec, const void* ZT, int nq, int naux, int n,
   });
 }
 
+cudaError_t launch_pack_cplx(int prec, const void* ZT, int nq, int naux, int n, int q0, const int* neg, void* Xt,
+                             long long sstride, long long Rtot, const float* sx, cudaStream_t s) {
+  const long long gx = (long long)((n + PC_T - 1) / PC_T) * n;
+  if (gx > 0x7fffffffLL || nq > 65535 || (naux + PC_T - 1) / PC_T > 65535) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)gx, (naux + PC_T - 1) / PC_T, nq);
+  return with_prec(prec, [&](auto tag) -> cudaError_t {
+    using P = decltype(tag);
+    pack_cplx_kernel<P><<<grid, 256, 0, s>>>((const float4*)ZT, naux, n, nq, q0, neg, (typename P::T*)Xt, sstride,
+                                             Rtot, sx);
+    return cudaGetLastError();
+  });
+}
+
 cudaError_t launch_tc_split_t(int prec, int bn, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs,
                               int njobs, const tc::Segment* segs, void* out, long long K2, int nao, int nemb,
                               const tc::TcCtl& ctl, const float* fac, cudaStream_t s) {
@@ -580,6 +661,17 @@ cudaError_t launch_tc_rect(int prec, const CUtensorMap& A, const CUtensorMap& B,
   return with_prec(prec, [&](auto tag) -> cudaError_t {
     using P = decltype(tag);
     return launch_tc_bn<P, 128, tc::EpiRect>(A, B, jobs, njobs, segs, p, ctl, fac, s);
+  });
+}
+
+cudaError_t launch_tc_herm(int prec, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
+                           const tc::Segment* segs, double* out, long long n2, double scale, const tc::TcCtl& ctl,
+                           const float* fac, cudaStream_t s) {
+  const float sh = (float)scale;
+  tc::EpiHerm::Params p{out, 2 * n2, sh, (float)(scale - (double)sh)};
+  return with_prec(prec, [&](auto tag) -> cudaError_t {
+    using P = decltype(tag);
+    return launch_tc_bn<P, 128, tc::EpiHerm>(A, B, jobs, njobs, segs, p, ctl, fac, s);
   });
 }
 

@@ -200,6 +200,11 @@ struct MixedPlan {
   // the correction sum read back after every segment (at the NiO-shaped workload, K = 57 600: the
   // alpha-beta block's error fell from 1.5e-6 with whole-job correction runs to 3.8e-7, at +3% time).
   int kseg_def = 128, kseg1_def = 64, crun_def = 1;
+  // General (complex) orbitals: every q is contracted (weight 1, 2 n_aux K rows each: Re, Im), and
+  // the contraction operand of spin s has 3 n_s^2 rows (bra rows ij, then ket rows 2 kl + c);
+  // real orbitals: n_pair rows. xrows[s] is that row count.
+  bool cplx = false;
+  long long xrows[2] = {0, 0};
   int bn1 = 128, bn2 = 128;            // output tile widths of the two transform GEMMs
   long long Rtot = 0, R1 = 0;
   std::vector<Block> blocks;           // contraction order, q-blocks within one weight class
@@ -392,8 +397,9 @@ dmet_status_t validate_desc(const dmet_emb_desc_t& d, int idx) {
     return fail(DMET_ERR_INVALID_ARG, "problem %d: prec = %d", idx, d.prec);
   if (d.prec != DMET_PREC_FP64) {
     const int pack = d.eri_pack == DMET_PACK_AUTO ? (d.sym == DMET_SYM_REAL ? DMET_PACK_S8 : DMET_PACK_FULL) : d.eri_pack;
-    if (d.sym != DMET_SYM_REAL || pack != DMET_PACK_S8)
-      return fail(DMET_ERR_UNSUPPORTED, "problem %d: the tensor-core paths need sym = REAL and 8-fold packing", idx);
+    if (d.sym == DMET_SYM_REAL && pack != DMET_PACK_S8)
+      return fail(DMET_ERR_UNSUPPORTED, "problem %d: the tensor-core paths write real orbitals' ERIs 8-fold packed",
+                  idx);
   }
   const long long nmax = std::max(d.n_emb[0], d.n_spin == 2 ? d.n_emb[1] : 0);
   if ((long long)d.n_aux * nmax > INT_MAX / 2 || (long long)d.n_aux * d.n_ao > INT_MAX / 2)
@@ -798,8 +804,9 @@ WsSizes ws_for(const Prob& pr, int bq) {
   std::memset(&w, 0, sizeof(w));
   const int nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
   w.S = (size_t)pr.orth_groups * nmax * nmax * 16;
-  // The split-BF16 path needs only the orthonormality product here; dmet_emb_transform_3idx (FP64)
-  // grows its transform buffers on first use (mixed_transform_ws).
+  if (pr.pack == DMET_PACK_S4) w.full = (size_t)nmax * nmax * nmax * nmax * 16;
+  // The tensor-core paths need only the orthonormality product here (and the full block before
+  // 4-fold packing).
   if (pr.mixed) return w;
   int E = max_entries(pr.nat, bq);
   if (pr.pack == DMET_PACK_S8) E = std::max(E, max_entries(pr.con, bq));
@@ -810,7 +817,6 @@ WsSizes ws_for(const Prob& pr, int bq) {
     if (pr.pack == DMET_PACK_S8) w.X[s] = (size_t)bq * pr.naux * 2 * pr.npair[s] * 8;
     else w.lq_all[s] = (size_t)pr.nk * pr.naux * pr.n[s] * pr.n[s] * 16;
   }
-  if (pr.pack == DMET_PACK_S4) w.full = (size_t)nmax * nmax * nmax * nmax * 16;
   return w;
 }
 
@@ -939,13 +945,17 @@ void build_mixed(Prob& pr) {
   for (int q : pr.con.order) nrep_max = std::max(nrep_max, pr.s.nrep[q]);
   m.K2 = (int)padk(2LL * nrep_max * nao);
   m.blocks = pr.con_blocks;
+  m.cplx = pr.d.sym == DMET_SYM_NONE;
+  for (int s = 0; s < 2; ++s) m.xrows[s] = s < pr.nspin ? (m.cplx ? 3LL * pr.n[s] * pr.n[s] : pr.npair[s]) : 0;
   int n1 = 0, n2 = 0;
   for (int q : pr.con.order) (pr.s.qw[q] == 1 ? n1 : n2)++;
-  m.R1 = padk((long long)n1 * naux);
+  // K rows of a q: n_aux for a weight-1 q of real orbitals, 2 n_aux (Re, Im) otherwise
+  const long long kq1 = m.cplx ? 2LL * naux : naux;
+  m.R1 = padk((long long)n1 * kq1);
   m.Rtot = m.R1 + padk((long long)n2 * 2 * naux);
   m.row_base.clear();
   for (const Block& b : m.blocks)
-    m.row_base.push_back(b.w == 1 ? (long long)b.b0 * naux : m.R1 + (long long)(b.b0 - n1) * 2 * naux);
+    m.row_base.push_back(b.w == 1 ? (long long)b.b0 * kq1 : m.R1 + (long long)(b.b0 - n1) * 2 * naux);
   m.segs.clear();
   m.jobs.clear();
   // segments [0, n1seg): the K range of step 1
@@ -1024,7 +1034,25 @@ void build_mixed(Prob& pr) {
     }
     m.A2_rows[sp] = (long long)pr.bq * naux * n;
   }
-  for (int blk = 0; blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
+  for (int blk = 0; m.cplx && blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
+    // General orbitals: bra rows ij (n_a^2) against ket rows 2 kl + c (2 n_b^2, from row n_b^2 of
+    // the ket spin's operand). Same-spin blocks: only the tiles that hold some kl <= ij.
+    const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
+    const long long ma = (long long)pr.n[sa] * pr.n[sa], nb = 2LL * pr.n[sb] * pr.n[sb];
+    m.jc_off[blk] = (int)m.jobs.size();
+    m.jc_split_n[blk] = 0;
+    m.jc_split_f[blk] = 1;
+    const int mts = cdiv(ma, T), nts = cdiv(nb, T), band = 8;
+    for (int m0b = 0; m0b < mts; m0b += band)
+      for (int nt = 0; nt < nts; ++nt)
+        for (int mt = m0b; mt < std::min(mts, m0b + band); ++mt) {
+          if (blk != 1 && (long long)nt * (T / 2) > (long long)mt * T + T - 1) continue;
+          m.jobs.push_back({mt * T, (int)(nb / 2 + (long long)nt * T), (int)std::min<long long>(T, ma - (long long)mt * T),
+                            (int)std::min<long long>(T, nb - (long long)nt * T), sc_off, sc_cnt, mt * T, nt * T, 0, 0});
+        }
+    m.jc_cnt[blk] = (int)m.jobs.size() - m.jc_off[blk];
+  }
+  for (int blk = 0; !m.cplx && blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
     const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
     const long long pa = pr.npair[sa], pb = pr.npair[sb];
     m.jc_off[blk] = (int)m.jobs.size();
@@ -1081,9 +1109,17 @@ void build_mixed(Prob& pr) {
       m.useful_t1 += 8.0 * n * naux * nao * nao * pr.s.nrep[q];
       m.useful_t2 += 8.0 * n * naux * n * nao * pr.s.nrep[q];
     }
-    m.useful_c += (double)pr.npair[sp] * (pr.npair[sp] + 1.0) * K;
+    if (m.cplx) {
+      // complex products over every q: 8 flops per multiply-add of (ij|kl) over the n_aux terms
+      const double n2 = (double)pr.n[sp] * pr.n[sp];
+      m.useful_c += 8.0 * n2 * n2 * pr.naux * (double)pr.con.order.size();
+    } else {
+      m.useful_c += (double)pr.npair[sp] * (pr.npair[sp] + 1.0) * K;
+    }
   }
-  if (pr.nspin == 2) m.useful_c += 2.0 * pr.npair[0] * pr.npair[1] * K;
+  if (pr.nspin == 2)
+    m.useful_c += m.cplx ? 8.0 * pr.n[0] * pr.n[0] * (double)pr.n[1] * pr.n[1] * pr.naux * (double)pr.con.order.size()
+                         : 2.0 * pr.npair[0] * pr.npair[1] * K;
   (void)nk;
 }
 
@@ -1111,7 +1147,7 @@ MixedWs mixed_ws(const Prob& pr) {
   w.Ls = se * m.Ls_rows * m.K1;
   for (int s = 0; s < 2; ++s) {
     w.Cb[s] = s < pr.nspin ? se * pr.nk * 2 * pr.n[s] * m.K1 : 0;
-    w.Xt[s] = s < pr.nspin ? se * pr.npair[s] * m.Rtot : 0;
+    w.Xt[s] = s < pr.nspin ? se * m.xrows[s] * m.Rtot : 0;
   }
   w.Cc = se * pr.bq * 2 * nmax * m.K2;
   w.A2 = se * pr.bq * pr.naux * nmax * m.K2;
@@ -1135,7 +1171,7 @@ dmet_status_t mixed_maps(dmet_emb_plan_s* P, const Prob& pr, MixedMaps& mm) {
     CK(make_tmap_3d(&mm.Cb[s], pc, P->W->Cb[s], m.K1, pr.nk * 2 * n, ns, m.K1, pr.nk * 2 * n * m.K1, m.bn1));
     CK(make_tmap_3d(&mm.Cc[s], pc, P->W->Cc, m.K2, (long long)pr.bq * 2 * n, ns, m.K2, cc_rows * m.K2, m.bn2));
     CK(make_tmap_interleaved(&mm.A2[s], pc, P->W->A2, m.K2, (long long)pr.bq * pr.naux * n, ns, T));
-    CK(make_tmap_3d(&mm.Xt[s], pc, P->W->Xt[s], m.Rtot, pr.npair[s], ns, m.Rtot, pr.npair[s] * m.Rtot, T));
+    CK(make_tmap_3d(&mm.Xt[s], pc, P->W->Xt[s], m.Rtot, m.xrows[s], ns, m.Rtot, m.xrows[s] * m.Rtot, T));
   }
   return DMET_OK;
 }
@@ -1162,7 +1198,8 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
   const long long cc_rows = (long long)pr.bq * 2 * nmax;
   int n1 = 0;
   for (int q : pr.con.order) n1 += pr.s.qw[q] == 1;
-  const long long used1 = (long long)n1 * pr.naux, used2 = ((long long)pr.con.order.size() - n1) * 2 * pr.naux;
+  const long long used1 = (long long)n1 * pr.naux * (m.cplx ? 2 : 1);
+  const long long used2 = ((long long)pr.con.order.size() - n1) * 2 * pr.naux;
   const int pc = m.prec;
   const double se = (double)m.ns * m.esz;  // bytes of all slices of one operand element
   MixScales* sc = P->W->sc;
@@ -1180,7 +1217,7 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
   for (int s = 0; s < pr.nspin; ++s) {
     // padding rows of the contraction operand read as zeros
     const size_t pitch = (size_t)m.Rtot * m.esz;
-    const long long h = (long long)m.ns * pr.npair[s];
+    const long long h = (long long)m.ns * m.xrows[s];
     if (!req && m.R1 > used1)
       CK(cudaMemset2DAsync((char*)P->W->Xt[s] + used1 * m.esz, pitch, 0, (size_t)(m.R1 - used1) * m.esz, h, P->cs));
     if (!req && m.Rtot - m.R1 > used2)
@@ -1241,11 +1278,16 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
           const long long slot_el = (long long)pr.naux * n * n;
           Timed t(P, KC_PACK, 0.0, 16.0 * slot_el + 16.0 * slot_el);
           CK(launch_lq_from_pairs((const char*)P->W->ZT + (size_t)(sl - bl.b0) * slot_el * 2 * sizeof(float2), pr.naux,
-                                  n, pr.lq_scale, req->conj[i], req->out[s] + i * slot_el, P->cs));
+                                  n, pr.lq_scale, req->conj[i], m.cplx ? 0 : 1, req->out[s] + i * slot_el, P->cs));
         }
         continue;
       }
-      {
+      if (m.cplx) {
+        // every q of a general-orbital problem is its own slot (q = slot)
+        Timed t(P, KC_TC_PACK, 0.0, 16.0 * nq * pr.naux * (double)n * n + se * 6.0 * nq * pr.naux * (double)n * n);
+        CK(launch_pack_cplx(pc, P->W->ZT, nq, pr.naux, n, pr.con.order[bl.b0], pr.d_neg, P->W->Xt[s],
+                            m.xrows[s] * m.Rtot, m.Rtot, &sc->sX[s], P->cs));
+      } else {
         const int nc = bl.w == 1 ? 1 : 2;
         Timed t(P, KC_TC_PACK, 0.0, 16.0 * nq * pr.naux * (double)n * n + se * nq * pr.naux * nc * pr.npair[s]);
         CK(launch_pack_split(pc, P->W->ZT, nq, pr.naux, n, nc, P->W->Xt[s], pr.npair[s] * m.Rtot, m.Rtot,
@@ -1256,9 +1298,33 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
   if (req) return DMET_OK;
   long long K = 0;
   for (int q : pr.con.order) K += (long long)pr.naux * (pr.s.qw[q] == 1 ? 1 : 2);
-  // The operand holds Z + Z^T; L^q = s (Z + Z^T), so the product carries s^2, and 1/Nk.
+  // The operand holds Z + Z^T (general orbitals: Z); L^q = s (Z + Z^T) (s Z), so the product
+  // carries s^2, and 1/Nk.
   const double oscale = pr.lq_scale * pr.lq_scale / pr.nk;
-  for (int blk = 0; blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
+  for (int blk = 0; m.cplx && blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
+    const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
+    const long long na2 = (long long)pr.n[sa] * pr.n[sa], nb2 = (long long)pr.n[sb] * pr.n[sb];
+    const double fl = 8.0 * (double)na2 * nb2 * pr.naux * (double)pr.con.order.size();
+    // S4: the block's full ERI in the workspace first, then packed
+    const bool s4 = pr.pack == DMET_PACK_S4;
+    double* dst = s4 ? (double*)P->W->full : (double*)out[blk];
+    {
+      // algorithmic bytes: the bra rows' and ket rows' slices read once, the complex block written once
+      const double by = se * m.Rtot * (double)(na2 + 2 * nb2) + 16.0 * (double)na2 * nb2;
+      Timed t(P, KC_TC_CONTRACT, fl, by, 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk], tc::kTile));
+      if (blk == 1)
+        CK(launch_tc_rect(pc, mm.Xt[0], mm.Xt[1], m.d_jobs + m.jc_off[1], m.jc_cnt[1], m.d_segs, dst, 2 * nb2, oscale,
+                          P->ctl(), scaled ? &sc->fc[1] : nullptr, P->cs));
+      else
+        CK(launch_tc_herm(pc, mm.Xt[sa], mm.Xt[sa], m.d_jobs + m.jc_off[blk], m.jc_cnt[blk], m.d_segs, dst, na2,
+                          oscale, P->ctl(), scaled ? &sc->fc[blk] : nullptr, P->cs));
+    }
+    if (s4) {
+      Timed t(P, KC_PACK, 0.0, 16.0 * (double)na2 * nb2 + (double)eri_bytes_of(pr.d, blk));
+      CK(launch_pack_s4((const double2*)dst, pr.n[sa], pr.n[sb], blk == 1, (double2*)out[blk], P->cs));
+    }
+  }
+  for (int blk = 0; !m.cplx && blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
     const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
     const double fl = blk == 1 ? 2.0 * pr.npair[0] * (double)pr.npair[1] * K
                                : (double)pr.npair[sa] * (pr.npair[sa] + 1.0) * K;
@@ -1535,7 +1601,9 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     }
     build_tables(pr.s, nat, pr.nao, pr.nat);
     std::vector<int> con, wts;
-    if (pr.pack == DMET_PACK_S8) {
+    pr.mixed = pr.d.prec != DMET_PREC_FP64;
+    if (pr.pack == DMET_PACK_S8 || pr.mixed) {
+      // (general orbitals: every q, in increasing order, weight 1)
       contraction_order(pr.d, pr.s, con, wts);
       build_tables(pr.s, con, pr.nao, pr.con);
     }
@@ -1561,7 +1629,6 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     }
     // q-block size: the largest (<= 8, or <= DMET_QBLOCK, entries per launch <= 65535) whose
     // workspace fits.
-    pr.mixed = pr.d.prec != DMET_PREC_FP64;
     if (pr.mixed) tune_cache_lookup(pr, pr.mx.bn1, pr.mx.bn2);
     auto total_for = [&](int b) {
       size_t t = ws_for(pr, b).total();
@@ -1586,7 +1653,7 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     }
     WsSizes w = ws_for(pr, bq);
     pr.bq = bq;
-    if (pr.pack == DMET_PACK_S8) partition(pr, pr.con, wts, bq, pr.con_blocks);
+    if (pr.pack == DMET_PACK_S8 || pr.mixed) partition(pr, pr.con, wts, bq, pr.con_blocks);
     std::memset(&mneed[p], 0, sizeof(MixedWs));
     if (pr.mixed) {
       build_mixed(pr);
@@ -1688,7 +1755,7 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
   for (int p = 0; st == DMET_OK && p < n_problems; ++p) {
     Prob& pr = P->probs[p];
     st = upload_tables(pr.nat);
-    if (st == DMET_OK && pr.pack == DMET_PACK_S8) st = upload_tables(pr.con);
+    if (st == DMET_OK && (pr.pack == DMET_PACK_S8 || pr.mixed)) st = upload_tables(pr.con);
     if (st == DMET_OK && pr.mixed) {
       MixedPlan& m = pr.mx;
       if (cudaMalloc(&m.d_jobs, m.jobs.size() * sizeof(tc::TcJob)) != cudaSuccess ||

@@ -470,5 +470,32 @@ struct EpiRect {
   }
 };
 
+// A same-spin block of complex ERIs (general orbitals): row ij of the GEMM against the ket rows
+// 2 kl + c gives component c of (ij|kl); the output holds (re, im) doubles, out[ij * ldo + 2 kl + c]
+// with ldo = 2 n^2. Only elements with kl <= ij are stored from their own tile, each also at its
+// mirror (kl|ij) = (ij|kl) (the electron exchange symmetry; it holds exactly after the sum over q),
+// so the tiles wholly above the diagonal are never computed.
+struct EpiHerm {
+  static constexpr bool kAInterleaved = false;
+  struct Params {
+    double* out;
+    long long ldo;
+    float sh, sl;
+  };
+  static constexpr bool kStaged = true;
+  static __device__ __forceinline__ unsigned long long value(const Params& p, const TcJob&, float hi, float lo) {
+    return (unsigned long long)__double_as_longlong(scaled_pair(hi, lo, p.sh, p.sl));
+  }
+  static __device__ __forceinline__ void put(const Params& p, const TcJob& j, int row, int col,
+                                             unsigned long long v) {
+    if (row >= j.m_valid || col >= j.n_valid) return;
+    const long long ij = (long long)j.o0 + row, c = (long long)j.o1 + col, kl = c >> 1;
+    if (kl > ij) return;
+    const double x = __longlong_as_double((long long)v);
+    p.out[ij * p.ldo + c] = x;
+    if (kl < ij) p.out[kl * p.ldo + 2 * ij + (c & 1)] = x;
+  }
+};
+
 }  // namespace tc
 }  // namespace dmet

@@ -195,3 +195,20 @@ def test_partial_shard_needs_s8():
     with pytest.raises(B.DmetError) as e:
         dm.dmet_emb_plan(d)
     assert e.value.status == B.DMET_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("pack", [B.DMET_PACK_FULL, B.DMET_PACK_S4, B.DMET_PACK_AUTO])
+def test_tensor_core_precisions_take_complex_orbitals(pack):
+    """General orbitals pass validation with a tensor-core precision (the plan then needs a GPU);
+    real orbitals on a tensor-core precision still need the 8-fold packed output."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    d = dm.make_desc((2, 2, 1), 8, 40, 16, sym=B.DMET_SYM_NONE, eri_pack=pack, prec=B.DMET_PREC_BF16X3)
+    with pytest.raises(B.DmetError) as e:
+        dm.dmet_emb_plan(d)
+    assert e.value.status == B.DMET_ERR_CUDA
+    d = dm.make_desc((2, 2, 1), 8, 40, 16, eri_pack=B.DMET_PACK_FULL, prec=B.DMET_PREC_BF16X3)
+    with pytest.raises(B.DmetError) as e:
+        dm.dmet_emb_plan(d)
+    assert e.value.status == B.DMET_ERR_UNSUPPORTED
