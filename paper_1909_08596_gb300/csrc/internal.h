@@ -189,6 +189,25 @@ cudaError_t launch_pack_cplx(int prec, const void* ZT, int nq, int naux, int n, 
 cudaError_t launch_tc_herm(int prec, const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                            const tc::Segment* segs, double* out, long long n2, double scale, const tc::TcCtl& ctl,
                            const float* fac, cudaStream_t s);
+// Grouped tensor-core launches (one persistent launch over the tiles of many problems): the kinds
+// of table entry, what an entry holds, its size per precision, the host-side fill and the launch.
+enum { kGroupSplitT = 0, kGroupPairs = 1, kGroupContract = 2 };
+struct GroupSpec {
+  const CUtensorMap* a;
+  const CUtensorMap* b;
+  const tc::Segment* segs;
+  const float* fac;     // device factor, or null
+  void* out;            // step 1: the A2 operand; step 2: the Z pairs
+  double* const* outp;  // contraction: device slot holding the ERI block's pointer
+  long long ld;         // step 1: K2; step 2: 2 n; contraction: the row pitch (mode 1, 2)
+  int nao, n;           // step 1
+  double scale;         // contraction
+  int mode;             // contraction: 0 packed, 1 rectangular, 2 complex same-spin
+};
+size_t tc_group_bytes(int kind, int prec);
+cudaError_t tc_group_fill(int kind, int prec, const GroupSpec* specs, int count, void* host_dst);
+cudaError_t launch_tc_grouped(int kind, int prec, int bn, const void* groups, const tc::TcJob* jobs, int njobs,
+                              const tc::TcCtl& ctl, cudaStream_t s);
 // Sums the K parts of the split tiles of a packed contraction (the parts' jobs: jobs[0 .. ntiles * f)).
 cudaError_t launch_combine_parts(const tc::TcJob* jobs, int ntiles, int f, const void* part, double* out, double scale,
                                  cudaStream_t s);

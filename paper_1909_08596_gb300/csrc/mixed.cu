@@ -19,6 +19,8 @@
 // magnitudes (a sum of K products is at most K times the largest product); each GEMM's results are
 // multiplied back by the exact power of two its operands' scales leave.
 
+#include <cstring>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -358,7 +360,7 @@ struct EpiPairs {
 template <class PREC, int BN, class EPI>
 cudaError_t launch_tc_bn(const CUtensorMap& A, const CUtensorMap& B, const tc::TcJob* jobs, int njobs,
                          const tc::Segment* segs, const typename EPI::Params& ep, const tc::TcCtl& ctl, const float* fac,
-                         cudaStream_t s) {
+                         cudaStream_t s, const tc::TcGroup<EPI>* groups = nullptr) {
   using Cfg = tc::TcCfg<PREC, BN, EPI::kStaged>;
   static bool attr = false;
   if (!attr) {
@@ -382,7 +384,8 @@ cudaError_t launch_tc_bn(const CUtensorMap& A, const CUtensorMap& B, const tc::T
     if (e != cudaSuccess) return e;
   }
   const int grid = njobs < nsm ? njobs : nsm;
-  tc::tc_gemm_kernel<PREC, BN, EPI><<<grid, tc::kThreads, Cfg::SMEM, s>>>(A, B, jobs, njobs, segs, ep, ctl, fac);
+  tc::tc_gemm_kernel<PREC, BN, EPI><<<grid, tc::kThreads, Cfg::SMEM, s>>>(A, B, jobs, njobs, segs, ep, ctl, fac,
+                                                                          groups);
   return cudaGetLastError();
 }
 
@@ -394,6 +397,22 @@ cudaError_t launch_tc(int bn, const CUtensorMap& A, const CUtensorMap& B, const 
     case 128: return launch_tc_bn<PREC, 128, EPI>(A, B, jobs, njobs, segs, ep, ctl, fac, s);
     case 112: return launch_tc_bn<PREC, 112, EPI>(A, B, jobs, njobs, segs, ep, ctl, fac, s);
     case 96: return launch_tc_bn<PREC, 96, EPI>(A, B, jobs, njobs, segs, ep, ctl, fac, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// A grouped launch of the functor EPI: the maps, segments, factors and parameters come from the
+// device table `groups`; the kernel's own map and parameter arguments are unused placeholders.
+template <class PREC, class EPI>
+cudaError_t launch_tc_group(int bn, const void* groups, const tc::TcJob* jobs, int njobs, const tc::TcCtl& ctl,
+                            cudaStream_t s) {
+  static const CUtensorMap none{};
+  const typename EPI::Params ep{};
+  const auto* g = static_cast<const tc::TcGroup<EPI>*>(groups);
+  switch (bn) {
+    case 128: return launch_tc_bn<PREC, 128, EPI>(none, none, jobs, njobs, nullptr, ep, ctl, nullptr, s, g);
+    case 112: return launch_tc_bn<PREC, 112, EPI>(none, none, jobs, njobs, nullptr, ep, ctl, nullptr, s, g);
+    case 96: return launch_tc_bn<PREC, 96, EPI>(none, none, jobs, njobs, nullptr, ep, ctl, nullptr, s, g);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -661,6 +680,62 @@ cudaError_t launch_tc_rect(int prec, const CUtensorMap& A, const CUtensorMap& B,
   return with_prec(prec, [&](auto tag) -> cudaError_t {
     using P = decltype(tag);
     return launch_tc_bn<P, 128, tc::EpiRect>(A, B, jobs, njobs, segs, p, ctl, fac, s);
+  });
+}
+
+// Host side of the grouped launches: the table entry of each kind, filled from a GroupSpec.
+template <class EPI>
+void fill_group(tc::TcGroup<EPI>* g, const GroupSpec& sp, const typename EPI::Params& ep) {
+  std::memset((void*)g, 0, sizeof(*g));
+  std::memcpy(&g->a, sp.a, sizeof(CUtensorMap));
+  std::memcpy(&g->b, sp.b, sizeof(CUtensorMap));
+  g->segs = sp.segs;
+  g->fac = sp.fac;
+  g->ep = ep;
+}
+
+size_t tc_group_bytes(int kind, int prec) {
+  size_t b = 0;
+  with_prec(prec, [&](auto tag) -> cudaError_t {
+    using P = decltype(tag);
+    b = kind == kGroupSplitT ? sizeof(tc::TcGroup<EpiSplitT<P>>)
+                             : (kind == kGroupPairs ? sizeof(tc::TcGroup<EpiPairs>) : sizeof(tc::TcGroup<tc::EpiAny>));
+    return cudaSuccess;
+  });
+  return b;
+}
+
+cudaError_t tc_group_fill(int kind, int prec, const GroupSpec* specs, int count, void* dst) {
+  return with_prec(prec, [&](auto tag) -> cudaError_t {
+    using P = decltype(tag);
+    for (int i = 0; i < count; ++i) {
+      const GroupSpec& sp = specs[i];
+      if (kind == kGroupSplitT) {
+        typename EpiSplitT<P>::Params ep{(typename P::T*)sp.out, sp.ld, sp.nao, sp.n};
+        fill_group(static_cast<tc::TcGroup<EpiSplitT<P>>*>(dst) + i, sp, ep);
+      } else if (kind == kGroupPairs) {
+        EpiPairs::Params ep{(float2*)sp.out, sp.ld};
+        fill_group(static_cast<tc::TcGroup<EpiPairs>*>(dst) + i, sp, ep);
+      } else if (kind == kGroupContract) {
+        const float sh = (float)sp.scale;
+        tc::EpiAny::Params ep{sp.outp, nullptr, sp.ld, sh, (float)(sp.scale - (double)sh), sp.mode};
+        fill_group(static_cast<tc::TcGroup<tc::EpiAny>*>(dst) + i, sp, ep);
+      } else {
+        return cudaErrorInvalidValue;
+      }
+    }
+    return cudaSuccess;
+  });
+}
+
+cudaError_t launch_tc_grouped(int kind, int prec, int bn, const void* groups, const tc::TcJob* jobs, int njobs,
+                              const tc::TcCtl& ctl, cudaStream_t s) {
+  return with_prec(prec, [&](auto tag) -> cudaError_t {
+    using P = decltype(tag);
+    if (kind == kGroupSplitT) return launch_tc_group<P, EpiSplitT<P>>(bn, groups, jobs, njobs, ctl, s);
+    if (kind == kGroupPairs) return launch_tc_group<P, EpiPairs>(bn, groups, jobs, njobs, ctl, s);
+    if (kind == kGroupContract && bn == 128) return launch_tc_group<P, tc::EpiAny>(128, groups, jobs, njobs, ctl, s);
+    return cudaErrorInvalidValue;
   });
 }
 

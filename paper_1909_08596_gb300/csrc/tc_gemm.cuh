@@ -67,6 +67,20 @@ struct TcJob {
   int m_valid, n_valid;
   int seg0, nseg;
   int o0, o1, o2, o3;  // output-functor parameters (tile origin in the output's own indexing)
+  int grp;             // grouped launches: the job's entry of the group table (0 otherwise)
+};
+
+// One entry of a grouped launch's table (one problem, or one block of a problem): its operand
+// tensor maps, segment list, output-functor parameters and result factor. The table lives in
+// global memory, written by a host copy before the launch; the producer thread acquires each map
+// for the tensor-map proxy (fence.proxy.tensormap, system scope, since a host copy wrote it)
+// before its first copy through it.
+template <class EPI>
+struct alignas(128) TcGroup {
+  CUtensorMap a, b;
+  const Segment* segs;
+  const float* fac;
+  typename EPI::Params ep;
 };
 
 // Run-time controls of one launch.
@@ -174,17 +188,30 @@ __device__ __forceinline__ void staged_store(const typename EPI::Params& ep, con
   }
 }
 
+// Output functors whose parameters hold indirections (an output pointer kept in a device slot that
+// each call rewrites) resolve them once per job of a grouped launch: EPI::resolve(params).
+template <class E>
+__device__ __forceinline__ auto epi_resolve(typename E::Params& p, int) -> decltype(E::resolve(p)) {
+  E::resolve(p);
+}
+template <class E>
+__device__ __forceinline__ void epi_resolve(typename E::Params&, long) {}
+
 // Output functors either store per thread, EPI::store<H>(params, job, row, col0, hi, lo) with
 // row = tile-local row (< 128) and columns col0 .. col0+H-1, or (kStaged) give the 8-byte
 // value of an element, EPI::value(params, job, hi, lo), and write it, EPI::put(params, job, row,
 // col, v), skipping elements outside the job's valid region.
 // fac (device, or null for 1): a power of two that multiplies every result before the output functor
 // sees it (it undoes the operand scaling of the FP16 precision).
+// groups (device, or null): a grouped launch, in which every job names its entry of this table and
+// takes the maps, segments, output parameters and factor from there instead of tmA, tmB, segs, ep
+// and fac. One persistent launch then works through the tiles of many problems of one shape class.
 template <class PREC, int BN, class EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcJob* __restrict__ jobs, int njobs, const Segment* __restrict__ segs,
-                   const typename EPI::Params ep, const TcCtl ctl, const float* __restrict__ fac) {
+                   const typename EPI::Params ep, const TcCtl ctl, const float* __restrict__ fac,
+                   const TcGroup<EPI>* __restrict__ groups) {
   using Cfg = TcCfg<PREC, BN, EPI::kStaged>;
   constexpr int NSLICE = Cfg::NSLICE;
   constexpr int ROWB = Cfg::ROWB;
@@ -241,13 +268,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kCtrlRegs));
     if (warp == 0 && lane == 0) {
       // ---------------- TMA producer ----------------
-      prefetch_tmap(&tmA);
-      prefetch_tmap(&tmB);
+      const void* ma = &tmA;
+      const void* mb = &tmB;
+      const Segment* sgs = segs;
+      if (!groups) {
+        prefetch_tmap(ma);
+        prefetch_tmap(mb);
+      }
+      int cur = -1;
       bool ok = !ctl.withhold_loads;
       for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x) {
       const TcJob job = jobs[jb];
+      if (groups && job.grp != cur) {
+        cur = job.grp;
+        ma = &groups[cur].a;
+        mb = &groups[cur].b;
+        sgs = groups[cur].segs;
+        tmap_acquire(ma);
+        tmap_acquire(mb);
+      }
       for (int g = 0; g < job.nseg && ok; ++g) {
-        const Segment sg = segs[job.seg0 + g];
+        const Segment sg = sgs[job.seg0 + g];
         const int nkb = sg.nk / Cfg::BK;
         for (int kb = 0; kb < nkb; ++kb) {
           const int s = issued % S, ph = (issued / S) & 1;
@@ -261,10 +302,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int t = 0; t < NSLICE; ++t) {
             // A operands stored slice-interleaved ([row][K / 32][slice][32]) come through a 4D map
             if constexpr (EPI::kAInterleaved)
-              tma_load_4d(a_tile(s, t), &tmA, full(s), 0, t, k / Cfg::BK, job.a_row0);
+              tma_load_4d(a_tile(s, t), ma, full(s), 0, t, k / Cfg::BK, job.a_row0);
             else
-              tma_load_3d(a_tile(s, t), &tmA, full(s), k, job.a_row0, t);
-            tma_load_3d(b_tile(s, t), &tmB, full(s), k, job.b_row0, t);
+              tma_load_3d(a_tile(s, t), ma, full(s), k, job.a_row0, t);
+            tma_load_3d(b_tile(s, t), mb, full(s), k, job.b_row0, t);
           }
           ++issued;
         }
@@ -277,6 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x) {
       const TcJob job = jobs[jb];
+      const Segment* sgs = groups ? groups[job.grp].segs : segs;
       for (int g = 0; g < job.nseg && ok; ++g, ++gs) {
         const int b = gs & 1, u = gs >> 1;
         // The buffer of segment gs - 2 is free once the epilogue has read it; the epilogue
@@ -284,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // also frees the correction buffer of run `run - 1` (every run has >= 1 segment).
         if (!mbar_wait(acce(b), (u & 1) ^ 1, err, 2u, lim)) break;
         tc_fence_after();
-        const Segment sg = segs[job.seg0 + g];
+        const Segment sg = sgs[job.seg0 + g];
         const bool first = g == 0 || (sg.flags & kRunFirst);
         run += first;
         // 128-column aligned: leading sums at 0 / 128, correction sums at 256 / 384
@@ -325,12 +367,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue ----------------
     const int quad = warp & 3, half = (warp - 4) >> 2;  // (half: this warp's column share)
     const int row = quad * 32 + lane;
-    const float f = fac ? *fac : 1.f;
+    const float f0 = fac ? *fac : 1.f;
     float hi[H], lo[H];
     bool ok = true;
     int gs = 0, run = -1;
     for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x) {
       const TcJob job = jobs[jb];
+      const Segment* sgs = groups ? groups[job.grp].segs : segs;
       for (int g = 0; g < job.nseg; ++g, ++gs) {
         const int b = gs & 1, u = gs >> 1;
         if (!mbar_wait(accf(b), u & 1, err, 8u, lim)) {
@@ -338,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const Segment sg = segs[job.seg0 + g];
+        const Segment sg = sgs[job.seg0 + g];
         const float w = sg.w;
         run += g == 0 || (sg.flags & kRunFirst);
         const bool last = Cfg::NPROD > 1 && (g == job.nseg - 1 || (sg.flags & kRunLast));
@@ -384,6 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(acce(b));
       }
+      const float f = groups ? (groups[job.grp].fac ? *groups[job.grp].fac : 1.f) : f0;
       if (f != 1.f) {
 #pragma unroll
         for (int c = 0; c < H; ++c) {
@@ -391,10 +435,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           lo[c] *= f;
         }
       }
-      if constexpr (EPI::kStaged) {
-        if (ok) staged_store<H, EPI>(ep, job, quad * 32, half * H, hi, lo, staging + (warp - 4) * 256, lane);
+      if (groups) {
+        typename EPI::Params gep = groups[job.grp].ep;
+        epi_resolve<EPI>(gep, 0);
+        if constexpr (EPI::kStaged) {
+          if (ok) staged_store<H, EPI>(gep, job, quad * 32, half * H, hi, lo, staging + (warp - 4) * 256, lane);
+        } else {
+          if (ok && row < job.m_valid) EPI::template store<H>(gep, job, row, half * H, hi, lo);
+        }
       } else {
-        if (ok && row < job.m_valid) EPI::template store<H>(ep, job, row, half * H, hi, lo);
+        if constexpr (EPI::kStaged) {
+          if (ok) staged_store<H, EPI>(ep, job, quad * 32, half * H, hi, lo, staging + (warp - 4) * 256, lane);
+        } else {
+          if (ok && row < job.m_valid) EPI::template store<H>(ep, job, row, half * H, hi, lo);
+        }
       }
     }
   }
@@ -494,6 +548,42 @@ struct EpiHerm {
     const double x = __longlong_as_double((long long)v);
     p.out[ij * p.ldo + c] = x;
     if (kl < ij) p.out[kl * p.ldo + 2 * ij + (c & 1)] = x;
+  }
+};
+
+// The contraction of a grouped launch, one table entry per ERI block of every problem: mode 0 is
+// EpiPacked's 8-fold packed layout, 1 EpiRect's rectangular one, 2 EpiHerm's complex same-spin
+// block. The block's output pointer sits in a device slot (outp) that each call rewrites, so the
+// table itself is written once, when the plan is made.
+struct EpiAny {
+  static constexpr bool kAInterleaved = false;
+  struct Params {
+    double* const* outp;
+    double* out;  // *outp, resolved per job
+    long long ldo;
+    float sh, sl;
+    int mode;
+  };
+  static constexpr bool kStaged = true;
+  static __device__ __forceinline__ void resolve(Params& p) { p.out = *p.outp; }
+  static __device__ __forceinline__ unsigned long long value(const Params& p, const TcJob&, float hi, float lo) {
+    return (unsigned long long)__double_as_longlong(scaled_pair(hi, lo, p.sh, p.sl));
+  }
+  static __device__ __forceinline__ void put(const Params& p, const TcJob& j, int row, int col,
+                                             unsigned long long v) {
+    if (row >= j.m_valid || col >= j.n_valid) return;
+    const long long m = (long long)j.o0 + row, n = (long long)j.o1 + col;
+    const double x = __longlong_as_double((long long)v);
+    if (p.mode == 0) {
+      if (n <= m) p.out[m * (m + 1) / 2 + n] = x;
+    } else if (p.mode == 1) {
+      p.out[m * p.ldo + n] = x;
+    } else {
+      const long long kl = n >> 1;
+      if (kl > m) return;
+      p.out[m * p.ldo + n] = x;
+      if (kl < m) p.out[kl * p.ldo + 2 * m + (n & 1)] = x;
+    }
   }
 };
 
