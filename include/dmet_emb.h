@@ -340,13 +340,29 @@ DMET_API dmet_status_t dmet_fftdf_plane_waves(const int32_t* mesh, int32_t q, co
  * plan's stream (different buffers: captured again; host buffers or profiling: no graph). */
 DMET_API dmet_status_t dmet_emb_graph(dmet_emb_plan_t plan, int32_t enable);
 
+/* Execution of a plan of several problems. mode 1 (the default) runs the batch as grouped
+ * persistent launches whenever every problem is on a tensor-core precision, every problem got its
+ * own workspace, the inputs and outputs are device buffers, and no complex ERI is 4-fold packed:
+ * per round r (block r of the q-blocks of every problem that has one) and spin, one launch of the
+ * first half transform and one of the second for all problems (one per precision and tile width),
+ * and at the end one launch of the contraction of every ERI block of every problem, each a
+ * persistent tcgen05 kernel over a device table of per-problem tensor maps, segment lists and
+ * output parameters; each problem's element-wise kernels (checks, operand splitting, packing) run
+ * on the side streams between them. Every problem then completes with the last launch, so the
+ * per-problem times of dmet_emb_problem_ms are the batch's. mode 0 runs each problem on its own
+ * side stream (or one after another), as described for dmet_emb_graph. *active (optional)
+ * receives 1 if calls with device buffers will run grouped, else 0. A captured graph is discarded
+ * when the mode changes. No counterpart in the paper (a GPU scheduling choice). */
+DMET_API dmet_status_t dmet_emb_batch_mode(dmet_emb_plan_t plan, int32_t mode, int32_t* active);
+
 /* Device milliseconds of problem `problem` in the last call made while profiling was enabled
  * (CUDA events around that problem's work on its stream). Waits for the stream. */
 DMET_API dmet_status_t dmet_emb_problem_ms(dmet_emb_plan_t plan, int32_t problem, double* ms);
 
 /* Autotuner of the split-BF16 path: for every problem it times the two transform GEMMs'
  * output tile widths (128, 112 and 96 columns; the width that wastes least on the problem's
- * 2 n_emb output columns is not always the fastest) by running dmet_emb_eri on the given
+ * 2 n_emb output columns is not always the fastest), each problem on its own side stream, by
+ * running dmet_emb_eri on the given
  * buffers (device pointers; the outputs are overwritten with valid results), keeps the
  * fastest for each problem and, if the environment variable DMET_TUNE_CACHE names a file,
  * appends the choice there; dmet_emb_plan reads that file for later plans of the same shape.

@@ -138,6 +138,8 @@ def lib() -> ctypes.CDLL:
         L.dmet_emb_profile_read.restype = st
         L.dmet_emb_graph.argtypes = [_P, ctypes.c_int32]
         L.dmet_emb_graph.restype = st
+        L.dmet_emb_batch_mode.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.dmet_emb_batch_mode.restype = st
         L.dmet_emb_problem_ms.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
         L.dmet_emb_problem_ms.restype = st
         L.dmet_emb_autotune.argtypes = [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.POINTER(_P)),
@@ -342,6 +344,14 @@ def dmet_emb_profile_read(plan, kernel):
 
 def dmet_emb_graph(plan, enable):
     _check(lib().dmet_emb_graph(_P(plan), 1 if enable else 0))
+
+
+def dmet_emb_batch_mode(plan, mode):
+    """Sets the batch mode (1 grouped launches, 0 per-problem side streams); returns whether calls
+    with device buffers will run grouped."""
+    active = ctypes.c_int32()
+    _check(lib().dmet_emb_batch_mode(_P(plan), int(mode), ctypes.byref(active)))
+    return bool(active.value)
 
 
 def dmet_emb_problem_ms(plan, problem):

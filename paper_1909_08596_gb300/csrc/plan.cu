@@ -4,12 +4,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -216,6 +218,7 @@ struct MixedPlan {
   int jc_off[3] = {0, 0, 0}, jc_cnt[3] = {0, 0, 0};
   // per contraction block: split tiles (their K parts are the last jc_split_n * jc_split_f jobs)
   int jc_split_n[3] = {0, 0, 0}, jc_split_f[3] = {1, 1, 1};
+  int jc_seg0 = 0, jc_nseg = 0;  // the contraction's segment list (a whole tile's K)
   tc::TcJob* d_jobs = nullptr;
   tc::Segment* d_segs = nullptr;
   long long Ls_rows = 0, A2_rows[2] = {0, 0};
@@ -269,6 +272,27 @@ struct Workspace {
   void* Xt[2] = {nullptr, nullptr};
   MixScales* sc = nullptr;
   size_t Ls_b = 0, Cb_b[2] = {0, 0}, Cc_b = 0, A2_b = 0, ZT_b = 0, Xt_b[2] = {0, 0}, sc_b = 0;
+};
+
+// One grouped tensor-core launch: its job table (every job naming its entry of the group table),
+// the group table, and the work it stands for.
+struct GroupedLaunch {
+  int kind = 0, prec = 0, bn = 128;
+  tc::TcJob* d_jobs = nullptr;
+  int njobs = 0;
+  void* d_groups = nullptr;
+  double flops = 0, bytes = 0, exec = 0;
+};
+
+// The batch as grouped launches: round r (block r of every problem that has one), spin s: the
+// first and the second half transforms of all those problems, one launch per (precision, tile
+// width) class; then the contraction of every ERI block of every problem, one launch per precision.
+struct GroupedPlan {
+  bool built = false;
+  int rounds = 0;
+  std::vector<std::vector<GroupedLaunch>> step1, step2;  // [r * 2 + s]
+  std::vector<GroupedLaunch> contract;
+  double** d_slots = nullptr;  // [problem * 3 + block]: the ERI block pointers of the call
 };
 
 struct dmet_emb_plan_s {
@@ -327,6 +351,9 @@ struct dmet_emb_plan_s {
   KStat ks[KC_COUNT];
   std::vector<cudaEvent_t> pool;
   long long launches = 0;
+  // grouped execution of a batch (dmet_emb_batch_mode): requested mode and the launch tables
+  int batch_mode = 1;
+  GroupedPlan grp;
   // bounded waits of the tensor-core kernels
   unsigned long long wait_ns = tc::kWaitLimitNs;
   int withhold_loads = 0;
@@ -607,7 +634,7 @@ dmet_status_t run_l_check(dmet_emb_plan_s* P, Prob& pr, int p, const double2* L)
 // sym = NONE, L^q scaled by lq_scale directly into `dest` (slot-major, z0 = b0).
 dmet_status_t run_half_transform(dmet_emb_plan_s* P, Prob& pr, const Tables& tb, int b0, int b1, int s,
                                  const double2* L, const double2* C, double2* dest, int dest_slot0) {
-  const int n = pr.n[s], nao = pr.nao, naux = pr.naux, nk = pr.nk;
+  const int n = pr.n[s], nao = pr.nao, naux = pr.naux;
   const int e0 = tb.start[b0], E = tb.start[b1] - e0;
   if (E <= 0) return DMET_OK;
   {
@@ -845,6 +872,21 @@ void free_workspace(Workspace& w) {
   w = Workspace();
 }
 
+void free_grouped(GroupedPlan& g) {
+  for (auto* v : {&g.step1, &g.step2})
+    for (auto& ls : *v)
+      for (auto& l : ls) {
+        cudaFree(l.d_jobs);
+        cudaFree(l.d_groups);
+      }
+  for (auto& l : g.contract) {
+    cudaFree(l.d_jobs);
+    cudaFree(l.d_groups);
+  }
+  cudaFree(g.d_slots);
+  g = GroupedPlan();
+}
+
 void destroy_plan(dmet_emb_plan_s* P) {
   if (!P) return;
   if (P->stream) cudaStreamSynchronize(P->stream);
@@ -858,6 +900,7 @@ void destroy_plan(dmet_emb_plan_s* P) {
     cudaFree(pr.mx.d_segs);
   }
   for (auto& w : P->ws) free_workspace(w);
+  free_grouped(P->grp);
   cudaFree(P->derr);
   cudaFree(P->dstats);
   cudaFree(P->stage_in);
@@ -979,6 +1022,8 @@ void build_mixed(Prob& pr) {
   for (long long k0 = m.R1; k0 < m.Rtot; k0 += m.kseg)
     m.segs.push_back({(int)k0, (int)std::min<long long>(m.Rtot - k0, m.kseg), 2.0f, 0});
   const int sc_cnt = (int)m.segs.size() - sc_off;
+  m.jc_seg0 = sc_off;
+  m.jc_nseg = sc_cnt;
   // A correction-sum run never spans a change of weight, nor more than crun segments of one list.
   auto bound = [&](size_t i) {  // a run ends at segment i - 1 and the next starts at i
     m.segs[i - 1].flags |= tc::kRunLast;
@@ -1176,36 +1221,62 @@ dmet_status_t mixed_maps(dmet_emb_plan_s* P, const Prob& pr, MixedMaps& mm) {
   return DMET_OK;
 }
 
-// What dmet_emb_transform_3idx asks of the tensor-core path: L^q for q in [q_begin, q_end) of every
-// spin, from the contraction slot slot[q - q_begin] (conjugated where conj[q - q_begin]).
-struct Lq3Req {
-  int q_begin = 0, q_end = 0;
-  std::vector<int> slot;
-  std::vector<char> conj;
-  double2* const* out = nullptr;
-};
+// Algorithmic work of block bi's half transforms, spin s: flops and bytes (operands read once,
+// results written once).
+void step1_work(const Prob& pr, int bi, int s, double& fl, double& by) {
+  const MixedPlan& m = pr.mx;
+  const Block& bl = m.blocks[bi];
+  const int E = pr.con.start[bl.b1] - pr.con.start[bl.b0], n = pr.n[s];
+  const double se = (double)m.ns * m.esz;
+  fl = 8.0 * n * (double)pr.naux * pr.nao * pr.nao * E;
+  by = se * E * pr.naux * pr.nao * (m.K1 + 2.0 * n);  // L slices read, T slices written
+}
+void step2_work(const Prob& pr, int bi, int s, double& fl, double& by) {
+  const MixedPlan& m = pr.mx;
+  const Block& bl = m.blocks[bi];
+  const int n = pr.n[s];
+  const double se = (double)m.ns * m.esz;
+  fl = by = 0;
+  for (int i = bl.b0; i < bl.b1; ++i) {
+    fl += 8.0 * n * (double)pr.naux * n * pr.con.t2[i].w;
+    // the slot's T slices (K = its padded 2 n_rep n_AO) read once, Z written as two-float pairs
+    const double K = (double)padk(2LL * pr.s.nrep[pr.con.order[i]] * pr.nao);
+    by += se * pr.naux * n * K + se * 2 * n * K + 8.0 * pr.naux * n * 2.0 * n;
+  }
+}
+// Flops and bytes of ERI block blk's contraction.
+void contract_work(const Prob& pr, int blk, double& fl, double& by) {
+  const MixedPlan& m = pr.mx;
+  const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
+  const double se = (double)m.ns * m.esz;
+  if (m.cplx) {
+    const double na2 = (double)pr.n[sa] * pr.n[sa], nb2 = (double)pr.n[sb] * pr.n[sb];
+    fl = 8.0 * na2 * nb2 * pr.naux * (double)pr.con.order.size();
+    // the bra rows' and ket rows' slices read once, the complex block written once
+    by = se * m.Rtot * (na2 + 2 * nb2) + 16.0 * na2 * nb2;
+    return;
+  }
+  long long K = 0;
+  for (int q : pr.con.order) K += (long long)pr.naux * (pr.s.qw[q] == 1 ? 1 : 2);
+  fl = blk == 1 ? 2.0 * pr.npair[0] * (double)pr.npair[1] * K : (double)pr.npair[sa] * (pr.npair[sa] + 1.0) * K;
+  // both operands' slices read once, the packed FP64 result written once
+  by = se * m.Rtot * (double)(pr.npair[sa] + (blk == 1 ? pr.npair[sb] : 0)) +
+       8.0 * (blk == 1 ? (double)pr.npair[sa] * pr.npair[sb] : pr.npair[sa] * (pr.npair[sa] + 1.0) / 2);
+}
 
-// The tensor-core path of Algorithm 1: the operand scales and the orbital operands, then block by
-// block the split of L, the two half transforms and the pair packing, then the contraction. With
-// `req`, only the blocks that hold requested q run, their L^q are written out, and nothing is
-// packed or contracted (dmet_emb_transform_3idx).
-dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, void* const* out,
-                        const Lq3Req* req = nullptr) {
+// Phases of the tensor-core path of one problem (Algorithm 1), on P->cs with workspace P->W.
+// (1) The FP16 operand scales (from the maxima of the L blocks the call reads and of C), the zero
+// padding of the contraction operand (pad) and the ket-side orbital operands of every spin.
+dmet_status_t mixed_prep(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, bool pad) {
   MixedPlan& m = pr.mx;
-  MixedMaps mm;
-  TRY(mixed_maps(P, pr, mm));
-  const long long nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
-  const long long cc_rows = (long long)pr.bq * 2 * nmax;
   int n1 = 0;
   for (int q : pr.con.order) n1 += pr.s.qw[q] == 1;
   const long long used1 = (long long)n1 * pr.naux * (m.cplx ? 2 : 1);
   const long long used2 = ((long long)pr.con.order.size() - n1) * 2 * pr.naux;
   const int pc = m.prec;
-  const double se = (double)m.ns * m.esz;  // bytes of all slices of one operand element
+  const double se = (double)m.ns * m.esz;
   MixScales* sc = P->W->sc;
-  const bool scaled = prec_scaled(pc);
-  if (scaled) {
-    // the FP16 operand scales, from the maxima of the L blocks this call reads and of C
+  if (prec_scaled(pc)) {
     const int E_all = (int)pr.con.t1.size();
     int nrep_max = 1;
     for (int q : pr.con.order) nrep_max = std::max(nrep_max, pr.s.nrep[q]);
@@ -1215,122 +1286,144 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
                          nrep_max, sc, P->cs));
   }
   for (int s = 0; s < pr.nspin; ++s) {
-    // padding rows of the contraction operand read as zeros
+    // padding columns of the contraction operand read as zeros
     const size_t pitch = (size_t)m.Rtot * m.esz;
     const long long h = (long long)m.ns * m.xrows[s];
-    if (!req && m.R1 > used1)
+    if (pad && m.R1 > used1)
       CK(cudaMemset2DAsync((char*)P->W->Xt[s] + used1 * m.esz, pitch, 0, (size_t)(m.R1 - used1) * m.esz, h, P->cs));
-    if (!req && m.Rtot - m.R1 > used2)
+    if (pad && m.Rtot - m.R1 > used2)
       CK(cudaMemset2DAsync((char*)P->W->Xt[s] + (m.R1 + used2) * m.esz, pitch, 0,
                            (size_t)(m.Rtot - m.R1 - used2) * m.esz, h, P->cs));
     Timed t(P, KC_SPLIT, 0.0, 16.0 * pr.nk * pr.nao * pr.n[s] + se * pr.nk * 2 * pr.n[s] * m.K1);
     CK(launch_build_Cb(pc, C[s], pr.nk, pr.nao, pr.n[s], m.K1, P->W->Cb[s], (long long)pr.nk * 2 * pr.n[s] * m.K1,
                        &sc->sC[s], P->cs));
   }
-  for (size_t bi = 0; bi < m.blocks.size(); ++bi) {
-    const Block& bl = m.blocks[bi];
-    const int e0 = pr.con.start[bl.b0], E = pr.con.start[bl.b1] - e0, nq = bl.b1 - bl.b0;
-    if (req) {
-      bool any = false;
-      for (int sl : req->slot) any |= sl >= bl.b0 && sl < bl.b1;
-      if (!any) continue;
-    }
+  return DMET_OK;
+}
+
+// (2) Block bi's inputs for spin s: the split of its L blocks (with spin 0; both spins read it)
+// and the bra-side orbital operand of spin s.
+dmet_status_t mixed_block_in(dmet_emb_plan_s* P, Prob& pr, int bi, int s, const double2* L, const double2* const* C) {
+  MixedPlan& m = pr.mx;
+  const Block& bl = m.blocks[bi];
+  const int e0 = pr.con.start[bl.b0], E = pr.con.start[bl.b1] - e0, nq = bl.b1 - bl.b0;
+  const int pc = m.prec;
+  const double se = (double)m.ns * m.esz;
+  MixScales* sc = P->W->sc;
+  if (s == 0) {
     if (P->xpending) {
-      TRY(queue_block_copies(P, pr, (int)bi));
+      TRY(queue_block_copies(P, pr, bi));
       CK(cudaStreamWaitEvent(P->cs, P->xev[bi], 0));
     }
-    {
-      const double rows = (double)E * pr.naux * pr.nao;
-      Timed t(P, KC_SPLIT, 0.0, rows * (16.0 * pr.nao + se * m.K1));
-      CK(launch_split_L(pc, L, pr.con.d_t1, e0, E, pr.naux, pr.nao, m.K1, P->W->Ls, m.Ls_rows * m.K1, sc, P->cs));
-    }
-    for (int s = 0; s < pr.nspin; ++s) {
-      const int n = pr.n[s];
-      {
-        Timed t(P, KC_SPLIT, 0.0, se * nq * 2 * n * m.K2);
-        CK(launch_build_Cc(pc, C[s], pr.con.d_gather, pr.con.d_t2, bl.b0, nq, pr.nao, n, m.K2, P->W->Cc,
-                           cc_rows * m.K2, &sc->sC[s], P->cs));
-      }
-      {
-        // algorithmic bytes: the L slices read once, T written once as slices
-        const double by = se * E * pr.naux * pr.nao * (m.K1 + 2.0 * n);
-        Timed t(P, KC_TC_TRANSFORM_1, 8.0 * n * (double)pr.naux * pr.nao * pr.nao * E, by, 1,
-                exec_flops(m, m.j1_off[s][bi], m.j1_cnt[s][bi], m.bn1));
-        CK(launch_tc_split_t(pc, m.bn1, mm.Ls, mm.Cb[s], m.d_jobs + m.j1_off[s][bi], m.j1_cnt[s][bi], m.d_segs,
-                             P->W->A2, m.K2, pr.nao, n, P->ctl(), scaled ? &sc->f1[s] : nullptr, P->cs));
-      }
-      {
-        double fl = 0, by = 0;
-        for (int i = bl.b0; i < bl.b1; ++i) {
-          fl += 8.0 * n * (double)pr.naux * n * pr.con.t2[i].w;
-          // the slot's T slices (K = its padded 2 n_rep n_AO) read once, Z written as two-float pairs
-          const double K = (double)padk(2LL * pr.s.nrep[pr.con.order[i]] * pr.nao);
-          by += se * pr.naux * n * K + se * 2 * n * K + 8.0 * pr.naux * n * 2.0 * n;
-        }
-        Timed t(P, KC_TC_TRANSFORM_2, fl, by, 1, exec_flops(m, m.j2_off[s][bi], m.j2_cnt[s][bi], m.bn2));
-        CK(launch_tc_pairs(pc, m.bn2, mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs,
-                           P->W->ZT, 2LL * n, P->ctl(), scaled ? &sc->f2[s] : nullptr, P->cs));
-      }
-      if (req) {
-        for (int i = 0; i < req->q_end - req->q_begin; ++i) {
-          const int sl = req->slot[i];
-          if (sl < bl.b0 || sl >= bl.b1) continue;
-          const long long slot_el = (long long)pr.naux * n * n;
-          Timed t(P, KC_PACK, 0.0, 16.0 * slot_el + 16.0 * slot_el);
-          CK(launch_lq_from_pairs((const char*)P->W->ZT + (size_t)(sl - bl.b0) * slot_el * 2 * sizeof(float2), pr.naux,
-                                  n, pr.lq_scale, req->conj[i], m.cplx ? 0 : 1, req->out[s] + i * slot_el, P->cs));
-        }
-        continue;
-      }
-      if (m.cplx) {
-        // every q of a general-orbital problem is its own slot (q = slot)
-        Timed t(P, KC_TC_PACK, 0.0, 16.0 * nq * pr.naux * (double)n * n + se * 6.0 * nq * pr.naux * (double)n * n);
-        CK(launch_pack_cplx(pc, P->W->ZT, nq, pr.naux, n, pr.con.order[bl.b0], pr.d_neg, P->W->Xt[s],
-                            m.xrows[s] * m.Rtot, m.Rtot, &sc->sX[s], P->cs));
-      } else {
-        const int nc = bl.w == 1 ? 1 : 2;
-        Timed t(P, KC_TC_PACK, 0.0, 16.0 * nq * pr.naux * (double)n * n + se * nq * pr.naux * nc * pr.npair[s]);
-        CK(launch_pack_split(pc, P->W->ZT, nq, pr.naux, n, nc, P->W->Xt[s], pr.npair[s] * m.Rtot, m.Rtot,
-                             m.row_base[bi], &sc->sX[s], P->cs));
-      }
-    }
+    const double rows = (double)E * pr.naux * pr.nao;
+    Timed t(P, KC_SPLIT, 0.0, rows * (16.0 * pr.nao + se * m.K1));
+    CK(launch_split_L(pc, L, pr.con.d_t1, e0, E, pr.naux, pr.nao, m.K1, P->W->Ls, m.Ls_rows * m.K1, sc, P->cs));
   }
-  if (req) return DMET_OK;
-  long long K = 0;
-  for (int q : pr.con.order) K += (long long)pr.naux * (pr.s.qw[q] == 1 ? 1 : 2);
-  // The operand holds Z + Z^T (general orbitals: Z); L^q = s (Z + Z^T) (s Z), so the product
-  // carries s^2, and 1/Nk.
-  const double oscale = pr.lq_scale * pr.lq_scale / pr.nk;
-  for (int blk = 0; m.cplx && blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
-    const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
-    const long long na2 = (long long)pr.n[sa] * pr.n[sa], nb2 = (long long)pr.n[sb] * pr.n[sb];
-    const double fl = 8.0 * (double)na2 * nb2 * pr.naux * (double)pr.con.order.size();
-    // S4: the block's full ERI in the workspace first, then packed
-    const bool s4 = pr.pack == DMET_PACK_S4;
-    double* dst = s4 ? (double*)P->W->full : (double*)out[blk];
-    {
-      // algorithmic bytes: the bra rows' and ket rows' slices read once, the complex block written once
-      const double by = se * m.Rtot * (double)(na2 + 2 * nb2) + 16.0 * (double)na2 * nb2;
-      Timed t(P, KC_TC_CONTRACT, fl, by, 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk], tc::kTile));
-      if (blk == 1)
-        CK(launch_tc_rect(pc, mm.Xt[0], mm.Xt[1], m.d_jobs + m.jc_off[1], m.jc_cnt[1], m.d_segs, dst, 2 * nb2, oscale,
-                          P->ctl(), scaled ? &sc->fc[1] : nullptr, P->cs));
-      else
-        CK(launch_tc_herm(pc, mm.Xt[sa], mm.Xt[sa], m.d_jobs + m.jc_off[blk], m.jc_cnt[blk], m.d_segs, dst, na2,
-                          oscale, P->ctl(), scaled ? &sc->fc[blk] : nullptr, P->cs));
-    }
-    if (s4) {
-      Timed t(P, KC_PACK, 0.0, 16.0 * (double)na2 * nb2 + (double)eri_bytes_of(pr.d, blk));
-      CK(launch_pack_s4((const double2*)dst, pr.n[sa], pr.n[sb], blk == 1, (double2*)out[blk], P->cs));
-    }
+  const long long nmax = std::max(pr.n[0], pr.nspin == 2 ? pr.n[1] : 0);
+  const long long cc_rows = (long long)pr.bq * 2 * nmax;
+  Timed t(P, KC_SPLIT, 0.0, se * nq * 2 * pr.n[s] * m.K2);
+  CK(launch_build_Cc(pc, C[s], pr.con.d_gather, pr.con.d_t2, bl.b0, nq, pr.nao, pr.n[s], m.K2, P->W->Cc,
+                     cc_rows * m.K2, &sc->sC[s], P->cs));
+  return DMET_OK;
+}
+
+// (3) Block bi's two half transforms of spin s (this problem's own launches).
+dmet_status_t mixed_block_gemms(dmet_emb_plan_s* P, Prob& pr, const MixedMaps& mm, int bi, int s) {
+  MixedPlan& m = pr.mx;
+  const int pc = m.prec, n = pr.n[s];
+  const bool scaled = prec_scaled(pc);
+  MixScales* sc = P->W->sc;
+  double fl = 0, by = 0;
+  step1_work(pr, bi, s, fl, by);
+  {
+    Timed t(P, KC_TC_TRANSFORM_1, fl, by, 1, exec_flops(m, m.j1_off[s][bi], m.j1_cnt[s][bi], m.bn1));
+    CK(launch_tc_split_t(pc, m.bn1, mm.Ls, mm.Cb[s], m.d_jobs + m.j1_off[s][bi], m.j1_cnt[s][bi], m.d_segs, P->W->A2,
+                         m.K2, pr.nao, n, P->ctl(), scaled ? &sc->f1[s] : nullptr, P->cs));
   }
-  for (int blk = 0; !m.cplx && blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
-    const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
-    const double fl = blk == 1 ? 2.0 * pr.npair[0] * (double)pr.npair[1] * K
-                               : (double)pr.npair[sa] * (pr.npair[sa] + 1.0) * K;
-    // algorithmic bytes: both operands' slices read once, the packed FP64 result written once
-    const double by = se * m.Rtot * (double)(pr.npair[sa] + (blk == 1 ? pr.npair[sb] : 0)) +
-                      8.0 * (blk == 1 ? (double)pr.npair[sa] * pr.npair[sb] : pr.npair[sa] * (pr.npair[sa] + 1.0) / 2);
+  step2_work(pr, bi, s, fl, by);
+  Timed t(P, KC_TC_TRANSFORM_2, fl, by, 1, exec_flops(m, m.j2_off[s][bi], m.j2_cnt[s][bi], m.bn2));
+  CK(launch_tc_pairs(pc, m.bn2, mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs, P->W->ZT,
+                     2LL * n, P->ctl(), scaled ? &sc->f2[s] : nullptr, P->cs));
+  return DMET_OK;
+}
+
+// What dmet_emb_transform_3idx asks of the tensor-core path: L^q for q in [q_begin, q_end) of every
+// spin, from the contraction slot slot[q - q_begin] (conjugated where conj[q - q_begin]).
+struct Lq3Req {
+  int q_begin = 0, q_end = 0;
+  std::vector<int> slot;
+  std::vector<char> conj;
+  double2* const* out = nullptr;
+};
+
+// (4) Block bi's rows of the contraction operand of spin s (pair packing), or with req the L^q it
+// holds.
+dmet_status_t mixed_block_out(dmet_emb_plan_s* P, Prob& pr, int bi, int s, const Lq3Req* req) {
+  MixedPlan& m = pr.mx;
+  const Block& bl = m.blocks[bi];
+  const int nq = bl.b1 - bl.b0, n = pr.n[s], pc = m.prec;
+  const double se = (double)m.ns * m.esz;
+  MixScales* sc = P->W->sc;
+  if (req) {
+    for (int i = 0; i < req->q_end - req->q_begin; ++i) {
+      const int sl = req->slot[i];
+      if (sl < bl.b0 || sl >= bl.b1) continue;
+      const long long slot_el = (long long)pr.naux * n * n;
+      Timed t(P, KC_PACK, 0.0, 16.0 * slot_el + 16.0 * slot_el);
+      CK(launch_lq_from_pairs((const char*)P->W->ZT + (size_t)(sl - bl.b0) * slot_el * 2 * sizeof(float2), pr.naux, n,
+                              pr.lq_scale, req->conj[i], m.cplx ? 0 : 1, req->out[s] + i * slot_el, P->cs));
+    }
+    return DMET_OK;
+  }
+  if (m.cplx) {
+    // every q of a general-orbital problem is its own slot (q = slot)
+    Timed t(P, KC_TC_PACK, 0.0, 16.0 * nq * pr.naux * (double)n * n + se * 6.0 * nq * pr.naux * (double)n * n);
+    CK(launch_pack_cplx(pc, P->W->ZT, nq, pr.naux, n, pr.con.order[bl.b0], pr.d_neg, P->W->Xt[s],
+                        m.xrows[s] * m.Rtot, m.Rtot, &sc->sX[s], P->cs));
+  } else {
+    const int nc = bl.w == 1 ? 1 : 2;
+    Timed t(P, KC_TC_PACK, 0.0, 16.0 * nq * pr.naux * (double)n * n + se * nq * pr.naux * nc * pr.npair[s]);
+    CK(launch_pack_split(pc, P->W->ZT, nq, pr.naux, n, nc, P->W->Xt[s], pr.npair[s] * m.Rtot, m.Rtot,
+                         m.row_base[bi], &sc->sX[s], P->cs));
+  }
+  return DMET_OK;
+}
+
+// The contraction's output scale: the operand holds Z + Z^T (general orbitals: Z); L^q = s (Z + Z^T)
+// (s Z), so the product carries s^2, and 1/Nk.
+double contract_scale(const Prob& pr) { return pr.lq_scale * pr.lq_scale / pr.nk; }
+
+// (5) The contraction of every ERI block (this problem's own launches).
+dmet_status_t mixed_contract(dmet_emb_plan_s* P, Prob& pr, const MixedMaps& mm, void* const* out) {
+  MixedPlan& m = pr.mx;
+  const int pc = m.prec;
+  const bool scaled = prec_scaled(pc);
+  MixScales* sc = P->W->sc;
+  const double oscale = contract_scale(pr);
+  for (int blk = 0; blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
+    const int sa = blk == 2 ? 1 : 0;
+    double fl = 0, by = 0;
+    contract_work(pr, blk, fl, by);
+    if (m.cplx) {
+      const long long na2 = (long long)pr.n[sa] * pr.n[sa], nb2 = (long long)pr.n[blk == 0 ? 0 : 1] * pr.n[blk == 0 ? 0 : 1];
+      // S4: the block's full ERI in the workspace first, then packed
+      const bool s4 = pr.pack == DMET_PACK_S4;
+      double* dst = s4 ? (double*)P->W->full : (double*)out[blk];
+      {
+        Timed t(P, KC_TC_CONTRACT, fl, by, 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk], tc::kTile));
+        if (blk == 1)
+          CK(launch_tc_rect(pc, mm.Xt[0], mm.Xt[1], m.d_jobs + m.jc_off[1], m.jc_cnt[1], m.d_segs, dst, 2 * nb2, oscale,
+                            P->ctl(), scaled ? &sc->fc[1] : nullptr, P->cs));
+        else
+          CK(launch_tc_herm(pc, mm.Xt[sa], mm.Xt[sa], m.d_jobs + m.jc_off[blk], m.jc_cnt[blk], m.d_segs, dst, na2,
+                            oscale, P->ctl(), scaled ? &sc->fc[blk] : nullptr, P->cs));
+      }
+      if (s4) {
+        Timed t(P, KC_PACK, 0.0, 16.0 * (double)na2 * nb2 + (double)eri_bytes_of(pr.d, blk));
+        CK(launch_pack_s4((const double2*)dst, pr.n[sa], pr.n[blk == 0 ? 0 : 1], blk == 1, (double2*)out[blk], P->cs));
+      }
+      continue;
+    }
     const int nsplit = m.jc_split_n[blk], f = m.jc_split_f[blk];
     Timed t(P, KC_TC_CONTRACT, fl, by, nsplit ? 2 : 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk], tc::kTile));
     if (blk == 1) {
@@ -1345,6 +1438,33 @@ dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const do
     }
   }
   return DMET_OK;
+}
+
+// The tensor-core path of Algorithm 1 for one problem: the operand scales and the orbital operands,
+// then block by block the split of L, the two half transforms and the pair packing, then the
+// contraction. With `req`, only the blocks that hold requested q run, their L^q are written out,
+// and nothing is packed or contracted (dmet_emb_transform_3idx).
+dmet_status_t eri_mixed(dmet_emb_plan_s* P, Prob& pr, const double2* L, const double2* const* C, void* const* out,
+                        const Lq3Req* req = nullptr) {
+  MixedPlan& m = pr.mx;
+  MixedMaps mm;
+  TRY(mixed_maps(P, pr, mm));
+  TRY(mixed_prep(P, pr, L, C, !req));
+  for (int bi = 0; bi < (int)m.blocks.size(); ++bi) {
+    const Block& bl = m.blocks[bi];
+    if (req) {
+      bool any = false;
+      for (int sl : req->slot) any |= sl >= bl.b0 && sl < bl.b1;
+      if (!any) continue;
+    }
+    for (int s = 0; s < pr.nspin; ++s) {
+      TRY(mixed_block_in(P, pr, bi, s, L, C));
+      TRY(mixed_block_gemms(P, pr, mm, bi, s));
+      TRY(mixed_block_out(P, pr, bi, s, req));
+    }
+  }
+  if (req) return DMET_OK;
+  return mixed_contract(P, pr, mm, out);
 }
 
 // Clears the per-kernel counters (their events go back to the pool).
@@ -1985,11 +2105,306 @@ static dmet_status_t enqueue_problem(dmet_emb_plan_s* P, int p, const void* L, c
   return DMET_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Grouped execution of a batch: the tensor-core GEMMs of every problem as persistent launches over
+// device tables of per-problem tensor maps, segment lists and output parameters.
+
+// Available when the plan holds several problems, all on tensor-core precisions, each with its own
+// workspace (they all fit the limit together), and none whose complex ERI is 4-fold packed (that
+// output passes through a per-problem full-block buffer).
+bool grouped_available(const dmet_emb_plan_s* P) {
+  if (P->probs.size() < 2 || P->side.empty()) return false;
+  for (const Prob& pr : P->probs)
+    if (!pr.mixed || (pr.mx.cplx && pr.pack == DMET_PACK_S4)) return false;
+  return true;
+}
+
+bool grouped_active(const dmet_emb_plan_s* P) { return P->batch_mode == 1 && grouped_available(P); }
+
+struct SlotArgs {
+  double* p[256];
+};
+__global__ void set_slots_kernel(double** slots, SlotArgs a, int n) {
+  if ((int)threadIdx.x < n) slots[threadIdx.x] = a.p[threadIdx.x];
+}
+
+// Uploads one launch: its jobs and its group table (entries filled on the host).
+dmet_status_t upload_launch(GroupedLaunch& l, const std::vector<GroupSpec>& specs, const std::vector<tc::TcJob>& jobs) {
+  const size_t gb = tc_group_bytes(l.kind, l.prec);
+  if (!gb || specs.empty() || jobs.empty()) return fail(DMET_ERR_CUDA, "empty grouped launch");
+  std::vector<unsigned char> host(gb * specs.size() + 128);
+  unsigned char* h = host.data() + ((128 - ((uintptr_t)host.data() & 127)) & 127);
+  CK(tc_group_fill(l.kind, l.prec, specs.data(), (int)specs.size(), h));
+  CK(cudaMalloc(&l.d_groups, gb * specs.size()));
+  CK(cudaMemcpy(l.d_groups, h, gb * specs.size(), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&l.d_jobs, jobs.size() * sizeof(tc::TcJob)));
+  CK(cudaMemcpy(l.d_jobs, jobs.data(), jobs.size() * sizeof(tc::TcJob), cudaMemcpyHostToDevice));
+  l.njobs = (int)jobs.size();
+  return DMET_OK;
+}
+
+// A class of one grouped launch being assembled: its table entries and jobs.
+struct LaunchBuild {
+  GroupedLaunch l;
+  std::vector<GroupSpec> specs;
+  std::vector<tc::TcJob> jobs;
+};
+
+// Appends problem jobs [off, off + cnt) of table m.jobs to class lb as entry `spec`.
+void add_group(LaunchBuild& lb, const GroupSpec& spec, const MixedPlan& m, int off, int cnt) {
+  const int g = (int)lb.specs.size();
+  lb.specs.push_back(spec);
+  for (int i = off; i < off + cnt; ++i) {
+    tc::TcJob j = m.jobs[i];
+    j.grp = g;
+    lb.jobs.push_back(j);
+  }
+}
+
+// Drops the captured graph (its nodes refer to the launch tables of the mode it was captured in).
+dmet_status_t drop_graph(dmet_emb_plan_s* P) {
+  if (!P->gexec) return DMET_OK;
+  CK(cudaStreamSynchronize(P->stream));
+  CK(cudaGraphExecDestroy(P->gexec));
+  P->gexec = nullptr;
+  P->gkey.clear();
+  return DMET_OK;
+}
+
+dmet_status_t build_grouped(dmet_emb_plan_s* P) {
+  TRY(drop_graph(P));
+  if (P->grp.built) CK(cudaStreamSynchronize(P->stream));
+  free_grouped(P->grp);
+  GroupedPlan& G = P->grp;
+  const int np = (int)P->probs.size();
+  // the workspace maps of every problem (the tables keep copies)
+  std::vector<MixedMaps> maps(np);
+  for (int p = 0; p < np; ++p) {
+    P->W = &P->ws[P->ws_of[p]];
+    TRY(mixed_maps(P, P->probs[p], maps[p]));
+  }
+  for (const Prob& pr : P->probs) G.rounds = std::max(G.rounds, (int)pr.mx.blocks.size());
+  CK(cudaMalloc(&G.d_slots, sizeof(double*) * 3 * np));
+  CK(cudaMemset(G.d_slots, 0, sizeof(double*) * 3 * np));
+  G.step1.assign(2 * G.rounds, {});
+  G.step2.assign(2 * G.rounds, {});
+  for (int r = 0; r < G.rounds; ++r)
+    for (int s = 0; s < 2; ++s) {
+      std::map<std::pair<int, int>, LaunchBuild> c1, c2;  // by (precision, tile width)
+      for (int p = 0; p < np; ++p) {
+        Prob& pr = P->probs[p];
+        const MixedPlan& m = pr.mx;
+        if (r >= (int)m.blocks.size() || s >= pr.nspin) continue;
+        Workspace& W = P->ws[P->ws_of[p]];
+        const bool scaled = prec_scaled(m.prec);
+        GroupSpec a{};
+        a.a = &maps[p].Ls;
+        a.b = &maps[p].Cb[s];
+        a.segs = m.d_segs;
+        a.fac = scaled ? &W.sc->f1[s] : nullptr;
+        a.out = W.A2;
+        a.ld = m.K2;
+        a.nao = pr.nao;
+        a.n = pr.n[s];
+        LaunchBuild& b1 = c1[{m.prec, m.bn1}];
+        b1.l.kind = kGroupSplitT;
+        b1.l.prec = m.prec;
+        b1.l.bn = m.bn1;
+        add_group(b1, a, m, m.j1_off[s][r], m.j1_cnt[s][r]);
+        double fl = 0, by = 0;
+        step1_work(pr, r, s, fl, by);
+        b1.l.flops += fl;
+        b1.l.bytes += by;
+        b1.l.exec += exec_flops(m, m.j1_off[s][r], m.j1_cnt[s][r], m.bn1);
+        GroupSpec z{};
+        z.a = &maps[p].A2[s];
+        z.b = &maps[p].Cc[s];
+        z.segs = m.d_segs;
+        z.fac = scaled ? &W.sc->f2[s] : nullptr;
+        z.out = W.ZT;
+        z.ld = 2LL * pr.n[s];
+        LaunchBuild& b2 = c2[{m.prec, m.bn2}];
+        b2.l.kind = kGroupPairs;
+        b2.l.prec = m.prec;
+        b2.l.bn = m.bn2;
+        add_group(b2, z, m, m.j2_off[s][r], m.j2_cnt[s][r]);
+        step2_work(pr, r, s, fl, by);
+        b2.l.flops += fl;
+        b2.l.bytes += by;
+        b2.l.exec += exec_flops(m, m.j2_off[s][r], m.j2_cnt[s][r], m.bn2);
+      }
+      for (auto& kv : c1) {
+        TRY(upload_launch(kv.second.l, kv.second.specs, kv.second.jobs));
+        G.step1[2 * r + s].push_back(kv.second.l);
+      }
+      for (auto& kv : c2) {
+        TRY(upload_launch(kv.second.l, kv.second.specs, kv.second.jobs));
+        G.step2[2 * r + s].push_back(kv.second.l);
+      }
+    }
+  // the contraction: every block of every problem, whole tiles (no K split: the tiles of all
+  // problems share the launch's last wave)
+  std::map<int, LaunchBuild> cc;
+  for (int p = 0; p < np; ++p) {
+    Prob& pr = P->probs[p];
+    const MixedPlan& m = pr.mx;
+    Workspace& W = P->ws[P->ws_of[p]];
+    const bool scaled = prec_scaled(m.prec);
+    for (int blk = 0; blk < (pr.nspin == 1 ? 1 : 3); ++blk) {
+      const int sa = blk == 2 ? 1 : 0, sb = blk == 0 ? 0 : 1;
+      GroupSpec c{};
+      c.a = &maps[p].Xt[sa];
+      c.b = &maps[p].Xt[sb];
+      c.segs = m.d_segs;
+      c.fac = scaled ? &W.sc->fc[blk] : nullptr;
+      c.outp = G.d_slots + 3 * p + blk;
+      c.scale = contract_scale(pr);
+      if (m.cplx) {
+        c.mode = blk == 1 ? 1 : 2;
+        c.ld = 2LL * pr.n[sb] * pr.n[sb];
+      } else {
+        c.mode = blk == 1 ? 1 : 0;
+        c.ld = pr.npair[sb];
+      }
+      LaunchBuild& b = cc[m.prec];
+      b.l.kind = kGroupContract;
+      b.l.prec = m.prec;
+      b.l.bn = tc::kTile;
+      const int g = (int)b.specs.size();
+      b.specs.push_back(c);
+      const int f = m.jc_split_f[blk], nsplit = m.jc_split_n[blk];
+      const int whole = m.jc_cnt[blk] - nsplit * f;
+      long long kc = 0;  // K of a whole tile
+      for (int gi = m.jc_seg0; gi < m.jc_seg0 + m.jc_nseg; ++gi) kc += m.segs[gi].nk;
+      const size_t before = b.jobs.size();
+      for (int i = m.jc_off[blk]; i < m.jc_off[blk] + m.jc_cnt[blk]; ++i) {
+        tc::TcJob j = m.jobs[i];
+        if (i - m.jc_off[blk] >= whole) {
+          // a split tile: its first part stands for the tile, over the whole K
+          if ((i - m.jc_off[blk] - whole) % f) continue;
+          j.seg0 = m.jc_seg0;
+          j.nseg = m.jc_nseg;
+          j.o2 = j.o3 = 0;
+        }
+        j.grp = g;
+        b.jobs.push_back(j);
+      }
+      double fl = 0, by = 0;
+      contract_work(pr, blk, fl, by);
+      b.l.flops += fl;
+      b.l.bytes += by;
+      b.l.exec += (double)(b.jobs.size() - before) * m.nprod * 2.0 * tc::kTile * tc::kTile * (double)kc;
+    }
+  }
+  for (auto& kv : cc) {
+    TRY(upload_launch(kv.second.l, kv.second.specs, kv.second.jobs));
+    G.contract.push_back(kv.second.l);
+  }
+  G.built = true;
+  return DMET_OK;
+}
+
+// Fork: the side streams wait for `origin`'s work so far. Join: `origin` waits for theirs.
+static dmet_status_t fork_sides(dmet_emb_plan_s* P, cudaStream_t origin) {
+  CK(cudaEventRecord(P->fork, origin));
+  for (cudaStream_t st : P->side) CK(cudaStreamWaitEvent(st, P->fork, 0));
+  return DMET_OK;
+}
+static dmet_status_t join_sides(dmet_emb_plan_s* P, cudaStream_t origin) {
+  for (size_t i = 0; i < P->side.size(); ++i) {
+    CK(cudaEventRecord(P->join[i], P->side[i]));
+    CK(cudaStreamWaitEvent(origin, P->join[i], 0));
+  }
+  return DMET_OK;
+}
+
+static dmet_status_t run_grouped(dmet_emb_plan_s* P, const GroupedLaunch& l, int kc) {
+  Timed t(P, kc, l.flops, l.bytes, 1, l.exec);
+  CK(launch_tc_grouped(l.kind, l.prec, l.bn, l.d_groups, l.d_jobs, l.njobs, P->ctl(), P->cs));
+  return DMET_OK;
+}
+
+// The batch in grouped form (device inputs only). Per problem, on the side streams: the checks,
+// the output clearing, the operand scales and the ket-side orbital operands. Then per round r and
+// spin s: each problem's split of its block r and bra-side operand (side streams), the grouped
+// first and second half transforms of all problems (the caller's stream), each problem's pair
+// packing (side streams). Last, the grouped contraction of every ERI block.
+static dmet_status_t enqueue_grouped(dmet_emb_plan_s* P, cudaStream_t origin, const void* const* L,
+                                     const void* const* const* C, void* const* const* eri_out) {
+  const int np = (int)P->probs.size(), ns = (int)P->side.size();
+  GroupedPlan& G = P->grp;
+  // this call's ERI block pointers, carried to the device by a kernel's parameters (so that a
+  // captured graph replays them)
+  for (int p0 = 0; p0 < 3 * np; p0 += 256) {
+    SlotArgs a;
+    std::memset(&a, 0, sizeof(a));
+    const int cnt = std::min(256, 3 * np - p0);
+    for (int i = 0; i < cnt; ++i) {
+      const int p = (p0 + i) / 3, b = (p0 + i) % 3;
+      a.p[i] = b < (P->probs[p].nspin == 1 ? 1 : 3) ? (double*)eri_out[p][b] : nullptr;
+    }
+    set_slots_kernel<<<1, 256, 0, origin>>>(G.d_slots + p0, a, cnt);
+    CK(cudaGetLastError());
+    P->launches += 1;
+  }
+  std::vector<const double2*> Ld(np, nullptr);
+  std::vector<std::array<const double2*, 2>> Cd(np, {nullptr, nullptr});
+  TRY(fork_sides(P, origin));
+  for (int p = 0; p < np; ++p) {
+    Prob& pr = P->probs[p];
+    P->cs = P->side[p % ns];
+    P->W = &P->ws[P->ws_of[p]];
+    if (P->prof) {
+      if ((int)P->pev.size() < np) P->pev.resize(np, {nullptr, nullptr});
+      for (cudaEvent_t* e : {&P->pev[p].first, &P->pev[p].second})
+        if (!*e) CK(cudaEventCreate(e));
+      CK(cudaEventRecord(P->pev[p].first, P->cs));
+    }
+    TRY(stage_inputs(P, pr, L[p], C[p], &Ld[p], Cd[p].data()));
+    CK(cudaMemsetAsync(P->dstats + 8 * p, 0, 8 * sizeof(double), P->cs));
+    TRY(run_orbital_checks(P, pr, p, Cd[p].data()));
+    TRY(run_l_check(P, pr, p, Ld[p]));
+    for (int b = 0; b < (pr.nspin == 1 ? 1 : 3); ++b)
+      CK(cudaMemsetAsync(eri_out[p][b], 0, eri_bytes_of(pr.d, b), P->cs));
+    TRY(mixed_prep(P, pr, Ld[p], Cd[p].data(), true));
+  }
+  for (int r = 0; r < G.rounds; ++r)
+    for (int s = 0; s < 2; ++s) {
+      if (G.step1[2 * r + s].empty()) continue;
+      for (int p = 0; p < np; ++p) {
+        Prob& pr = P->probs[p];
+        if (r >= (int)pr.mx.blocks.size() || s >= pr.nspin) continue;
+        P->cs = P->side[p % ns];
+        P->W = &P->ws[P->ws_of[p]];
+        TRY(mixed_block_in(P, pr, r, s, Ld[p], Cd[p].data()));
+      }
+      TRY(join_sides(P, origin));
+      P->cs = origin;
+      for (const GroupedLaunch& l : G.step1[2 * r + s]) TRY(run_grouped(P, l, KC_TC_TRANSFORM_1));
+      for (const GroupedLaunch& l : G.step2[2 * r + s]) TRY(run_grouped(P, l, KC_TC_TRANSFORM_2));
+      TRY(fork_sides(P, origin));
+      for (int p = 0; p < np; ++p) {
+        Prob& pr = P->probs[p];
+        if (r >= (int)pr.mx.blocks.size() || s >= pr.nspin) continue;
+        P->cs = P->side[p % ns];
+        P->W = &P->ws[P->ws_of[p]];
+        TRY(mixed_block_out(P, pr, r, s, nullptr));
+      }
+    }
+  TRY(join_sides(P, origin));
+  P->cs = origin;
+  for (const GroupedLaunch& l : G.contract) TRY(run_grouped(P, l, KC_TC_CONTRACT));
+  if (P->prof)
+    for (int p = 0; p < np; ++p) CK(cudaEventRecord(P->pev[p].second, origin));
+  return DMET_OK;
+}
+
 // Queues every problem behind `origin`: concurrently on the side streams (fork/join) when each
 // problem has its own workspace and no host staging is needed, else one after another.
 static dmet_status_t enqueue_all(dmet_emb_plan_s* P, cudaStream_t origin, bool staged, const void* const* L,
                                  const void* const* const* C, void* const* const* eri_out) {
   const int np = (int)P->probs.size();
+  if (!staged && grouped_active(P)) return enqueue_grouped(P, origin, L, C, eri_out);
   if (!staged && !P->side.empty()) {
     const int ns = (int)P->side.size();
     CK(cudaEventRecord(P->fork, origin));
@@ -2040,6 +2455,7 @@ dmet_status_t dmet_emb_eri(dmet_emb_plan_t P, const void* const* L, const void* 
       key.push_back(eri_out[p][b]);
     }
   }
+  if (!staged && grouped_active(P) && !P->grp.built) TRY(build_grouped(P));
   if (!staged && P->use_graph && !P->prof) {
     // Replay the captured graph while the buffers are the same; otherwise capture anew.
     if (!(P->gexec && key == P->gkey)) {
@@ -2112,12 +2528,12 @@ dmet_status_t dmet_emb_autotune(dmet_emb_plan_t P, const void* const* L, const v
   for (const Prob& pr : P->probs) any |= pr.mixed;
   if (!any) return DMET_OK;
   const bool prof = P->prof;
-  if (P->gexec) {
-    CK(cudaStreamSynchronize(P->stream));
-    CK(cudaGraphExecDestroy(P->gexec));
-    P->gexec = nullptr;
-    P->gkey.clear();
-  }
+  TRY(drop_graph(P));
+  // each problem is timed on its own (side-stream mode); the grouped tables are rebuilt afterwards
+  const int mode = P->batch_mode;
+  P->batch_mode = 0;
+  CK(cudaStreamSynchronize(P->stream));
+  free_grouped(P->grp);
   const int cand[3] = {128, 112, 96};
   const int np = (int)P->probs.size();
   int nmixed = 0;
@@ -2168,6 +2584,20 @@ dmet_status_t dmet_emb_autotune(dmet_emb_plan_t P, const void* const* L, const v
   }
   reset_profile(P);
   P->prof = prof;
+  TRY(drop_graph(P));
+  P->batch_mode = mode;
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_batch_mode(dmet_emb_plan_t P, int32_t mode, int32_t* active) {
+  clear_error();
+  if (!P) return fail(DMET_ERR_INVALID_ARG, "plan is NULL");
+  if (mode != 0 && mode != 1) return fail(DMET_ERR_INVALID_ARG, "batch mode %d", mode);
+  if (mode != P->batch_mode) {
+    TRY(drop_graph(P));
+    P->batch_mode = mode;
+  }
+  if (active) *active = grouped_active(P) ? 1 : 0;
   return DMET_OK;
 }
 
