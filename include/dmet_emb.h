@@ -364,11 +364,19 @@ DMET_API dmet_status_t dmet_emb_problem_ms(dmet_emb_plan_t plan, int32_t problem
  * 2 n_emb output columns is not always the fastest), each problem on its own side stream, by
  * running dmet_emb_eri on the given
  * buffers (device pointers; the outputs are overwritten with valid results), keeps the
- * fastest for each problem and, if the environment variable DMET_TUNE_CACHE names a file,
+ * fastest for each problem, then in the same way the K split of the contraction's last wave
+ * (dmet_emb_split_parts) and, if the environment variable DMET_TUNE_CACHE names a file,
  * appends the choice there; dmet_emb_plan reads that file for later plans of the same shape.
  * A captured graph is discarded. No counterpart in the paper (it is a GPU tiling choice). */
 DMET_API dmet_status_t dmet_emb_autotune(dmet_emb_plan_t plan, const void* const* L, const void* const* const* C,
                                          void* const* const* eri_out);
+
+/* The K split of the contraction's last wave in use for `problem` (side-stream and single-problem
+ * execution; grouped launches run whole tiles): for ERI block b (0 aa, 1 ab, 2 bb),
+ * parts[2 b] = the number of tiles split and parts[2 b + 1] = the parts per tile (1 = none).
+ * dmet_emb_autotune times the split factors 1, 2, 4 and 8 against the default (as many parts as
+ * fill the GPU's SMs, at most 8) and keeps the fastest. */
+DMET_API dmet_status_t dmet_emb_split_parts(dmet_emb_plan_t plan, int32_t problem, int32_t* parts);
 
 /* The tile widths in use for `problem`: bn[0] (half transform 1), bn[1] (half transform 2). */
 DMET_API dmet_status_t dmet_emb_tile_widths(dmet_emb_plan_t plan, int32_t problem, int32_t* bn);

@@ -140,6 +140,8 @@ def lib() -> ctypes.CDLL:
         L.dmet_emb_graph.restype = st
         L.dmet_emb_batch_mode.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.dmet_emb_batch_mode.restype = st
+        L.dmet_emb_split_parts.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.dmet_emb_split_parts.restype = st
         L.dmet_emb_problem_ms.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
         L.dmet_emb_problem_ms.restype = st
         L.dmet_emb_autotune.argtypes = [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.POINTER(_P)),
@@ -352,6 +354,13 @@ def dmet_emb_batch_mode(plan, mode):
     active = ctypes.c_int32()
     _check(lib().dmet_emb_batch_mode(_P(plan), int(mode), ctypes.byref(active)))
     return bool(active.value)
+
+
+def dmet_emb_split_parts(plan, problem):
+    """[(tiles split, parts per tile)] of the aa, ab and bb contraction blocks."""
+    a = (ctypes.c_int32 * 6)()
+    _check(lib().dmet_emb_split_parts(_P(plan), problem, a))
+    return [(a[2 * b], a[2 * b + 1]) for b in range(3)]
 
 
 def dmet_emb_problem_ms(plan, problem):

@@ -219,6 +219,10 @@ struct MixedPlan {
   // per contraction block: split tiles (their K parts are the last jc_split_n * jc_split_f jobs)
   int jc_split_n[3] = {0, 0, 0}, jc_split_f[3] = {1, 1, 1};
   int jc_seg0 = 0, jc_nseg = 0;  // the contraction's segment list (a whole tile's K)
+  int jc_tail[3] = {0, 0, 0};    // tiles past the last multiple of the SM count
+  // K parts of each last-wave tile: 0 = the heuristic (enough to fill the GPU, at most 8), 1 = no
+  // split, 2..8 = that many (dmet_emb_autotune times them)
+  int split_pref = 0;
   tc::TcJob* d_jobs = nullptr;
   tc::Segment* d_segs = nullptr;
   long long Ls_rows = 0, A2_rows[2] = {0, 0};
@@ -1121,7 +1125,8 @@ void build_mixed(Prob& pr) {
     if (blk != 1) {
       const int G = device_sms();
       const int tail = m.jc_cnt[blk] % G;
-      int f = tail ? std::min(G / tail, 8) : 1;
+      m.jc_tail[blk] = tail;
+      int f = tail ? (m.split_pref >= 1 ? std::min(m.split_pref, 8) : std::min(G / tail, 8)) : 1;
       f = std::min(f, sc_cnt);
       const long long cap = zt_bytes(pr) / ((long long)T * T * 8);
       while (f >= 2 && (long long)tail * f > cap) --f;
@@ -1508,7 +1513,7 @@ std::string tune_key(const Prob& pr) {
   return b;
 }
 
-bool tune_cache_lookup(const Prob& pr, int& bn1, int& bn2) {
+bool tune_cache_lookup(const Prob& pr, int& bn1, int& bn2, int& split) {
   const char* path = std::getenv("DMET_TUNE_CACHE");
   if (!path) return false;
   FILE* f = fopen(path, "r");
@@ -1517,15 +1522,18 @@ bool tune_cache_lookup(const Prob& pr, int& bn1, int& bn2) {
   char line[256];
   bool found = false;
   while (fgets(line, sizeof(line), f)) {
-    int v[10];
-    if (sscanf(line, "%d %d %d %d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7], &v[8],
-               &v[9]) != 10)
-      continue;
+    int v[11];
+    v[10] = 0;
+    const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
+                           &v[7], &v[8], &v[9], &v[10]);
+    if (got != 10 && got != 11) continue;
     char k[160];
     snprintf(k, sizeof(k), "%d %d %d %d %d %d %d %d", v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]);
-    if (key == k && (v[8] == 128 || v[8] == 112 || v[8] == 96) && (v[9] == 128 || v[9] == 112 || v[9] == 96)) {
+    if (key == k && (v[8] == 128 || v[8] == 112 || v[8] == 96) && (v[9] == 128 || v[9] == 112 || v[9] == 96) &&
+        v[10] >= 0 && v[10] <= 8) {
       bn1 = v[8];
       bn2 = v[9];
+      split = v[10];
       found = true;
     }
   }
@@ -1538,7 +1546,7 @@ void tune_cache_store(const Prob& pr) {
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d\n", tune_key(pr).c_str(), pr.mx.bn1, pr.mx.bn2);
+  fprintf(f, "%s %d %d %d\n", tune_key(pr).c_str(), pr.mx.bn1, pr.mx.bn2, pr.mx.split_pref);
   fclose(f);
 }
 
@@ -1749,7 +1757,7 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     }
     // q-block size: the largest (<= 8, or <= DMET_QBLOCK, entries per launch <= 65535) whose
     // workspace fits.
-    if (pr.mixed) tune_cache_lookup(pr, pr.mx.bn1, pr.mx.bn2);
+    if (pr.mixed) tune_cache_lookup(pr, pr.mx.bn1, pr.mx.bn2, pr.mx.split_pref);
     auto total_for = [&](int b) {
       size_t t = ws_for(pr, b).total();
       if (pr.mixed) {
@@ -2580,6 +2588,47 @@ dmet_status_t dmet_emb_autotune(dmet_emb_plan_t P, const void* const* L, const v
     pr.mx.bn1 = bn1[p];
     pr.mx.bn2 = bn2[p];
     TRY(upload_mixed(pr));
+  }
+  // split-K of the contraction's last wave (problems whose packed blocks leave a partial wave):
+  // the heuristic, no split, 2, 4 and 8 parts per tile, timed the same way
+  bool tail = false;
+  for (const Prob& pr : P->probs) tail |= pr.mixed && (pr.mx.jc_tail[0] > 0 || pr.mx.jc_tail[2] > 0);
+  if (tail) {
+    std::vector<double> bs(np, 1e300);
+    std::vector<int> bf(np, 0);
+    for (int f : {0, 1, 2, 4, 8}) {
+      for (Prob& pr : P->probs)
+        if (pr.mixed) {
+          pr.mx.split_pref = f;
+          TRY(upload_mixed(pr));
+        }
+      P->prof = false;
+      TRY(dmet_emb_eri(P, L, C, eri_out));
+      reset_profile(P);
+      P->prof = true;
+      TRY(dmet_emb_eri(P, L, C, eri_out));
+      CK(cudaStreamSynchronize(P->stream));
+      double tc = 0;
+      for (auto& e : P->ks[KC_TC_CONTRACT].ev) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e.first, e.second));
+        tc += ms;
+      }
+      for (int p = 0; p < np; ++p) {
+        if (!P->probs[p].mixed) continue;
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, P->pev[p].first, P->pev[p].second));
+        const double t = nmixed == 1 ? tc : ms;
+        if (t < bs[p]) bs[p] = t, bf[p] = f;
+      }
+    }
+    for (int p = 0; p < np; ++p)
+      if (P->probs[p].mixed) P->probs[p].mx.split_pref = bf[p];
+  }
+  for (int p = 0; p < np; ++p) {
+    Prob& pr = P->probs[p];
+    if (!pr.mixed) continue;
+    TRY(upload_mixed(pr));
     tune_cache_store(pr);
   }
   reset_profile(P);
@@ -2598,6 +2647,18 @@ dmet_status_t dmet_emb_batch_mode(dmet_emb_plan_t P, int32_t mode, int32_t* acti
     P->batch_mode = mode;
   }
   if (active) *active = grouped_active(P) ? 1 : 0;
+  return DMET_OK;
+}
+
+dmet_status_t dmet_emb_split_parts(dmet_emb_plan_t P, int32_t problem, int32_t* parts) {
+  clear_error();
+  if (!P || !parts) return fail(DMET_ERR_INVALID_ARG, "NULL argument");
+  if (problem < 0 || problem >= (int)P->probs.size()) return fail(DMET_ERR_INVALID_ARG, "problem %d", problem);
+  const Prob& pr = P->probs[problem];
+  for (int b = 0; b < 3; ++b) {
+    parts[2 * b] = pr.mixed ? pr.mx.jc_split_n[b] : 0;
+    parts[2 * b + 1] = pr.mixed ? pr.mx.jc_split_f[b] : 1;
+  }
   return DMET_OK;
 }
 

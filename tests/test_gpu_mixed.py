@@ -146,6 +146,7 @@ def test_mixed_autotune(torch, tmp_path, monkeypatch):
     try:
         dm.dmet_emb_autotune(plan, [Ld], [Cd], [[out]])
         widths = dm.dmet_emb_tile_widths(plan, 0)
+        parts = dm.dmet_emb_split_parts(plan, 0)
         out.fill_(float("nan"))
         dm.dmet_emb_eri(plan, [Ld], [Cd], [[out]])
         st, _ = dm.dmet_emb_status(plan, 0)
@@ -153,7 +154,10 @@ def test_mixed_autotune(torch, tmp_path, monkeypatch):
         dm.dmet_emb_destroy(plan)
     assert st == B.DMET_OK
     assert widths[0] in (128, 112, 96) and widths[1] in (128, 112, 96)
-    assert cache.read_text().split()[-2:] == [str(widths[0]), str(widths[1])]
+    fields = cache.read_text().split()
+    assert fields[-3:-1] == [str(widths[0]), str(widths[1])]
+    assert int(fields[-1]) in (0, 1, 2, 4, 8)
+    assert parts[0][1] >= 1
     check(out.cpu().numpy(), oracle.pack_s8(oracle.embedded_eri(L, Cs[0], spec.mesh).real))
 
 
@@ -209,3 +213,29 @@ def test_mixed_qblock_cap_matches_oracle(torch, monkeypatch, qblock):
     assert np.array_equal(dev[0], host[0])
     check(dev[0], ref)
     assert rel_fro(dev[0], base[0]) < TOL
+
+
+@pytest.mark.parametrize("split", [1, 2, 8])
+def test_mixed_split_parts(torch, split, tmp_path, monkeypatch):
+    """The K split of the contraction's last wave (forced through the tuning cache) changes only
+    the summation grouping of the tail tiles: parity holds for every factor."""
+    import paper_1909_08596_gb300 as dm
+    spec = spec_of((3, 3, 1), 10, 37, 70)
+    L, Cs, _ = synth.make_problem(spec)
+    cache = tmp_path / "tune.txt"
+    cache.write_text(f"3 3 1 10 37 70 0 1 128 128 {split}\n")
+    monkeypatch.setenv("DMET_TUNE_CACHE", str(cache))
+    d = desc_of(spec)
+    Ld = torch.from_numpy(L).cuda()
+    Cd = [torch.from_numpy(c).cuda() for c in Cs]
+    out = torch.full((B.dmet_emb_eri_bytes(d, 0) // 8,), float("nan"), dtype=torch.float64, device="cuda")
+    plan = dm.dmet_emb_plan(d, stream=torch.cuda.current_stream().cuda_stream)
+    try:
+        tiles, f = dm.dmet_emb_split_parts(plan, 0)[0]
+        dm.dmet_emb_eri(plan, [Ld], [Cd], [[out]])
+        st, _ = dm.dmet_emb_status(plan, 0)
+    finally:
+        dm.dmet_emb_destroy(plan)
+    assert st == B.DMET_OK
+    assert f == (1 if split == 1 or tiles == 0 else split) or (tiles > 0 and f < split)
+    check(out.cpu().numpy(), oracle.pack_s8(oracle.embedded_eri(L, Cs[0], spec.mesh).real))
