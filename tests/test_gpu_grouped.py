@@ -101,9 +101,12 @@ def test_grouped_matches_oracle_and_side_streams(torch):
     _check_oracle(probs, g)
     s_, st2, active2, _ = _run(torch, probs, 0)
     assert not active2 and all(s == B.DMET_OK for s in st2)
+    # The side-stream run splits the last wave's tiles in K; the two groupings of the same segment
+    # sums may round the FP32 result differently (one unit in the last place, 2^-24 relative).
     for ra, rb in zip(g, s_):
         for x, y in zip(ra, rb):
-            assert rel_fro(x, y) < 1e-12
+            assert np.abs(x - y).max() <= 2.0 ** -22 * np.abs(y).max()
+            assert rel_fro(x, y) < 1e-7
 
 
 def test_grouped_graph_replay_is_exact(torch):
