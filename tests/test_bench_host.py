@@ -48,3 +48,23 @@ def test_useful_flops_nio_shape():
     tot, t, c = bench.useful_flops(spec, [300, 300])
     assert abs(c - 470e12) / 470e12 < 0.01      # aa + bb SYRK and the ab GEMM at K = 57 600
     assert 150e12 < t < 250e12
+
+
+def test_resident_groups_cover_in_order_within_budget():
+    needs = [5, 3, 9, 1, 1, 12, 2, 2]
+    groups = bench.resident_groups(needs, 10)
+    assert [i for g in groups for i in g] == list(range(len(needs)))
+    for g in groups:
+        assert len(g) == 1 or sum(needs[i] for i in g) <= 10
+    assert groups == [[0, 1], [2, 3], [4], [5], [6, 7]]
+    assert bench.resident_groups([], 10) == []
+
+
+def test_stated_batch_specs_follow_the_stated_ranges():
+    import synth
+    specs = synth.batch_specs(48, n_ao_range=(26, 104), n_emb_range=(40, 300))
+    assert len(specs) == 48
+    assert all(26 <= s.n_ao <= 104 and 40 <= s.n_emb <= 300 for s in specs)
+    assert all(s.n_aux == int(8.5 * s.n_ao + 0.5) for s in specs)
+    assert {s.nk for s in specs} <= {8, 27, 36, 64}
+    assert sum(s.n_spin == 2 for s in specs) == 24
