@@ -1160,9 +1160,9 @@ void build_mixed(Prob& pr) {
       m.useful_t2 += 8.0 * n * naux * n * nao * pr.s.nrep[q];
     }
     if (m.cplx) {
-      // complex products over every q: 8 flops per multiply-add of (ij|kl) over the n_aux terms
+      // complex products over every q: 8 flops per multiply-add of (ij|kl), kl <= ij, over the n_aux terms
       const double n2 = (double)pr.n[sp] * pr.n[sp];
-      m.useful_c += 8.0 * n2 * n2 * pr.naux * (double)pr.con.order.size();
+      m.useful_c += 4.0 * n2 * (n2 + 1.0) * pr.naux * (double)pr.con.order.size();
     } else {
       m.useful_c += (double)pr.npair[sp] * (pr.npair[sp] + 1.0) * K;
     }
@@ -1256,7 +1256,9 @@ void contract_work(const Prob& pr, int blk, double& fl, double& by) {
   const double se = (double)m.ns * m.esz;
   if (m.cplx) {
     const double na2 = (double)pr.n[sa] * pr.n[sa], nb2 = (double)pr.n[sb] * pr.n[sb];
-    fl = 8.0 * na2 * nb2 * pr.naux * (double)pr.con.order.size();
+    // 8 flops per complex multiply-add; a same-spin block counts its (ij|kl) with kl <= ij only
+    // ((kl|ij) = (ij|kl)), as the real blocks count their symmetric half
+    fl = (blk == 1 ? 8.0 * na2 * nb2 : 4.0 * na2 * (na2 + 1.0)) * pr.naux * (double)pr.con.order.size();
     // the bra rows' and ket rows' slices read once, the complex block written once
     by = se * m.Rtot * (na2 + 2 * nb2) + 16.0 * na2 * nb2;
     return;
