@@ -658,6 +658,7 @@ def run_batch(args):
             dm.dmet_emb_profile(plan, True)
             dm.dmet_emb_eri(plan, Ls, Cds, outs)
             lat = sorted(dm.dmet_emb_problem_ms(plan, p) for p in range(len(specs)))
+            kern = kernel_table([dm.dmet_emb_profile_read(plan, k) for k in range(dm.dmet_emb_profile_count())])
             dm.dmet_emb_profile(plan, False)
             dm.dmet_emb_graph(plan, True)
             for _ in range(args.warmup):
@@ -681,7 +682,8 @@ def run_batch(args):
                     "latency": "batch completion (every problem ends with the last grouped launch)" if grouped
                     else "per problem on its side stream",
                     "grouped_launches": bool(grouped), "gpu_launches_per_batch": int(launches) // max(steps, 1),
-                    "all_ok": all(x == 0 for x in st), "steps": steps}
+                    "all_ok": all(x == 0 for x in st), "steps": steps,
+                    "kernels_profiled_call": kern}
         results[arm] = [[o.cpu().numpy() for o in row] for row in outs]
     # errors vs the oracle on 8-orbital subsets of every problem (alpha block)
     import oracle

@@ -1771,9 +1771,17 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
       return t;
     };
     int bq = 8;
+    bool capped = false;
     if (const char* e = std::getenv("DMET_QBLOCK")) {
       const int v = std::atoi(e);
-      if (v >= 1 && v < bq) bq = v;
+      if (v >= 1 && v < bq) bq = v, capped = true;
+    }
+    // A small problem takes every q of a weight class in one block when that workspace stays under
+    // 512 MiB: fewer, fuller launches (the batched workloads), the same results.
+    const int all = std::max(1, (int)std::max(pr.con.order.size(), pr.nat.order.size()));
+    if (!capped && all > bq) {
+      const size_t small = std::min(P->ws_limit, (size_t)512 << 20);
+      if (total_for(all) <= small && max_entries(pr.nat, all) <= 65535 && max_entries(pr.con, all) <= 65535) bq = all;
     }
     while (bq > 1 && (total_for(bq) > P->ws_limit || max_entries(pr.nat, bq) > 65535)) --bq;
     const size_t tot = total_for(bq);
