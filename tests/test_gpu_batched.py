@@ -73,9 +73,15 @@ def test_batched_shared_workspace_same_result():
     probs = _problems(seed=78)
     a, _, _, _ = _run(torch, probs)
     b, _, _, _ = _run(torch, probs, workspace_limit=1 << 26)  # too small for all: problems run in turn
-    for ra, rb in zip(a, b):
+    # The smaller limit can also change a problem's q-block size: FP64 sums then run in another order
+    # (1e-12), and a tensor-core problem's last-wave K split may change, which can move its FP32 result
+    # rounding by one unit in the last place (2^-24 relative).
+    for (_, _, _, d), ra, rb in zip(probs, a, b):
         for x, y in zip(ra, rb):
-            assert rel_fro(y, x) < 1e-12
+            if d.prec == B.DMET_PREC_FP64:
+                assert rel_fro(y, x) < 1e-12
+            else:
+                assert np.abs(x - y).max() <= 2.0 ** -22 * np.abs(x).max()
 
 
 def test_graph_replay_same_result():
