@@ -27,6 +27,7 @@
 #pragma once
 
 #include <cstring>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -61,6 +62,42 @@ template <class T>
 struct __align__(2 * sizeof(T)) Pair2 {
   T a, b;
 };
+
+// The slices of the two real components (re = hr + lr, im = hi + li) of one complex element, as
+// (re, im) pairs per slice: the precision's own split (prec.cuh), with the two components of each
+// 16-bit slice rounded by one paired conversion (the same round-to-nearest of each value).
+template <class PREC>
+__device__ __forceinline__ void split_pair(float hr, float lr, float hi, float li, Pair2<typename PREC::T>* out) {
+  using T = typename PREC::T;
+  if constexpr (std::is_same<T, __nv_bfloat16>::value || std::is_same<T, __half>::value) {
+    using T2 = typename std::conditional<std::is_same<T, __half>::value, __half2, __nv_bfloat162>::type;
+    auto cvt = [](float a, float b) -> T2 {
+      if constexpr (std::is_same<T, __half>::value) return __floats2half2_rn(a, b);
+      else return __floats2bfloat162_rn(a, b);
+    };
+    auto back = [](T2 v) -> float2 {
+      if constexpr (std::is_same<T, __half>::value) return __half22float2(v);
+      else return __bfloat1622float2(v);
+    };
+    T2 s = cvt(hr, hi);
+    out[0] = *reinterpret_cast<Pair2<T>*>(&s);
+    float2 f = back(s);
+    const float rr = (hr - f.x) + lr, ri = (hi - f.y) + li;
+    s = cvt(rr, ri);
+    out[1] = *reinterpret_cast<Pair2<T>*>(&s);
+    if constexpr (PREC::kSlices == 3) {
+      f = back(s);
+      s = cvt(rr - f.x, ri - f.y);
+      out[2] = *reinterpret_cast<Pair2<T>*>(&s);
+    }
+  } else {
+    T a[3], b[3];
+    PREC::split(hr, lr, a);
+    PREC::split(hi, li, b);
+#pragma unroll
+    for (int t = 0; t < PREC::kSlices; ++t) out[t] = Pair2<T>{a[t], b[t]};
+  }
+}
 
 // x * s as a two-float (hi, lo): the two-float form of the double x, scaled exactly.
 __device__ __forceinline__ float2 scaled_ff(double x, float s) {
@@ -102,11 +139,10 @@ __global__ void __launch_bounds__(256) split_L_kernel(const double2* __restrict_
       const int x = x0 + u * stride;
       if (x >= total) break;
       const float2 re = scaled_ff(v[u].x, s), im = scaled_ff(v[u].y, s);
-      T a[3], b[3];
-      PREC::split(re.x, re.y, a);
-      PREC::split(im.x, im.y, b);
+      Pair2<T> pr[3];
+      split_pair<PREC>(re.x, re.y, im.x, im.y, pr);
 #pragma unroll
-      for (int t = 0; t < PREC::kSlices; ++t) dst[x + t * ss] = Pair2<T>{a[t], b[t]};
+      for (int t = 0; t < PREC::kSlices; ++t) dst[x + t * ss] = pr[t];
     }
   }
 }
@@ -339,12 +375,11 @@ struct EpiSplitT {
     for (int c = 0; c < H; c += 2) {
       if (col0 + c >= j.n_valid) break;
       const int jj = (j.o1 + col0 + c) >> 1;
-      T a[3], b[3];  // (re, im) of each slice
-      PREC::split(hi[c], lo[c], a);
-      PREC::split(hi[c + 1], lo[c + 1], b);
+      Pair2<T> pr[3];  // (re, im) of each slice
+      split_pair<PREC>(hi[c], lo[c], hi[c + 1], lo[c + 1], pr);
       T* o = p.out + (rbase + jj) * NS * p.K2 + (cidx / BK) * (NS * BK) + (cidx % BK);
 #pragma unroll
-      for (int t = 0; t < NS; ++t) *reinterpret_cast<Pair2<T>*>(o + t * BK) = Pair2<T>{a[t], b[t]};
+      for (int t = 0; t < NS; ++t) *reinterpret_cast<Pair2<T>*>(o + t * BK) = pr[t];
     }
   }
 };
