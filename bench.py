@@ -904,8 +904,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=-1, help="timed end-to-end steps (-1: 3, or 2 above 100 GB)")
     ap.add_argument("--e2e-qblock", type=int, default=1,
                     help="q-block cap (DMET_QBLOCK) of the end-to-end plan; 0 = the plan's own choice")
-    ap.add_argument("--check-orbitals", type=int, default=48,
-                    help="orbitals per spin of the seeded subset on which the oracle checks every result")
+    ap.add_argument("--check-orbitals", type=int, default=-1,
+                    help="orbitals per spin of the seeded subset on which the oracle checks every result "
+                         "(-1: 48, or 24 when L exceeds 100 GB, where the oracle streams every aux function's "
+                         "L and its time grows with the subset)")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle check and the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-autotune", action="store_true")
@@ -966,7 +968,8 @@ def main():
     gen_s = time.perf_counter() - t0
     L_bytes = holder["Ld"].numel() * 16
 
-    S = subset_orbitals(spec, args.check_orbitals)
+    n_check = args.check_orbitals if args.check_orbitals > 0 else (24 if L_bytes > (100 << 30) else 48)
+    S = subset_orbitals(spec, n_check)
     positions = block_positions(spec, S)
     nblk = len(positions)
 

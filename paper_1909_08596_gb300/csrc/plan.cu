@@ -198,10 +198,13 @@ struct MixedPlan {
   // Defaults of the segment knobs. The tensor cores add each MMA's products into the FP32 accumulator
   // with an error of about 2^-24 of the accumulator per MMA that grows linearly with the MMAs a
   // segment accumulates (measured 5.5e-8 per MMA of K = 16 on an h-BN-shaped contraction), so every
-  // FP32 sum is kept short: 128 K (8 MMAs) per leading-sum segment, 64 for the first transform, and
+  // FP32 sum is kept short: 128 K (8 MMAs) per leading-sum segment, also for the first transform, and
   // the correction sum read back after every segment (at the NiO-shaped workload, K = 57 600: the
   // alpha-beta block's error fell from 1.5e-6 with whole-job correction runs to 3.8e-7, at +3% time).
-  int kseg_def = 128, kseg1_def = 64, crun_def = 1;
+  // 64-K segments in the first transform lower the NiO-shaped errors further (4.6e-7 / 3.8e-7 against
+  // 5.3e-7 / 4.5e-7) but cost 4% of the call: its epilogue then reads an accumulator every two K blocks
+  // while the previous tile's stores keep it busy.
+  int kseg_def = 128, kseg1_def = 128, crun_def = 1;
   // General (complex) orbitals: every q is contracted (weight 1, 2 n_aux K rows each: Re, Im), and
   // the contraction operand of spin s has 3 n_s^2 rows (bra rows ij, then ket rows 2 kl + c);
   // real orbitals: n_pair rows. xrows[s] is that row count.
