@@ -885,6 +885,76 @@ def run_complex(args):
     return 0
 
 
+def run_shard_emulation(args):
+    """The q-shard split of one problem (the multi-GPU path of `--multi qshard`) run shard after shard on
+    this one GPU: each shard is the plan of one rank (its q range, its blocks of the reduced L), timed on
+    its own; the FP64 sum of the shards' partial ERI blocks is compared with the unsharded call. The
+    shards never wait on one another. What a multi-GPU run adds, the sum-reduce of the ERI blocks over
+    NCCL, is not measured here: its bytes are reported."""
+    import torch
+    import paper_1909_08596_gb300 as dm
+    from paper_1909_08596_gb300 import build as libbuild
+    from synth import gpu as sgpu
+    libbuild.build()
+    spec = synth.CONFIGS[args.workload]
+    n_list = [spec.n_emb] * spec.n_spin
+    nshard = args.emulate_shards
+    ranges = shard_ranges(spec.mesh, spec.n_ao, n_list, nshard)
+    _, Cs, _ = synth.make_problem(spec, with_L=False)
+    Cd = [torch.from_numpy(c).cuda() for c in Cs]
+    pcode = PREC_CODES[args.prec]
+    layout = dm.binding.DMET_L_REDUCED
+    stream = torch.cuda.current_stream()
+
+    def one(q_range, outs):
+        d = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, n_list, n_spin=spec.n_spin, l_layout=layout,
+                         q_range=q_range, prec=pcode)
+        Ld = sgpu.make_L_pairs_device(torch, spec, dm.dmet_emb_l_pairs(d))
+        torch.cuda.synchronize()
+        plan = dm.dmet_emb_plan(d, stream=stream.cuda_stream, workspace_limit=torch.cuda.mem_get_info()[0] - (2 << 30))
+        try:
+            dm.dmet_emb_eri(plan, [Ld], [Cd], [outs])
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                dm.dmet_emb_eri(plan, [Ld], [Cd], [outs])
+            e1.record(stream)
+            stream.synchronize()
+            st = dm.dmet_emb_status(plan, 0)[0]
+        finally:
+            dm.dmet_emb_destroy(plan)
+        del Ld
+        torch.cuda.empty_cache()
+        return e0.elapsed_time(e1) / args.steps, st
+
+    d0 = dm.make_desc(spec.mesh, spec.n_ao, spec.n_aux, n_list, n_spin=spec.n_spin, l_layout=layout, prec=pcode)
+    nblk = 1 if spec.n_spin == 1 else 3
+    full = [torch.empty(dm.dmet_emb_eri_bytes(d0, b) // 8, dtype=torch.float64, device="cuda") for b in range(nblk)]
+    ms_full, st_full = one(None, full)
+    total = [torch.zeros_like(t) for t in full]
+    part = [torch.empty_like(t) for t in full]
+    shard_ms, sts = [], []
+    for r in ranges:
+        ms, st = one(r, part)
+        shard_ms.append(ms)
+        sts.append(st)
+        for t, x in zip(total, part):
+            t += x
+    diff = max(float(torch.linalg.norm(t - f) / torch.linalg.norm(f)) for t, f in zip(total, full))
+    line = {"metric": METRIC, "workload": f"{args.workload}: q-shard split emulated shard by shard on one GPU",
+            "shards": nshard, "q_ranges": ranges, "dtype": args.prec, "unsharded_ms": ms_full,
+            "shard_ms": shard_ms, "sum_of_shards_ms": sum(shard_ms),
+            "balance_max_over_mean": max(shard_ms) / (sum(shard_ms) / nshard),
+            "slowest_shard_ms": max(shard_ms),
+            "reduce_bytes_per_rank": int(sum(t.numel() * 8 for t in full)),
+            "partial_sum_vs_unsharded_rel_fro": diff, "all_ok": st_full == 0 and all(x == 0 for x in sts),
+            "note": "no multi-GPU time is claimed: the N-GPU step would be the slowest shard plus an FP64 "
+                    "sum-reduce of reduce_bytes_per_rank over NCCL, neither measured together here"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -911,6 +981,9 @@ def main():
     ap.add_argument("--no-check", action="store_true", help="skip the oracle check and the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--emulate-shards", type=int, default=0,
+                    help="run the q-shard split of the workload over this many shards one after another on this "
+                         "GPU (each shard timed alone; the shards' FP64 partial sum checked against one call)")
     ap.add_argument("--multi", default="weak", choices=["weak", "qshard"],
                     help="N > 1: weak = one problem per rank (no exchange); qshard = one problem split into q "
                          "shards over the ranks, with an FP64 sum of the partial ERIs (strong scaling)")
@@ -919,6 +992,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args)
+    if args.emulate_shards > 1:
+        return run_shard_emulation(args)
     if args.workload == "batch48":
         return run_batch(args)
     if args.workload == "batch48_stated":
