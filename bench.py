@@ -50,10 +50,28 @@ REF_SAMPLE_ORBITALS = 24
 PREC_CODES = {"fp64": 0, "bf16x3": 1, "tf32": 2, "tf32x3": 3, "fp16x2": 4}
 PEAK_RATIO = {"bf16x3": 1.0, "fp16x2": 1.0, "tf32": 0.5, "tf32x3": 0.5}
 PREC_DTYPE = {"fp64": "f64", "bf16x3": "bf16x3", "fp16x2": "fp16x2", "tf32": "tf32", "tf32x3": "tf32x3"}
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of a tensor kernel, from an ncu capture of the
-# kernels as they are now: (workload, path, kernel class) -> bytes. Empty until such a capture exists; the
-# roofline's traffic is then null.
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel class, from an ncu capture:
+# (workload, path, kernel class) -> (bytes per launch, digest of the kernel sources at the capture). The
+# bytes are the class's DRAM bytes per call over its launches per call (the same per-launch unit as the
+# roofline's `achieved`). The roofline reports them only while the sources still have that digest
+# (kernel_sources_digest); after any change to the kernels or their job tables, traffic is null.
+KERNEL_SOURCES = ["tc_gemm.cuh", "tc_common.cuh", "prec.cuh", "split.cuh", "mixed_impl.cuh", "plan.cu"]
 TRAFFIC = {}
+
+
+def kernel_sources_digest():
+    import hashlib
+    h = hashlib.sha256()
+    base = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1909_08596_gb300", "csrc")
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(base, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(key):
+    t = TRAFFIC.get(key)
+    return t[0] if t and t[1] == kernel_sources_digest() else None
 
 
 def schedule_counts(mesh):
@@ -349,7 +367,7 @@ def roofline(spec, prec, kstats, sustained=False):
         peak = SMS * DFMA_PER_SM_CLK * 2 * 2070e6 / 1e12
         achieved = top["flops"] / (top["ms"] / 1e3) / 1e12 if top["ms"] > 0 else 0.0
         return {"bound": "alu", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": TRAFFIC.get((spec.name, prec, top["name"])),
+                "frac": achieved / peak, "traffic": traffic_of((spec.name, prec, top["name"])),
                 "flops_counted": "algorithmic FP64 flops",
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (FP64 runs on the CUDA cores)",
                 "avg_launch_ms": avg_ms}
@@ -369,7 +387,7 @@ def roofline(spec, prec, kstats, sustained=False):
     main, other = (hbm, tensor) if t_hbm > t_tensor else (tensor, hbm)
     useful = top["flops"] / (top["ms"] / 1e3) / 1e12 if top["ms"] > 0 else 0.0
     return {"bound": "hbm" if main is hbm else "tensor", "kernel": top["name"], **main,
-            "traffic": TRAFFIC.get((spec.name, prec, top["name"])),
+            "traffic": traffic_of((spec.name, prec, top["name"])),
             "other_bound": {"bound": "tensor" if main is hbm else "hbm", **other},
             "flops_counted": "executed tensor flops (every slice product issued, whole tiles)",
             "bytes_counted": "algorithmic bytes per launch: operands read once, result written once",

@@ -68,3 +68,12 @@ def test_stated_batch_specs_follow_the_stated_ranges():
     assert all(s.n_aux == int(8.5 * s.n_ao + 0.5) for s in specs)
     assert {s.nk for s in specs} <= {8, 27, 36, 64}
     assert sum(s.n_spin == 2 for s in specs) == 24
+
+
+def test_traffic_only_for_the_captured_kernel_sources(monkeypatch):
+    key = ("w", "bf16x3", "tc_contract")
+    monkeypatch.setattr(bench, "TRAFFIC", {key: (123.0, bench.kernel_sources_digest())})
+    assert bench.traffic_of(key) == 123.0
+    monkeypatch.setattr(bench, "TRAFFIC", {key: (123.0, "0" * 16)})
+    assert bench.traffic_of(key) is None
+    assert bench.traffic_of(("other", "bf16x3", "tc_contract")) is None

@@ -139,3 +139,34 @@ def test_grouped_needs_tensor_core_problems(torch):
     probs = _problems(n=3, seed=95, precs=[B.DMET_PREC_BF16X3, B.DMET_PREC_FP64])
     _, st, active, _ = _run(torch, probs, 1)
     assert not active and all(s == B.DMET_OK for s in st)
+
+
+def test_grouped_medium_problems(torch):
+    """Grouped launches over problems of a few thousand pairs (several tile rows per block, uneven
+    rounds), unrestricted and restricted: every block within the FP32 output rounding of the
+    side-stream run, and one problem's 12-orbital subset against the oracle."""
+    specs = [synth.LatticeSpec((2, 2, 2), 18, 150, 96, 2, 0.6, 0.0, 501, "g0"),
+             synth.LatticeSpec((3, 3, 1), 22, 180, 130, 1, 0.6, 0.0, 502, "g1"),
+             synth.LatticeSpec((2, 2, 1), 26, 220, 70, 1, 0.6, 0.0, 503, "g2")]
+    probs = []
+    for sp in specs:
+        L, Cs, _ = synth.make_problem(sp)
+        ne = [sp.n_emb, sp.n_emb] if sp.n_spin == 2 else sp.n_emb
+        probs.append((sp, L, Cs, B.make_desc(sp.mesh, sp.n_ao, sp.n_aux, ne, n_spin=sp.n_spin,
+                                             prec=B.DMET_PREC_BF16X3)))
+    g, st, active, _ = _run(torch, probs, 1)
+    assert active and all(s == B.DMET_OK for s in st)
+    s_, st2, _, _ = _run(torch, probs, 0)
+    assert all(s == B.DMET_OK for s in st2)
+    for ra, rb in zip(g, s_):
+        for x, y in zip(ra, rb):
+            assert np.isfinite(x).all()
+            assert np.abs(x - y).max() <= 2.0 ** -22 * np.abs(y).max()
+    sp, L, Cs, _ = probs[1]
+    S = np.sort(np.random.default_rng(3).choice(sp.n_emb, 12, replace=False))
+    ref = oracle.embedded_eri(L, np.ascontiguousarray(Cs[0][:, :, S]), sp.mesh).real
+    i, j, k, l = np.meshgrid(*([S] * 4), indexing="ij")
+    from gpu_helpers import s8_index
+    got = g[1][0][s8_index(i, j, k, l)]
+    e = rel_fro(got, ref)
+    assert e < 1e-6, e
