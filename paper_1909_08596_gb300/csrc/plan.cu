@@ -364,7 +364,12 @@ struct dmet_emb_plan_s {
   // bounded waits of the tensor-core kernels
   unsigned long long wait_ns = tc::kWaitLimitNs;
   int withhold_loads = 0;
-  tc::TcCtl ctl() const { return tc::TcCtl{derr, wait_ns, withhold_loads}; }
+  // job pacing of the contraction launches: one counter per workspace and one for the grouped launch
+  unsigned int* dsync = nullptr;
+  bool pace = true;
+  tc::TcCtl ctl(unsigned int* sync = nullptr) const {
+    return tc::TcCtl{derr, wait_ns, withhold_loads, pace ? sync : nullptr};
+  }
 };
 
 
@@ -908,6 +913,7 @@ void destroy_plan(dmet_emb_plan_s* P) {
   }
   for (auto& w : P->ws) free_workspace(w);
   free_grouped(P->grp);
+  cudaFree(P->dsync);
   cudaFree(P->derr);
   cudaFree(P->dstats);
   cudaFree(P->stage_in);
@@ -1404,6 +1410,15 @@ dmet_status_t mixed_block_out(dmet_emb_plan_s* P, Prob& pr, int bi, int s, const
 double contract_scale(const Prob& pr) { return pr.lq_scale * pr.lq_scale / pr.nk; }
 
 // (5) The contraction of every ERI block (this problem's own launches).
+// The pacing counter of the problem's workspace, cleared on the stream before a contraction launch.
+// Not with concurrent problems on side streams: their grids share the SMs, so a grid's CTAs need not
+// all be resident at once, and pacing would only wait for its limit.
+static unsigned int* pace_counter(dmet_emb_plan_s* P) {
+  if (!P->pace || !P->dsync || !P->side.empty()) return nullptr;
+  unsigned int* c = P->dsync + (P->W - P->ws.data());
+  return cudaMemsetAsync(c, 0, sizeof(unsigned int), P->cs) == cudaSuccess ? c : nullptr;
+}
+
 dmet_status_t mixed_contract(dmet_emb_plan_s* P, Prob& pr, const MixedMaps& mm, void* const* out) {
   MixedPlan& m = pr.mx;
   const int pc = m.prec;
@@ -1421,12 +1436,13 @@ dmet_status_t mixed_contract(dmet_emb_plan_s* P, Prob& pr, const MixedMaps& mm, 
       double* dst = s4 ? (double*)P->W->full : (double*)out[blk];
       {
         Timed t(P, KC_TC_CONTRACT, fl, by, 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk], tc::kTile));
+        unsigned int* sync = pace_counter(P);
         if (blk == 1)
           CK(launch_tc_rect(pc, mm.Xt[0], mm.Xt[1], m.d_jobs + m.jc_off[1], m.jc_cnt[1], m.d_segs, dst, 2 * nb2, oscale,
-                            P->ctl(), scaled ? &sc->fc[1] : nullptr, P->cs));
+                            P->ctl(sync), scaled ? &sc->fc[1] : nullptr, P->cs));
         else
           CK(launch_tc_herm(pc, mm.Xt[sa], mm.Xt[sa], m.d_jobs + m.jc_off[blk], m.jc_cnt[blk], m.d_segs, dst, na2,
-                            oscale, P->ctl(), scaled ? &sc->fc[blk] : nullptr, P->cs));
+                            oscale, P->ctl(sync), scaled ? &sc->fc[blk] : nullptr, P->cs));
       }
       if (s4) {
         Timed t(P, KC_PACK, 0.0, 16.0 * (double)na2 * nb2 + (double)eri_bytes_of(pr.d, blk));
@@ -1436,12 +1452,13 @@ dmet_status_t mixed_contract(dmet_emb_plan_s* P, Prob& pr, const MixedMaps& mm, 
     }
     const int nsplit = m.jc_split_n[blk], f = m.jc_split_f[blk];
     Timed t(P, KC_TC_CONTRACT, fl, by, nsplit ? 2 : 1, exec_flops(m, m.jc_off[blk], m.jc_cnt[blk], tc::kTile));
+    unsigned int* sync = pace_counter(P);
     if (blk == 1) {
       CK(launch_tc_rect(pc, mm.Xt[0], mm.Xt[1], m.d_jobs + m.jc_off[1], m.jc_cnt[1], m.d_segs, (double*)out[1],
-                        pr.npair[1], oscale, P->ctl(), scaled ? &sc->fc[1] : nullptr, P->cs));
+                        pr.npair[1], oscale, P->ctl(sync), scaled ? &sc->fc[1] : nullptr, P->cs));
     } else {
       CK(launch_tc_packed(pc, mm.Xt[sa], mm.Xt[sa], m.d_jobs + m.jc_off[blk], m.jc_cnt[blk], m.d_segs,
-                          (double*)out[blk], oscale, P->W->ZT, P->ctl(), scaled ? &sc->fc[blk] : nullptr, P->cs));
+                          (double*)out[blk], oscale, P->W->ZT, P->ctl(sync), scaled ? &sc->fc[blk] : nullptr, P->cs));
       if (nsplit)
         CK(launch_combine_parts(m.d_jobs + m.jc_off[blk] + m.jc_cnt[blk] - nsplit * f, nsplit, f, P->W->ZT,
                                 (double*)out[blk], oscale, P->cs));
@@ -1887,6 +1904,11 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     st = fail(DMET_ERR_OOM, "error word allocation failed");
   }
   if (st == DMET_OK && cudaMemset(P->derr, 0, sizeof(unsigned int)) != cudaSuccess) st = fail(DMET_ERR_CUDA, "memset");
+  if (st == DMET_OK && cudaMalloc(&P->dsync, sizeof(unsigned int) * (P->ws.size() + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    st = fail(DMET_ERR_OOM, "pacing counter allocation failed");
+  }
+  if (const char* e = std::getenv("DMET_TC_PACE")) P->pace = std::atoi(e) != 0;
   if (st == DMET_OK && cudaMalloc(&P->dstats, sizeof(double) * 8 * n_problems) != cudaSuccess) {
     cudaGetLastError();
     st = fail(DMET_ERR_OOM, "stats allocation failed");
@@ -2340,8 +2362,13 @@ static dmet_status_t join_sides(dmet_emb_plan_s* P, cudaStream_t origin) {
 }
 
 static dmet_status_t run_grouped(dmet_emb_plan_s* P, const GroupedLaunch& l, int kc) {
+  unsigned int* sync = nullptr;
+  if (l.kind == kGroupContract && P->pace && P->dsync) {
+    sync = P->dsync + P->ws.size();
+    CK(cudaMemsetAsync(sync, 0, sizeof(unsigned int), P->cs));
+  }
   Timed t(P, kc, l.flops, l.bytes, 1, l.exec);
-  CK(launch_tc_grouped(l.kind, l.prec, l.bn, l.d_groups, l.d_jobs, l.njobs, P->ctl(), P->cs));
+  CK(launch_tc_grouped(l.kind, l.prec, l.bn, l.d_groups, l.d_jobs, l.njobs, P->ctl(sync), P->cs));
   return DMET_OK;
 }
 

@@ -81,6 +81,22 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
   }
 }
 
+// Job pacing of the persistent GEMM (TcCtl::jobsync): how long a producer waits for the other CTAs
+// before it stops pacing for the rest of the launch.
+constexpr unsigned long long kJobSyncLimitNs = 2000000ull;
+
+// Waits until the counter in global memory reaches target; false if that took longer than limit_ns.
+__device__ __forceinline__ bool counter_wait(const unsigned int* cnt, unsigned int target,
+                                             unsigned long long limit_ns) {
+  if (*(const volatile unsigned int*)cnt >= target) return true;
+  const unsigned long long t0 = globaltimer();
+  while (*(const volatile unsigned int*)cnt < target) {
+    if (globaltimer() - t0 > limit_ns) return false;
+    __nanosleep(128);
+  }
+  return true;
+}
+
 // 3-D tiled TMA load into shared memory, completion counted on `bar` in bytes.
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, uint32_t bar, int x, int y, int z) {
   asm volatile(

@@ -89,6 +89,14 @@ struct TcCtl {
   unsigned long long wait_ns;  // limit of every bounded wait
   int withhold_loads;          // test hook: the producer issues no copies, so the MMA thread's and
                                // the epilogue's waits expire with no copy or MMA in flight
+  unsigned int* jobsync;       // job pacing (or null): a counter, zero at launch, of the jobs whose
+                               // loads the CTAs have issued. Before its (k+1)-th job a CTA's producer
+                               // waits until every CTA has issued its k-th job's loads, so the CTAs
+                               // work on neighbouring tiles at neighbouring K and share their operand
+                               // blocks in L2 instead of drifting apart over a long job. A pacing wait
+                               // that takes longer than kJobSyncLimitNs (CTAs that are not all
+                               // resident) ends the pacing for the rest of the launch; it is a
+                               // scheduling aid only and never changes a result.
 };
 
 constexpr int kTile = 128;
@@ -277,7 +285,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       int cur = -1;
       bool ok = !ctl.withhold_loads;
-      for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x) {
+      bool pace = ctl.jobsync != nullptr;
+      unsigned int kjob = 0;  // jobs of this CTA whose loads are issued
+      for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x, ++kjob) {
+      if (pace && kjob > 0) pace = counter_wait(ctl.jobsync, kjob * gridDim.x, kJobSyncLimitNs);
       const TcJob job = jobs[jb];
       if (groups && job.grp != cur) {
         cur = job.grp;
@@ -310,6 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++issued;
         }
       }
+      if (ctl.jobsync && ok) atomicAdd(ctl.jobsync, 1u);
       }
     } else if (warp == 1 && lane == 0) {
       // ---------------- MMA issuer ----------------
