@@ -239,3 +239,17 @@ def test_mixed_split_parts(torch, split, tmp_path, monkeypatch):
     assert st == B.DMET_OK
     assert f == (1 if split == 1 or tiles == 0 else split) or (tiles > 0 and f < split)
     check(out.cpu().numpy(), oracle.pack_s8(oracle.embedded_eri(L, Cs[0], spec.mesh).real))
+
+
+def test_job_pacing_changes_no_result(torch, monkeypatch):
+    """The contraction's job pacing (DMET_TC_PACE, on by default) only orders when the CTAs load their
+    tiles: the results are bit-for-bit those of the unpaced launch."""
+    spec = spec_of((3, 3, 1), 10, 37, 70)
+    L, Cs, _ = synth.make_problem(spec)
+    d = desc_of(spec)
+    monkeypatch.setenv("DMET_TC_PACE", "0")
+    a, st1, _ = run_eri(torch, d, L, Cs)
+    monkeypatch.setenv("DMET_TC_PACE", "1")
+    b, st2, _ = run_eri(torch, d, L, Cs)
+    assert st1 == st2 == B.DMET_OK
+    assert np.array_equal(a[0], b[0])
