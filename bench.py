@@ -57,9 +57,9 @@ PREC_DTYPE = {"fp64": "f64", "bf16x3": "bf16x3", "fp16x2": "fp16x2", "tf32": "tf
 # (kernel_sources_digest); after any change to the kernels or their job tables, traffic is null.
 KERNEL_SOURCES = ["tc_gemm.cuh", "tc_common.cuh", "prec.cuh", "split.cuh", "mixed_impl.cuh", "plan.cu"]
 TRAFFIC = {
-    # one-pass ncu capture of the contraction launches of one NiO-shaped call (aa 1825.9 GB, ab 5439.5 GB,
-    # bb 1739.9 GB read + written) over the class's 5 launches per call
-    ("nio_4x4x4_uhf", "bf16x3", "tc_contract"): (9005.3e9 / 5, "d76e1bba445d1591"),
+    # one-pass ncu capture of the contraction launches of one NiO-shaped call with job pacing (aa 526.2 GB,
+    # ab 1023.1 GB, bb 526.2 GB read + written) over the class's 5 launches per call
+    ("nio_4x4x4_uhf", "bf16x3", "tc_contract"): (2075.5e9 / 5, "ea2daa370fc7d2b3"),
 }
 
 
