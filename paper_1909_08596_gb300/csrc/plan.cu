@@ -364,9 +364,10 @@ struct dmet_emb_plan_s {
   // bounded waits of the tensor-core kernels
   unsigned long long wait_ns = tc::kWaitLimitNs;
   int withhold_loads = 0;
-  // job pacing of the contraction launches: one counter per workspace and one for the grouped launch
+  // job pacing (DMET_TC_PACE: bit 1 the contraction launches, the default; bit 2 the transforms too):
+  // one counter per workspace and one for the grouped launches
   unsigned int* dsync = nullptr;
-  bool pace = true;
+  int pace = 1;
   tc::TcCtl ctl(unsigned int* sync = nullptr) const {
     return tc::TcCtl{derr, wait_ns, withhold_loads, pace ? sync : nullptr};
   }
@@ -1343,6 +1344,15 @@ dmet_status_t mixed_block_in(dmet_emb_plan_s* P, Prob& pr, int bi, int s, const 
   return DMET_OK;
 }
 
+// The pacing counter of the problem's workspace, cleared on the stream before a contraction launch.
+// Not with concurrent problems on side streams: their grids share the SMs, so a grid's CTAs need not
+// all be resident at once, and pacing would only wait for its limit.
+static unsigned int* pace_counter(dmet_emb_plan_s* P, int bit = 1) {
+  if (!(P->pace & bit) || !P->dsync || !P->side.empty()) return nullptr;
+  unsigned int* c = P->dsync + (P->W - P->ws.data());
+  return cudaMemsetAsync(c, 0, sizeof(unsigned int), P->cs) == cudaSuccess ? c : nullptr;
+}
+
 // (3) Block bi's two half transforms of spin s (this problem's own launches).
 dmet_status_t mixed_block_gemms(dmet_emb_plan_s* P, Prob& pr, const MixedMaps& mm, int bi, int s) {
   MixedPlan& m = pr.mx;
@@ -1353,13 +1363,15 @@ dmet_status_t mixed_block_gemms(dmet_emb_plan_s* P, Prob& pr, const MixedMaps& m
   step1_work(pr, bi, s, fl, by);
   {
     Timed t(P, KC_TC_TRANSFORM_1, fl, by, 1, exec_flops(m, m.j1_off[s][bi], m.j1_cnt[s][bi], m.bn1));
+    unsigned int* sync = pace_counter(P, 2);
     CK(launch_tc_split_t(pc, m.bn1, mm.Ls, mm.Cb[s], m.d_jobs + m.j1_off[s][bi], m.j1_cnt[s][bi], m.d_segs, P->W->A2,
-                         m.K2, pr.nao, n, P->ctl(), scaled ? &sc->f1[s] : nullptr, P->cs));
+                         m.K2, pr.nao, n, P->ctl(sync), scaled ? &sc->f1[s] : nullptr, P->cs));
   }
   step2_work(pr, bi, s, fl, by);
   Timed t(P, KC_TC_TRANSFORM_2, fl, by, 1, exec_flops(m, m.j2_off[s][bi], m.j2_cnt[s][bi], m.bn2));
+  unsigned int* sync = pace_counter(P, 2);
   CK(launch_tc_pairs(pc, m.bn2, mm.A2[s], mm.Cc[s], m.d_jobs + m.j2_off[s][bi], m.j2_cnt[s][bi], m.d_segs, P->W->ZT,
-                     2LL * n, P->ctl(), scaled ? &sc->f2[s] : nullptr, P->cs));
+                     2LL * n, P->ctl(sync), scaled ? &sc->f2[s] : nullptr, P->cs));
   return DMET_OK;
 }
 
@@ -1410,15 +1422,6 @@ dmet_status_t mixed_block_out(dmet_emb_plan_s* P, Prob& pr, int bi, int s, const
 double contract_scale(const Prob& pr) { return pr.lq_scale * pr.lq_scale / pr.nk; }
 
 // (5) The contraction of every ERI block (this problem's own launches).
-// The pacing counter of the problem's workspace, cleared on the stream before a contraction launch.
-// Not with concurrent problems on side streams: their grids share the SMs, so a grid's CTAs need not
-// all be resident at once, and pacing would only wait for its limit.
-static unsigned int* pace_counter(dmet_emb_plan_s* P) {
-  if (!P->pace || !P->dsync || !P->side.empty()) return nullptr;
-  unsigned int* c = P->dsync + (P->W - P->ws.data());
-  return cudaMemsetAsync(c, 0, sizeof(unsigned int), P->cs) == cudaSuccess ? c : nullptr;
-}
-
 dmet_status_t mixed_contract(dmet_emb_plan_s* P, Prob& pr, const MixedMaps& mm, void* const* out) {
   MixedPlan& m = pr.mx;
   const int pc = m.prec;
@@ -1908,7 +1911,7 @@ dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, vo
     cudaGetLastError();
     st = fail(DMET_ERR_OOM, "pacing counter allocation failed");
   }
-  if (const char* e = std::getenv("DMET_TC_PACE")) P->pace = std::atoi(e) != 0;
+  if (const char* e = std::getenv("DMET_TC_PACE")) P->pace = std::atoi(e) & 3;
   if (st == DMET_OK && cudaMalloc(&P->dstats, sizeof(double) * 8 * n_problems) != cudaSuccess) {
     cudaGetLastError();
     st = fail(DMET_ERR_OOM, "stats allocation failed");
@@ -2363,7 +2366,7 @@ static dmet_status_t join_sides(dmet_emb_plan_s* P, cudaStream_t origin) {
 
 static dmet_status_t run_grouped(dmet_emb_plan_s* P, const GroupedLaunch& l, int kc) {
   unsigned int* sync = nullptr;
-  if (l.kind == kGroupContract && P->pace && P->dsync) {
+  if ((l.kind == kGroupContract ? (P->pace & 1) : (P->pace & 2)) && P->dsync) {
     sync = P->dsync + P->ws.size();
     CK(cudaMemsetAsync(sync, 0, sizeof(unsigned int), P->cs));
   }
