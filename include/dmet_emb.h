@@ -166,11 +166,17 @@ DMET_API size_t dmet_emb_eri_bytes(const dmet_emb_desc_t* desc, int32_t block);
  * the scheduler tables of momentum-conserving pairs per q). `stream` is a cudaStream_t
  * (NULL = legacy default stream) on which every later call of this plan queues its work.
  * workspace_limit bounds the plan's device workspace in bytes (0 = 8 GiB); the q-block
- * size (at most 8 values of q per block of work) is chosen to fit it. The environment
- * variable DMET_QBLOCK (1..8), read here, caps the q-block size: with host-resident L the
- * blocks' L pairs are copied one block ahead of the kernels that read them, so smaller
- * blocks expose less of the copy before the first kernels start, at some cost in kernel
- * efficiency. Allocates device memory. Host-side validation only; no kernel runs. */
+ * size (at most 8 values of q per block of work; every q of a weight class in one block when
+ * that workspace stays under 512 MiB) is chosen to fit it. Environment variables read here:
+ * DMET_QBLOCK (1..8) caps the q-block size (with host-resident L the blocks' L pairs are
+ * copied one block ahead of the kernels that read them, so smaller blocks expose less of the
+ * copy before the first kernels start, at some cost in kernel efficiency); DMET_TC_KSEG,
+ * DMET_TC_KSEG1 and DMET_TC_CRUN set the tensor-core paths' FP32 segment lengths (K elements,
+ * multiples of 32; defaults 128, 128) and correction-run length (segments; default 1);
+ * DMET_TC_PACE selects the job pacing of the tensor-core launches (bit 1: contractions, the
+ * default; bit 2: the transforms too; 0: none; it never changes a result); DMET_TUNE_CACHE
+ * names the tuning cache (dmet_emb_autotune). Allocates device memory. Host-side validation
+ * only; no kernel runs. */
 DMET_API dmet_status_t dmet_emb_plan(const dmet_emb_desc_t* descs, int32_t n_problems, void* stream,
                             size_t workspace_limit, dmet_emb_plan_t* plan);
 
