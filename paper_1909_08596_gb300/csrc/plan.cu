@@ -285,6 +285,7 @@ struct Workspace {
 // the group table, and the work it stands for.
 struct GroupedLaunch {
   int kind = 0, prec = 0, bn = 128;
+  int pace_bits = 2;  // DMET_TC_PACE bits that pace it
   tc::TcJob* d_jobs = nullptr;
   int njobs = 0;
   void* d_groups = nullptr;
@@ -1347,8 +1348,8 @@ dmet_status_t mixed_block_in(dmet_emb_plan_s* P, Prob& pr, int bi, int s, const 
 // The pacing counter of the problem's workspace, cleared on the stream before a contraction launch.
 // Not with concurrent problems on side streams: their grids share the SMs, so a grid's CTAs need not
 // all be resident at once, and pacing would only wait for its limit.
-static unsigned int* pace_counter(dmet_emb_plan_s* P, int bit = 1) {
-  if (!(P->pace & bit) || !P->dsync || !P->side.empty()) return nullptr;
+static unsigned int* pace_counter(dmet_emb_plan_s* P, int bits = 1) {
+  if (!(P->pace & bits) || !P->dsync || !P->side.empty()) return nullptr;
   unsigned int* c = P->dsync + (P->W - P->ws.data());
   return cudaMemsetAsync(c, 0, sizeof(unsigned int), P->cs) == cudaSuccess ? c : nullptr;
 }
@@ -1363,7 +1364,9 @@ dmet_status_t mixed_block_gemms(dmet_emb_plan_s* P, Prob& pr, const MixedMaps& m
   step1_work(pr, bi, s, fl, by);
   {
     Timed t(P, KC_TC_TRANSFORM_1, fl, by, 1, exec_flops(m, m.j1_off[s][bi], m.j1_cnt[s][bi], m.bn1));
-    unsigned int* sync = pace_counter(P, 2);
+    // (a first transform of K <= 64 is bound by its epilogue's stores; pacing helped it, 10.8 -> 9.4 ms
+    // per 10 h-BN-shaped calls, and slowed the K = 224 NiO-shaped one, so it goes with the default then)
+    unsigned int* sync = pace_counter(P, m.K1 <= 64 ? 3 : 2);
     CK(launch_tc_split_t(pc, m.bn1, mm.Ls, mm.Cb[s], m.d_jobs + m.j1_off[s][bi], m.j1_cnt[s][bi], m.d_segs, P->W->A2,
                          m.K2, pr.nao, n, P->ctl(sync), scaled ? &sc->f1[s] : nullptr, P->cs));
   }
@@ -2181,10 +2184,17 @@ dmet_status_t upload_launch(GroupedLaunch& l, const std::vector<GroupSpec>& spec
   std::vector<unsigned char> host(gb * specs.size() + 128);
   unsigned char* h = host.data() + ((128 - ((uintptr_t)host.data() & 127)) & 127);
   CK(tc_group_fill(l.kind, l.prec, specs.data(), (int)specs.size(), h));
-  CK(cudaMalloc(&l.d_groups, gb * specs.size()));
-  CK(cudaMemcpy(l.d_groups, h, gb * specs.size(), cudaMemcpyHostToDevice));
-  CK(cudaMalloc(&l.d_jobs, jobs.size() * sizeof(tc::TcJob)));
-  CK(cudaMemcpy(l.d_jobs, jobs.data(), jobs.size() * sizeof(tc::TcJob), cudaMemcpyHostToDevice));
+  if (cudaMalloc(&l.d_groups, gb * specs.size()) != cudaSuccess ||
+      cudaMemcpy(l.d_groups, h, gb * specs.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMalloc(&l.d_jobs, jobs.size() * sizeof(tc::TcJob)) != cudaSuccess ||
+      cudaMemcpy(l.d_jobs, jobs.data(), jobs.size() * sizeof(tc::TcJob), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(l.d_groups);
+    cudaFree(l.d_jobs);
+    l.d_groups = nullptr;
+    l.d_jobs = nullptr;
+    return fail(DMET_ERR_OOM, "grouped launch tables: device allocation or copy failed");
+  }
   l.njobs = (int)jobs.size();
   return DMET_OK;
 }
@@ -2254,6 +2264,8 @@ dmet_status_t build_grouped(dmet_emb_plan_s* P) {
         a.n = pr.n[s];
         LaunchBuild& b1 = c1[{m.prec, m.bn1}];
         b1.l.kind = kGroupSplitT;
+        if (!b1.specs.empty() && b1.l.pace_bits == 3 && m.K1 > 64) b1.l.pace_bits = 2;
+        if (b1.specs.empty()) b1.l.pace_bits = m.K1 <= 64 ? 3 : 2;
         b1.l.prec = m.prec;
         b1.l.bn = m.bn1;
         add_group(b1, a, m, m.j1_off[s][r], m.j1_cnt[s][r]);
@@ -2366,7 +2378,7 @@ static dmet_status_t join_sides(dmet_emb_plan_s* P, cudaStream_t origin) {
 
 static dmet_status_t run_grouped(dmet_emb_plan_s* P, const GroupedLaunch& l, int kc) {
   unsigned int* sync = nullptr;
-  if ((l.kind == kGroupContract ? (P->pace & 1) : (P->pace & 2)) && P->dsync) {
+  if ((l.kind == kGroupContract ? (P->pace & 1) : (P->pace & l.pace_bits)) && P->dsync) {
     sync = P->dsync + P->ws.size();
     CK(cudaMemsetAsync(sync, 0, sizeof(unsigned int), P->cs));
   }
