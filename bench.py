@@ -388,6 +388,7 @@ def roofline(spec, prec, kstats, sustained=False):
     hbm = {"achieved": by_l / secs / 1e9 if secs > 0 else 0.0, "peak": peak_b, "unit": "GB/s"}
     for d in (tensor, hbm):
         d["frac"] = d["achieved"] / d["peak"]
+    tensor["frac_of_burst_peak"] = tensor["achieved"] / (peaks["bf16_tflops"] * PEAK_RATIO[prec])
     main, other = (hbm, tensor) if t_hbm > t_tensor else (tensor, hbm)
     useful = top["flops"] / (top["ms"] / 1e3) / 1e12 if top["ms"] > 0 else 0.0
     return {"bound": "hbm" if main is hbm else "tensor", "kernel": top["name"], **main,
@@ -396,7 +397,9 @@ def roofline(spec, prec, kstats, sustained=False):
             "flops_counted": "executed tensor flops (every slice product issued, whole tiles)",
             "bytes_counted": "algorithmic bytes per launch: operands read once, result written once",
             "useful_achieved_tflops": useful, "useful_frac": useful / peak_t,
-            "peak_source": f"{peak_src} {key} x {PEAK_RATIO[prec]} ({prec}) and hbm_gbs", "avg_launch_ms": avg_ms}
+            "peak_source": f"{peak_src} {key} x {PEAK_RATIO[prec]} ({prec}) and hbm_gbs"
+                           + (" (sustained: the step runs the kernels for seconds under the power cap)" if sustained
+                              else " (burst: a short step)"), "avg_launch_ms": avg_ms}
 
 
 def kernel_table(kstats):
@@ -473,7 +476,9 @@ def measure(dm, torch, spec, desc, Ld, Cd, outs, steps, args, dist, world, local
         "value": job_tflops(1 if qshard else world, fl_total, steps, ms_total), "ms_per_step": ms_step,
         "useful_tflop_per_problem": fl_total / 1e12,
         "useful_split": {"transform": fl_t / 1e12, "contraction": fl_c / 1e12},
-        "roofline": roofline(spec, prec, kstats), "kernels": kernel_table(kstats), "gpu_launches": int(launches),
+        # a step of a second or more runs the kernels for seconds under the power cap: the sustained peak
+        "roofline": roofline(spec, prec, kstats, sustained=ms_step >= 1000.0), "kernels": kernel_table(kstats),
+        "gpu_launches": int(launches),
         "clocks": clk, "steps": steps, "tile_widths": tile_widths,
         "device_checks": {"status": int(st), "orthonormality": stats[0], "realness": stats[1],
                           "hermiticity_L": stats[2], "time_reversal_L": stats[3]},

@@ -77,3 +77,19 @@ def test_traffic_only_for_the_captured_kernel_sources(monkeypatch):
     monkeypatch.setattr(bench, "TRAFFIC", {key: (123.0, "0" * 16)})
     assert bench.traffic_of(key) is None
     assert bench.traffic_of(("other", "bf16x3", "tc_contract")) is None
+
+
+def test_roofline_peak_choice():
+    """A step of a second or more takes the sustained bf16 peak, a short one the burst peak; the
+    executed-flop fraction against the burst peak is reported beside it."""
+    import synth
+    spec = synth.CONFIGS["tiny_2x2x1"]
+    ks = [{"name": "tc_contract", "ms": 10.0, "launches": 2, "flops": 1e12, "exec_flops": 6e12, "bytes": 1e9},
+          {"name": "split_operands", "ms": 1.0, "launches": 1, "flops": 0.0, "exec_flops": 0.0, "bytes": 1e9}]
+    peaks, _ = bench.measured_peaks()
+    burst = bench.roofline(spec, "bf16x3", ks)
+    sus = bench.roofline(spec, "bf16x3", ks, sustained=True)
+    assert burst["kernel"] == sus["kernel"] == "tc_contract"
+    assert burst["achieved"] == sus["achieved"] == 6e12 / 2 / (5e-3) / 1e12
+    assert burst["peak"] == peaks["bf16_tflops"] and sus["peak"] == peaks["bf16_tflops_sustained"]
+    assert sus["frac_of_burst_peak"] == burst["frac"]
