@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace dmet {
@@ -33,6 +35,30 @@ __global__ void fftdf_phase_kernel(const double2* __restrict__ src, double2* __r
   }
 }
 
+// The same phase for a run of q values at once: blockIdx.y is the local index i of a q in the run,
+// qtab[i] its q (mesh triple from the mesh, C order). Source block: src + qtab[i] * ng * nx if by_table,
+// else src + i * ng * nx; destination block dst + i * ng * nx.
+__global__ void fftdf_phase_q_kernel(const double2* __restrict__ src, double2* __restrict__ dst,
+                                     const int* __restrict__ qtab, int by_table, int g0, int g1, int g2, int m0,
+                                     int m1, int m2, double sign, double s, long long nx) {
+  const long long ngx = (long long)g0 * g1 * g2 * nx;
+  const int i = blockIdx.y, q = qtab[i];
+  const int n0 = q / (m1 * m2), n1 = (q / m2) % m1, n2 = q % m2;
+  const double f0 = (double)n0 / ((double)m0 * g0), f1 = (double)n1 / ((double)m1 * g1),
+               f2 = (double)n2 / ((double)m2 * g2);
+  const double2* in = src + (long long)(by_table ? q : i) * ngx;
+  double2* out = dst + (long long)i * ngx;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ngx;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t / nx;
+    const int j2 = (int)(r % g2), j1 = (int)((r / g2) % g1), j0 = (int)(r / ((long long)g1 * g2));
+    double sn, cs;
+    sincospi(2.0 * sign * (j0 * f0 + j1 * f1 + j2 * f2), &sn, &cs);
+    const double2 a = in[t];
+    out[t] = make_double2(s * (a.x * cs - a.y * sn), s * (a.x * sn + a.y * cs));
+  }
+}
+
 // buf[G][x] *= v[G]
 __global__ void fftdf_kernel_mul(double2* __restrict__ buf, const double* __restrict__ v, long long ng, long long nx) {
   const long long total = ng * nx;
@@ -51,6 +77,18 @@ cudaError_t launch_fftdf_phase(const double2* src, double2* dst, const int grid[
   fftdf_phase_kernel<<<grid_for(total, 256, 152 * 16), 256, 0, st>>>(
       src, dst, grid[0], grid[1], grid[2], (double)nq[0] / ((double)mesh[0] * grid[0]),
       (double)nq[1] / ((double)mesh[1] * grid[1]), (double)nq[2] / ((double)mesh[2] * grid[2]), sign, s, nx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fftdf_phase_q(const double2* src, double2* dst, const int* qtab, int nq_run, int by_table,
+                                 const int grid[3], const int mesh[3], double sign, double s, long long nx,
+                                 cudaStream_t st) {
+  if (nq_run <= 0) return cudaSuccess;
+  if (nq_run > 65535) return cudaErrorInvalidValue;
+  const long long per = (long long)grid[0] * grid[1] * grid[2] * nx;
+  const int gx = grid_for(per, 256, std::max(1, 152 * 16 / nq_run));
+  fftdf_phase_q_kernel<<<dim3(gx, nq_run), 256, 0, st>>>(src, dst, qtab, by_table, grid[0], grid[1], grid[2], mesh[0],
+                                                         mesh[1], mesh[2], sign, s, nx);
   return cudaGetLastError();
 }
 

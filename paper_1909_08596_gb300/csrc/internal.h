@@ -85,6 +85,10 @@ cudaError_t launch_fock_combine(const double* F0, const double* J, const double*
 cudaError_t launch_fftdf_phase(const double2* src, double2* dst, const int grid[3], const int nq[3], const int mesh[3],
                                double sign, double s, long long nx, cudaStream_t st);
 cudaError_t launch_fftdf_kernel_mul(double2* buf, const double* v, long long ng, long long nx, cudaStream_t st);
+// The phase for nq_run q values at once (q = qtab[i] for block i; source block by q if by_table, else by i).
+cudaError_t launch_fftdf_phase_q(const double2* src, double2* dst, const int* qtab, int nq_run, int by_table,
+                                 const int grid[3], const int mesh[3], double sign, double s, long long nx,
+                                 cudaStream_t st);
 // Density-fitted J and K from the factors L^q (fock.cu), per chunk of z = (q, P) batch entries with
 // tab[z] = {z-th factor's index in Lq, the -q factor's index, z, n}:
 // v[z] = tr(L^{-q}_P gamma); J += s sum_z v[z] L^q_P; K += s sum_z Kb[z] (Kb[z] = L^q_P gamma L^{-q}_P).

@@ -3034,17 +3034,37 @@ dmet_status_t dmet_emb_eri_fftdf(dmet_emb_plan_t P, int32_t problem, const void*
                a2[3] = {lattice[6], lattice[7], lattice[8]};
   const double omega = std::fabs(a0[0] * (a1[1] * a2[2] - a1[2] * a2[1]) - a0[1] * (a1[0] * a2[2] - a1[2] * a2[0]) +
                                  a0[2] * (a1[0] * a2[1] - a1[1] * a2[0]));
-  // scratch: two [grid][n^2] buffers, the DFT matrices, the kernels
-  const size_t bbuf = (size_t)ng * nx_max * 16, oF = 2 * bbuf, oV = oF + (F.size() * 16 + 255) / 256 * 256;
+  // The q values run in chunks of qc at once. Reindexed by q' = -q, step 4 reads
+  //   (ij|kl) += Omega / (N_g^2 Nk) sum_q' sum_r w^{-q'}(r)_ij (r|0k 0l)^{q'},
+  // so a chunk of consecutive q' pairs the transformed factors of q = -q' (computed in that order)
+  // with a contiguous run of the untransformed ones: one GEMM over K = qc N_g per chunk and spin pair.
+  const long long g0 = grid[0], g1 = grid[1], g2 = grid[2];
+  int qc = nk;
+  while (qc > 1 && ((size_t)qc * ng * nx_max * 16 * 2 > ((size_t)4 << 30) || (long long)qc * g0 * g1 > 65535 ||
+                    (long long)qc * ng > INT_MAX))
+    qc = (qc + 1) / 2;
+  if ((long long)qc * g0 * g1 > 65535 || (long long)qc * ng > INT_MAX)
+    return fail(DMET_ERR_UNSUPPORTED, "FFTDF grid too large for one DFT launch");
+  std::vector<double> vp((size_t)nk * ng);  // kernels in q' order: v^{-q'}
+  std::vector<int> qtab(nk);                // q' -> q = -q'
+  for (int qq = 0; qq < nk; ++qq) {
+    qtab[qq] = pr.s.neg[qq];
+    std::memcpy(vp.data() + (size_t)qq * ng, vq.data() + (size_t)qtab[qq] * ng, sizeof(double) * ng);
+  }
+  // scratch: two [qc][grid][n^2] buffers, the DFT matrices, the kernels, the q table
+  const size_t bbuf = (size_t)qc * ng * nx_max * 16, oF = 2 * bbuf, oV = oF + (F.size() * 16 + 255) / 256 * 256;
+  const size_t oQ = oV + (vp.size() * 8 + 255) / 256 * 256;
   P->cs = P->stream;
-  TRY(ensure(&P->fft_ws, &P->fft_ws_b, oV + vq.size() * 8));
+  TRY(ensure(&P->fft_ws, &P->fft_ws_b, oQ + qtab.size() * sizeof(int)));
   char* w = (char*)P->fft_ws;
   double2* buf0 = (double2*)w;
   double2* buf1 = (double2*)(w + bbuf);
   double2* dF = (double2*)(w + oF);
   double* dV = (double*)(w + oV);
+  int* dQ = (int*)(w + oQ);
   CK(cudaMemcpyAsync(dF, F.data(), F.size() * 16, cudaMemcpyHostToDevice, P->cs));
-  CK(cudaMemcpyAsync(dV, vq.data(), vq.size() * 8, cudaMemcpyHostToDevice, P->cs));
+  CK(cudaMemcpyAsync(dV, vp.data(), vp.size() * 8, cudaMemcpyHostToDevice, P->cs));
+  CK(cudaMemcpyAsync(dQ, qtab.data(), qtab.size() * sizeof(int), cudaMemcpyHostToDevice, P->cs));
   // Step 1 of Algorithm 2 for every q and spin: (r|0i 0j) = s sum_k1 C^{k1+} rho^{k1,k1+q}(r) C^{k1+q}
   const double2* Cd[2] = {(const double2*)C[0], pr.nspin == 2 ? (const double2*)C[1] : nullptr};
   P->W = &P->ws[P->ws_of[problem]];
@@ -3053,42 +3073,42 @@ dmet_status_t dmet_emb_eri_fftdf(dmet_emb_plan_t P, int32_t problem, const void*
   double2* lq[2] = {P->W->lq_all[0], P->W->lq_all[1]};
   TRY(transform_range(P, pr, (const double2*)rho, Cd, 0, nk, lq, pr.bq));
   for (int b = 0; b < nblk; ++b) CK(cudaMemsetAsync(eri_out[b], 0, eri_bytes_of(pr.d, b), P->cs));
-  const long long g0 = grid[0], g1 = grid[1], g2 = grid[2];
   for (int sa = 0; sa < pr.nspin; ++sa) {
     const long long nx = (long long)pr.n[sa] * pr.n[sa];
-    for (int q = 0; q < nk; ++q) {
-      const int nq[3] = {(int)(q / (pr.d.mesh[1] * pr.d.mesh[2])), (int)((q / pr.d.mesh[2]) % pr.d.mesh[1]),
-                         (int)(q % pr.d.mesh[2])};
-      const double2* rq = lq[sa] + (long long)q * ng * nx;
-      Timed t(P, KC_FFTDF, 8.0 * ng * nx * 2.0 * (g0 + g1 + g2), 16.0 * ng * nx * 14, 9);
-      // 2. exp(-i q.r), forward DFT, 4 pi / |q + G|^2, inverse DFT, exp(+i q.r)
-      CK(launch_fftdf_phase(rq, buf0, grid, nq, pr.d.mesh, -1.0, 1.0, nx, P->cs));
-      TRY(dft_axis(P, dF + f_off[0][0], (int)g0, 1, g1 * g2 * nx, buf0, buf1));
-      TRY(dft_axis(P, dF + f_off[1][0], (int)g1, g0, g2 * nx, buf1, buf0));
-      TRY(dft_axis(P, dF + f_off[2][0], (int)g2, g0 * g1, nx, buf0, buf1));
-      CK(launch_fftdf_kernel_mul(buf1, dV + (size_t)q * ng, ng, nx, P->cs));
-      TRY(dft_axis(P, dF + f_off[0][1], (int)g0, 1, g1 * g2 * nx, buf1, buf0));
-      TRY(dft_axis(P, dF + f_off[1][1], (int)g1, g0, g2 * nx, buf0, buf1));
-      TRY(dft_axis(P, dF + f_off[2][1], (int)g2, g0 * g1, nx, buf1, buf0));
-      CK(launch_fftdf_phase(buf0, buf1, grid, nq, pr.d.mesh, 1.0, 1.0, nx, P->cs));
-      // 4. (ij|kl) += Omega / (N_g^2 Nk) sum_r w^q(r)_ij (r|0k 0l)^{-q} (one 1/N_g is the unnormalised DFTs')
+    for (int c0 = 0; c0 < nk; c0 += qc) {
+      const int nc = std::min(qc, nk - c0);
+      {
+        Timed t(P, KC_FFTDF, 8.0 * ng * nx * 2.0 * (g0 + g1 + g2) * nc, 16.0 * ng * nx * 14 * nc, 9);
+        // 2. exp(-i q.r), forward DFT, 4 pi / |q + G|^2, inverse DFT, exp(+i q.r), for q = -q', q' in the chunk
+        CK(launch_fftdf_phase_q(lq[sa], buf0, dQ + c0, nc, 1, grid, pr.d.mesh, -1.0, 1.0, nx, P->cs));
+        TRY(dft_axis(P, dF + f_off[0][0], (int)g0, nc, g1 * g2 * nx, buf0, buf1));
+        TRY(dft_axis(P, dF + f_off[1][0], (int)g1, nc * g0, g2 * nx, buf1, buf0));
+        TRY(dft_axis(P, dF + f_off[2][0], (int)g2, nc * g0 * g1, nx, buf0, buf1));
+        CK(launch_fftdf_kernel_mul(buf1, dV + (size_t)c0 * ng, (long long)nc * ng, nx, P->cs));
+        TRY(dft_axis(P, dF + f_off[0][1], (int)g0, nc, g1 * g2 * nx, buf1, buf0));
+        TRY(dft_axis(P, dF + f_off[1][1], (int)g1, nc * g0, g2 * nx, buf0, buf1));
+        TRY(dft_axis(P, dF + f_off[2][1], (int)g2, nc * g0 * g1, nx, buf1, buf0));
+        CK(launch_fftdf_phase_q(buf0, buf1, dQ + c0, nc, 0, grid, pr.d.mesh, 1.0, 1.0, nx, P->cs));
+      }
+      // 4. (ij|kl) += Omega / (N_g^2 Nk) sum_{q', r} w^{-q'}(r)_ij (r|0k 0l)^{q'} (one 1/N_g is the
+      // unnormalised DFTs'), K = nc N_g
       for (int sb = sa; sb < pr.nspin; ++sb) {
         const long long nxb = (long long)pr.n[sb] * pr.n[sb];
         const int blk = pr.nspin == 1 ? 0 : (sa == 0 ? (sb == 0 ? 0 : 1) : 2);
         ZgemmArgs z = zargs();
         z.A = buf1;
-        z.B = lq[sb] + (long long)pr.s.neg[q] * ng * nxb;
+        z.B = lq[sb] + (long long)c0 * ng * nxb;
         z.D = (double2*)eri_out[blk];
         z.M = (int)nx;
         z.N = (int)nxb;
-        z.K = (int)ng;
+        z.K = (int)((long long)nc * ng);
         z.lda = nx;
         z.ldb = nxb;
         z.dm_lo = nxb;
         z.dn_lo = 1;
         z.alpha = omega / ((double)ng * ng * nk);
         z.beta = 1;
-        Timed tc(P, KC_FFTDF, 8.0 * (double)nx * nxb * ng, 0.0);
+        Timed tc(P, KC_FFTDF, 8.0 * (double)nx * nxb * ng * nc, 0.0);
         CK(launch_zgemm(z, A_KM, false, B_KN, P->cs));
       }
     }
