@@ -69,7 +69,25 @@ __global__ void fftdf_kernel_mul(double2* __restrict__ buf, const double* __rest
   }
 }
 
+// out[i] += sum_p parts[p n + i]
+__global__ void sum_parts_kernel(const double2* __restrict__ parts, int np, long long n, double2* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double2 a = out[i];
+    for (int p = 0; p < np; ++p) {
+      const double2 b = parts[(long long)p * n + i];
+      a.x += b.x;
+      a.y += b.y;
+    }
+    out[i] = a;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_sum_parts(const double2* parts, int np, long long n, double2* out, cudaStream_t st) {
+  sum_parts_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(parts, np, n, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fftdf_phase(const double2* src, double2* dst, const int grid[3], const int nq[3], const int mesh[3],
                                double sign, double s, long long nx, cudaStream_t st) {

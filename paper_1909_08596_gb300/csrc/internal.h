@@ -85,6 +85,8 @@ cudaError_t launch_fock_combine(const double* F0, const double* J, const double*
 cudaError_t launch_fftdf_phase(const double2* src, double2* dst, const int grid[3], const int nq[3], const int mesh[3],
                                double sign, double s, long long nx, cudaStream_t st);
 cudaError_t launch_fftdf_kernel_mul(double2* buf, const double* v, long long ng, long long nx, cudaStream_t st);
+// out[i] += sum over the np parts of parts[p n + i] (the K parts of a split GEMM).
+cudaError_t launch_sum_parts(const double2* parts, int np, long long n, double2* out, cudaStream_t st);
 // The phase for nq_run q values at once (q = qtab[i] for block i; source block by q if by_table, else by i).
 cudaError_t launch_fftdf_phase_q(const double2* src, double2* dst, const int* qtab, int nq_run, int by_table,
                                  const int grid[3], const int mesh[3], double sign, double s, long long nx,

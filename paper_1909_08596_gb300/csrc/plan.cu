@@ -3051,17 +3051,26 @@ dmet_status_t dmet_emb_eri_fftdf(dmet_emb_plan_t P, int32_t problem, const void*
     qtab[qq] = pr.s.neg[qq];
     std::memcpy(vp.data() + (size_t)qq * ng, vq.data() + (size_t)qtab[qq] * ng, sizeof(double) * ng);
   }
-  // scratch: two [qc][grid][n^2] buffers, the DFT matrices, the kernels, the q table
+  // The contraction GEMM of a chunk is n^2 x n^2 with K = qc N_g: few output tiles over a long K, so
+  // it is split in K into kparts batches (partial blocks, summed afterwards) that fill the GPU.
+  const long long ktot = (long long)qc * ng, tiles_min = ((nx_max + 63) / 64) * ((nx_max + 63) / 64);
+  int kparts = 1;
+  while (kparts < 64 && tiles_min * kparts < 2 * 152 && ktot % (2 * kparts) == 0 && ktot / (2 * kparts) >= 64 &&
+         (size_t)(2 * kparts) * nx_max * nx_max * 16 <= ((size_t)1 << 30))
+    kparts *= 2;
+  // scratch: two [qc][grid][n^2] buffers, the DFT matrices, the kernels, the q table, the K parts
   const size_t bbuf = (size_t)qc * ng * nx_max * 16, oF = 2 * bbuf, oV = oF + (F.size() * 16 + 255) / 256 * 256;
   const size_t oQ = oV + (vp.size() * 8 + 255) / 256 * 256;
+  const size_t oP = oQ + (qtab.size() * sizeof(int) + 255) / 256 * 256;
   P->cs = P->stream;
-  TRY(ensure(&P->fft_ws, &P->fft_ws_b, oQ + qtab.size() * sizeof(int)));
+  TRY(ensure(&P->fft_ws, &P->fft_ws_b, oP + (kparts > 1 ? (size_t)kparts * nx_max * nx_max * 16 : 0)));
   char* w = (char*)P->fft_ws;
   double2* buf0 = (double2*)w;
   double2* buf1 = (double2*)(w + bbuf);
   double2* dF = (double2*)(w + oF);
   double* dV = (double*)(w + oV);
   int* dQ = (int*)(w + oQ);
+  double2* dPart = (double2*)(w + oP);
   CK(cudaMemcpyAsync(dF, F.data(), F.size() * 16, cudaMemcpyHostToDevice, P->cs));
   CK(cudaMemcpyAsync(dV, vp.data(), vp.size() * 8, cudaMemcpyHostToDevice, P->cs));
   CK(cudaMemcpyAsync(dQ, qtab.data(), qtab.size() * sizeof(int), cudaMemcpyHostToDevice, P->cs));
@@ -3095,21 +3104,29 @@ dmet_status_t dmet_emb_eri_fftdf(dmet_emb_plan_t P, int32_t problem, const void*
       for (int sb = sa; sb < pr.nspin; ++sb) {
         const long long nxb = (long long)pr.n[sb] * pr.n[sb];
         const int blk = pr.nspin == 1 ? 0 : (sa == 0 ? (sb == 0 ? 0 : 1) : 2);
+        const long long kc = (long long)nc * ng;
+        const int kp = (kparts > 1 && kc % kparts == 0) ? kparts : 1;
         ZgemmArgs z = zargs();
         z.A = buf1;
         z.B = lq[sb] + (long long)c0 * ng * nxb;
-        z.D = (double2*)eri_out[blk];
+        z.D = kp > 1 ? dPart : (double2*)eri_out[blk];
         z.M = (int)nx;
         z.N = (int)nxb;
-        z.K = (int)((long long)nc * ng);
+        z.K = (int)(kc / kp);
         z.lda = nx;
         z.ldb = nxb;
         z.dm_lo = nxb;
         z.dn_lo = 1;
         z.alpha = omega / ((double)ng * ng * nk);
-        z.beta = 1;
-        Timed tc(P, KC_FFTDF, 8.0 * (double)nx * nxb * ng * nc, 0.0);
+        z.beta = kp > 1 ? 0 : 1;
+        z.sA = (kc / kp) * nx;  // part p: K rows [p kc/kp, (p+1) kc/kp) of both operands
+        z.sB = (kc / kp) * nxb;
+        z.sD = nx * nxb;
+        z.batch = kp;
+        Timed tc(P, KC_FFTDF, 8.0 * (double)nx * nxb * ng * nc, kp > 1 ? 16.0 * kp * nx * nxb * 2 : 0.0,
+                 kp > 1 ? 2 : 1);
         CK(launch_zgemm(z, A_KM, false, B_KN, P->cs));
+        if (kp > 1) CK(launch_sum_parts(dPart, kp, nx * nxb, (double2*)eri_out[blk], P->cs));
       }
     }
   }
