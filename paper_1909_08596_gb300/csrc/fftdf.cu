@@ -69,6 +69,39 @@ __global__ void fftdf_kernel_mul(double2* __restrict__ buf, const double* __rest
   }
 }
 
+// A dense DFT along the middle axis of [outer][g][inner]: out[o][k][i] = sum_j F[k g + j] in[o][j][i],
+// for axes of at most kMaxDftAxis points. One thread per (o, i) column keeps the column's g inputs
+// in registers and F in shared memory; the reads and writes of a warp are runs of consecutive i.
+constexpr int kMaxDftAxis = 32;
+__global__ void __launch_bounds__(256) dft_axis_kernel(const double2* __restrict__ F, int g, long long outer,
+                                                      long long inner, const double2* __restrict__ in,
+                                                      double2* __restrict__ out) {
+  __shared__ double2 f[kMaxDftAxis * kMaxDftAxis];
+  for (int t = threadIdx.x; t < g * g; t += blockDim.x) f[t] = F[t];
+  __syncthreads();
+  const long long total = outer * inner;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
+       c += (long long)gridDim.x * blockDim.x) {
+    const long long o = c / inner, i = c - o * inner;
+    const long long base = o * g * inner + i;
+    double2 x[kMaxDftAxis];
+#pragma unroll
+    for (int j = 0; j < kMaxDftAxis; ++j)
+      if (j < g) x[j] = in[base + j * inner];
+    for (int k = 0; k < g; ++k) {
+      double re = 0.0, im = 0.0;
+#pragma unroll
+      for (int j = 0; j < kMaxDftAxis; ++j)
+        if (j < g) {
+          const double2 a = f[k * g + j];
+          re = fma(a.x, x[j].x, fma(-a.y, x[j].y, re));
+          im = fma(a.x, x[j].y, fma(a.y, x[j].x, im));
+        }
+      out[base + k * inner] = make_double2(re, im);
+    }
+  }
+}
+
 // out[i] += sum_p parts[p n + i]
 __global__ void sum_parts_kernel(const double2* __restrict__ parts, int np, long long n, double2* __restrict__ out) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -83,6 +116,15 @@ __global__ void sum_parts_kernel(const double2* __restrict__ parts, int np, long
 }
 
 }  // namespace
+
+bool fftdf_small_axis(int g) { return g >= 1 && g <= kMaxDftAxis; }
+
+cudaError_t launch_dft_axis_small(const double2* F, int g, long long outer, long long inner, const double2* in,
+                                  double2* out, cudaStream_t st) {
+  if (!fftdf_small_axis(g)) return cudaErrorInvalidValue;
+  dft_axis_kernel<<<grid_for(outer * inner, 256, 152 * 8), 256, 0, st>>>(F, g, outer, inner, in, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sum_parts(const double2* parts, int np, long long n, double2* out, cudaStream_t st) {
   sum_parts_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(parts, np, n, out);

@@ -85,6 +85,11 @@ cudaError_t launch_fock_combine(const double* F0, const double* J, const double*
 cudaError_t launch_fftdf_phase(const double2* src, double2* dst, const int grid[3], const int nq[3], const int mesh[3],
                                double sign, double s, long long nx, cudaStream_t st);
 cudaError_t launch_fftdf_kernel_mul(double2* buf, const double* v, long long ng, long long nx, cudaStream_t st);
+// A dense DFT along the middle axis of [outer][g][inner] for g <= 32 (fftdf_small_axis):
+// out[o][k][i] = sum_j F[k g + j] in[o][j][i].
+bool fftdf_small_axis(int g);
+cudaError_t launch_dft_axis_small(const double2* F, int g, long long outer, long long inner, const double2* in,
+                                  double2* out, cudaStream_t st);
 // out[i] += sum over the np parts of parts[p n + i] (the K parts of a split GEMM).
 cudaError_t launch_sum_parts(const double2* parts, int np, long long n, double2* out, cudaStream_t st);
 // The phase for nq_run q values at once (q = qtab[i] for block i; source block by q if by_table, else by i).

@@ -2966,6 +2966,11 @@ dmet_status_t dmet_emb_jk_df(dmet_emb_plan_t P, int32_t problem, int32_t spin, c
 // opB(j, k) = F[k][j], stored at out[o][k][x]).
 static dmet_status_t dft_axis(dmet_emb_plan_s* P, const double2* F, int g, long long outer, long long inner,
                               const double2* in, double2* out) {
+  if (fftdf_small_axis(g)) {
+    // a short axis: one thread per column (the GEMM form would use a g-wide sliver of each tile)
+    CK(launch_dft_axis_small(F, g, outer, inner, in, out, P->cs));
+    return DMET_OK;
+  }
   if (inner > INT_MAX || outer > 65535) return fail(DMET_ERR_UNSUPPORTED, "FFTDF grid too large for one DFT launch");
   ZgemmArgs z = zargs();
   z.A = in;

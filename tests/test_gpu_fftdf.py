@@ -14,7 +14,8 @@ from gpu_helpers import torch_cuda
 
 pytestmark = pytest.mark.gpu
 
-CASES = [((1, 1, 1), (4, 4, 4)), ((2, 2, 1), (3, 4, 3)), ((3, 1, 1), (3, 5, 3)), ((3, 3, 1), (3, 3, 5))]
+CASES = [((1, 1, 1), (4, 4, 4)), ((2, 2, 1), (3, 4, 3)), ((3, 1, 1), (3, 5, 3)), ((3, 3, 1), (3, 3, 5)),
+         ((2, 1, 1), (3, 2, 34))]   # an axis of more than 32 points takes the GEMM form of the DFT
 
 
 def _inputs(mesh, grid, complex_orbitals, n_emb=3, spin=0):
