@@ -51,11 +51,17 @@ __global__ void __launch_bounds__(256) coulomb_exchange_kernel(const double* __r
       gk[t] = gamma[(long long)k * n + t];
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    // The exchange rows: nsplit groups of n threads each take a share of l for every j (so that a
+    // block of 256 threads keeps busy when n is below 256); their partial sums meet in the atomic adds.
+    // (Pair indices fit 32 bits: n <= 2047.)
+    const int nsplit = n < (int)blockDim.x ? (int)blockDim.x / n : 1;
+    for (int t = threadIdx.x; t < nsplit * n; t += blockDim.x) {
+      const int j = t % n, h = t / n;
+      const int l0 = h * n / nsplit, l1 = (h + 1) * n / nsplit;
       double si = 0.0, sk = 0.0;
-      const long long jj = (long long)j * (j + 1) / 2;
-      for (int l = 0; l < n; ++l) {
-        const double v = row[l >= j ? (long long)l * (l + 1) / 2 + j : jj + l];
+      const int jj = j * (j + 1) / 2;
+      for (int l = l0; l < l1; ++l) {
+        const double v = row[l >= j ? l * (l + 1) / 2 + j : jj + l];
         si = fma(v, gk[l], si);
         sk = fma(v, gi[l], sk);
       }
