@@ -145,6 +145,37 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
   lo += e;
 }
 
+// Two columns at once on the paired FP32 pipe (add/sub.rn.f32x2): (hi, lo) += v with the same
+// TwoSum, each lane rounded as the scalar form.
+__device__ __forceinline__ void two_sum_acc2(float& h0, float& h1, float& l0, float& l1, uint32_t v0, uint32_t v1) {
+  asm("{\n\t.reg .b64 h, l, x, s, bv, t;\n\t"
+      "mov.b64 h, {%0, %1};\n\t"
+      "mov.b64 l, {%2, %3};\n\t"
+      "mov.b64 x, {%4, %5};\n\t"
+      "add.rn.f32x2 s, h, x;\n\t"
+      "sub.rn.f32x2 bv, s, h;\n\t"
+      "sub.rn.f32x2 t, s, bv;\n\t"
+      "sub.rn.f32x2 t, h, t;\n\t"
+      "sub.rn.f32x2 bv, x, bv;\n\t"
+      "add.rn.f32x2 t, t, bv;\n\t"
+      "add.rn.f32x2 l, l, t;\n\t"
+      "mov.b64 {%0, %1}, s;\n\t"
+      "mov.b64 {%2, %3}, l;\n\t}"
+      : "+f"(h0), "+f"(h1), "+f"(l0), "+f"(l1)
+      : "r"(v0), "r"(v1));
+}
+
+// (l0, l1) += (v0, v1) on the paired pipe.
+__device__ __forceinline__ void add_acc2(float& l0, float& l1, uint32_t v0, uint32_t v1) {
+  asm("{\n\t.reg .b64 l, x;\n\t"
+      "mov.b64 l, {%0, %1};\n\t"
+      "mov.b64 x, {%2, %3};\n\t"
+      "add.rn.f32x2 l, l, x;\n\t"
+      "mov.b64 {%0, %1}, l;\n\t}"
+      : "+f"(l0), "+f"(l1)
+      : "r"(v0), "r"(v1));
+}
+
 // Stores a warp's 32 rows x H columns through a 32 x 8 transpose in shared memory (element
 // (r, c) at r * 8 + (c ^ (r & 7)), a swizzle that keeps both phases at two to four
 // wavefronts): each store instruction then covers 4 rows x 8 consecutive columns.
@@ -381,11 +412,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row = quad * 32 + lane;
     const float f0 = fac ? *fac : 1.f;
     float hi[H], lo[H];
+    float wc = 1.f;
     bool ok = true;
     int gs = 0, run = -1;
     for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x) {
       const TcJob job = jobs[jb];
       const Segment* sgs = groups ? groups[job.grp].segs : segs;
+      wc = 1.f;
       for (int g = 0; g < job.nseg; ++g, ++gs) {
         const int b = gs & 1, u = gs >> 1;
         if (!mbar_wait(accf(b), u & 1, err, 8u, lim)) {
@@ -394,7 +427,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         const Segment sg = sgs[job.seg0 + g];
+        // The sums are kept in units of the current segment weight wc (powers of two, so every
+        // rescaling is exact and the result is that of adding w * v): a weight change inside a job
+        // rescales them, the job's end multiplies by wc.
         const float w = sg.w;
+        if (g == 0) {
+          wc = w;
+        } else if (w != wc) {
+          const float r = wc / w;
+#pragma unroll
+          for (int c = 0; c < H; ++c) {
+            hi[c] *= r;
+            lo[c] *= r;
+          }
+          wc = w;
+        }
         run += g == 0 || (sg.flags & kRunFirst);
         const bool last = Cfg::NPROD > 1 && (g == job.nseg - 1 || (sg.flags & kRunLast));
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + half * H;
@@ -403,22 +450,26 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int g0 = 0; g0 < H; g0 += kChunk) {
           uint32_t v[kChunk];
+          if (g0 + kChunk <= H) {
+            tmem_ld_32x32b_x32(tm_main + g0, v);
+          } else {
 #pragma unroll
-          for (int q = 0; q < kChunk / 8; ++q)
-            if (g0 + q * 8 < H) tmem_ld_32x32b_x8(tm_main + g0 + q * 8, v + q * 8);
+            for (int q = 0; q < kChunk / 8; ++q)
+              if (g0 + q * 8 < H) tmem_ld_32x32b_x8(tm_main + g0 + q * 8, v + q * 8);
+          }
           tmem_ld_wait();
           // A job's first segment starts the two-float sums (no TwoSum needed).
           if (g == 0) {
 #pragma unroll
             for (int c = 0; c < kChunk; ++c)
               if (g0 + c < H) {
-                hi[g0 + c] = w * __uint_as_float(v[c]);
+                hi[g0 + c] = __uint_as_float(v[c]);
                 lo[g0 + c] = 0.f;
               }
           } else {
 #pragma unroll
-            for (int c = 0; c < kChunk; ++c)
-              if (g0 + c < H) two_sum_acc(hi[g0 + c], lo[g0 + c], w * __uint_as_float(v[c]));
+            for (int c = 0; c < kChunk; c += 2)
+              if (g0 + c < H) two_sum_acc2(hi[g0 + c], hi[g0 + c + 1], lo[g0 + c], lo[g0 + c + 1], v[c], v[c + 1]);
           }
         }
         if (last) {
@@ -426,20 +477,24 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int g0 = 0; g0 < H; g0 += kChunk) {
             uint32_t v[kChunk];
+            if (g0 + kChunk <= H) {
+              tmem_ld_32x32b_x32(tm_corr + g0, v);
+            } else {
 #pragma unroll
-            for (int q = 0; q < kChunk / 8; ++q)
-              if (g0 + q * 8 < H) tmem_ld_32x32b_x8(tm_corr + g0 + q * 8, v + q * 8);
+              for (int q = 0; q < kChunk / 8; ++q)
+                if (g0 + q * 8 < H) tmem_ld_32x32b_x8(tm_corr + g0 + q * 8, v + q * 8);
+            }
             tmem_ld_wait();
 #pragma unroll
-            for (int c = 0; c < kChunk; ++c)
-              if (g0 + c < H) lo[g0 + c] += w * __uint_as_float(v[c]);
+            for (int c = 0; c < kChunk; c += 2)
+              if (g0 + c < H) add_acc2(lo[g0 + c], lo[g0 + c + 1], v[c], v[c + 1]);
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acce(b));
       }
-      const float f = groups ? (groups[job.grp].fac ? *groups[job.grp].fac : 1.f) : f0;
+      const float f = wc * (groups ? (groups[job.grp].fac ? *groups[job.grp].fac : 1.f) : f0);
       if (f != 1.f) {
 #pragma unroll
         for (int c = 0; c < H; ++c) {
